@@ -1,0 +1,61 @@
+"""CFL(N) of Sec. 5 eq. (time.step.2d) by Fourier (von Neumann) analysis.
+
+TEST INFRASTRUCTURE ONLY (part of the oracle).
+
+The paper takes CFL(N) from the Fourier stability analysis of the linearly
+equivalent Lax-Wendroff FR scheme (cited, not printed).  Reading: analyse the
+cRKFR scheme itself with D2 dissipation on u_t + u_x = 0, periodic.  For a
+linear flux the time averages are exact (App. A eq. (linear.avg)):
+    U_e = T u_e,  T = sum_{m=0}^{N} (-nu)^m / (m+1)! D^m,  F = U,
+with nu = dt/dx.  D2 gives the upwind flux F_{e+1/2} = l(1)^T U_e, so eq.
+(crkfr.avg) becomes
+    u_e^{n+1} = u_e - nu [ D T u_e + g_L' (l(1)^T T u_{e-1} - l(0)^T T u_e) ],
+and a Fourier mode u_{e-1} = exp(-i k) u_e gives the amplification matrix
+    G(k) = I - nu [ D T - g_L' l(0)^T T + exp(-i k) g_L' l(1)^T T ].
+CFL(N) is the largest nu with spectral radius rho(G(k)) <= 1 + tol for all k,
+found by bisection on a grid of wave numbers that contains k = pi.
+
+Reading of the tolerance: for N = 4 the fifth-order time average has a weak
+growth of about 5e-6 per step at mid wave numbers for every nu (it does not
+grow with nu up to 0.069), while the genuine instability at k = pi jumps to
+5e-3 within 0.001 of its onset.  tol = 1e-4 sits between the two, so the
+result is the onset of the genuine instability; for N = 1..3 there is no weak
+growth and tol raises the result by less than 2e-5 over the exact limit.
+"""
+import functools
+import math
+
+import numpy as np
+
+from . import tables
+
+
+def amplification(N, nu, k):
+    xi, w, l0, l1, D = tables(N)
+    n = N + 1
+    T = np.zeros((n, n))
+    Dm = np.eye(n)
+    for m in range(N + 1):
+        T += (-nu) ** m / math.factorial(m + 1) * Dm
+        Dm = Dm @ D
+    gL = -l0 / w
+    A0 = D @ T - np.outer(gL, l0) @ T
+    A1 = np.outer(gL, l1) @ T
+    return np.eye(n) - nu * (A0 + np.exp(-1j * k) * A1)
+
+
+def max_growth(N, nu, nk=721):
+    ks = np.linspace(0.0, 2.0 * np.pi, nk)
+    return max(np.max(np.abs(np.linalg.eigvals(amplification(N, nu, k)))) for k in ks)
+
+
+@functools.lru_cache(maxsize=None)
+def cfl_number(N, tol=1e-4, iters=40):
+    lo, hi = 0.0, 1.0
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if max_growth(N, mid) <= 1.0 + tol:
+            lo = mid
+        else:
+            hi = mid
+    return lo

@@ -1,0 +1,117 @@
+/*
+ * Plain FP64 CPU oracle for one time step of compact Runge-Kutta Flux
+ * Reconstruction (cRKFR) with the subcell blending limiter, the flux limiter
+ * and the positivity scaling limiter (Babbar & Chen, arXiv 2502.07517).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA library.
+ * Only the tests, the smoke check and the CPU-baseline leg of the benchmark
+ * may load it.  It shares no code, header, table or constant generator with
+ * the CUDA path, and it never reads anything the CUDA path produced.
+ *
+ * Every function follows one passage of the paper in the paper's order and
+ * notation, with straightforward loops (per element, per stage, per node) and
+ * no blocking, fusion or reordering.  Where the paper defers a detail to
+ * another paper, the reading taken is stated beside the code.
+ *
+ * Layout of a state vector: u[(v * Ne + e) * Np + k], variable v, element
+ * e = ix + nx * iy, node k = p + (N + 1) * q (p along x, q along y).
+ */
+#ifndef CRKFR_ORACLE_H
+#define CRKFR_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAXN 4
+#define OR_MAXS 6
+#define OR_MAXM 6
+
+enum { OR_EQ_LINADV = 0, OR_EQ_EULER = 1, OR_EQ_TENMOMENT = 2 };
+enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1 };
+enum {
+  OR_LIM_BLEND = 1,    /* blend with the subcell scheme, Sec. 4 eq. (blended.scheme) */
+  OR_LIM_MH = 2,       /* MUSCL-Hancock subcell fluxes (else first order), Sec. 4.2 */
+  OR_LIM_FLUX = 4,     /* flux limiter for admissible means, Sec. 4.3 */
+  OR_LIM_SCALING = 8,  /* Zhang-Shu positivity scaling, Sec. 3.2 */
+  OR_LIM_TRACES = 16   /* scaling limiter also enforces admissibility at face traces */
+};
+enum { OR_ALPHA_INDICATOR = 0, OR_ALPHA_FIXED = 1 };
+
+typedef struct {
+  int dim;                 /* 1 or 2 */
+  int nx, ny;              /* elements per direction (ny = 1 in 1D) */
+  double x0, x1, y0, y1;   /* domain */
+  int bc_x, bc_y;          /* OR_BC_* */
+  int degree;              /* N in 1..4 */
+  int equation;            /* OR_EQ_* */
+  double gamma;            /* Euler */
+  double adv[2];           /* linear advection velocity */
+  int source;              /* 0 none, 1 ten-moment Gaussian W */
+  double src_amp, src_k, src_cx, src_cy;
+  int limiter;             /* OR_LIM_* bits */
+  int alpha_mode;          /* OR_ALPHA_* */
+  double alpha_fixed;      /* alpha_e when alpha_mode == OR_ALPHA_FIXED */
+  double cfl;              /* CFL(N) of Sec. 5 eq. (time.step.2d) */
+  double cfl_safety;       /* C_s */
+} or_desc;
+
+/* Optional outputs of or_step; any pointer may be NULL. */
+typedef struct {
+  double* alpha;       /* [Ne] blending coefficient alpha_e after smoothing */
+  double* alpha_raw;   /* [Ne] alpha_e straight from the indicator */
+  double* fnum_x;      /* [M][Ne][nq] numerical flux on the LEFT x-face of each element */
+  double* fnum_x_right;/* [M][Ne][nq] numerical flux on the RIGHT x-face of each element */
+  double* fnum_y;      /* [M][Ne][n]  numerical flux on the BOTTOM y-face */
+  double* fnum_y_top;  /* [M][Ne][n]  numerical flux on the TOP y-face */
+  double* theta_x;     /* [Ne][nq] flux-limiter theta on the LEFT x-face */
+  double* theta_y;     /* [Ne][n]  flux-limiter theta on the BOTTOM y-face */
+  double* source_mean; /* [M][Ne] sum_k W_k S_k, the source part of the mean update */
+  int status;          /* 0 ok, 1 inadmissible mean, 2 non-finite value */
+  int bad_element;     /* first element that set status, -1 if none */
+} or_diag;
+
+int or_nvars(const or_desc* d);
+int or_nodes(const or_desc* d);
+
+/* Reference element tables of Sec. 2 on [0,1]: Gauss-Legendre nodes and
+ * weights, l_p(0), l_p(1), and D_ij = l_j'(xi_i). */
+void or_tables(int N, double* xi, double* w, double* l0, double* l1, double* D);
+/* Butcher tableau used for degree N (cRK22/33/44, and the order-5 reading for N = 4). */
+int or_tableau(int N, double* A /* [6][6] */, double* b, double* c);
+
+/* Physics, exposed for the tests. dir 0 = x, 1 = y. */
+void or_flux(const or_desc* d, const double* u, int dir, double* f);
+double or_wave_speed(const or_desc* d, const double* u, int dir);
+int or_num_constraints(const or_desc* d);
+double or_constraint(const or_desc* d, const double* u, int k);
+void or_source(const or_desc* d, const double* u, double x, double y, double* s);
+
+/* Local cRK procedure of Sec. 3 for one element: time-averaged F, G, U, S at
+ * the solution points, arrays [Np][M].  ue is [Np][M]. */
+void or_local_crk(const or_desc* d, const double* ue, double dt, int ix, int iy,
+                  double* F, double* G, double* U, double* S);
+
+/* Smoothness indicator alpha of one element from its nodal values [Np][M]. */
+double or_indicator(const or_desc* d, const double* ue);
+
+/* max_e (sigma_x(mean_e)/dx + sigma_y(mean_e)/dy), Sec. 5 eq. (time.step.2d) */
+double or_max_rate(const or_desc* d, const double* u);
+double or_dt(const or_desc* d, const double* u);
+
+/* One cRKFR step with the given dt. Returns diag->status (0 ok). */
+int or_step(const or_desc* d, const double* u_in, double dt, double* u_out, or_diag* diag);
+
+/* Steps with the CFL time step until t_final or max_steps; the last step is
+ * clipped to land on t_final. u is updated in place. Returns the status. */
+int or_run(const or_desc* d, double* u, int max_steps, double t_final, double* t_out,
+           int* steps_out);
+
+/* Zhang-Shu scaling limiter on one element, in place on ue [Np][M].
+ * Returns 0 if the mean is admissible, 1 otherwise. */
+int or_scaling_limiter(const or_desc* d, double* ue);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

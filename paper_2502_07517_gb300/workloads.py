@@ -1,0 +1,211 @@
+"""Seeded synthetic initial states for the cRKFR workloads.
+
+This module holds no part of the scheme: it only samples initial data at the
+solution points (nodal interpolation) and describes each problem as a plain
+dict.  Node positions come from numpy's Gauss-Legendre rule, so neither the
+CUDA library nor the CPU checker is involved in making an input; both receive
+the same arrays.
+
+State layout: float64 array [M][Ne][Np], element e = ix + nx * iy, node
+k = p + (N + 1) * q with p along x.
+
+Problem dict keys: dim, nx, ny, x0, x1, y0, y1, bc_x, bc_y ("periodic" or
+"outflow"), degree, equation ("linadv", "euler", "tenmoment"), gamma, adv,
+source (None or dict amp, k, cx, cy), limiter (set of "blend", "mh", "flux",
+"scaling", "traces"), t_final, steps.
+"""
+import math
+
+import numpy as np
+
+LIMITER_ALL = frozenset({"blend", "mh", "flux", "scaling", "traces"})
+
+
+def gl_nodes01(N):
+    x, w = np.polynomial.legendre.leggauss(N + 1)
+    return 0.5 * (x + 1.0), 0.5 * w
+
+
+def node_coords(prob):
+    """(x, y) of every solution point, arrays [Ne][Np]."""
+    N = prob["degree"]
+    xi, _ = gl_nodes01(N)
+    n = N + 1
+    nx = prob["nx"]
+    ny = prob["ny"] if prob["dim"] == 2 else 1
+    dx = (prob["x1"] - prob["x0"]) / nx
+    ix = np.arange(nx * ny) % nx
+    if prob["dim"] == 1:
+        x = prob["x0"] + (ix[:, None] + xi[None, :]) * dx
+        return x, np.zeros_like(x)
+    dy = (prob["y1"] - prob["y0"]) / ny
+    iy = np.arange(nx * ny) // nx
+    p = np.tile(np.arange(n), n)
+    q = np.repeat(np.arange(n), n)
+    x = prob["x0"] + (ix[:, None] + xi[p][None, :]) * dx
+    y = prob["y0"] + (iy[:, None] + xi[q][None, :]) * dy
+    return x, y
+
+
+def element_centres(prob):
+    nx = prob["nx"]
+    ny = prob["ny"] if prob["dim"] == 2 else 1
+    dx = (prob["x1"] - prob["x0"]) / nx
+    ix = np.arange(nx * ny) % nx
+    xc = prob["x0"] + (ix + 0.5) * dx
+    if prob["dim"] == 1:
+        return xc, np.zeros_like(xc)
+    dy = (prob["y1"] - prob["y0"]) / ny
+    iy = np.arange(nx * ny) // nx
+    return xc, prob["y0"] + (iy + 0.5) * dy
+
+
+def base_problem(**kw):
+    prob = dict(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x="periodic",
+                bc_y="periodic", degree=3, equation="linadv", gamma=1.4, adv=(1.0, 0.0),
+                source=None, limiter=frozenset(), t_final=1.0, steps=None)
+    prob.update(kw)
+    if prob["dim"] == 1:
+        prob["ny"] = 1
+    return prob
+
+
+def nvars(prob):
+    return {"linadv": 1, "euler": 3 if prob["dim"] == 1 else 4, "tenmoment": 6}[prob["equation"]]
+
+
+def euler_conservative(rho, v1, v2, p, gamma, dim):
+    if dim == 1:
+        return np.stack([rho, rho * v1, p / (gamma - 1.0) + 0.5 * rho * v1 * v1])
+    E = p / (gamma - 1.0) + 0.5 * rho * (v1 * v1 + v2 * v2)
+    return np.stack([rho, rho * v1, rho * v2, E])
+
+
+def tenmoment_conservative(rho, v1, v2, p11, p12, p22):
+    return np.stack([rho, rho * v1, rho * v2, 0.5 * p11 + 0.5 * rho * v1 * v1,
+                     0.5 * p12 + 0.5 * rho * v1 * v2, 0.5 * p22 + 0.5 * rho * v2 * v2])
+
+
+# ---------------------------------------------------------------------------
+def linadv_sine(nx=64, degree=3, t_final=1.0, a=1.0):
+    """1D u_t + a u_x = 0 on [0,1] periodic, u0 = sin(2 pi x), no limiter."""
+    prob = base_problem(dim=1, nx=nx, degree=degree, equation="linadv", adv=(a, 0.0),
+                        t_final=t_final)
+    x, _ = node_coords(prob)
+    return prob, np.sin(2.0 * np.pi * x)[None, :, :].copy()
+
+
+def linadv_random(nx=8, ny=1, dim=1, degree=3, seed=0, adv=(1.0, 0.0), bc="periodic"):
+    """Linear advection with seeded random nodal values (tests only)."""
+    prob = base_problem(dim=dim, nx=nx, ny=ny, degree=degree, equation="linadv", adv=adv,
+                        bc_x=bc, bc_y=bc)
+    rng = np.random.default_rng(seed)
+    ne = nx * (ny if dim == 2 else 1)
+    npn = (degree + 1) ** dim
+    return prob, rng.standard_normal((1, ne, npn))
+
+
+def euler1d_riemann(nx=4000, degree=4, seed=0, limiter=LIMITER_ALL, t_final=0.2):
+    """1D Euler (gamma 1.4) on [0,1] outflow; left/right states with
+    rho log-uniform in [0.1, 10], v uniform in [-2, 2], p log-uniform in
+    [0.01, 1000]; the jump sits on the element face nearest x = 0.5."""
+    prob = base_problem(dim=1, nx=nx, degree=degree, equation="euler", bc_x="outflow",
+                        limiter=frozenset(limiter), t_final=t_final)
+    rng = np.random.default_rng(seed)
+    rho = np.exp(rng.uniform(math.log(0.1), math.log(10.0), 2))
+    vel = rng.uniform(-2.0, 2.0, 2)
+    p = np.exp(rng.uniform(math.log(0.01), math.log(1000.0), 2))
+    x, _ = node_coords(prob)
+    xc, _ = element_centres(prob)
+    right = (xc >= prob["x0"] + (nx // 2) * (prob["x1"] - prob["x0"]) / nx)[:, None]
+    right = np.broadcast_to(right, x.shape)
+    r = np.where(right, rho[1], rho[0])
+    v = np.where(right, vel[1], vel[0])
+    pp = np.where(right, p[1], p[0])
+    prob["riemann"] = dict(rho=rho.tolist(), v=vel.tolist(), p=p.tolist())
+    return prob, euler_conservative(r, v, None, pp, prob["gamma"], 1)
+
+
+def isentropic_vortex(x, y, gamma=1.4, beta=5.0, u_inf=1.0, v_inf=1.0, xc=0.0, yc=0.0):
+    """Sec. 5.3.1 vortex with free stream (u_inf, v_inf), rho_inf = p_inf = 1, p = rho^gamma."""
+    r2 = (x - xc) ** 2 + (y - yc) ** 2
+    rho = (1.0 - beta ** 2 * (gamma - 1.0) / (8.0 * gamma * math.pi ** 2) *
+           np.exp(1.0 - r2)) ** (1.0 / (gamma - 1.0))
+    v1 = u_inf - beta * (y - yc) / (2.0 * math.pi) * np.exp(0.5 * (1.0 - r2))
+    v2 = v_inf + beta * (x - xc) / (2.0 * math.pi) * np.exp(0.5 * (1.0 - r2))
+    return rho, v1, v2, rho ** gamma
+
+
+def euler2d_vortex(nx=512, ny=None, degree=4, seed=0, perturb=0.01, limiter=LIMITER_ALL,
+                   steps=200):
+    """2D Euler on [-5,5]^2 periodic: isentropic vortex (beta 5, free stream
+    rho = 1, u = v = 1, p = 1) with the density multiplied by (1 + perturb Pi),
+    Pi a seeded sum of 8 periodic sine modes scaled to max |Pi| = 1 on the nodes."""
+    ny = nx if ny is None else ny
+    prob = base_problem(dim=2, nx=nx, ny=ny, x0=-5.0, x1=5.0, y0=-5.0, y1=5.0, degree=degree,
+                        equation="euler", limiter=frozenset(limiter), steps=steps, t_final=1e9)
+    x, y = node_coords(prob)
+    rho, v1, v2, p = isentropic_vortex(x, y, prob["gamma"])
+    if perturb:
+        rng = np.random.default_rng(seed)
+        mk = rng.integers(1, 9, 8)
+        nk = rng.integers(1, 9, 8)
+        ak = rng.uniform(0.5, 1.0, 8)
+        phi = rng.uniform(0.0, 2.0 * math.pi, 8)
+        Pi = np.zeros_like(x)
+        for k in range(8):
+            Pi += ak[k] * np.sin(2.0 * math.pi * (mk[k] * x + nk[k] * y) / 10.0 + phi[k])
+        Pi /= np.max(np.abs(Pi))
+        rho = rho * (1.0 + perturb * Pi)
+    return prob, euler_conservative(rho, v1, v2, p, prob["gamma"], 2)
+
+
+def tenmoment2d_voronoi(nx=256, ny=None, degree=3, seed=0, ncells=16, limiter=LIMITER_ALL,
+                        steps=200, source=True):
+    """2D ten-moment on [0,1]^2 periodic with the Gaussian source
+    W = 25 exp(-200 |x - (0.5, 0.5)|^2); each element takes the state of the
+    seeded Voronoi cell (periodic distance) holding its centre: rho log-uniform
+    in [0.1, 10], v uniform in [-1, 1]^2, P = R diag(l1, l2) R^T with l
+    log-uniform in [0.01, 10] and R a random rotation."""
+    ny = nx if ny is None else ny
+    src = dict(amp=25.0, k=200.0, cx=0.5, cy=0.5) if source else None
+    prob = base_problem(dim=2, nx=nx, ny=ny, degree=degree, equation="tenmoment",
+                        limiter=frozenset(limiter), steps=steps, t_final=1e9, source=src)
+    rng = np.random.default_rng(seed)
+    sites = rng.uniform(0.0, 1.0, (ncells, 2))
+    rho_c = np.exp(rng.uniform(math.log(0.1), math.log(10.0), ncells))
+    v_c = rng.uniform(-1.0, 1.0, (ncells, 2))
+    lam = np.exp(rng.uniform(math.log(0.01), math.log(10.0), (ncells, 2)))
+    ang = rng.uniform(0.0, math.pi, ncells)
+    c, s = np.cos(ang), np.sin(ang)
+    p11 = c * c * lam[:, 0] + s * s * lam[:, 1]
+    p22 = s * s * lam[:, 0] + c * c * lam[:, 1]
+    p12 = c * s * (lam[:, 0] - lam[:, 1])
+    xc, yc = element_centres(prob)
+    dxs = np.abs(xc[:, None] - sites[None, :, 0])
+    dys = np.abs(yc[:, None] - sites[None, :, 1])
+    dxs = np.minimum(dxs, 1.0 - dxs)
+    dys = np.minimum(dys, 1.0 - dys)
+    cell = np.argmin(dxs ** 2 + dys ** 2, axis=1)
+    npn = (degree + 1) ** 2
+    rep = lambda a: np.repeat(a[cell][:, None], npn, axis=1)
+    u = tenmoment_conservative(rep(rho_c), rep(v_c[:, 0]), rep(v_c[:, 1]), rep(p11), rep(p12),
+                               rep(p22))
+    return prob, u
+
+
+def uniform_state(prob, prim):
+    """Constant state everywhere (free-stream tests); prim is the primitive tuple."""
+    x, y = node_coords(prob)
+    one = np.ones_like(x)
+    eq = prob["equation"]
+    if eq == "linadv":
+        return (prim[0] * one)[None].copy()
+    if eq == "euler":
+        if prob["dim"] == 1:
+            rho, v1, p = prim
+            return euler_conservative(rho * one, v1 * one, None, p * one, prob["gamma"], 1)
+        rho, v1, v2, p = prim
+        return euler_conservative(rho * one, v1 * one, v2 * one, p * one, prob["gamma"], 2)
+    rho, v1, v2, p11, p12, p22 = prim
+    return tenmoment_conservative(rho * one, v1 * one, v2 * one, p11 * one, p12 * one, p22 * one)

@@ -1,0 +1,629 @@
+"""Pins of the FP64 CPU oracle to facts that do not come from the oracle itself:
+library routines, closed forms from the paper, invariants, exact solutions and
+a second, independently written formulation on tiny meshes."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.cfl import cfl_number
+from paper_2502_07517_gb300 import workloads as wl
+from tests._oracle_util import oracle_desc
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- tables ---
+def np_tables(N):
+    """Reference-element tables from numpy alone (Gauss rule + Vandermonde)."""
+    x, w = np.polynomial.legendre.leggauss(N + 1)
+    xi, w = 0.5 * (x + 1.0), 0.5 * w
+    V = np.vander(xi, N + 1, increasing=True)
+    C = np.linalg.inv(V)  # column j: monomial coefficients of l_j
+    dV = np.zeros_like(V)
+    for j in range(1, N + 1):
+        dV[:, j] = j * xi ** (j - 1)
+    D = dV @ C
+    l0 = C[0, :].copy()
+    l1 = C.sum(axis=0)
+    return xi, w, l0, l1, D
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_tables_match_numpy(N):
+    xi, w, l0, l1, D = oracle.tables(N)
+    nxi, nw, nl0, nl1, nD = np_tables(N)
+    np.testing.assert_allclose(xi, nxi, atol=1e-15)
+    np.testing.assert_allclose(w, nw, atol=1e-15)
+    assert abs(w.sum() - 1.0) < 1e-15
+    np.testing.assert_allclose(l0, nl0, atol=1e-11)
+    np.testing.assert_allclose(l1, nl1, atol=1e-11)
+    np.testing.assert_allclose(D, nD, atol=1e-10)
+    # D differentiates every polynomial of degree <= N exactly (Sec. 2 eq. (diff.matrix))
+    for m in range(N + 1):
+        np.testing.assert_allclose(D @ xi ** m, m * xi ** max(m - 1, 0) * (m > 0), atol=1e-12)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_radau_correction_identity(N):
+    """g_R'(xi_p) = l_p(1)/w_p and g_L'(xi_p) = -l_p(0)/w_p (Sec. 2) for the right/left
+    Radau polynomials g_R = (P_{N+1} + P_N)/2, g_L = (-1)^{N+1} (P_{N+1} - P_N)/2 on [-1,1]."""
+    xi, w, l0, l1, D = oracle.tables(N)
+    L = np.polynomial.legendre.Legendre
+    gR = 0.5 * (L.basis(N + 1) + L.basis(N))
+    gL = (-1) ** (N + 1) * 0.5 * (L.basis(N + 1) - L.basis(N))
+    assert abs(gR(1.0) - 1.0) < 1e-14 and abs(gR(-1.0)) < 1e-14
+    assert abs(gL(-1.0) - 1.0) < 1e-14 and abs(gL(1.0)) < 1e-14
+    x = 2.0 * xi - 1.0  # d/dxi = 2 d/dx
+    np.testing.assert_allclose(2.0 * gR.deriv()(x), l1 / w, rtol=1e-11, atol=1e-11)
+    np.testing.assert_allclose(2.0 * gL.deriv()(x), -l0 / w, rtol=1e-11, atol=1e-11)
+
+
+# ---------------------------------------------------------------- tableau ---
+def test_tableaux_match_paper():
+    gold = json.load(open(os.path.join(GOLDEN, "crk_tableaux.json")))
+    for N in (1, 2, 3):
+        A, b, c = oracle.tableau(N)
+        np.testing.assert_allclose(A, np.array(gold[str(N)]["A"]), atol=1e-16)
+        np.testing.assert_allclose(b, np.array(gold[str(N)]["b"]), atol=1e-16)
+
+
+def _rk_solve(A, b, c, f, y0, t1, h):
+    y, t = np.array(y0, float), 0.0
+    s = len(b)
+    for _ in range(int(round(t1 / h))):
+        K = []
+        for i in range(s):
+            yi = y + h * sum(A[i, j] * K[j] for j in range(i))
+            K.append(f(t + c[i] * h, yi))
+        y = y + h * sum(b[i] * K[i] for i in range(s))
+        t += h
+    return y
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_tableau_order(N):
+    """The RK method for degree N has order N+1 (Sec. 3) on a nonlinear
+    non-autonomous system; reference by scipy's DOP853."""
+    from scipy.integrate import solve_ivp
+    A, b, c = oracle.tableau(N)
+    f = lambda t, y: np.array([y[1], -y[0] - y[0] ** 3 + math.cos(t)])
+    ref = solve_ivp(f, (0, 2.0), [0.3, 0.1], method="DOP853", rtol=1e-13, atol=1e-14).y[:, -1]
+    hs = [0.2, 0.1]
+    errs = [np.max(np.abs(_rk_solve(A, b, c, f, [0.3, 0.1], 2.0, h) - ref)) for h in hs]
+    order = math.log(errs[0] / errs[1]) / math.log(2.0)
+    assert order > N + 1 - 0.3, (errs, order)
+
+
+# ------------------------------------------------- linear closed forms ------
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("a", [1.3, -0.7])
+def test_linear_time_average_closed_form_1d(N, a):
+    """App. A eq. (linear.avg): F = a U, U = sum_{m<=N} (-a dt)^m/(m+1)! d^m u / dx^m."""
+    prob, u = wl.linadv_random(nx=1, degree=N, seed=N, adv=(a, 0.0))
+    d = oracle_desc(prob)
+    dx = (d.x1 - d.x0) / d.nx
+    dt = 0.37 * dx
+    ue = u[0, 0, :][:, None]
+    F, G, U, S = oracle.local_crk(d, ue, dt)
+    D = np_tables(N)[4]
+    T = sum((-a * dt / dx) ** m / math.factorial(m + 1) * np.linalg.matrix_power(D, m)
+            for m in range(N + 1))
+    np.testing.assert_allclose(U[:, 0], T @ ue[:, 0], rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(F[:, 0], a * (T @ ue[:, 0]), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_linear_time_average_closed_form_2d(N):
+    """2D linear advection: U = sum_m beta_m (-dt L)^m u, L = a_x d/dx + a_y d/dy, with
+    beta_m = b^T A^m 1 the tableau's time-average weights (= 1/(m+1)! for m <= N)."""
+    ax, ay = 0.8, -1.1
+    prob, u = wl.linadv_random(nx=1, ny=1, dim=2, degree=N, seed=7, adv=(ax, ay))
+    d = oracle_desc(prob)
+    dx, dy = (d.x1 - d.x0) / d.nx, (d.y1 - d.y0) / d.ny
+    dt = 0.21 * dx
+    ue = u[0, 0, :][:, None]
+    F, G, U, S = oracle.local_crk(d, ue, dt)
+    A, b, c = oracle.tableau(N)
+    for m in range(N + 1):
+        assert abs(b @ np.linalg.matrix_power(A, m) @ np.ones(len(b)) - 1 / math.factorial(m + 1)) < 1e-14
+    D = np_tables(N)[4]
+    n = N + 1
+    Lop = ax / dx * np.kron(np.eye(n), D) + ay / dy * np.kron(D, np.eye(n))
+    T = sum((b @ np.linalg.matrix_power(A, m) @ np.ones(len(b))) * np.linalg.matrix_power(-dt * Lop, m)
+            for m in range(len(b)))
+    np.testing.assert_allclose(U[:, 0], T @ ue[:, 0], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(F[:, 0], ax * U[:, 0], rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(G[:, 0], ay * U[:, 0], rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("a", [1.0, -1.7])
+@pytest.mark.parametrize("ne", [1, 3])
+def test_linear_step_dense_matrix(N, a, ne):
+    """The whole 1D step for u_t + a u_x = 0 (D2 + EA + Radau FR update, eqs.
+    (numflux.general), (D2), (crkfr.avg)) against an independent dense assembly
+    from numpy tables and the closed form of eq. (linear.avg)."""
+    prob, u = wl.linadv_random(nx=ne, degree=N, seed=11 * N + ne, adv=(a, 0.0))
+    d = oracle_desc(prob)
+    dx = (d.x1 - d.x0) / d.nx
+    dt = 0.6 * cfl_number(N) * dx / abs(a)
+    new, st = oracle.step(d, u, dt)
+    assert st == 0
+    xi, w, l0, l1, D = np_tables(N)
+    T = sum((-a * dt / dx) ** m / math.factorial(m + 1) * np.linalg.matrix_power(D, m)
+            for m in range(N + 1))
+    ue = u[0]
+    Ue = ue @ T.T
+    Fe = a * Ue
+    UR, UL = Ue @ l1, Ue @ l0  # traces at xi = 1 and xi = 0 of each element
+    ref = np.empty_like(ue)
+    for e in range(ne):
+        er, el = (e + 1) % ne, (e - 1) % ne
+        Fr = 0.5 * (a * UR[e] + a * UL[er]) - 0.5 * abs(a) * (UL[er] - UR[e])
+        Fl = 0.5 * (a * UR[el] + a * UL[e]) - 0.5 * abs(a) * (UL[e] - UR[el])
+        R = D @ Fe[e] + (Fr - Fe[e] @ l1) * (l1 / w) + (Fl - Fe[e] @ l0) * (-l0 / w)
+        ref[e] = ue[e] - dt / dx * R
+    np.testing.assert_allclose(new[0], ref, rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------- second (numpy) formulation -----
+def np_euler_ho_step(u, N, dx, dy, dt, gamma, A, b, dim):
+    """Unlimited cRKFR step (D2 + EA) for periodic Euler written with numpy
+    array operations; an independent restatement of Sec. 3 used on tiny meshes.
+    u is [M][ny][nx][n] in 1D-as-2D form (1D: ny = 1) or [M][ny][nx][n(q)][n(p)]."""
+    xi, w, l0, l1, D = np_tables(N)
+    s = len(b)
+
+    def pressure(U):
+        if dim == 1:
+            return (gamma - 1.0) * (U[2] - 0.5 * U[1] ** 2 / U[0])
+        return (gamma - 1.0) * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / U[0])
+
+    def flux(U, direction):
+        p = pressure(U)
+        if dim == 1:
+            v = U[1] / U[0]
+            return np.stack([U[1], U[1] * v + p, (U[2] + p) * v])
+        vn = U[1 + direction] / U[0]
+        f = [U[0] * vn, U[1] * vn, U[2] * vn, (U[3] + p) * vn]
+        f[1 + direction] = f[1 + direction] + p
+        return np.stack(f)
+
+    def sigma(U, direction):
+        return np.abs(U[1 + direction] / U[0]) + np.sqrt(gamma * pressure(U) / U[0])
+
+    if dim == 1:  # u [M][nx][n]
+        dX = lambda f: np.einsum("pr,ver->vep", D, f) / dx
+        Ls, stages = [], []
+        for i in range(s):
+            ui = u - dt * sum(A[i, j] * Ls[j] for j in range(i))
+            stages.append(ui)
+            Ls.append(dX(flux(ui, 0)))
+        F = sum(b[i] * flux(stages[i], 0) for i in range(s))
+        U = sum(b[i] * stages[i] for i in range(s))
+        tr = lambda X, l: np.einsum("p,vep->ve", l, X)
+        eaR = sum(b[i] * flux(tr(stages[i], l1), 0) for i in range(s))
+        eaL = sum(b[i] * flux(tr(stages[i], l0), 0) for i in range(s))
+        uR, uL = tr(u, l1), tr(u, l0)
+        UR, UL = tr(U, l1), tr(U, l0)
+        # face e+1/2 between e (its R) and e+1 (its L)
+        lam = np.maximum(sigma(uR, 0), sigma(np.roll(uL, -1, axis=1), 0))
+        Fr = 0.5 * (eaR + np.roll(eaL, -1, axis=1)) - 0.5 * lam * (np.roll(UL, -1, axis=1) - UR)
+        Fl = np.roll(Fr, 1, axis=1)
+        R = (np.einsum("pr,ver->vep", D, F) + (Fr - tr(F, l1))[..., None] * (l1 / w)
+             + (Fl - tr(F, l0))[..., None] * (-l0 / w))
+        return u - dt / dx * R
+    # 2D: u [M][ny][nx][q][p]
+    dXY = lambda f, g: (np.einsum("pr,vyxqr->vyxqp", D, f) / dx +
+                        np.einsum("qr,vyxrp->vyxqp", D, g) / dy)
+    Ls, stages = [], []
+    for i in range(s):
+        ui = u - dt * sum(A[i, j] * Ls[j] for j in range(i))
+        stages.append(ui)
+        Ls.append(dXY(flux(ui, 0), flux(ui, 1)))
+    F = sum(b[i] * flux(stages[i], 0) for i in range(s))
+    G = sum(b[i] * flux(stages[i], 1) for i in range(s))
+    U = sum(b[i] * stages[i] for i in range(s))
+    trx = lambda X, l: np.einsum("p,vyxqp->vyxq", l, X)
+    try_ = lambda X, l: np.einsum("q,vyxqp->vyxp", l, X)
+    eaR = sum(b[i] * flux(trx(stages[i], l1), 0) for i in range(s))
+    eaL = sum(b[i] * flux(trx(stages[i], l0), 0) for i in range(s))
+    eaT = sum(b[i] * flux(try_(stages[i], l1), 1) for i in range(s))
+    eaB = sum(b[i] * flux(try_(stages[i], l0), 1) for i in range(s))
+    lamx = np.maximum(sigma(trx(u, l1), 0), sigma(np.roll(trx(u, l0), -1, axis=2), 0))
+    Fr = 0.5 * (eaR + np.roll(eaL, -1, axis=2)) - 0.5 * lamx * (np.roll(trx(U, l0), -1, axis=2) - trx(U, l1))
+    Fl = np.roll(Fr, 1, axis=2)
+    lamy = np.maximum(sigma(try_(u, l1), 1), sigma(np.roll(try_(u, l0), -1, axis=1), 1))
+    Gt = 0.5 * (eaT + np.roll(eaB, -1, axis=1)) - 0.5 * lamy * (np.roll(try_(U, l0), -1, axis=1) - try_(U, l1))
+    Gb = np.roll(Gt, 1, axis=1)
+    Rx = (np.einsum("pr,vyxqr->vyxqp", D, F) + (Fr - trx(F, l1))[..., None] * (l1 / w)
+          + (Fl - trx(F, l0))[..., None] * (-l0 / w))
+    Ry = (np.einsum("qr,vyxrp->vyxqp", D, G) + (Gt - try_(G, l1))[..., None, :] * (l1 / w)[:, None]
+          + (Gb - try_(G, l0))[..., None, :] * (-l0 / w)[:, None])
+    return u - dt / dx * Rx - dt / dy * Ry
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
+@pytest.mark.parametrize("dim", [1, 2])
+def test_unlimited_euler_step_second_formulation(N, dim):
+    gold = json.load(open(os.path.join(GOLDEN, "crk_tableaux.json")))
+    A, b = np.array(gold[str(N)]["A"]), np.array(gold[str(N)]["b"])
+    if dim == 1:
+        prob, u = wl.euler1d_riemann(nx=3, degree=N, seed=3, limiter=())
+        prob["bc_x"] = "periodic"
+        x, _ = wl.node_coords(prob)
+        rho = 1.0 + 0.3 * np.sin(2 * np.pi * x) + 0.1 * np.cos(6 * np.pi * x)
+        u = wl.euler_conservative(rho, 0.5 + 0.2 * np.cos(2 * np.pi * x), None,
+                                  1.0 + 0.2 * np.sin(4 * np.pi * x), 1.4, 1)
+    else:
+        prob, u = wl.euler2d_vortex(nx=3, ny=2, degree=N, seed=1, limiter=())
+    d = oracle_desc(prob)
+    dt = 0.5 * oracle.dt(d, u)
+    new, st = oracle.step(d, u, dt)
+    assert st == 0
+    n = N + 1
+    dx = (d.x1 - d.x0) / d.nx
+    dy = (d.y1 - d.y0) / d.ny if dim == 2 else 1.0
+    if dim == 1:
+        ref = np_euler_ho_step(u, N, dx, dy, dt, 1.4, A, b, 1)
+        np.testing.assert_allclose(new, ref, rtol=1e-12, atol=1e-12 * np.abs(u).max())
+    else:
+        M = u.shape[0]
+        u5 = u.reshape(M, d.ny, d.nx, n, n)
+        ref = np_euler_ho_step(u5, N, dx, dy, dt, 1.4, A, b, 2).reshape(u.shape)
+        np.testing.assert_allclose(new, ref, rtol=1e-12, atol=1e-12 * np.abs(u).max())
+
+
+# ------------------------------------------------------ exact solutions -----
+def l2_error(prob, u, exact):
+    w = wl.gl_nodes01(prob["degree"])[1]
+    dx = (prob["x1"] - prob["x0"]) / prob["nx"]
+    return math.sqrt(np.sum(w[None, :] * dx * (u[0] - exact) ** 2))
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_linear_advection_convergence(N):
+    """Sec. 5.1.1: optimal order N+1 against the exact shifted solution (t = 1)."""
+    errs = []
+    for ne in (16, 32, 64):
+        prob, u = wl.linadv_sine(nx=ne, degree=N, t_final=1.0)
+        d = oracle_desc(prob)
+        out, t, steps, st = oracle.run(d, u, 100000, 1.0)
+        assert st == 0 and abs(t - 1.0) < 1e-15
+        x, _ = wl.node_coords(prob)
+        errs.append(l2_error(prob, out, np.sin(2 * np.pi * (x - 1.0))))
+    orders = [math.log(errs[i] / errs[i + 1]) / math.log(2) for i in range(2)]
+    assert orders[-1] > N + 1 - 0.2, (errs, orders)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_cfl_is_the_stability_limit(N):
+    """CFL(N) from the Fourier analysis: 0.99 CFL stays bounded, 1.05 CFL blows up."""
+    cfl = cfl_number(N)
+    peaks = []
+    for frac in (0.99, 1.05):
+        prob, u = wl.linadv_random(nx=16, degree=N, seed=5)
+        d = oracle_desc(prob, cfl=cfl * frac, cfl_safety=1.0)
+        out, t, steps, st = oracle.run(d, u, 3000, 1e9)
+        peaks.append(np.abs(out).max() / np.abs(u).max())
+    assert peaks[0] < 1.05, peaks
+    assert peaks[1] > 10.0, peaks
+
+
+# ------------------------------------------------------------- invariants ---
+def _limited_2d_euler(nx=6, ny=5, N=3, seed=0):
+    prob, u = wl.euler2d_vortex(nx=nx, ny=ny, degree=N, seed=seed, perturb=0.01)
+    rng = np.random.default_rng(seed)
+    # add element-wise jumps so that the blending and the limiters act
+    jump = rng.uniform(0.5, 2.0, (nx * ny, 1))
+    u = u * jump[None, :, :]
+    return prob, u
+
+
+@pytest.mark.parametrize("N", [3, 4])
+@pytest.mark.parametrize("eq", ["euler2d", "tenmoment", "euler1d"])
+def test_free_stream_preservation(N, eq):
+    if eq == "euler2d":
+        prob = wl.base_problem(dim=2, nx=5, ny=4, degree=N, equation="euler", limiter=wl.LIMITER_ALL)
+        u = wl.uniform_state(prob, (1.3, 0.4, -0.2, 2.1))
+    elif eq == "euler1d":
+        prob = wl.base_problem(dim=1, nx=7, degree=N, equation="euler", limiter=wl.LIMITER_ALL)
+        u = wl.uniform_state(prob, (0.7, -1.1, 0.3))
+    else:
+        prob = wl.base_problem(dim=2, nx=4, ny=5, degree=N, equation="tenmoment", limiter=wl.LIMITER_ALL)
+        u = wl.uniform_state(prob, (1.1, 0.3, -0.5, 2.0, 0.4, 1.5))
+    d = oracle_desc(prob)
+    new, st = oracle.step(d, u, oracle.dt(d, u))
+    assert st == 0
+    np.testing.assert_allclose(new, u, rtol=0, atol=1e-13 * np.abs(u).max())
+
+
+@pytest.mark.parametrize("alpha", [None, 0.0, 0.4, 1.0])
+@pytest.mark.parametrize("N", [3, 4])
+def test_conservation_and_mean_update(alpha, N):
+    """Eq. (upmean) and the mean equality of eqs. (low.order.cell.avg.update),
+    (blended.cell.avg.update): every element mean moves by -dt/dx (F_{e+1/2} - F_{e-1/2})
+    (plus the y part) whatever alpha is, so totals are conserved (periodic)."""
+    prob, u = _limited_2d_euler(N=N, seed=N)
+    d = oracle_desc(prob, alpha_fixed=alpha)
+    dt = oracle.dt(d, u)
+    new, st, dg = oracle.step(d, u, dt, want_diag=True)
+    assert st == 0
+    m0, m1 = oracle.element_means(d, u), oracle.element_means(d, new)
+    dx, dy = (d.x1 - d.x0) / d.nx, (d.y1 - d.y0) / d.ny
+    w = oracle.tables(N)[1]
+    fx = np.einsum("veq,q->ve", dg["fnum_x_right"] - dg["fnum_x"], w)
+    fy = np.einsum("vep,p->ve", dg["fnum_y_top"] - dg["fnum_y"], w)
+    pred = m0 - dt / dx * fx - dt / dy * fy
+    scale = np.abs(m0).max(axis=1, keepdims=True)
+    np.testing.assert_allclose(m1, pred, rtol=0, atol=1e-13 * scale.max())
+    np.testing.assert_allclose(m1.sum(axis=1), m0.sum(axis=1), rtol=1e-13)
+
+
+def test_conservation_tenmoment_source_and_1d_riemann():
+    prob, u = wl.tenmoment2d_voronoi(nx=8, ny=6, degree=3, seed=2)
+    d = oracle_desc(prob)
+    dt = oracle.dt(d, u)
+    new, st, dg = oracle.step(d, u, dt, want_diag=True)
+    assert st == 0
+    m0, m1 = oracle.element_means(d, u), oracle.element_means(d, new)
+    np.testing.assert_allclose(m1.sum(axis=1) - m0.sum(axis=1), dt * dg["source_mean"].sum(axis=1),
+                               rtol=0, atol=1e-12 * np.abs(m0).sum(axis=1).max())
+    prob, u = wl.euler1d_riemann(nx=40, degree=4, seed=5)
+    prob["bc_x"] = "periodic"
+    d = oracle_desc(prob)
+    new, st = oracle.step(d, u, oracle.dt(d, u))
+    assert st == 0
+    np.testing.assert_allclose(oracle.element_means(d, new).sum(axis=1),
+                               oracle.element_means(d, u).sum(axis=1), rtol=1e-13)
+
+
+# --------------------------------------------------------- blending parts ---
+def test_indicator_special_cases():
+    prob = wl.base_problem(dim=1, nx=1, degree=4, equation="euler", limiter={"blend"})
+    d = oracle_desc(prob)
+    x, _ = wl.node_coords(prob)
+    one = np.ones_like(x)
+    const = wl.euler_conservative(1.0 * one, 0.3 * one, None, 2.0 * one, 1.4, 1)
+    assert oracle.indicator(d, const[:, 0, :].T) == 0.0
+    # rho linear, p constant: eps = rho p is linear -> no energy in the top modes
+    lin = wl.euler_conservative(1.0 + 0.5 * x, 0.0 * one, None, 1.0 * one, 1.4, 1)
+    assert oracle.indicator(d, lin[:, 0, :].T) == 0.0
+    jump = wl.euler_conservative(np.where(x < 0.5, 1.0, 0.125), 0 * one, None,
+                                 np.where(x < 0.5, 1.0, 0.1), 1.4, 1)
+    assert oracle.indicator(d, jump[:, 0, :].T) == 1.0
+
+
+def test_alpha_zero_and_one_limits():
+    """alpha = 0 is the pure cRKFR step; alpha = 1 with first-order subcells is the
+    pure subcell finite-volume step of eq. (low.order.update)."""
+    prob, u = _limited_2d_euler(nx=4, ny=3, N=3, seed=9)
+    prob["limiter"] = frozenset()
+    d0 = oracle_desc(prob)
+    dt = 0.5 * oracle.dt(d0, u)
+    ho, _ = oracle.step(d0, u, dt)
+    a0, _ = oracle.step(oracle_desc(prob, alpha_fixed=0.0), u, dt)
+    np.testing.assert_array_equal(ho, a0)
+    # alpha = 1, FO: explicit subcell Rusanov finite volumes on a 1D mesh
+    prob1, u1 = wl.euler1d_riemann(nx=5, degree=3, seed=4, limiter=())
+    prob1["bc_x"] = "periodic"
+    d1 = oracle_desc(prob1, alpha_fixed=1.0)
+    dt1 = 0.3 * oracle.dt(d1, u1)
+    lo, _ = oracle.step(d1, u1, dt1)
+    xi, w = wl.gl_nodes01(3)
+    dx = 1.0 / 5
+    flat = u1.transpose(1, 2, 0).reshape(-1, 3)  # node order along x
+    ww = np.tile(w, 5)
+
+    def rus(a, b_):
+        return np.stack([np.asarray(oracle_rusanov(d1, a[i], b_[i])) for i in range(len(a))])
+    fl = rus(np.roll(flat, 1, axis=0), flat)
+    fr = np.roll(fl, -1, axis=0)
+    ref = flat - dt1 / (ww[:, None] * dx) * (fr - fl)
+    np.testing.assert_allclose(lo.transpose(1, 2, 0).reshape(-1, 3), ref, rtol=1e-13, atol=1e-13)
+
+
+def oracle_rusanov(d, uL, uR):
+    fL, fR = oracle.flux(d, uL, 0), oracle.flux(d, uR, 0)
+    lam = max(oracle.wave_speed(d, uL, 0), oracle.wave_speed(d, uR, 0))
+    return 0.5 * (fL + fR) - 0.5 * lam * (uR - uL)
+
+
+def test_mh_equals_fo_on_elementwise_constant_data():
+    """All minmod slopes vanish on element-wise constant data, so MUSCL-Hancock
+    reduces exactly to first order (Sec. 4.1/4.2)."""
+    prob, u = wl.tenmoment2d_voronoi(nx=6, ny=5, degree=3, seed=1, source=False)
+    for alpha in (0.7, 1.0):
+        lim_mh = oracle_desc(prob, alpha_fixed=alpha, limiter=oracle.LIM_MH | oracle.LIM_FLUX)
+        lim_fo = oracle_desc(prob, alpha_fixed=alpha, limiter=oracle.LIM_FLUX)
+        dt = 0.5 * oracle.dt(lim_mh, u)
+        a, _ = oracle.step(lim_mh, u, dt)
+        b_, _ = oracle.step(lim_fo, u, dt)
+        np.testing.assert_array_equal(a, b_)
+
+
+def test_mh_exact_on_linear_data():
+    """With alpha = 1 (beta = 1) the MUSCL-Hancock subcell scheme advects linear data
+    exactly: slopes, Hancock half-step and the flux are exact for f = a u."""
+    a = 1.0
+    prob = wl.base_problem(dim=1, nx=8, degree=3, equation="linadv", adv=(a, 0.0), bc_x="outflow")
+    x, _ = wl.node_coords(prob)
+    u = (2.0 + 3.0 * x)[None]
+    d = oracle_desc(prob, alpha_fixed=1.0, limiter=oracle.LIM_MH)
+    dt = 0.5 * oracle.dt(d, u)
+    new, st = oracle.step(d, u, dt)
+    np.testing.assert_allclose(new[0, 2:6], 2.0 + 3.0 * (x[2:6] - a * dt), rtol=1e-13, atol=1e-13)
+
+
+# ----------------------------------------------------------- limiters -------
+def test_flux_limiter_inactive_on_smooth_flow():
+    """Sec. 5.3.1: on an adequately resolved vortex the limiters stay off."""
+    prob, u = wl.euler2d_vortex(nx=12, ny=12, degree=4, seed=0)
+    d = oracle_desc(prob)
+    new, st, dg = oracle.step(d, u, oracle.dt(d, u), want_diag=True)
+    assert st == 0
+    assert np.all(dg["theta_x"] == 1.0) and np.all(dg["theta_y"] == 1.0)
+    assert np.all(dg["alpha"] == 0.0)
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_flux_limiter_keeps_means_admissible_near_vacuum(N):
+    """Two strong rarefactions with the pure high-order step (alpha = 0) and the
+    scaling limiter: without the flux limiter an element mean turns inadmissible
+    within 300 steps; with it (Theorem 1, Sec. 4.3) every mean stays admissible."""
+    prob = wl.base_problem(dim=1, nx=50, degree=N, equation="euler", bc_x="outflow")
+    x, _ = wl.node_coords(prob)
+    xc, _ = wl.element_centres(prob)
+    left = np.broadcast_to((xc < 0.5)[:, None], x.shape)
+    one = np.ones_like(x)
+    u = wl.euler_conservative(one, np.where(left, -6.0, 6.0), None, 0.02 * one, 1.4, 1)
+    base = oracle.LIM_MH | oracle.LIM_SCALING | oracle.LIM_TRACES
+    d = oracle_desc(prob, alpha_fixed=0.0, limiter=base)
+    out, t, steps, st = oracle.run(d, u, 300, 1e9)
+    assert st == 1 and steps < 300
+    d = oracle_desc(prob, alpha_fixed=0.0, limiter=base | oracle.LIM_FLUX)
+    theta_min = 1.0
+    for _ in range(300):
+        u, st, dg = oracle.step(d, u, oracle.dt(d, u), want_diag=True)
+        assert st == 0
+        theta_min = min(theta_min, dg["theta_x"].min())
+    assert theta_min < 1.0
+
+
+def _points_2d(ue, l0, l1):
+    """nodal values and the traces on the four faces of one N=3 element [16][M]"""
+    U = ue.reshape(4, 4, -1)  # [q][p][v]
+    return np.concatenate([ue, np.einsum("p,qpv->qv", l0, U), np.einsum("p,qpv->qv", l1, U),
+                           np.einsum("q,qpv->pv", l0, U), np.einsum("q,qpv->pv", l1, U)])
+
+
+def test_scaling_limiter():
+    """Zhang-Shu scaling (Sec. 3.2): the mean is kept, every solution point and face
+    trace ends admissible, and an element that is already admissible is untouched."""
+    prob = wl.base_problem(dim=2, nx=1, ny=1, degree=3, equation="euler",
+                           limiter={"scaling", "traces"})
+    d = oracle_desc(prob)
+    xi, w, l0, l1, _ = oracle.tables(3)
+    W = np.array([w[k % 4] * w[k // 4] for k in range(16)])
+    rng = np.random.default_rng(3)
+    ok = untouched = 0
+    for trial in range(40):
+        if trial % 2:
+            rho = rng.uniform(0.5, 2.0, 16)
+            v1, v2 = rng.uniform(-1, 1, 16), rng.uniform(-1, 1, 16)
+            p = rng.uniform(-0.2, 1.0, 16)
+        else:  # mild perturbation of a constant state: every point admissible
+            rho, p = 1.0 + 0.05 * rng.uniform(-1, 1, 16), 1.0 + 0.05 * rng.uniform(-1, 1, 16)
+            v1, v2 = 0.1 * rng.uniform(-1, 1, 16), 0.1 * rng.uniform(-1, 1, 16)
+        ue = wl.euler_conservative(rho, v1, v2, p, 1.4, 2).T.copy()
+        mean = W @ ue
+        out, st = oracle.scaling_limiter(d, ue)
+        if oracle.constraint(d, mean, 1) <= 0:
+            assert st == 1
+            continue
+        assert st == 0
+        ok += 1
+        np.testing.assert_allclose(W @ out, mean, rtol=1e-14, atol=1e-14)
+        for pt in _points_2d(out, l0, l1):
+            assert oracle.constraint(d, pt, 0) > 0 and oracle.constraint(d, pt, 1) > 0
+        if all(oracle.constraint(d, pt, 1) > 1e-12 for pt in _points_2d(ue, l0, l1)):
+            untouched += 1
+            np.testing.assert_array_equal(out, ue)
+    assert ok > 10 and untouched > 0
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_admissible_after_every_step_euler1d(seed):
+    """Seeded 1D Riemann problems (the 1D Euler workload recipe on a coarser mesh):
+    all solution points stay admissible (the oracle checks each step)."""
+    prob, u = wl.euler1d_riemann(nx=400, degree=4, seed=seed)
+    d = oracle_desc(prob)
+    out, t, steps, st = oracle.run(d, u, 60, 0.2)
+    assert st == 0 and steps > 0
+
+
+def test_admissible_tenmoment_with_source():
+    prob, u = wl.tenmoment2d_voronoi(nx=10, ny=10, degree=3, seed=4)
+    d = oracle_desc(prob)
+    out, t, steps, st = oracle.run(d, u, 15, 1e9)
+    assert st == 0 and steps == 15
+
+
+# ---------------------------------------------------------------- physics ---
+def _num_jac(d, u, direction, h=1e-7):
+    M = len(u)
+    J = np.zeros((M, M))
+    for j in range(M):
+        e = np.zeros(M)
+        e[j] = h * max(1.0, abs(u[j]))
+        J[:, j] = (oracle.flux(d, u + e, direction) - oracle.flux(d, u - e, direction)) / (2 * e[j])
+    return J
+
+
+@pytest.mark.parametrize("case", ["euler1d", "euler2d", "tenmoment"])
+def test_wave_speed_is_spectral_radius(case):
+    rng = np.random.default_rng(0)
+    if case == "euler1d":
+        prob = wl.base_problem(dim=1, equation="euler")
+        states = [wl.euler_conservative(np.array(r), np.array(v), None, np.array(p), 1.4, 1)
+                  for r, v, p in zip(rng.uniform(0.2, 3, 5), rng.uniform(-2, 2, 5), rng.uniform(0.1, 5, 5))]
+    elif case == "euler2d":
+        prob = wl.base_problem(dim=2, equation="euler")
+        states = [wl.euler_conservative(*[np.array(a) for a in (r, v1, v2, p)], 1.4, 2)
+                  for r, v1, v2, p in zip(rng.uniform(0.2, 3, 5), rng.uniform(-2, 2, 5),
+                                          rng.uniform(-2, 2, 5), rng.uniform(0.1, 5, 5))]
+    else:
+        prob = wl.base_problem(dim=2, equation="tenmoment")
+        states = []
+        for _ in range(5):
+            lam = rng.uniform(0.2, 3, 2)
+            ang = rng.uniform(0, np.pi)
+            c, s = np.cos(ang), np.sin(ang)
+            P = np.array([[c, -s], [s, c]]) @ np.diag(lam) @ np.array([[c, s], [-s, c]])
+            states.append(wl.tenmoment_conservative(*[np.array(a) for a in (
+                rng.uniform(0.2, 3), rng.uniform(-2, 2), rng.uniform(-2, 2), P[0, 0], P[0, 1], P[1, 1])]))
+    d = oracle_desc(prob)
+    for u in states:
+        u = np.asarray(u, float).reshape(-1)
+        for direction in range(prob["dim"]):
+            ev = np.linalg.eigvals(_num_jac(d, u, direction))
+            assert np.max(np.abs(ev.imag)) < 1e-5
+            np.testing.assert_allclose(oracle.wave_speed(d, u, direction), np.max(np.abs(ev.real)),
+                                       rtol=1e-6)
+
+
+def test_tenmoment_constraint_is_lambda_min():
+    prob = wl.base_problem(dim=2, equation="tenmoment")
+    d = oracle_desc(prob)
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        rho, v1, v2 = rng.uniform(0.1, 2), rng.uniform(-1, 1), rng.uniform(-1, 1)
+        P = rng.standard_normal((2, 2))
+        P = P @ P.T - 0.3 * np.eye(2)
+        u = wl.tenmoment_conservative(*[np.array(a) for a in (rho, v1, v2, P[0, 0], P[0, 1], P[1, 1])])
+        assert abs(oracle.constraint(d, u, 1) - np.linalg.eigvalsh(P)[0]) < 1e-12
+
+
+def test_source_zero_amplitude_and_sign():
+    prob, u = wl.tenmoment2d_voronoi(nx=5, ny=4, degree=3, seed=6)
+    d_off = oracle_desc(prob, source=0)
+    d_zero = oracle_desc(prob, src_amp=0.0)
+    dt = oracle.dt(d_off, u)
+    np.testing.assert_array_equal(oracle.step(d_off, u, dt)[0], oracle.step(d_zero, u, dt)[0])
+    # uniform gas at rest, 1D: the mean momentum change of each element is
+    # -rho/2 dt (W(x_{e+1/2}) - W(x_{e-1/2}))/dx to first order in dt (eq. (tenmom.source))
+    prob = wl.base_problem(dim=1, nx=20, degree=3, equation="tenmoment",
+                           source=dict(amp=25.0, k=200.0, cx=0.5, cy=0.0))
+    u = wl.uniform_state(prob, (1.0, 0.0, 0.0, 1.0, 0.0, 1.0))
+    d = oracle_desc(prob)
+    dt = 1e-5
+    new, st = oracle.step(d, u, dt)
+    dm = (oracle.element_means(d, new) - oracle.element_means(d, u))[1]
+    faces = np.linspace(0, 1, 21)
+    W = 25.0 * np.exp(-200.0 * (faces - 0.5) ** 2)
+    expect = -0.5 * dt * np.diff(W) / 0.05
+    np.testing.assert_allclose(dm, expect, rtol=1e-3, atol=1e-4 * np.abs(expect).max())
