@@ -1,0 +1,305 @@
+"""Benchmark of the GB300 cRKFR step (one JSON line on rank 0).
+
+Workload: 2D Euler (gamma 1.4), degree N = 4 (25 Gauss-Legendre points per
+element, 4 variables), 512 x 512 elements on [-5,5]^2 periodic, isentropic
+vortex with a seeded 1% density perturbation, all limiters on (blending with
+MUSCL-Hancock subcells, flux limiter, scaling limiter); one step = one
+cRKFR time step at the CFL time step over the whole mesh.
+
+Metric: DOF-updates/s = solution points x steps / second (whole job).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|fp32] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank runs an independent
+replica of the workload (different seed): weak scaling, no collective on the
+data path; timing is the max over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2502_07517_gb300 import workloads as wl  # noqa: E402
+
+WORKLOAD = dict(name="euler2d_vortex_512x512_N4", nx=512, degree=4)
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# ALU peaks from the unit counts and the maximum SM clock: 152 SMs; FP64 2 FMA
+# lanes per SM per clock (1.25 TFLOP/s nominal), FP32 128 FMA lanes per SM.
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic FLOP model of one step (add/sub/mul/div/sqrt = 1, fma = 2).
+# Per-evaluation costs: (M, flux per direction, wave speed, 2nd constraint,
+# indicator variable, source).
+EQ_COST = {"linadv1d": (1, 1, 1, 0, 0, 0), "linadv2d": (1, 1, 1, 0, 0, 0),
+           "euler1d": (3, 10, 10, 5, 6, 0), "euler2d": (4, 14, 12, 7, 8, 0),
+           "tenmoment1d": (6, 24, 8, 19, 9, 8), "tenmoment2d": (6, 24, 8, 19, 9, 8)}
+TABLEAU = {1: (2, 1, 1), 2: (3, 2, 2), 3: (4, 3, 4), 4: (6, 12, 5)}  # stages, nnz(A), nnz(b)
+
+
+def flop_model(dim, N, eq, source=False):
+    """Per solution point flops of (k_local, k_face, k_update) for one step with
+    all limiters on (the face kernel's flops are spread over the element's points)."""
+    M, fl, sp, c2, ind, src = EQ_COST[eq]
+    n = N + 1
+    NP = n ** dim
+    nslot = (4 * n if dim == 2 else 2) / NP  # face-node slots per point
+    S, nnza, nnzb = TABLEAU[N]
+    loc = nnza * M * 2                                # stage values
+    loc += S * (dim * fl + (src if source else 0))    # fluxes and source at the points
+    loc += nnzb * (dim + 2) * M * 2                   # F, (G), U, S accumulation
+    loc += (S - 1) * M * (dim * 2 * n + dim + 1)      # D contractions of the stage fluxes
+    loc += nnzb * nslot * (M * 2 * n + fl + 2 * M)    # EA traces and fluxes
+    loc += M * (dim * 2 * n + dim)                    # high-order volume part
+    loc += nslot * (2 * M * 2 * n + sp)               # U and u^n traces, wave speed
+    loc += dim * M * 9 + 2 * dim * M * 2 + 2 * dim * fl + dim * M * 5 + 2 * dim * M  # MUSCL-Hancock
+    loc += 4 * dim * c2                               # admissibility of face/evolved states
+    loc += dim * (N / n) * (2 * fl + 2 * sp + 5 * M)  # subcell Rusanov fluxes
+    loc += dim * M * 3 + nslot * M * 2 + M * 7        # low-order residual, face data, partial update
+    face_nodes = (2 * n if dim == 2 else 1) / NP      # face nodes per point
+    face = face_nodes * (M * 4 + 2 * fl + 2 * sp + 5 * M + 3 * M + 2 * 2 * 2 * (2 * M + c2) + 3 * M)
+    upd = dim * (M * 4 + 4) + 2 * M + nslot * M * 2 * n + (1 + nslot) * c2 + ind + 2 * n * dim + 1
+    return loc, face, upd
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def make_workload(seed, nx=None):
+    prob, u = wl.euler2d_vortex(nx=nx or WORKLOAD["nx"], degree=WORKLOAD["degree"], seed=seed)
+    return prob, u
+
+
+def cpu_baseline(target_s=10.0, nx=256):
+    """The FP64 oracle as it stands, single thread, on a bounded sample: nx x nx
+    elements of the same recipe, whole oracle steps until target_s has passed."""
+    import oracle
+    from tests._oracle_util import oracle_desc
+    prob, u = make_workload(0, nx=nx)
+    d = oracle_desc(prob)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        u, st = oracle.step(d, u, oracle.dt(d, u))
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= target_s or st != 0:
+            break
+    nodes = u.shape[1] * u.shape[2]
+    return {"value": nodes * steps / el, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "%dx%d elements of the same workload recipe, %d oracle step(s), %.1f s"
+                      % (nx, nx, steps, el)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cb_total = []
+    for _ in range(args.warmup):
+        cpu_baseline(target_s=0.0, nx=96)
+    for _ in range(args.steps):
+        cb_total.append(cpu_baseline(target_s=0.0, nx=128))
+    val = statistics.median(c["value"] for c in cb_total)
+    line = {"impl": "reference", "metric": "DOF-updates/s", "value": val, "unit": "DOF-updates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 128 * 128 * 25 / val * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "sample": "128x128 elements per step"},
+            "cpu_baseline": {"value": val, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": "one oracle step of 128x128 elements of the workload recipe per bench step"},
+            "e2e": {"value": val, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    from paper_2502_07517_gb300 import build as lib_build
+    if rank == 0:
+        lib_build.build()
+    if world > 1:
+        tdist.barrier()
+    from paper_2502_07517_gb300 import crkfr
+
+    mixed = args.mode == "fp32"
+    prob, u = make_workload(seed=rank)
+    M, ne, npn = u.shape
+    nodes = ne * npn
+    stream = torch.cuda.Stream()
+    desc = crkfr.desc_from_problem(prob, precision=crkfr.CR_FP32_BULK if mixed else crkfr.CR_FP64,
+                                   stream=stream.cuda_stream)
+    ctx = crkfr.cr_init_mesh(desc)
+    crkfr.cr_set_state(ctx, u)
+    launches = crkfr.cr_launches_per_step(ctx)
+    crkfr.cr_step_async(ctx, args.warmup, 1e300)
+    crkfr.cr_sync(ctx)
+
+    # ---- timed region: K steps, CUDA events on the library's stream ----
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        crkfr.cr_step_async(ctx, args.steps, 1e300)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t_s, n_s = crkfr.cr_sync(ctx)
+    if world > 1:
+        tdist.barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_per_step = ms / args.steps
+    value = world * nodes * args.steps / (ms * 1e-3)
+
+    # ---- per-kernel device times (same workload, every kernel between events) ----
+    kms = crkfr.cr_profile_steps(ctx, args.steps, 1e300) / args.steps
+    names = ["k_local", "k_face", "k_update"]
+    dom = int(np.argmax(kms))
+    flops = flop_model(2, WORKLOAD["degree"], "euler2d")
+    achieved = flops[dom] * nodes / (kms[dom] * 1e-3) / 1e12
+    peak = PEAK_FP32_TFLOPS if mixed else PEAK_FP64_TFLOPS
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": names[dom],
+                "peak_source": "derived: 152 SMs x %s FMA lanes x 2 x 2070 MHz"
+                               % ("128 FP32" if mixed else "2 FP64"),
+                "algorithmic_flops_per_point": flops[dom],
+                "kernel_ms": {nm: float(x) for nm, x in zip(names, kms)},
+                "step_tflops": sum(flops) * nodes / (ms_per_step * 1e-3) / 1e12}
+
+    # ---- end to end through the public API with host buffers ----
+    host_in = torch.from_numpy(u).pin_memory()
+    host_out = torch.empty(u.shape, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        crkfr.lib().cr_set_state(ctx.handle, host_in.data_ptr(), 0)
+        crkfr.cr_step(ctx, 1, 1e300)
+        crkfr.lib().cr_get_state(ctx.handle, host_out.data_ptr(), 0)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    nbytes = u.size * 8
+    e2e = {"value": world * nodes / e2e_s, "unit": "DOF-updates/s", "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_s * 1e3}
+
+    if rank != 0:
+        if world > 1:
+            tdist.barrier()
+            tdist.destroy_process_group()
+        return
+    cb = cpu_baseline() if world == 1 else None
+    clocks = clk.summary()
+    line = {
+        "metric": "DOF-updates/s", "value": value, "unit": "DOF-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "elements": ne, "points_per_element": npn,
+                   "variables": M, "mode": args.mode,
+                   "limiters": "blend+MUSCL-Hancock+flux+scaling",
+                   "l2": "inputs larger than L2 (state %.0f MB)" % (u.size * (4 if mixed else 8) / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": launches * args.steps, "t_reached": t_s, "steps_run": n_s,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--mode", choices=("fp64", "fp32"), default="fp64")
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * cr.h - C ABI of libcrkfr.so, the GB300 (sm_103a) implementation of one time
+ * step of compact Runge-Kutta Flux Reconstruction (cRKFR) with the subcell
+ * blending limiter, the flux limiter for admissible means and the positivity
+ * scaling limiter, after Babbar & Chen, "Compact Runge-Kutta Flux
+ * Reconstruction for Hyperbolic Conservation Laws with admissibility
+ * preservation", arXiv 2502.07517.
+ *
+ * Conventions shared by every entry point:
+ *  - All calls return a cr_status; CR_OK is 0, errors are negative.  No call
+ *    aborts the process.  cr_last_error(ctx) gives a one-line description of
+ *    the last error on a context.
+ *  - State arrays are FP64, structure-of-arrays u[v][e][k]: variable v,
+ *    element e = ix + nx * iy, solution point k = p + (N+1) * q (p along x,
+ *    q along y; in 1D k = p).  Solution points are the N+1 Gauss-Legendre
+ *    nodes of [0,1] in each direction (Sec. 2, eq. (soln.points)).
+ *  - A pointer argument with on_device != 0 is a CUDA device pointer that the
+ *    caller owns and keeps valid until the stream work has finished; with
+ *    on_device == 0 it is host memory.  The library never frees caller memory.
+ *  - Work is ordered on the stream given in cr_mesh_desc.stream (NULL: the
+ *    legacy default stream).  Calls that return results on the host
+ *    synchronise that stream.
+ *  - A context owns its device workspace: either the caller passes a device
+ *    buffer of cr_workspace_bytes() bytes to cr_init_mesh, or passes NULL and
+ *    the library allocates (and later frees) it with cudaMalloc.
+ *  - Contexts are not thread-safe; use one context per host thread.
+ */
+#ifndef CRKFR_CR_H
+#define CRKFR_CR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cr_ctx cr_ctx;
+
+typedef enum {
+  CR_OK = 0,
+  CR_E_INVALID_ARG = -1,   /* a descriptor field, size or pointer is out of range */
+  CR_E_INVALID_STATE = -2, /* cr_set_state: a solution point is inadmissible or not finite */
+  CR_E_INADMISSIBLE = -3,  /* cr_step: an element mean or a limited point left the
+                              admissible set, or a value is not finite */
+  CR_E_TIMEOUT = -4,       /* a bounded device wait gave up */
+  CR_E_CUDA = -5,          /* a CUDA runtime call failed (message in cr_last_error) */
+  CR_E_NOMEM = -6,         /* device or host allocation failed */
+  CR_E_UNSUPPORTED = -7    /* this combination (equation, dim, degree, precision) is not built */
+} cr_status;
+
+enum { CR_EQ_LINADV = 0, CR_EQ_EULER = 1, CR_EQ_TENMOMENT = 2 };
+enum { CR_BC_PERIODIC = 0, CR_BC_OUTFLOW = 1 };
+enum {
+  CR_LIM_BLEND = 1,   /* blend with the subcell scheme, Sec. 4 eq. (blended.scheme) */
+  CR_LIM_MH = 2,      /* MUSCL-Hancock subcell fluxes (otherwise first order), Sec. 4.2 */
+  CR_LIM_FLUX = 4,    /* flux limiter for admissibility in means, Sec. 4.3 */
+  CR_LIM_SCALING = 8, /* Zhang-Shu positivity scaling after the update, Sec. 3.2 */
+  CR_LIM_TRACES = 16  /* the scaling limiter also checks the element-face traces */
+};
+enum { CR_ALPHA_INDICATOR = 0, CR_ALPHA_FIXED = 1 };
+enum { CR_FP64 = 0, CR_FP32_BULK = 1 };
+
+typedef struct {
+  int dim;               /* 1 or 2 */
+  int nx, ny;            /* elements per direction, >= 1 (ny ignored in 1D) */
+  double x0, x1, y0, y1; /* domain [x0,x1] x [y0,y1] */
+  int bc_x, bc_y;        /* CR_BC_*; outflow is the fully-outflow rule of Sec. 3.3 */
+  int degree;            /* N, 1..4; the RK method has order N+1 (Sec. 3) */
+  int equation;          /* CR_EQ_*: u_t + a.grad u = 0 (Sec. 5.1.1), Euler (Sec. 5.2,
+                            5.3), ten-moment (Sec. 5.4) */
+  double gamma;          /* Euler adiabatic constant */
+  double adv[2];         /* linear advection velocity */
+  int source;            /* 0 none; 1 ten-moment source of eq. (tenmom.source) with
+                            W = src_amp exp(-src_k |x - (src_cx, src_cy)|^2) */
+  double src_amp, src_k, src_cx, src_cy;
+  int limiter;           /* CR_LIM_* bits */
+  int alpha_mode;        /* CR_ALPHA_*: smoothness indicator, or alpha_e = alpha_fixed */
+  double alpha_fixed;
+  int precision;         /* CR_FP64, or CR_FP32_BULK: FP32 stage arithmetic with FP64
+                            element means, FP64 flux-limiter and scaling-limiter theta */
+  double cfl;            /* CFL(N) of eq. (time.step.2d); <= 0: Fourier analysis */
+  double cfl_safety;     /* C_s of eq. (time.step.2d); <= 0: 0.98 */
+  void* stream;          /* cudaStream_t or NULL */
+} cr_mesh_desc;
+
+/* Device workspace needed by cr_init_mesh for this descriptor.
+ * Errors: CR_E_INVALID_ARG for a bad descriptor or NULL bytes. */
+cr_status cr_workspace_bytes(const cr_mesh_desc* desc, size_t* bytes);
+
+/* Create a context for one mesh.  workspace: device buffer of at least
+ * cr_workspace_bytes() bytes owned by the caller, aligned to 256 bytes, or
+ * NULL to let the library allocate it.  The state is undefined until
+ * cr_set_state.  Errors: CR_E_INVALID_ARG, CR_E_UNSUPPORTED, CR_E_NOMEM,
+ * CR_E_CUDA; *out is NULL on error. */
+cr_status cr_init_mesh(const cr_mesh_desc* desc, void* workspace, size_t workspace_bytes,
+                       cr_ctx** out);
+
+/* Release the context (and the workspace if the library allocated it). */
+void cr_destroy(cr_ctx* ctx);
+
+/* Copy the state u[M][Ne][Np] (FP64) in, reset time to 0, and compute the
+ * first time step (eq. (time.step.2d)) and the indicator.  Synchronises.
+ * Errors: CR_E_INVALID_STATE when a solution point is not finite or (for
+ * equations with an admissible set, Sec. 2 eq. (uad.form)) not admissible. */
+cr_status cr_set_state(cr_ctx* ctx, const double* u, int on_device);
+
+/* Copy the current state out as u[M][Ne][Np] (FP64); synchronises when
+ * on_device == 0.  In CR_FP32_BULK mode values are mean + FP32 fluctuation. */
+cr_status cr_get_state(cr_ctx* ctx, double* u, int on_device);
+
+/* Advance up to max_steps cRKFR steps (Sec. 3 eq. (crkfr.avg), blended by
+ * eq. (blended.scheme), with source eq. (crkfr.source)).  dt comes from eq.
+ * (time.step.2d) on the current element means, or is dt_fixed when
+ * dt_fixed > 0; the last step is shortened to land exactly on t_final.
+ * Synchronises and returns the time reached and the number of steps taken
+ * (either pointer may be NULL).  Errors: CR_E_INADMISSIBLE (the step that
+ * failed is counted; the state is the failed step's output). */
+cr_status cr_step(cr_ctx* ctx, int max_steps, double t_final, double dt_fixed, double* t_out,
+                  int* steps_out);
+
+/* As cr_step but only enqueues the work on the stream; cr_sync reports. */
+cr_status cr_step_async(cr_ctx* ctx, int max_steps, double t_final, double dt_fixed);
+
+/* Wait for the context's stream and report time, steps and the step status. */
+cr_status cr_sync(cr_ctx* ctx, double* t_out, int* steps_out);
+
+/* alpha_e (after neighbour smoothing) used by the most recent step, [Ne]
+ * FP64.  Synchronises when on_device == 0. */
+cr_status cr_get_alpha(cr_ctx* ctx, double* alpha, int on_device);
+
+/* Time step the next cr_step would take without t_final clipping. Synchronises. */
+cr_status cr_next_dt(cr_ctx* ctx, double* dt);
+
+/* Number of kernel launches one step enqueues. */
+cr_status cr_launches_per_step(cr_ctx* ctx, int* launches);
+
+/* As cr_step_async, but launches every kernel of every step directly (no CUDA
+ * graph) between CUDA events on the context's stream and adds each kernel's
+ * device time in milliseconds to kernel_ms[i], i < cr_launches_per_step()
+ * (in launch order: element-local kernel, face kernel, update kernel).
+ * Synchronises.  For measurement; the state advances exactly as in cr_step. */
+cr_status cr_profile_steps(cr_ctx* ctx, int max_steps, double t_final, double dt_fixed,
+                           double* kernel_ms);
+
+/* CFL(N) of eq. (time.step.2d) from the library's Fourier analysis of the
+ * D2 scheme for linear advection (host only, no device needed). */
+cr_status cr_cfl_number(int degree, double* cfl);
+
+/* Reference-element tables the kernels use (host only): Gauss-Legendre nodes
+ * xi[N+1] and weights w[N+1] on [0,1], and D[(N+1)*(N+1)], D_ij = l_j'(xi_i)
+ * (Sec. 2 eq. (diff.matrix)).  Any pointer may be NULL. */
+cr_status cr_reference_tables(int degree, double* xi, double* w, double* D);
+
+/* Last error message of ctx (or of the last failed cr_init_mesh when ctx is NULL). */
+const char* cr_last_error(const cr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,261 @@
+"""Python binding of libcrkfr.so (include/cr.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels.  PyTorch supplies
+device memory (the workspace and device state tensors) and the CUDA stream.
+The library must have been built (paper_2502_07517_gb300.build.build());
+loading fails loudly otherwise, there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcrkfr.so")
+
+CR_OK = 0
+STATUS = {0: "CR_OK", -1: "CR_E_INVALID_ARG", -2: "CR_E_INVALID_STATE", -3: "CR_E_INADMISSIBLE",
+          -4: "CR_E_TIMEOUT", -5: "CR_E_CUDA", -6: "CR_E_NOMEM", -7: "CR_E_UNSUPPORTED"}
+CR_EQ_LINADV, CR_EQ_EULER, CR_EQ_TENMOMENT = 0, 1, 2
+CR_BC_PERIODIC, CR_BC_OUTFLOW = 0, 1
+CR_LIM_BLEND, CR_LIM_MH, CR_LIM_FLUX, CR_LIM_SCALING, CR_LIM_TRACES = 1, 2, 4, 8, 16
+CR_ALPHA_INDICATOR, CR_ALPHA_FIXED = 0, 1
+CR_FP64, CR_FP32_BULK = 0, 1
+
+# C symbols declared in include/cr.h
+SYMBOLS = ("cr_workspace_bytes", "cr_init_mesh", "cr_destroy", "cr_set_state", "cr_get_state",
+           "cr_step", "cr_step_async", "cr_sync", "cr_get_alpha", "cr_next_dt",
+           "cr_launches_per_step", "cr_profile_steps", "cr_cfl_number", "cr_reference_tables",
+           "cr_last_error")
+
+
+class CrError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+
+
+class cr_mesh_desc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+        ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
+        ("degree", ctypes.c_int), ("equation", ctypes.c_int),
+        ("gamma", ctypes.c_double), ("adv", ctypes.c_double * 2),
+        ("source", ctypes.c_int),
+        ("src_amp", ctypes.c_double), ("src_k", ctypes.c_double),
+        ("src_cx", ctypes.c_double), ("src_cy", ctypes.c_double),
+        ("limiter", ctypes.c_int), ("alpha_mode", ctypes.c_int),
+        ("alpha_fixed", ctypes.c_double), ("precision", ctypes.c_int),
+        ("cfl", ctypes.c_double), ("cfl_safety", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libcrkfr.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libcrkfr.so is missing at %s: build it with "
+                               "paper_2502_07517_gb300.build.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, D, V = ctypes.POINTER(cr_mesh_desc), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
+        I = ctypes.c_int
+        L.cr_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.cr_init_mesh.argtypes = [P, V, ctypes.c_size_t, ctypes.POINTER(V)]
+        L.cr_destroy.argtypes = [V]
+        L.cr_destroy.restype = None
+        L.cr_set_state.argtypes = [V, V, I]
+        L.cr_get_state.argtypes = [V, V, I]
+        L.cr_step.argtypes = [V, I, ctypes.c_double, ctypes.c_double, D, ctypes.POINTER(I)]
+        L.cr_step_async.argtypes = [V, I, ctypes.c_double, ctypes.c_double]
+        L.cr_sync.argtypes = [V, D, ctypes.POINTER(I)]
+        L.cr_get_alpha.argtypes = [V, V, I]
+        L.cr_next_dt.argtypes = [V, D]
+        L.cr_launches_per_step.argtypes = [V, ctypes.POINTER(I)]
+        L.cr_profile_steps.argtypes = [V, I, ctypes.c_double, ctypes.c_double, D]
+        L.cr_cfl_number.argtypes = [I, D]
+        L.cr_reference_tables.argtypes = [I, D, D, D]
+        L.cr_last_error.argtypes = [V]
+        L.cr_last_error.restype = ctypes.c_char_p
+        for s in SYMBOLS:
+            if s not in ("cr_destroy", "cr_last_error"):
+                getattr(L, s).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st, ctx=None):
+    if st != CR_OK:
+        msg = lib().cr_last_error(ctx)
+        raise CrError(st, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ------------------------------------------------------------------ C ABI ---
+def cr_cfl_number(degree):
+    out = ctypes.c_double()
+    _check(lib().cr_cfl_number(int(degree), ctypes.byref(out)))
+    return out.value
+
+
+def cr_reference_tables(degree):
+    n = degree + 1
+    xi, w, D = np.zeros(n), np.zeros(n), np.zeros((n, n))
+    _check(lib().cr_reference_tables(int(degree), _dptr(xi), _dptr(w), _dptr(D)))
+    return xi, w, D
+
+
+def cr_workspace_bytes(desc):
+    out = ctypes.c_size_t()
+    _check(lib().cr_workspace_bytes(ctypes.byref(desc), ctypes.byref(out)))
+    return out.value
+
+
+class Context:
+    """Owns a cr_ctx and (when the caller gave none) the torch workspace tensor."""
+
+    def __init__(self, handle, workspace, desc):
+        self.handle = handle
+        self.workspace = workspace
+        self.desc = desc
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().cr_destroy(self.handle)
+            self.handle = None
+
+
+def cr_init_mesh(desc, workspace=None):
+    """Create a context.  workspace=None allocates the device workspace as a
+    torch uint8 tensor on the current device (256-byte aligned)."""
+    import torch
+    nbytes = cr_workspace_bytes(desc)
+    if workspace is None:
+        workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    base = workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    handle = ctypes.c_void_p()
+    _check(lib().cr_init_mesh(ctypes.byref(desc), ctypes.c_void_p(aligned),
+                              nbytes, ctypes.byref(handle)))
+    return Context(handle, workspace, desc)
+
+
+def cr_destroy(ctx):
+    if ctx.handle:
+        lib().cr_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def cr_set_state(ctx, u):
+    """u: numpy float64 [M][Ne][Np] (host) or a torch float64 CUDA tensor."""
+    if isinstance(u, np.ndarray):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        _check(lib().cr_set_state(ctx.handle, u.ctypes.data, 0), ctx.handle)
+    else:
+        assert u.is_cuda and u.dtype.is_floating_point and u.element_size() == 8 and u.is_contiguous()
+        _check(lib().cr_set_state(ctx.handle, u.data_ptr(), 1), ctx.handle)
+
+
+def cr_get_state(ctx, out=None, shape=None):
+    """Returns a numpy array (out=None, needs shape) or fills a torch CUDA tensor."""
+    if out is None:
+        out = np.empty(shape, dtype=np.float64)
+    if isinstance(out, np.ndarray):
+        _check(lib().cr_get_state(ctx.handle, out.ctypes.data, 0), ctx.handle)
+    else:
+        _check(lib().cr_get_state(ctx.handle, out.data_ptr(), 1), ctx.handle)
+    return out
+
+
+def cr_step(ctx, max_steps, t_final, dt_fixed=0.0):
+    """Returns (t, steps); raises CrError on an inadmissible step."""
+    t = ctypes.c_double()
+    n = ctypes.c_int()
+    _check(lib().cr_step(ctx.handle, int(max_steps), float(t_final), float(dt_fixed),
+                         ctypes.byref(t), ctypes.byref(n)), ctx.handle)
+    return t.value, n.value
+
+
+def cr_step_async(ctx, max_steps, t_final, dt_fixed=0.0):
+    _check(lib().cr_step_async(ctx.handle, int(max_steps), float(t_final), float(dt_fixed)),
+           ctx.handle)
+
+
+def cr_sync(ctx):
+    t = ctypes.c_double()
+    n = ctypes.c_int()
+    _check(lib().cr_sync(ctx.handle, ctypes.byref(t), ctypes.byref(n)), ctx.handle)
+    return t.value, n.value
+
+
+def cr_get_alpha(ctx, ne):
+    out = np.empty(ne, dtype=np.float64)
+    _check(lib().cr_get_alpha(ctx.handle, out.ctypes.data, 0), ctx.handle)
+    return out
+
+
+def cr_next_dt(ctx):
+    out = ctypes.c_double()
+    _check(lib().cr_next_dt(ctx.handle, ctypes.byref(out)), ctx.handle)
+    return out.value
+
+
+def cr_launches_per_step(ctx):
+    out = ctypes.c_int()
+    _check(lib().cr_launches_per_step(ctx.handle, ctypes.byref(out)), ctx.handle)
+    return out.value
+
+
+def cr_profile_steps(ctx, max_steps, t_final, dt_fixed=0.0):
+    """Runs the steps with per-kernel CUDA events; returns device ms per kernel."""
+    n = cr_launches_per_step(ctx)
+    ms = np.zeros(n)
+    _check(lib().cr_profile_steps(ctx.handle, int(max_steps), float(t_final), float(dt_fixed),
+                                  _dptr(ms)), ctx.handle)
+    return ms
+
+
+def cr_last_error(ctx=None):
+    msg = lib().cr_last_error(ctx.handle if ctx else None)
+    return msg.decode() if msg else ""
+
+
+# ------------------------------------------------------ problem marshalling -
+_EQ = {"linadv": CR_EQ_LINADV, "euler": CR_EQ_EULER, "tenmoment": CR_EQ_TENMOMENT}
+_BC = {"periodic": CR_BC_PERIODIC, "outflow": CR_BC_OUTFLOW}
+_LIM = {"blend": CR_LIM_BLEND, "mh": CR_LIM_MH, "flux": CR_LIM_FLUX, "scaling": CR_LIM_SCALING,
+        "traces": CR_LIM_TRACES}
+
+
+def desc_from_problem(prob, precision=CR_FP64, alpha_fixed=None, stream=None, **over):
+    """cr_mesh_desc from a workload problem dict (see workloads.py)."""
+    d = cr_mesh_desc()
+    d.dim, d.nx, d.ny = prob["dim"], prob["nx"], prob["ny"] if prob["dim"] == 2 else 1
+    d.x0, d.x1, d.y0, d.y1 = prob["x0"], prob["x1"], prob["y0"], prob["y1"]
+    d.bc_x, d.bc_y = _BC[prob["bc_x"]], _BC[prob["bc_y"]]
+    d.degree, d.equation, d.gamma = prob["degree"], _EQ[prob["equation"]], prob["gamma"]
+    d.adv[0], d.adv[1] = prob["adv"]
+    src = prob.get("source")
+    if src:
+        d.source, d.src_amp, d.src_k, d.src_cx, d.src_cy = 1, src["amp"], src["k"], src["cx"], src["cy"]
+    lim = 0
+    for name in prob["limiter"]:
+        lim |= _LIM[name]
+    d.limiter = lim
+    if alpha_fixed is not None:
+        d.alpha_mode, d.alpha_fixed = CR_ALPHA_FIXED, alpha_fixed
+    d.precision = precision
+    d.cfl, d.cfl_safety = 0.0, 0.98
+    d.stream = stream
+    for k, v in over.items():
+        setattr(d, k, v)
+    return d

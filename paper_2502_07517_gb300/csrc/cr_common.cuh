@@ -1,0 +1,290 @@
+// Shared device-side definitions of the cRKFR library: the time-control
+// record, the per-degree tables, launch parameters, the Butcher tableaux and
+// the equation functors.  Everything here is compiled for sm_103a only.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace crk {
+
+constexpr int kMaxN = 4;
+constexpr int kMaxNodes1 = kMaxN + 1;
+
+// Status bits kept in TimeCtl::status.
+enum : int { kStInadmissible = 1, kStNonFinite = 2, kStInvalidInput = 4 };
+
+// Time control of one context, resident in device memory.  Every kernel of a
+// step derives the step size from it (step_dt), so a whole run can be
+// enqueued without host round trips; only the last block of the update kernel
+// writes it (t, rate_last), after every other block has finished reading.
+struct TimeCtl {
+  double t;                 // current time
+  double t_final;           // the run stops here; the last step is clipped to it
+  double dt_fixed;          // > 0: use this dt instead of the CFL rule
+  double cfl_factor;        // C_s * CFL(N), eq. (time.step.2d)
+  double rate_last;         // max_e sigma_x(mean)/dx + sigma_y(mean)/dy of the current state
+  unsigned long long rate_acc;  // running max (bit pattern of a non-negative double)
+  unsigned int blocks_done; // last-block counter of the update kernel
+  int status;               // kSt* bits, sticky until cr_set_state
+  int bad_elem;             // smallest element index that set a status bit
+  int steps;                // steps taken since cr_set_state
+  double dt_step;           // dt of the step in flight (written by the first kernel of a step)
+  int last_step;            // 1 when that step lands on t_final
+};
+
+// dt of the step about to run (0: nothing to do).  Identical arithmetic in
+// every kernel of the step, from the same TimeCtl fields.
+__device__ __forceinline__ double step_dt(const TimeCtl* c, bool* last) {
+  *last = false;
+  if (c->status != 0) return 0.0;
+  double rem = c->t_final - c->t;
+  if (!(rem > 0.0)) return 0.0;
+  double dtc = c->dt_fixed > 0.0 ? c->dt_fixed : c->cfl_factor / c->rate_last;
+  if (dtc >= rem) {
+    *last = true;
+    return rem;
+  }
+  return dtc;
+}
+
+// Reference-element tables for degree N in the arithmetic type of the kernel
+// (filled on the host from FP64 values).
+template <typename real>
+struct Tab {
+  real xi[kMaxNodes1], w[kMaxNodes1], invw[kMaxNodes1];
+  real l0[kMaxNodes1], l1[kMaxNodes1];     // l_p(0), l_p(1)
+  real D[kMaxNodes1 * kMaxNodes1];         // D[i*n+j] = l_j'(xi_i), Sec. 2 eq. (diff.matrix)
+  real Dt[kMaxNodes1 * kMaxNodes1];        // D - g_R' l(1)^T - g_L' l(0)^T (FR volume part)
+  real gR[kMaxNodes1], gL[kMaxNodes1];     // g_R'(xi_p) = l_p(1)/w_p, g_L'(xi_p) = -l_p(0)/w_p
+  real dm[kMaxNodes1], dp[kMaxNodes1];     // subcell faces relative to the node: x_{p-+1/2} - xi_p
+  real ihm[kMaxNodes1], ihp[kMaxNodes1], ihc[kMaxNodes1];  // inverse node spacings incl. halo nodes
+  real V[kMaxNodes1 * kMaxNodes1];         // V[j*n+p] = (2j+1) w_p L_j(2 xi_p - 1) (Legendre modes)
+};
+
+// Mesh, physics and limiter switches (one struct per launch, by value).
+struct Mesh {
+  int nx, ny, ne, nfx, nfy;  // elements and faces per direction (nf = n or n+1)
+  int bcx, bcy;              // 0 periodic, 1 outflow
+  double x0, y0, dx, dy, invdx, invdy;
+  int limiter;               // CR_LIM_* bits
+  int alpha_mode;            // 0 indicator, 1 fixed
+  double alpha_fixed;
+  double gamma, ax, ay;
+  int source;
+  double src_amp, src_k, src_cx, src_cy;
+  double T_ind, s_ind;       // indicator threshold T(N) and sharpness s
+};
+
+enum : int { kLimBlend = 1, kLimMH = 2, kLimFlux = 4, kLimScaling = 8, kLimTraces = 16 };
+
+// Device buffers of one context (all inside the workspace).
+template <typename real>
+struct Bufs {
+  real* u;           // state [M][Ne][Np] (FP32_BULK: fluctuation about the mean)
+  double* umean;     // FP32_BULK: element means [M][Ne] (FP64)
+  real* P;           // partial update [M][Ne][Np] (everything but the element-face fluxes)
+  double* smean;     // FP32_BULK: sum_k W_k S_k per element [M][Ne] (FP64)
+  real* slot;        // per element face-node data [4M+1][nside][Ne][nfn]
+  real* fx;          // x-face numerical flux [M][ny][nfx][nq]
+  real* fy;          // y-face numerical flux [M][nfy][nx][n]
+  double* alpha_raw; // indicator alpha of the current state [Ne]
+  double* alpha;     // smoothed alpha used by the last step [Ne]
+  TimeCtl* ctl;
+};
+
+template <typename real>
+struct KParams {
+  Mesh m;
+  Tab<real> tb;      // tables in the bulk type
+  Tab<double> td;    // FP64 tables (limiters, means)
+  Bufs<real> b;
+};
+
+// ---------------------------------------------------------------------------
+// Butcher tableaux (Sec. 2 eq. (butcher)); degree N uses order N+1 (Sec. 3).
+// N=1 cRK22 eq. (crk22), N=2 cRK33 eq. (crk33), N=3 cRK44 eq. (crk44).  The
+// paper prints no fifth-order scheme for N=4; the six-stage fifth-order method
+// of Butcher with c = (0, 1/4, 1/4, 1/2, 3/4, 1) is used.
+template <int N> struct Tableau;
+template <> struct Tableau<1> {
+  static constexpr int S = 2;
+  __host__ __device__ static constexpr double a(int i, int j) { return (i == 1 && j == 0) ? 0.5 : 0.0; }
+  __host__ __device__ static constexpr double b(int i) { return i == 1 ? 1.0 : 0.0; }
+};
+template <> struct Tableau<2> {
+  static constexpr int S = 3;
+  __host__ __device__ static constexpr double a(int i, int j) {
+    return (i == 1 && j == 0) ? 1.0 / 3.0 : (i == 2 && j == 1) ? 2.0 / 3.0 : 0.0;
+  }
+  __host__ __device__ static constexpr double b(int i) { return i == 0 ? 0.25 : i == 2 ? 0.75 : 0.0; }
+};
+template <> struct Tableau<3> {
+  static constexpr int S = 4;
+  __host__ __device__ static constexpr double a(int i, int j) {
+    return (j == i - 1) ? (i == 3 ? 1.0 : 0.5) : 0.0;
+  }
+  __host__ __device__ static constexpr double b(int i) {
+    return (i == 0 || i == 3) ? 1.0 / 6.0 : 1.0 / 3.0;
+  }
+};
+template <> struct Tableau<4> {
+  static constexpr int S = 6;
+  __host__ __device__ static constexpr double a(int i, int j) {
+    return i == 1 ? (j == 0 ? 0.25 : 0.0)
+         : i == 2 ? (j < 2 ? 0.125 : 0.0)
+         : i == 3 ? (j == 1 ? -0.5 : j == 2 ? 1.0 : 0.0)
+         : i == 4 ? (j == 0 ? 3.0 / 16.0 : j == 3 ? 9.0 / 16.0 : 0.0)
+         : i == 5 ? (j == 0 ? -3.0 / 7.0 : j == 1 ? 2.0 / 7.0 : j == 2 ? 12.0 / 7.0
+                   : j == 3 ? -12.0 / 7.0 : j == 4 ? 8.0 / 7.0 : 0.0)
+         : 0.0;
+  }
+  __host__ __device__ static constexpr double b(int i) {
+    return i == 0 ? 7.0 / 90.0 : i == 2 ? 32.0 / 90.0 : i == 3 ? 12.0 / 90.0
+         : i == 4 ? 32.0 / 90.0 : i == 5 ? 7.0 / 90.0 : 0.0;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Equation functors.  dir = 0 (x) or 1 (y); calls with a literal dir fold.
+template <typename real>
+__device__ __forceinline__ real sqrt_pos(real x) { return sqrt(x > real(0) ? x : real(0)); }
+
+struct EqLinAdv {  // u_t + a . grad u = 0, Sec. 5.1.1
+  static constexpr int M = 1, K = 0;
+  template <typename real>
+  __device__ static void flux(const real* u, int dir, real* f, const Mesh& m) {
+    f[0] = real(dir == 0 ? m.ax : m.ay) * u[0];
+  }
+  template <typename real>
+  __device__ static real speed(const real* u, int dir, const Mesh& m) {
+    return real(fabs(dir == 0 ? m.ax : m.ay));
+  }
+  template <typename real>
+  __device__ static real constraint(const real*, int, const Mesh&) { return real(1); }
+  template <typename real>
+  __device__ static real indicator_var(const real* u, const Mesh&) { return u[0]; }
+};
+
+// Euler, Sec. 5.2 eq. (1deuler) (DIM 1, u = rho, rho v, E) and Sec. 5.3
+// eq. (2deuler) (DIM 2, u = rho, rho v1, rho v2, E); p from eqs. (state), (2dstate).
+template <int DIM>
+struct EqEuler {
+  static constexpr int M = DIM == 1 ? 3 : 4, K = 2;
+  template <typename real>
+  __device__ static real pressure(const real* u, const Mesh& m) {
+    real g1 = real(m.gamma - 1.0);
+    if (DIM == 1) return g1 * (u[2] - real(0.5) * u[1] * u[1] / u[0]);
+    return g1 * (u[3] - real(0.5) * (u[1] * u[1] + u[2] * u[2]) / u[0]);
+  }
+  template <typename real>
+  __device__ static void flux(const real* u, int dir, real* f, const Mesh& m) {
+    real rinv = real(1) / u[0];
+    if (DIM == 1) {
+      real v = u[1] * rinv;
+      real p = real(m.gamma - 1.0) * (u[2] - real(0.5) * u[1] * v);
+      f[0] = u[1];
+      f[1] = u[1] * v + p;
+      f[2] = (u[2] + p) * v;
+      return;
+    }
+    real v1 = u[1] * rinv, v2 = u[2] * rinv;
+    real p = real(m.gamma - 1.0) * (u[3] - real(0.5) * (u[1] * v1 + u[2] * v2));
+    real vn = dir == 0 ? v1 : v2;
+    f[0] = u[1 + dir];
+    f[1] = u[1] * vn + (dir == 0 ? p : real(0));
+    f[2] = u[2] * vn + (dir == 1 ? p : real(0));
+    f[3] = (u[3] + p) * vn;
+  }
+  template <typename real>
+  __device__ static real speed(const real* u, int dir, const Mesh& m) {
+    real v = u[1 + dir] / u[0];
+    return fabs(v) + sqrt_pos(real(m.gamma) * pressure(u, m) / u[0]);
+  }
+  template <typename real>
+  __device__ static real constraint(const real* u, int k, const Mesh& m) {
+    return k == 0 ? u[0] : pressure(u, m);
+  }
+  template <typename real>
+  __device__ static real indicator_var(const real* u, const Mesh& m) { return u[0] * pressure(u, m); }
+};
+
+// Ten-moment equations, Sec. 5.4 eq. (tmp); u = (rho, rho v1, rho v2, E11, E12, E22),
+// P = 2E - rho v (x) v.  Admissibility: rho > 0 and lambda_min(P) > 0.
+struct EqTenMoment {
+  static constexpr int M = 6, K = 2;
+  template <typename real>
+  __device__ static void flux(const real* u, int dir, real* f, const Mesh&) {
+    real rinv = real(1) / u[0];
+    real v1 = u[1] * rinv, v2 = u[2] * rinv;
+    real p11 = real(2) * u[3] - u[1] * v1;
+    real p12 = real(2) * u[4] - u[1] * v2;
+    real p22 = real(2) * u[5] - u[2] * v2;
+    if (dir == 0) {
+      f[0] = u[1];
+      f[1] = p11 + u[1] * v1;
+      f[2] = p12 + u[1] * v2;
+      f[3] = (u[3] + p11) * v1;
+      f[4] = u[4] * v1 + real(0.5) * (p11 * v2 + p12 * v1);
+      f[5] = u[5] * v1 + p12 * v2;
+    } else {
+      f[0] = u[2];
+      f[1] = p12 + u[1] * v2;
+      f[2] = p22 + u[2] * v2;
+      f[3] = u[3] * v2 + p12 * v1;
+      f[4] = u[4] * v2 + real(0.5) * (p12 * v2 + p22 * v1);
+      f[5] = (u[5] + p22) * v2;
+    }
+  }
+  template <typename real>
+  __device__ static real speed(const real* u, int dir, const Mesh&) {
+    real rinv = real(1) / u[0];
+    real v = u[1 + dir] * rinv;
+    real pdd = real(2) * u[3 + 2 * dir] - u[1 + dir] * v;
+    return fabs(v) + sqrt_pos(real(3) * pdd * rinv);
+  }
+  template <typename real>
+  __device__ static real constraint(const real* u, int k, const Mesh&) {
+    if (k == 0) return u[0];
+    real rinv = real(1) / u[0];
+    real p11 = real(2) * u[3] - u[1] * u[1] * rinv;
+    real p12 = real(2) * u[4] - u[1] * u[2] * rinv;
+    real p22 = real(2) * u[5] - u[2] * u[2] * rinv;
+    real h = real(0.5) * (p11 - p22);
+    return real(0.5) * (p11 + p22) - sqrt(h * h + p12 * p12);
+  }
+  template <typename real>
+  __device__ static real indicator_var(const real* u, const Mesh&) {
+    real rinv = real(1) / u[0];
+    real p11 = real(2) * u[3] - u[1] * u[1] * rinv;
+    real p22 = real(2) * u[5] - u[2] * u[2] * rinv;
+    return u[0] * real(0.5) * (p11 + p22);
+  }
+};
+
+// Gradient of W = amp exp(-k |x - c|^2) for the ten-moment source (eq. (tenmom.source)).
+template <int DIM>
+__device__ __forceinline__ void source_grad(const Mesh& m, double x, double y, double* dWx,
+                                            double* dWy) {
+  double rx = x - m.src_cx, ry = DIM == 2 ? y - m.src_cy : 0.0;
+  double W = m.src_amp * exp(-m.src_k * (rx * rx + ry * ry));
+  *dWx = -2.0 * m.src_k * rx * W;
+  *dWy = DIM == 2 ? -2.0 * m.src_k * ry * W : 0.0;
+}
+
+// s = s^x + s^y of eq. (tenmom.source), linear in u for fixed grad W.
+template <class EQ, typename real>
+__device__ __forceinline__ void source_eval(const real* u, real dWx, real dWy, real* s) {
+  if constexpr (EQ::M == 6) {
+    s[0] = real(0);
+    s[1] = real(-0.5) * u[0] * dWx;
+    s[2] = real(-0.5) * u[0] * dWy;
+    s[3] = real(-0.5) * u[1] * dWx;
+    s[4] = real(-0.25) * (u[2] * dWx + u[1] * dWy);
+    s[5] = real(-0.5) * u[2] * dWy;
+  } else {
+    for (int v = 0; v < EQ::M; ++v) s[v] = real(0);
+  }
+}
+
+}  // namespace crk

@@ -1,0 +1,704 @@
+// Host side of libcrkfr.so: reference tables, the Fourier CFL analysis, the
+// device workspace, CUDA-graph launches of whole steps and the C ABI of
+// include/cr.h.
+#include <climits>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "../../include/cr.h"
+#include "cr_launch.cuh"
+
+using namespace crk;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Reference element (Sec. 2): Gauss-Legendre nodes on [0,1] by Newton's method
+// on P_{N+1} from Chebyshev starting points; Lagrange values and the
+// differentiation matrix from barycentric weights.
+void legendre_pd(int n, double x, double* P, double* dP) {
+  double pm = 1.0, p = x;
+  if (n == 0) {
+    *P = 1.0;
+    *dP = 0.0;
+    return;
+  }
+  for (int k = 2; k <= n; ++k) {
+    const double pn = ((2 * k - 1) * x * p - (k - 1) * pm) / k;
+    pm = p;
+    p = pn;
+  }
+  *P = p;
+  *dP = n * (pm - x * p) / (1.0 - x * x);
+}
+
+struct HostTables {
+  int N;
+  double xi[kMaxNodes1], w[kMaxNodes1], l0[kMaxNodes1], l1[kMaxNodes1];
+  double D[kMaxNodes1 * kMaxNodes1];
+};
+
+void build_tables(int N, HostTables* t) {
+  const int n = N + 1;
+  t->N = N;
+  for (int i = 0; i < n; ++i) {
+    double x = -std::cos(M_PI * (2.0 * i + 1.0) / (2.0 * n));
+    for (int it = 0; it < 60; ++it) {
+      double P, dP;
+      legendre_pd(n, x, &P, &dP);
+      const double dx = P / dP;
+      x -= dx;
+      if (std::fabs(dx) <= 1e-16) break;
+    }
+    double P, dP;
+    legendre_pd(n, x, &P, &dP);
+    t->xi[i] = 0.5 * (x + 1.0);
+    t->w[i] = 1.0 / ((1.0 - x * x) * dP * dP);  // 2/((1-x^2)P'^2), halved for [0,1]
+  }
+  double lam[kMaxNodes1];
+  for (int j = 0; j < n; ++j) {
+    double prod = 1.0;
+    for (int m = 0; m < n; ++m)
+      if (m != j) prod *= (t->xi[j] - t->xi[m]);
+    lam[j] = 1.0 / prod;
+  }
+  for (int side = 0; side < 2; ++side) {
+    const double x = side;
+    double den = 0.0;
+    for (int m = 0; m < n; ++m) den += lam[m] / (x - t->xi[m]);
+    for (int j = 0; j < n; ++j) (side ? t->l1 : t->l0)[j] = lam[j] / (x - t->xi[j]) / den;
+  }
+  for (int i = 0; i < n; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      const double d = (lam[j] / lam[i]) / (t->xi[i] - t->xi[j]);
+      t->D[i * n + j] = d;
+      diag -= d;
+    }
+    t->D[i * n + i] = diag;
+  }
+}
+
+double legendre01(int j, double xi) {
+  double P, dP;
+  legendre_pd(j, 2.0 * xi - 1.0, &P, &dP);
+  return P;
+}
+
+template <typename real>
+void fill_tab(const HostTables& h, Tab<real>* t) {
+  memset(t, 0, sizeof(*t));
+  const int N = h.N, n = N + 1;
+  double X[kMaxNodes1 + 2];
+  X[0] = h.xi[N] - 1.0;  // neighbour node across the left face
+  for (int p = 0; p < n; ++p) X[p + 1] = h.xi[p];
+  X[n + 1] = 1.0 + h.xi[0];
+  double xs = 0.0;
+  for (int p = 0; p < n; ++p) {
+    t->xi[p] = real(h.xi[p]);
+    t->w[p] = real(h.w[p]);
+    t->invw[p] = real(1.0 / h.w[p]);
+    t->l0[p] = real(h.l0[p]);
+    t->l1[p] = real(h.l1[p]);
+    t->gR[p] = real(h.l1[p] / h.w[p]);
+    t->gL[p] = real(-h.l0[p] / h.w[p]);
+    // subcells of Sec. 4 eq. (subcell.defn): widths w_p
+    t->dm[p] = real(xs - h.xi[p]);
+    t->dp[p] = real(xs + h.w[p] - h.xi[p]);
+    xs += h.w[p];
+    t->ihm[p] = real(1.0 / (X[p + 1] - X[p]));
+    t->ihp[p] = real(1.0 / (X[p + 2] - X[p + 1]));
+    t->ihc[p] = real(1.0 / (X[p + 2] - X[p]));
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      t->D[i * n + j] = real(h.D[i * n + j]);
+      // FR update of eq. (crkfr.avg) with the trace terms F^delta(0), F^delta(1)
+      // folded into the volume matrix
+      t->Dt[i * n + j] = real(h.D[i * n + j] - (h.l1[i] / h.w[i]) * h.l1[j] +
+                              (h.l0[i] / h.w[i]) * h.l0[j]);
+      t->V[i * n + j] = real((2.0 * i + 1.0) * h.w[j] * legendre01(i, h.xi[j]));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CFL(N) of eq. (time.step.2d) by Fourier analysis of the linear D2 scheme
+// (u_t + u_x = 0, periodic).  With exact linear time averages
+// U = T u, T = sum_{m<=N} (-nu)^m/(m+1)! D^m, the upwind D2 flux and the FR
+// update give the amplification matrix
+//   G(k) = I - nu [ D T - g_L' l(0)^T T + exp(-ik) g_L' l(1)^T T ];
+// CFL is the largest nu with spectral radius <= 1 + 1e-4 on 721 wave numbers
+// (the tolerance passes over the weak ~5e-6 growth of the fifth-order average
+// at N = 4 and stops at the genuine k = pi instability).  Eigenvalues: the
+// characteristic polynomial by Faddeev-LeVerrier, roots by Durand-Kerner.
+using cd = std::complex<double>;
+
+double spectral_radius(const cd* G, int n) {
+  cd Mk[25] = {}, GM[25], c[6];
+  c[n] = 1.0;
+  for (int k = 1; k <= n; ++k) {
+    // Mk = G * M_{k-1} + c_{n-k+1} I
+    cd T[25];
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        cd acc = 0.0;
+        for (int r = 0; r < n; ++r) acc += G[i * n + r] * Mk[r * n + j];
+        T[i * n + j] = acc + (i == j ? c[n - k + 1] : cd(0.0));
+      }
+    for (int i = 0; i < n * n; ++i) Mk[i] = T[i];
+    cd tr = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int r = 0; r < n; ++r) tr += G[i * n + r] * Mk[r * n + i];
+    c[n - k] = -tr / double(k);
+  }
+  (void)GM;
+  cd z[5];
+  const cd seed(0.4, 0.9);
+  z[0] = 1.0;
+  for (int i = 1; i < n; ++i) z[i] = z[i - 1] * seed;
+  for (int it = 0; it < 2000; ++it) {
+    double change = 0.0;
+    for (int i = 0; i < n; ++i) {
+      cd pv = 1.0;
+      for (int k = n - 1; k >= 0; --k) pv = pv * z[i] + c[k];
+      cd den = 1.0;
+      for (int j = 0; j < n; ++j)
+        if (j != i) den *= (z[i] - z[j]);
+      const cd dz = pv / den;
+      z[i] -= dz;
+      change = std::fmax(change, std::abs(dz));
+    }
+    if (change < 1e-15) break;
+  }
+  double r = 0.0;
+  for (int i = 0; i < n; ++i) r = std::fmax(r, std::abs(z[i]));
+  return r;
+}
+
+double max_growth(const HostTables& h, double nu) {
+  const int n = h.N + 1;
+  double T[25] = {}, Dm[25] = {}, tmp[25];
+  for (int i = 0; i < n; ++i) Dm[i * n + i] = 1.0;
+  double fact = 1.0;
+  for (int m = 0; m <= h.N; ++m) {
+    fact *= (m + 1);
+    const double cm = std::pow(-nu, m) / fact;
+    for (int i = 0; i < n * n; ++i) T[i] += cm * Dm[i];
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int r = 0; r < n; ++r) acc += Dm[i * n + r] * h.D[r * n + j];
+        tmp[i * n + j] = acc;
+      }
+    memcpy(Dm, tmp, sizeof(tmp));
+  }
+  double A0[25], A1[25];
+  for (int i = 0; i < n; ++i) {
+    const double gL = -h.l0[i] / h.w[i];
+    for (int j = 0; j < n; ++j) {
+      double dt = 0.0, l0T = 0.0, l1T = 0.0;
+      for (int r = 0; r < n; ++r) {
+        dt += h.D[i * n + r] * T[r * n + j];
+        l0T += h.l0[r] * T[r * n + j];
+        l1T += h.l1[r] * T[r * n + j];
+      }
+      A0[i * n + j] = dt - gL * l0T;
+      A1[i * n + j] = gL * l1T;
+    }
+  }
+  double g = 0.0;
+  const int nk = 721;
+  for (int ik = 0; ik < nk; ++ik) {
+    const double k = 2.0 * M_PI * ik / (nk - 1);
+    const cd ph = std::exp(cd(0.0, -k));
+    cd G[25];
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        G[i * n + j] = (i == j ? 1.0 : 0.0) - nu * (A0[i * n + j] + ph * A1[i * n + j]);
+    g = std::fmax(g, spectral_radius(G, n));
+  }
+  return g;
+}
+
+double cfl_compute(int N) {
+  static double cache[kMaxN + 1] = {0, 0, 0, 0, 0};
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (cache[N] > 0.0) return cache[N];
+  HostTables h;
+  build_tables(N, &h);
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 40; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (max_growth(h, mid) <= 1.0 + 1e-4) lo = mid;
+    else hi = mid;
+  }
+  cache[N] = lo;
+  return lo;
+}
+
+std::string g_init_error;
+
+__global__ void k_reset_ctl(TimeCtl* c, double cfl_factor) {
+  c->t = 0.0;
+  c->t_final = 0.0;
+  c->dt_fixed = 0.0;
+  c->cfl_factor = cfl_factor;
+  c->rate_last = 0.0;
+  c->rate_acc = 0ull;
+  c->blocks_done = 0u;
+  c->status = 0;
+  c->bad_elem = INT_MAX;
+  c->steps = 0;
+  c->dt_step = 0.0;
+  c->last_step = 0;
+}
+
+__global__ void k_set_run(TimeCtl* c, double t_final, double dt_fixed) {
+  c->t_final = t_final;
+  c->dt_fixed = dt_fixed;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t ctl, u, umean, P, smean, slot, fx, fy, alpha_raw, alpha, staging, total;
+};
+
+int nvars_of(const cr_mesh_desc* d) {
+  if (d->equation == CR_EQ_LINADV) return 1;
+  if (d->equation == CR_EQ_EULER) return d->dim == 1 ? 3 : 4;
+  return 6;
+}
+
+Layout layout_of(const cr_mesh_desc* d) {
+  const int n = d->degree + 1, dim = d->dim;
+  const int np = dim == 2 ? n * n : n, M = nvars_of(d);
+  const size_t ny = dim == 2 ? d->ny : 1, nx = d->nx, ne = nx * ny;
+  const size_t nfx = d->bc_x == CR_BC_PERIODIC ? nx : nx + 1;
+  const size_t nfy = dim == 2 ? (d->bc_y == CR_BC_PERIODIC ? ny : ny + 1) : 0;
+  const size_t rs = d->precision == CR_FP32_BULK ? sizeof(float) : sizeof(double);
+  const size_t nside = dim == 2 ? 4 : 2, nfn = dim == 2 ? n : 1;
+  const bool mixed = d->precision == CR_FP32_BULK;
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  L.ctl = take(sizeof(TimeCtl));
+  L.u = take(M * ne * np * rs);
+  L.umean = take(mixed ? M * ne * sizeof(double) : 0);
+  L.P = take(M * ne * np * rs);
+  L.smean = take(mixed ? M * ne * sizeof(double) : 0);
+  L.slot = take((4 * M + 1) * nside * ne * nfn * rs);
+  L.fx = take(M * ny * nfx * nfn * rs);
+  L.fy = take(dim == 2 ? M * nfy * nx * n * rs : 0);
+  L.alpha_raw = take(ne * sizeof(double));
+  L.alpha = take(ne * sizeof(double));
+  L.staging = take(mixed ? M * ne * np * sizeof(double) : 0);
+  L.total = off;
+  return L;
+}
+
+const KernelSet* lookup(const cr_mesh_desc* d) {
+  const int mixed = d->precision == CR_FP32_BULK;
+  if (d->equation == CR_EQ_LINADV)
+    return d->dim == 1 ? kernels_linadv1d(d->degree, mixed) : kernels_linadv2d(d->degree, mixed);
+  if (d->equation == CR_EQ_EULER)
+    return d->dim == 1 ? kernels_euler1d(d->degree, mixed) : kernels_euler2d(d->degree, mixed);
+  return d->dim == 1 ? kernels_tenmoment1d(d->degree, mixed)
+                     : kernels_tenmoment2d(d->degree, mixed);
+}
+
+const char* check_desc(const cr_mesh_desc* d) {
+  if (!d) return "descriptor is NULL";
+  if (d->dim != 1 && d->dim != 2) return "dim must be 1 or 2";
+  if (d->degree < 1 || d->degree > kMaxN) return "degree must be in 1..4";
+  if (d->nx < 1 || (d->dim == 2 && d->ny < 1)) return "nx, ny must be >= 1";
+  if ((double)d->nx * (d->dim == 2 ? d->ny : 1) > 2.0e8) return "too many elements";
+  if (!(d->x1 > d->x0) || (d->dim == 2 && !(d->y1 > d->y0))) return "empty domain";
+  if (d->bc_x < 0 || d->bc_x > 1 || (d->dim == 2 && (d->bc_y < 0 || d->bc_y > 1)))
+    return "unknown boundary condition";
+  if (d->equation < 0 || d->equation > 2) return "unknown equation";
+  if (d->equation == CR_EQ_EULER && !(d->gamma > 1.0)) return "gamma must be > 1";
+  if (d->precision != CR_FP64 && d->precision != CR_FP32_BULK) return "unknown precision";
+  if (d->alpha_mode != CR_ALPHA_INDICATOR && d->alpha_mode != CR_ALPHA_FIXED)
+    return "unknown alpha mode";
+  if (d->alpha_mode == CR_ALPHA_FIXED && !(d->alpha_fixed >= 0.0 && d->alpha_fixed <= 1.0))
+    return "alpha_fixed must be in [0,1]";
+  if (d->source != 0 && !(d->source == 1 && d->equation == CR_EQ_TENMOMENT))
+    return "source 1 needs the ten-moment equations";
+  if (d->limiter < 0 || d->limiter > 31) return "unknown limiter bits";
+  return nullptr;
+}
+
+}  // namespace
+
+struct cr_ctx {
+  cr_mesh_desc d;
+  const KernelSet* ks = nullptr;
+  KParams<double> pd;
+  KParams<float> pf;
+  const void* params = nullptr;
+  Layout L;
+  unsigned char* ws = nullptr;
+  bool owns_ws = false;
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;
+  cudaGraphExec_t g1 = nullptr, g8 = nullptr;
+  bool graphs_tried = false;
+  TimeCtl* h_ctl = nullptr;  // pinned mirror
+  TimeCtl* d_ctl = nullptr;
+  double cfl = 0.0;
+  std::string err;
+};
+
+namespace {
+
+cr_status fail(cr_ctx* c, cr_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_init_error = msg;
+  return st;
+}
+
+cr_status cuda_fail(cr_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, CR_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CR_CUDA(c, call)                                    \
+  do {                                                      \
+    cudaError_t _e = (call);                                \
+    if (_e != cudaSuccess) return cuda_fail((c), _e, #call); \
+  } while (0)
+
+template <typename real>
+void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
+  const cr_mesh_desc& d = c->d;
+  Mesh& m = P->m;
+  memset(&m, 0, sizeof(m));
+  m.nx = d.nx;
+  m.ny = d.dim == 2 ? d.ny : 1;
+  m.ne = m.nx * m.ny;
+  m.nfx = d.bc_x == CR_BC_PERIODIC ? m.nx : m.nx + 1;
+  m.nfy = d.dim == 2 ? (d.bc_y == CR_BC_PERIODIC ? m.ny : m.ny + 1) : 0;
+  m.bcx = d.bc_x;
+  m.bcy = d.dim == 2 ? d.bc_y : 0;
+  m.x0 = d.x0;
+  m.y0 = d.dim == 2 ? d.y0 : 0.0;
+  m.dx = (d.x1 - d.x0) / d.nx;
+  m.dy = d.dim == 2 ? (d.y1 - d.y0) / d.ny : 1.0;
+  m.invdx = 1.0 / m.dx;
+  m.invdy = d.dim == 2 ? 1.0 / m.dy : 0.0;
+  m.limiter = d.limiter;
+  m.alpha_mode = d.alpha_mode;
+  m.alpha_fixed = d.alpha_fixed;
+  m.gamma = d.gamma;
+  m.ax = d.adv[0];
+  m.ay = d.adv[1];
+  m.source = d.source;
+  m.src_amp = d.src_amp;
+  m.src_k = d.src_k;
+  m.src_cx = d.src_cx;
+  m.src_cy = d.src_cy;
+  // indicator constants (Hennemann et al. form): T(N) = 0.5 10^(-1.8 (N+1)^(1/4)),
+  // s = ln((1 - 1e-4)/1e-4)
+  m.T_ind = 0.5 * std::pow(10.0, -1.8 * std::pow(d.degree + 1.0, 0.25));
+  m.s_ind = std::log((1.0 - 1e-4) / 1e-4);
+  fill_tab(h, &P->tb);
+  fill_tab(h, &P->td);
+  Bufs<real>& b = P->b;
+  unsigned char* w = c->ws;
+  b.ctl = reinterpret_cast<TimeCtl*>(w + c->L.ctl);
+  b.u = reinterpret_cast<real*>(w + c->L.u);
+  b.umean = reinterpret_cast<double*>(w + c->L.umean);
+  b.P = reinterpret_cast<real*>(w + c->L.P);
+  b.smean = reinterpret_cast<double*>(w + c->L.smean);
+  b.slot = reinterpret_cast<real*>(w + c->L.slot);
+  b.fx = reinterpret_cast<real*>(w + c->L.fx);
+  b.fy = reinterpret_cast<real*>(w + c->L.fy);
+  b.alpha_raw = reinterpret_cast<double*>(w + c->L.alpha_raw);
+  b.alpha = reinterpret_cast<double*>(w + c->L.alpha);
+}
+
+cr_status read_ctl(cr_ctx* c) {
+  CR_CUDA(c, cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(TimeCtl), cudaMemcpyDeviceToHost, c->stream));
+  CR_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CR_OK;
+}
+
+cr_status build_graphs(cr_ctx* c) {
+  c->graphs_tried = true;
+  for (int which = 0; which < 2; ++which) {
+    const int nsteps = which == 0 ? 1 : 8;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return CR_OK;  // launch directly instead
+    }
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < nsteps && e == cudaSuccess; ++s) e = c->ks->step(c->params, c->stream);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return CR_OK;
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return CR_OK;
+    }
+    (which == 0 ? c->g1 : c->g8) = ex;
+  }
+  return CR_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+cr_status cr_cfl_number(int degree, double* cfl) {
+  if (degree < 1 || degree > kMaxN || !cfl) return CR_E_INVALID_ARG;
+  *cfl = cfl_compute(degree);
+  return CR_OK;
+}
+
+cr_status cr_reference_tables(int degree, double* xi, double* w, double* D) {
+  if (degree < 1 || degree > kMaxN) return CR_E_INVALID_ARG;
+  HostTables h;
+  build_tables(degree, &h);
+  const int n = degree + 1;
+  for (int i = 0; i < n; ++i) {
+    if (xi) xi[i] = h.xi[i];
+    if (w) w[i] = h.w[i];
+  }
+  if (D) memcpy(D, h.D, sizeof(double) * n * n);
+  return CR_OK;
+}
+
+cr_status cr_workspace_bytes(const cr_mesh_desc* desc, size_t* bytes) {
+  if (!bytes) return fail(nullptr, CR_E_INVALID_ARG, "bytes is NULL");
+  if (const char* why = check_desc(desc)) return fail(nullptr, CR_E_INVALID_ARG, why);
+  *bytes = layout_of(desc).total;
+  return CR_OK;
+}
+
+cr_status cr_init_mesh(const cr_mesh_desc* desc, void* workspace, size_t workspace_bytes,
+                       cr_ctx** out) {
+  if (!out) return fail(nullptr, CR_E_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (const char* why = check_desc(desc)) return fail(nullptr, CR_E_INVALID_ARG, why);
+  const KernelSet* ks = lookup(desc);
+  if (!ks) return fail(nullptr, CR_E_UNSUPPORTED, "this equation/dimension/degree/precision is not built");
+  cr_ctx* c = new (std::nothrow) cr_ctx();
+  if (!c) return fail(nullptr, CR_E_NOMEM, "host allocation failed");
+  c->d = *desc;
+  c->ks = ks;
+  c->L = layout_of(desc);
+  auto bail = [&](cr_status st) {
+    g_init_error = c->err;
+    cr_destroy(c);
+    return st;
+  };
+  if (workspace) {
+    if (workspace_bytes < c->L.total || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+      return bail(fail(c, CR_E_INVALID_ARG, "workspace too small or not 256-byte aligned"));
+    c->ws = static_cast<unsigned char*>(workspace);
+  } else {
+    cudaError_t e = cudaMalloc(&c->ws, c->L.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return bail(fail(c, CR_E_NOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e)));
+    }
+    c->owns_ws = true;
+  }
+  if (desc->stream) {
+    c->stream = static_cast<cudaStream_t>(desc->stream);
+  } else {
+    cudaError_t e = cudaStreamCreate(&c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamCreate"));
+    c->owns_stream = true;
+  }
+  cudaError_t e = cudaMallocHost(&c->h_ctl, sizeof(TimeCtl));
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMallocHost"));
+  e = ks->configure();
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaFuncSetAttribute"));
+  c->cfl = desc->cfl > 0.0 ? desc->cfl : cfl_compute(desc->degree);
+  if (!(c->d.cfl_safety > 0.0)) c->d.cfl_safety = 0.98;
+  HostTables h;
+  build_tables(desc->degree, &h);
+  if (ks->mixed) {
+    fill_params(c, &c->pf, h);
+    c->params = &c->pf;
+    c->d_ctl = c->pf.b.ctl;
+  } else {
+    fill_params(c, &c->pd, h);
+    c->params = &c->pd;
+    c->d_ctl = c->pd.b.ctl;
+  }
+  k_reset_ctl<<<1, 1, 0, c->stream>>>(c->d_ctl, c->d.cfl_safety * c->cfl);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "k_reset_ctl"));
+  *out = c;
+  return CR_OK;
+}
+
+void cr_destroy(cr_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->g1) cudaGraphExecDestroy(c->g1);
+  if (c->g8) cudaGraphExecDestroy(c->g8);
+  if (c->owns_ws && c->ws) cudaFree(c->ws);
+  if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+cr_status cr_set_state(cr_ctx* c, const double* u, int on_device) {
+  if (!c || !u) return fail(c, CR_E_INVALID_ARG, "NULL argument");
+  const size_t nvals = (size_t)c->ks->nvars * c->d.nx * (c->d.dim == 2 ? c->d.ny : 1) * c->ks->nodes;
+  if (!on_device)
+    for (size_t i = 0; i < nvals; ++i)
+      if (!std::isfinite(u[i])) return fail(c, CR_E_INVALID_STATE, "state holds a non-finite value");
+  k_reset_ctl<<<1, 1, 0, c->stream>>>(c->d_ctl, c->d.cfl_safety * c->cfl);
+  CR_CUDA(c, cudaGetLastError());
+  const double* src = u;
+  if (c->ks->mixed) {
+    double* staging = reinterpret_cast<double*>(c->ws + c->L.staging);
+    CR_CUDA(c, cudaMemcpyAsync(staging, u, nvals * sizeof(double), cudaMemcpyDefault, c->stream));
+    src = staging;
+  }
+  CR_CUDA(c, c->ks->split(c->params, src, c->stream));
+  CR_CUDA(c, c->ks->prologue(c->params, c->stream));
+  cr_status st = read_ctl(c);
+  if (st != CR_OK) return st;
+  if (c->h_ctl->status & kStInvalidInput)
+    return fail(c, CR_E_INVALID_STATE,
+                "inadmissible or non-finite input at element " + std::to_string(c->h_ctl->bad_elem));
+  return CR_OK;
+}
+
+cr_status cr_get_state(cr_ctx* c, double* u, int on_device) {
+  if (!c || !u) return fail(c, CR_E_INVALID_ARG, "NULL argument");
+  const size_t nvals = (size_t)c->ks->nvars * c->d.nx * (c->d.dim == 2 ? c->d.ny : 1) * c->ks->nodes;
+  if (c->ks->mixed && !on_device) {
+    double* staging = reinterpret_cast<double*>(c->ws + c->L.staging);
+    CR_CUDA(c, c->ks->join(c->params, staging, c->stream));
+    CR_CUDA(c, cudaMemcpyAsync(u, staging, nvals * sizeof(double), cudaMemcpyDefault, c->stream));
+  } else {
+    CR_CUDA(c, c->ks->join(c->params, u, c->stream));
+  }
+  if (!on_device) CR_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CR_OK;
+}
+
+cr_status cr_step_async(cr_ctx* c, int max_steps, double t_final, double dt_fixed) {
+  if (!c) return fail(c, CR_E_INVALID_ARG, "NULL context");
+  if (max_steps < 0 || !(t_final == t_final)) return fail(c, CR_E_INVALID_ARG, "bad max_steps or t_final");
+  if (!c->graphs_tried) {
+    cr_status st = build_graphs(c);
+    if (st != CR_OK) return st;
+  }
+  k_set_run<<<1, 1, 0, c->stream>>>(c->d_ctl, t_final, dt_fixed);
+  CR_CUDA(c, cudaGetLastError());
+  int left = max_steps;
+  while (left > 0) {
+    if (left >= 8 && c->g8) {
+      CR_CUDA(c, cudaGraphLaunch(c->g8, c->stream));
+      left -= 8;
+    } else if (c->g1) {
+      CR_CUDA(c, cudaGraphLaunch(c->g1, c->stream));
+      left -= 1;
+    } else {
+      CR_CUDA(c, c->ks->step(c->params, c->stream));
+      left -= 1;
+    }
+  }
+  return CR_OK;
+}
+
+cr_status cr_profile_steps(cr_ctx* c, int max_steps, double t_final, double dt_fixed,
+                           double* kernel_ms) {
+  if (!c || !kernel_ms || max_steps < 0) return fail(c, CR_E_INVALID_ARG, "bad argument");
+  const int nk = c->ks->launches_per_step;
+  cudaEvent_t ev[4];
+  for (int i = 0; i <= nk; ++i) CR_CUDA(c, cudaEventCreate(&ev[i]));
+  k_set_run<<<1, 1, 0, c->stream>>>(c->d_ctl, t_final, dt_fixed);
+  CR_CUDA(c, cudaGetLastError());
+  cr_status st = CR_OK;
+  for (int s = 0; s < max_steps && st == CR_OK; ++s) {
+    for (int i = 0; i < nk; ++i) {
+      CR_CUDA(c, cudaEventRecord(ev[i], c->stream));
+      CR_CUDA(c, c->ks->launch[i](c->params, c->stream));
+    }
+    CR_CUDA(c, cudaEventRecord(ev[nk], c->stream));
+    CR_CUDA(c, cudaEventSynchronize(ev[nk]));
+    for (int i = 0; i < nk; ++i) {
+      float ms = 0.0f;
+      CR_CUDA(c, cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+      kernel_ms[i] += ms;
+    }
+  }
+  for (int i = 0; i <= nk; ++i) cudaEventDestroy(ev[i]);
+  return st;
+}
+
+cr_status cr_sync(cr_ctx* c, double* t_out, int* steps_out) {
+  if (!c) return fail(c, CR_E_INVALID_ARG, "NULL context");
+  cr_status st = read_ctl(c);
+  if (st != CR_OK) return st;
+  if (t_out) *t_out = c->h_ctl->t;
+  if (steps_out) *steps_out = c->h_ctl->steps;
+  if (c->h_ctl->status & (kStInadmissible | kStNonFinite))
+    return fail(c, CR_E_INADMISSIBLE,
+                "inadmissible or non-finite state after a step, element " +
+                    std::to_string(c->h_ctl->bad_elem));
+  return CR_OK;
+}
+
+cr_status cr_step(cr_ctx* c, int max_steps, double t_final, double dt_fixed, double* t_out,
+                  int* steps_out) {
+  cr_status st = cr_step_async(c, max_steps, t_final, dt_fixed);
+  if (st != CR_OK) return st;
+  return cr_sync(c, t_out, steps_out);
+}
+
+cr_status cr_get_alpha(cr_ctx* c, double* alpha, int on_device) {
+  if (!c || !alpha) return fail(c, CR_E_INVALID_ARG, "NULL argument");
+  const size_t ne = (size_t)c->d.nx * (c->d.dim == 2 ? c->d.ny : 1);
+  CR_CUDA(c, cudaMemcpyAsync(alpha, c->ws + c->L.alpha, ne * sizeof(double), cudaMemcpyDefault,
+                             c->stream));
+  if (!on_device) CR_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CR_OK;
+}
+
+cr_status cr_next_dt(cr_ctx* c, double* dt) {
+  if (!c || !dt) return fail(c, CR_E_INVALID_ARG, "NULL argument");
+  cr_status st = read_ctl(c);
+  if (st != CR_OK) return st;
+  *dt = c->h_ctl->cfl_factor / c->h_ctl->rate_last;
+  return CR_OK;
+}
+
+cr_status cr_launches_per_step(cr_ctx* c, int* launches) {
+  if (!c || !launches) return CR_E_INVALID_ARG;
+  *launches = c->ks->launches_per_step;
+  return CR_OK;
+}
+
+const char* cr_last_error(const cr_ctx* c) {
+  return c ? c->err.c_str() : g_init_error.c_str();
+}
+
+}  // extern "C"

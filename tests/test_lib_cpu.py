@@ -1,0 +1,61 @@
+"""CPU checks of the CUDA library: it loads without a GPU, exports every symbol
+include/cr.h declares, and its host-only routines (no device work) agree with
+the oracle's independently written ones."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2502_07517_gb300 import build as lib_build
+from paper_2502_07517_gb300 import crkfr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    lib_build.build()
+    return crkfr.lib()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "cr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cr_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(built):
+    syms = declared_symbols()
+    assert len(syms) >= 14
+    for s in syms:
+        assert hasattr(built, s), s
+    assert set(syms) == set(crkfr.SYMBOLS)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_library_cfl_matches_oracle(built, N):
+    from oracle.cfl import cfl_number
+    assert abs(crkfr.cr_cfl_number(N) - cfl_number(N)) < 1e-6
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_library_tables_match_numpy(built, N):
+    xi, w, D = crkfr.cr_reference_tables(N)
+    x, ww = np.polynomial.legendre.leggauss(N + 1)
+    np.testing.assert_allclose(xi, 0.5 * (x + 1), atol=1e-15)
+    np.testing.assert_allclose(w, 0.5 * ww, atol=1e-15)
+    for m in range(N + 1):
+        np.testing.assert_allclose(D @ xi ** m, m * xi ** max(m - 1, 0) * (m > 0), atol=1e-12)
+
+
+def test_invalid_descriptor_rejected(built):
+    from paper_2502_07517_gb300 import workloads as wl
+    prob, _ = wl.linadv_sine(nx=8, degree=3)
+    d = crkfr.desc_from_problem(prob)
+    d.degree = 7
+    with pytest.raises(crkfr.CrError) as ei:
+        crkfr.cr_workspace_bytes(d)
+    assert ei.value.status == -1
+    d.degree = 3
+    assert crkfr.cr_workspace_bytes(d) > 0
