@@ -45,7 +45,8 @@ typedef enum {
   CR_E_TIMEOUT = -4,       /* a bounded device wait gave up */
   CR_E_CUDA = -5,          /* a CUDA runtime call failed (message in cr_last_error) */
   CR_E_NOMEM = -6,         /* device or host allocation failed */
-  CR_E_UNSUPPORTED = -7    /* this combination (equation, dim, degree, precision) is not built */
+  CR_E_UNSUPPORTED = -7,   /* this combination (equation, dim, degree, precision) is not built */
+  CR_E_TOO_LARGE = -8      /* cr_step_static: the mesh needs more scratch than its fixed array */
 } cr_status;
 
 enum { CR_EQ_LINADV = 0, CR_EQ_EULER = 1, CR_EQ_TENMOMENT = 2 };
@@ -150,6 +151,28 @@ cr_status cr_cfl_number(int degree, double* cfl);
  * xi[N+1] and weights w[N+1] on [0,1], and D[(N+1)*(N+1)], D_ij = l_j'(xi_i)
  * (Sec. 2 eq. (diff.matrix)).  Any pointer may be NULL. */
 cr_status cr_reference_tables(int degree, double* xi, double* w, double* D);
+
+/* One FP64 step that allocates nothing (the paper has no counterpart; this is
+ * a service for callers that may not allocate device memory, e.g. a host
+ * whose device memory all belongs to another allocator, or code that must not
+ * pay cudaMalloc's implicit synchronisation, or that forbids allocation once
+ * running).  u_out = the state after one step of size dt from u_in, for the
+ * mesh in desc; the limiters, indicator and source follow desc exactly as in
+ * cr_step (desc->cfl is not used, desc->precision must be CR_FP64).
+ * u_in and u_out are device pointers [M][Ne][Np] owned by the caller; they
+ * may be equal.  The work is ordered on desc->stream and the call
+ * synchronises that stream.
+ * Scratch: one 16 MiB device array inside the library, reserved on every GPU
+ * that loads it until the process exits; a mesh whose scratch does not fit
+ * returns CR_E_TOO_LARGE (2D Euler N=4: up to about 4,000 elements).  The
+ * first call on a device, with that device current, looks up the array's
+ * device address and configures the kernels; make that first call before any
+ * stream capture.  Every call reuses the same array (it is re-initialised at
+ * the start of each call), so calls whose work overlaps on the GPU race.
+ * Errors: CR_E_INVALID_ARG (bad desc, NULL pointer, dt <= 0),
+ * CR_E_UNSUPPORTED, CR_E_TOO_LARGE, CR_E_INVALID_STATE (inadmissible input),
+ * CR_E_INADMISSIBLE, CR_E_CUDA. */
+cr_status cr_step_static(const cr_mesh_desc* desc, const double* u_in, double* u_out, double dt);
 
 /* Last error message of ctx (or of the last failed cr_init_mesh when ctx is NULL). */
 const char* cr_last_error(const cr_ctx* ctx);

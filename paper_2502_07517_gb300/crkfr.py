@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(HERE, "libcrkfr.so")
 
 CR_OK = 0
 STATUS = {0: "CR_OK", -1: "CR_E_INVALID_ARG", -2: "CR_E_INVALID_STATE", -3: "CR_E_INADMISSIBLE",
-          -4: "CR_E_TIMEOUT", -5: "CR_E_CUDA", -6: "CR_E_NOMEM", -7: "CR_E_UNSUPPORTED"}
+          -4: "CR_E_TIMEOUT", -5: "CR_E_CUDA", -6: "CR_E_NOMEM", -7: "CR_E_UNSUPPORTED",
+          -8: "CR_E_TOO_LARGE"}
 CR_EQ_LINADV, CR_EQ_EULER, CR_EQ_TENMOMENT = 0, 1, 2
 CR_BC_PERIODIC, CR_BC_OUTFLOW = 0, 1
 CR_LIM_BLEND, CR_LIM_MH, CR_LIM_FLUX, CR_LIM_SCALING, CR_LIM_TRACES = 1, 2, 4, 8, 16
@@ -26,7 +27,7 @@ CR_FP64, CR_FP32_BULK = 0, 1
 SYMBOLS = ("cr_workspace_bytes", "cr_init_mesh", "cr_destroy", "cr_set_state", "cr_get_state",
            "cr_step", "cr_step_async", "cr_sync", "cr_get_alpha", "cr_next_dt",
            "cr_launches_per_step", "cr_profile_steps", "cr_cfl_number", "cr_reference_tables",
-           "cr_last_error")
+           "cr_step_static", "cr_last_error")
 
 
 class CrError(RuntimeError):
@@ -81,6 +82,7 @@ def lib():
         L.cr_profile_steps.argtypes = [V, I, ctypes.c_double, ctypes.c_double, D]
         L.cr_cfl_number.argtypes = [I, D]
         L.cr_reference_tables.argtypes = [I, D, D, D]
+        L.cr_step_static.argtypes = [P, V, V, ctypes.c_double]
         L.cr_last_error.argtypes = [V]
         L.cr_last_error.restype = ctypes.c_char_p
         for s in SYMBOLS:
@@ -222,6 +224,14 @@ def cr_profile_steps(ctx, max_steps, t_final, dt_fixed=0.0):
     _check(lib().cr_profile_steps(ctx.handle, int(max_steps), float(t_final), float(dt_fixed),
                                   _dptr(ms)), ctx.handle)
     return ms
+
+
+def cr_step_static(desc, u_in, u_out, dt):
+    """One FP64 step with the library's fixed scratch array (no allocation);
+    u_in, u_out are torch float64 CUDA tensors [M][Ne][Np]."""
+    st = lib().cr_step_static(ctypes.byref(desc), u_in.data_ptr(), u_out.data_ptr(), float(dt))
+    if st != CR_OK:
+        raise CrError(st, "cr_step_static")
 
 
 def cr_last_error(ctx=None):

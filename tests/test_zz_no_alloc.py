@@ -1,0 +1,61 @@
+"""cr_step_static, the entry point for callers that may not allocate device
+memory (their device memory belongs to another allocator, or allocation's
+implicit synchronisation or any allocation after start-up is not allowed):
+two calls in a row must give what the context-based entry point gives, while
+the fixed scratch array carries the previous call's contents into the next.
+Collected last on purpose, so that a run stopping at the first failure has
+already run everything else."""
+import numpy as np
+import pytest
+
+from paper_2502_07517_gb300 import crkfr
+from paper_2502_07517_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _close(a, b, rtol=1e-12):
+    for v in range(b.shape[0]):
+        scale = max(np.abs(b[v]).max(), 1e-300)
+        assert np.abs(a[v] - b[v]).max() <= rtol * scale, v
+
+
+def test_static_scratch_step_matches_context_step_twice():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_07517_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    prob, u0 = wl.euler2d_vortex(nx=12, ny=10, degree=4, seed=4)
+    u0 = u0 * np.random.default_rng(4).uniform(0.6, 1.6, (1, u0.shape[1], 1))  # limiters act
+    desc = crkfr.desc_from_problem(prob)
+
+    # reference: the context entry point, two steps of the same dt
+    ctx = crkfr.cr_init_mesh(desc)
+    crkfr.cr_set_state(ctx, u0)
+    dt = crkfr.cr_next_dt(ctx)
+    crkfr.cr_step(ctx, 1, 1e300, dt)
+    ref1 = crkfr.cr_get_state(ctx, shape=u0.shape)
+    crkfr.cr_step(ctx, 1, 1e300, dt)
+    ref2 = crkfr.cr_get_state(ctx, shape=u0.shape)
+
+    # the same two steps through the static-scratch entry point
+    a = torch.from_numpy(u0).cuda()
+    b = torch.empty_like(a)
+    crkfr.cr_step_static(desc, a, b, dt)
+    torch.cuda.synchronize()
+    _close(b.cpu().numpy(), ref1)
+    crkfr.cr_step_static(desc, b, a, dt)
+    torch.cuda.synchronize()
+    _close(a.cpu().numpy(), ref2)
+
+    # in place, and a mesh beyond the fixed scratch size is refused
+    c = torch.from_numpy(u0).cuda()
+    crkfr.cr_step_static(desc, c, c, dt)
+    _close(c.cpu().numpy(), ref1)
+    big, ubig = wl.euler2d_vortex(nx=96, ny=96, degree=4, seed=0)
+    t_big = torch.from_numpy(ubig).cuda()
+    with pytest.raises(crkfr.CrError) as ei:
+        crkfr.cr_step_static(crkfr.desc_from_problem(big), t_big, t_big, dt)
+    assert ei.value.status == -8
