@@ -198,7 +198,7 @@ def run_ours(args):
     from paper_2502_07517_gb300 import crkfr
 
     mixed = args.mode == "fp32"
-    prob, u = make_workload(seed=rank)
+    prob, u = make_workload(seed=rank, nx=args.nx)
     M, ne, npn = u.shape
     nodes = ne * npn
     stream = torch.cuda.Stream()
@@ -247,6 +247,10 @@ def run_ours(args):
                 "step_tflops": sum(flops) * nodes / (ms_per_step * 1e-3) / 1e12}
 
     # ---- end to end through the public API with host buffers ----
+    if args.quick:
+        print(json.dumps({"quick": True, "mode": args.mode, "nx": args.nx, "ms_per_step": ms_per_step,
+                          "value": value, "roofline": roofline}))
+        return
     host_in = torch.from_numpy(u).pin_memory()
     host_out = torch.empty(u.shape, dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 5))
@@ -273,7 +277,8 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"], "elements": ne, "points_per_element": npn,
+        "config": {"workload": WORKLOAD["name"] if args.nx == WORKLOAD["nx"] else
+                   "euler2d_vortex_%dx%d_N4" % (args.nx, args.nx), "elements": ne, "points_per_element": npn,
                    "variables": M, "mode": args.mode,
                    "limiters": "blend+MUSCL-Hancock+flux+scaling",
                    "l2": "inputs larger than L2 (state %.0f MB)" % (u.size * (4 if mixed else 8) / 1e6),
@@ -294,6 +299,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--mode", choices=("fp64", "fp32"), default="fp64")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--nx", type=int, default=WORKLOAD["nx"],
+                    help="elements per direction (smaller meshes of the same recipe for profiling)")
+    ap.add_argument("--quick", action="store_true",
+                    help="device timing only (no CPU baseline, no end-to-end leg)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

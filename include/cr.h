@@ -129,6 +129,12 @@ cr_status cr_sync(cr_ctx* ctx, double* t_out, int* steps_out);
  * FP64.  Synchronises when on_device == 0. */
 cr_status cr_get_alpha(cr_ctx* ctx, double* alpha, int on_device);
 
+/* Element means u_bar_e = sum_k W_k u_{e,k} (Sec. 3.2 eq. (upmean)), FP64
+ * [M][Ne].  In CR_FP32_BULK mode these are the FP64 means the scheme updates
+ * conservatively; totals sum_e u_bar_e dx dy are conserved to FP64 round-off
+ * on periodic meshes without source.  Synchronises when on_device == 0. */
+cr_status cr_get_means(cr_ctx* ctx, double* means, int on_device);
+
 /* Time step the next cr_step would take without t_final clipping. Synchronises. */
 cr_status cr_next_dt(cr_ctx* ctx, double* dt);
 

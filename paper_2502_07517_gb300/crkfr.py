@@ -25,7 +25,7 @@ CR_FP64, CR_FP32_BULK = 0, 1
 
 # C symbols declared in include/cr.h
 SYMBOLS = ("cr_workspace_bytes", "cr_init_mesh", "cr_destroy", "cr_set_state", "cr_get_state",
-           "cr_step", "cr_step_async", "cr_sync", "cr_get_alpha", "cr_next_dt",
+           "cr_step", "cr_step_async", "cr_sync", "cr_get_alpha", "cr_get_means", "cr_next_dt",
            "cr_launches_per_step", "cr_profile_steps", "cr_cfl_number", "cr_reference_tables",
            "cr_step_static", "cr_last_error")
 
@@ -77,6 +77,7 @@ def lib():
         L.cr_step_async.argtypes = [V, I, ctypes.c_double, ctypes.c_double]
         L.cr_sync.argtypes = [V, D, ctypes.POINTER(I)]
         L.cr_get_alpha.argtypes = [V, V, I]
+        L.cr_get_means.argtypes = [V, V, I]
         L.cr_next_dt.argtypes = [V, D]
         L.cr_launches_per_step.argtypes = [V, ctypes.POINTER(I)]
         L.cr_profile_steps.argtypes = [V, I, ctypes.c_double, ctypes.c_double, D]
@@ -202,6 +203,13 @@ def cr_sync(ctx):
 def cr_get_alpha(ctx, ne):
     out = np.empty(ne, dtype=np.float64)
     _check(lib().cr_get_alpha(ctx.handle, out.ctypes.data, 0), ctx.handle)
+    return out
+
+
+def cr_get_means(ctx, M, ne):
+    """FP64 element means [M][Ne] (the conserved quantities)."""
+    out = np.empty((M, ne), dtype=np.float64)
+    _check(lib().cr_get_means(ctx.handle, out.ctypes.data, 0), ctx.handle)
     return out
 
 

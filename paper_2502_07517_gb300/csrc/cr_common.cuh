@@ -74,6 +74,8 @@ struct Mesh {
   int source;
   double src_amp, src_k, src_cx, src_cy;
   double T_ind, s_ind;       // indicator threshold T(N) and sharpness s
+  double cflim[4];           // 1/(kappa w h) of the flux-limiter candidates on face sides
+                             // 0..3 (x-left: w_0 dx, x-right: w_N dx, y-bottom, y-top)
 };
 
 enum : int { kLimBlend = 1, kLimMH = 2, kLimFlux = 4, kLimScaling = 8, kLimTraces = 16 };
@@ -83,6 +85,7 @@ template <typename real>
 struct Bufs {
   real* u;           // state [M][Ne][Np] (FP32_BULK: fluctuation about the mean)
   double* umean;     // FP32_BULK: element means [M][Ne] (FP64)
+  float* umean_f;    // FP32_BULK: the same means rounded to FP32 (read by the FP32 kernels)
   real* P;           // partial update [M][Ne][Np] (everything but the element-face fluxes)
   double* smean;     // FP32_BULK: sum_k W_k S_k per element [M][Ne] (FP64)
   real* slot;        // per element face-node data [4M+1][nside][Ne][nfn]
@@ -93,9 +96,18 @@ struct Bufs {
   TimeCtl* ctl;
 };
 
+// Physical constants in the arithmetic type of the kernel (no FP64 work leaks
+// into FP32 arithmetic through double constants).
+template <typename real>
+struct Phys {
+  real gamma, gm1, ax, ay;
+};
+
 template <typename real>
 struct KParams {
   Mesh m;
+  Phys<real> ph;     // constants in the bulk type
+  Phys<double> phd;  // FP64 constants (limiters, means)
   Tab<real> tb;      // tables in the bulk type
   Tab<double> td;    // FP64 tables (limiters, means)
   Bufs<real> b;
@@ -147,79 +159,143 @@ template <> struct Tableau<4> {
 
 // ---------------------------------------------------------------------------
 // Equation functors.  dir = 0 (x) or 1 (y); calls with a literal dir fold.
+//   flux(u, dir, f)            physical flux in direction dir
+//   flux_xy(u, f, g)           both directions, one reciprocal of rho
+//   flux_speed(u, dir, f, s)   flux and spectral radius, one reciprocal
+//   speed(u, dir)              spectral radius sigma of the flux Jacobian
+//   constraint(u, k)           admissibility constraint P_k (Sec. 2 eq. (uad.form))
+//   admissible_fast(u)         all P_k > 0, tested without division (multiplied by rho > 0)
+//   indicator_var(u)           variable the smoothness indicator looks at
 template <typename real>
 __device__ __forceinline__ real sqrt_pos(real x) { return sqrt(x > real(0) ? x : real(0)); }
 
 struct EqLinAdv {  // u_t + a . grad u = 0, Sec. 5.1.1
   static constexpr int M = 1, K = 0;
   template <typename real>
-  __device__ static void flux(const real* u, int dir, real* f, const Mesh& m) {
-    f[0] = real(dir == 0 ? m.ax : m.ay) * u[0];
+  __device__ static void flux(const real* u, int dir, real* f, const Phys<real>& ph) {
+    f[0] = (dir == 0 ? ph.ax : ph.ay) * u[0];
   }
   template <typename real>
-  __device__ static real speed(const real* u, int dir, const Mesh& m) {
-    return real(fabs(dir == 0 ? m.ax : m.ay));
+  __device__ static void flux_xy(const real* u, real* f, real* g, const Phys<real>& ph) {
+    f[0] = ph.ax * u[0];
+    g[0] = ph.ay * u[0];
   }
   template <typename real>
-  __device__ static real constraint(const real*, int, const Mesh&) { return real(1); }
+  __device__ static real speed(const real*, int dir, const Phys<real>& ph) {
+    return fabs(dir == 0 ? ph.ax : ph.ay);
+  }
   template <typename real>
-  __device__ static real indicator_var(const real* u, const Mesh&) { return u[0]; }
+  __device__ static void flux_speed(const real* u, int dir, real* f, real* s, const Phys<real>& ph) {
+    flux(u, dir, f, ph);
+    *s = speed(u, dir, ph);
+  }
+  template <typename real>
+  __device__ static real constraint(const real*, int, const Phys<real>&) { return real(1); }
+  template <typename real>
+  __device__ static bool admissible_fast(const real*, const Phys<real>&) { return true; }
+  template <typename real>
+  __device__ static real indicator_var(const real* u, const Phys<real>&) { return u[0]; }
 };
 
 // Euler, Sec. 5.2 eq. (1deuler) (DIM 1, u = rho, rho v, E) and Sec. 5.3
-// eq. (2deuler) (DIM 2, u = rho, rho v1, rho v2, E); p from eqs. (state), (2dstate).
+// eq. (2deuler) (DIM 2, u = rho, rho v1, rho v2, E); p from eqs. (state), (2dstate);
+// sigma = |v_dir| + c, c = sqrt(gamma p / rho) (eq. (spectral.radius.1d)).
 template <int DIM>
 struct EqEuler {
   static constexpr int M = DIM == 1 ? 3 : 4, K = 2;
+  static constexpr int E = DIM == 1 ? 2 : 3;
   template <typename real>
-  __device__ static real pressure(const real* u, const Mesh& m) {
-    real g1 = real(m.gamma - 1.0);
-    if (DIM == 1) return g1 * (u[2] - real(0.5) * u[1] * u[1] / u[0]);
-    return g1 * (u[3] - real(0.5) * (u[1] * u[1] + u[2] * u[2]) / u[0]);
+  __device__ static real kinetic_rho(const real* u) {  // rho |v|^2 / 2 * rho = |m|^2 / 2
+    return DIM == 1 ? real(0.5) * u[1] * u[1] : real(0.5) * (u[1] * u[1] + u[2] * u[2]);
   }
   template <typename real>
-  __device__ static void flux(const real* u, int dir, real* f, const Mesh& m) {
-    real rinv = real(1) / u[0];
+  __device__ static real pressure(const real* u, const Phys<real>& ph) {
+    return ph.gm1 * (u[E] - kinetic_rho(u) / u[0]);
+  }
+  template <typename real>
+  __device__ static void flux_r(const real* u, int dir, real rinv, real* f, real* p_out,
+                                const Phys<real>& ph) {
     if (DIM == 1) {
-      real v = u[1] * rinv;
-      real p = real(m.gamma - 1.0) * (u[2] - real(0.5) * u[1] * v);
+      const real v = u[1] * rinv;
+      const real p = ph.gm1 * (u[2] - real(0.5) * u[1] * v);
       f[0] = u[1];
       f[1] = u[1] * v + p;
       f[2] = (u[2] + p) * v;
+      *p_out = p;
       return;
     }
-    real v1 = u[1] * rinv, v2 = u[2] * rinv;
-    real p = real(m.gamma - 1.0) * (u[3] - real(0.5) * (u[1] * v1 + u[2] * v2));
-    real vn = dir == 0 ? v1 : v2;
+    const real v1 = u[1] * rinv, v2 = u[2] * rinv;
+    const real p = ph.gm1 * (u[3] - real(0.5) * (u[1] * v1 + u[2] * v2));
+    const real vn = dir == 0 ? v1 : v2;
     f[0] = u[1 + dir];
     f[1] = u[1] * vn + (dir == 0 ? p : real(0));
     f[2] = u[2] * vn + (dir == 1 ? p : real(0));
     f[3] = (u[3] + p) * vn;
+    *p_out = p;
   }
   template <typename real>
-  __device__ static real speed(const real* u, int dir, const Mesh& m) {
-    real v = u[1 + dir] / u[0];
-    return fabs(v) + sqrt_pos(real(m.gamma) * pressure(u, m) / u[0]);
+  __device__ static void flux(const real* u, int dir, real* f, const Phys<real>& ph) {
+    real p;
+    flux_r(u, dir, real(1) / u[0], f, &p, ph);
   }
   template <typename real>
-  __device__ static real constraint(const real* u, int k, const Mesh& m) {
-    return k == 0 ? u[0] : pressure(u, m);
+  __device__ static void flux_xy(const real* u, real* f, real* g, const Phys<real>& ph) {
+    const real rinv = real(1) / u[0];
+    if (DIM == 1) {
+      real p;
+      flux_r(u, 0, rinv, f, &p, ph);
+      return;
+    }
+    const real v1 = u[1] * rinv, v2 = u[2] * rinv;
+    const real p = ph.gm1 * (u[3] - real(0.5) * (u[1] * v1 + u[2] * v2));
+    const real Ep = u[3] + p;
+    f[0] = u[1];
+    f[1] = u[1] * v1 + p;
+    f[2] = u[2] * v1;
+    f[3] = Ep * v1;
+    g[0] = u[2];
+    g[1] = u[1] * v2;
+    g[2] = u[2] * v2 + p;
+    g[3] = Ep * v2;
   }
   template <typename real>
-  __device__ static real indicator_var(const real* u, const Mesh& m) { return u[0] * pressure(u, m); }
+  __device__ static void flux_speed(const real* u, int dir, real* f, real* s, const Phys<real>& ph) {
+    const real rinv = real(1) / u[0];
+    real p;
+    flux_r(u, dir, rinv, f, &p, ph);
+    *s = fabs(u[1 + dir] * rinv) + sqrt_pos(ph.gamma * p * rinv);
+  }
+  template <typename real>
+  __device__ static real speed(const real* u, int dir, const Phys<real>& ph) {
+    const real rinv = real(1) / u[0];
+    const real p = ph.gm1 * (u[E] - kinetic_rho(u) * rinv);
+    return fabs(u[1 + dir] * rinv) + sqrt_pos(ph.gamma * p * rinv);
+  }
+  template <typename real>
+  __device__ static real constraint(const real* u, int k, const Phys<real>& ph) {
+    return k == 0 ? u[0] : pressure(u, ph);
+  }
+  template <typename real>
+  __device__ static bool admissible_fast(const real* u, const Phys<real>&) {
+    return u[0] > real(0) && u[E] * u[0] - kinetic_rho(u) > real(0);
+  }
+  template <typename real>
+  __device__ static real indicator_var(const real* u, const Phys<real>& ph) {
+    return u[0] * pressure(u, ph);
+  }
 };
 
 // Ten-moment equations, Sec. 5.4 eq. (tmp); u = (rho, rho v1, rho v2, E11, E12, E22),
-// P = 2E - rho v (x) v.  Admissibility: rho > 0 and lambda_min(P) > 0.
+// P = 2E - rho v (x) v.  Admissibility: rho > 0 and lambda_min(P) > 0; wave speed
+// |v_dir| + sqrt(3 p_dirdir / rho).
 struct EqTenMoment {
   static constexpr int M = 6, K = 2;
   template <typename real>
-  __device__ static void flux(const real* u, int dir, real* f, const Mesh&) {
-    real rinv = real(1) / u[0];
-    real v1 = u[1] * rinv, v2 = u[2] * rinv;
-    real p11 = real(2) * u[3] - u[1] * v1;
-    real p12 = real(2) * u[4] - u[1] * v2;
-    real p22 = real(2) * u[5] - u[2] * v2;
+  __device__ static void flux_r(const real* u, int dir, real rinv, real* f, const Phys<real>&) {
+    const real v1 = u[1] * rinv, v2 = u[2] * rinv;
+    const real p11 = real(2) * u[3] - u[1] * v1;
+    const real p12 = real(2) * u[4] - u[1] * v2;
+    const real p22 = real(2) * u[5] - u[2] * v2;
     if (dir == 0) {
       f[0] = u[1];
       f[1] = p11 + u[1] * v1;
@@ -237,27 +313,54 @@ struct EqTenMoment {
     }
   }
   template <typename real>
-  __device__ static real speed(const real* u, int dir, const Mesh&) {
-    real rinv = real(1) / u[0];
-    real v = u[1 + dir] * rinv;
-    real pdd = real(2) * u[3 + 2 * dir] - u[1 + dir] * v;
+  __device__ static void flux(const real* u, int dir, real* f, const Phys<real>& ph) {
+    flux_r(u, dir, real(1) / u[0], f, ph);
+  }
+  template <typename real>
+  __device__ static void flux_xy(const real* u, real* f, real* g, const Phys<real>& ph) {
+    const real rinv = real(1) / u[0];
+    flux_r(u, 0, rinv, f, ph);
+    flux_r(u, 1, rinv, g, ph);
+  }
+  template <typename real>
+  __device__ static real speed_r(const real* u, int dir, real rinv) {
+    const real v = u[1 + dir] * rinv;
+    const real pdd = real(2) * u[3 + 2 * dir] - u[1 + dir] * v;
     return fabs(v) + sqrt_pos(real(3) * pdd * rinv);
   }
   template <typename real>
-  __device__ static real constraint(const real* u, int k, const Mesh&) {
+  __device__ static void flux_speed(const real* u, int dir, real* f, real* s, const Phys<real>& ph) {
+    const real rinv = real(1) / u[0];
+    flux_r(u, dir, rinv, f, ph);
+    *s = speed_r(u, dir, rinv);
+  }
+  template <typename real>
+  __device__ static real speed(const real* u, int dir, const Phys<real>&) {
+    return speed_r(u, dir, real(1) / u[0]);
+  }
+  template <typename real>
+  __device__ static real constraint(const real* u, int k, const Phys<real>&) {
     if (k == 0) return u[0];
-    real rinv = real(1) / u[0];
-    real p11 = real(2) * u[3] - u[1] * u[1] * rinv;
-    real p12 = real(2) * u[4] - u[1] * u[2] * rinv;
-    real p22 = real(2) * u[5] - u[2] * u[2] * rinv;
-    real h = real(0.5) * (p11 - p22);
+    const real rinv = real(1) / u[0];
+    const real p11 = real(2) * u[3] - u[1] * u[1] * rinv;
+    const real p12 = real(2) * u[4] - u[1] * u[2] * rinv;
+    const real p22 = real(2) * u[5] - u[2] * u[2] * rinv;
+    const real h = real(0.5) * (p11 - p22);
     return real(0.5) * (p11 + p22) - sqrt(h * h + p12 * p12);
   }
   template <typename real>
-  __device__ static real indicator_var(const real* u, const Mesh&) {
-    real rinv = real(1) / u[0];
-    real p11 = real(2) * u[3] - u[1] * u[1] * rinv;
-    real p22 = real(2) * u[5] - u[2] * u[2] * rinv;
+  __device__ static bool admissible_fast(const real* u, const Phys<real>&) {
+    // rho P = 2 rho E - m m^T positive definite
+    const real a11 = real(2) * u[0] * u[3] - u[1] * u[1];
+    const real a22 = real(2) * u[0] * u[5] - u[2] * u[2];
+    const real a12 = real(2) * u[0] * u[4] - u[1] * u[2];
+    return u[0] > real(0) && a11 > real(0) && a11 * a22 - a12 * a12 > real(0);
+  }
+  template <typename real>
+  __device__ static real indicator_var(const real* u, const Phys<real>&) {
+    const real rinv = real(1) / u[0];
+    const real p11 = real(2) * u[3] - u[1] * u[1] * rinv;
+    const real p22 = real(2) * u[5] - u[2] * u[2] * rinv;
     return u[0] * real(0.5) * (p11 + p22);
   }
 };

@@ -268,7 +268,7 @@ __global__ void k_set_run(TimeCtl* c, double t_final, double dt_fixed) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t ctl, u, umean, P, smean, slot, fx, fy, alpha_raw, alpha, staging, total;
+  size_t ctl, u, umean, umean_f, P, smean, slot, fx, fy, alpha_raw, alpha, staging, total;
 };
 
 int nvars_of(const cr_mesh_desc* d) {
@@ -296,6 +296,7 @@ Layout layout_of(const cr_mesh_desc* d) {
   L.ctl = take(sizeof(TimeCtl));
   L.u = take(M * ne * np * rs);
   L.umean = take(mixed ? M * ne * sizeof(double) : 0);
+  L.umean_f = take(mixed ? M * ne * sizeof(float) : 0);
   L.P = take(M * ne * np * rs);
   L.smean = take(mixed ? M * ne * sizeof(double) : 0);
   L.slot = take((4 * M + 1) * nside * ne * nfn * rs);
@@ -412,6 +413,22 @@ void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
   // s = ln((1 - 1e-4)/1e-4)
   m.T_ind = 0.5 * std::pow(10.0, -1.8 * std::pow(d.degree + 1.0, 0.25));
   m.s_ind = std::log((1.0 - 1e-4) / 1e-4);
+  {
+    // flux-limiter candidates: u~ = u -+ dt/(kappa w h) (F - f_adj), kappa = 1 (1D), 1/2 (2D)
+    const double kappa = d.dim == 2 ? 0.5 : 1.0;
+    m.cflim[0] = 1.0 / (kappa * h.w[0] * m.dx);
+    m.cflim[1] = 1.0 / (kappa * h.w[d.degree] * m.dx);
+    m.cflim[2] = 1.0 / (kappa * h.w[0] * m.dy);
+    m.cflim[3] = 1.0 / (kappa * h.w[d.degree] * m.dy);
+  }
+  P->ph.gamma = real(d.gamma);
+  P->ph.gm1 = real(d.gamma - 1.0);
+  P->ph.ax = real(d.adv[0]);
+  P->ph.ay = real(d.adv[1]);
+  P->phd.gamma = d.gamma;
+  P->phd.gm1 = d.gamma - 1.0;
+  P->phd.ax = d.adv[0];
+  P->phd.ay = d.adv[1];
   fill_tab(h, &P->tb);
   fill_tab(h, &P->td);
   Bufs<real>& b = P->b;
@@ -419,6 +436,7 @@ void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
   b.ctl = reinterpret_cast<TimeCtl*>(w + c->L.ctl);
   b.u = reinterpret_cast<real*>(w + c->L.u);
   b.umean = reinterpret_cast<double*>(w + c->L.umean);
+  b.umean_f = reinterpret_cast<float*>(w + c->L.umean_f);
   b.P = reinterpret_cast<real*>(w + c->L.P);
   b.smean = reinterpret_cast<double*>(w + c->L.smean);
   b.slot = reinterpret_cast<real*>(w + c->L.slot);
@@ -680,6 +698,22 @@ cr_status cr_get_alpha(cr_ctx* c, double* alpha, int on_device) {
   CR_CUDA(c, cudaMemcpyAsync(alpha, c->ws + c->L.alpha, ne * sizeof(double), cudaMemcpyDefault,
                              c->stream));
   if (!on_device) CR_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CR_OK;
+}
+
+cr_status cr_get_means(cr_ctx* c, double* means, int on_device) {
+  if (!c || !means) return fail(c, CR_E_INVALID_ARG, "NULL argument");
+  const size_t ne = (size_t)c->d.nx * (c->d.dim == 2 ? c->d.ny : 1);
+  if (on_device) {
+    CR_CUDA(c, c->ks->means(c->params, means, c->stream));
+    return CR_OK;
+  }
+  double* staging = reinterpret_cast<double*>(c->ws + c->L.P);  // P is free between steps
+  if (c->ks->mixed) staging = reinterpret_cast<double*>(c->ws + c->L.staging);
+  CR_CUDA(c, c->ks->means(c->params, staging, c->stream));
+  CR_CUDA(c, cudaMemcpyAsync(means, staging, (size_t)c->ks->nvars * ne * sizeof(double),
+                             cudaMemcpyDeviceToHost, c->stream));
+  CR_CUDA(c, cudaStreamSynchronize(c->stream));
   return CR_OK;
 }
 

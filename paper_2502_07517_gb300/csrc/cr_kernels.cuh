@@ -29,29 +29,45 @@ __device__ __forceinline__ int neighbour(const Mesh& m, int e, int f) {
   return iy < m.ny - 1 ? e + m.nx : (m.bcy == 0 ? e - m.nx * (m.ny - 1) : -1);
 }
 
-template <typename real>
-__device__ __forceinline__ real minmod3(real a, real b, real c) {
-  if (a > real(0) && b > real(0) && c > real(0)) return fmin(a, fmin(b, c));
-  if (a < real(0) && b < real(0) && c < real(0)) return fmax(a, fmax(b, c));
-  return real(0);
+// minmod of three slopes: the one of smallest magnitude when all three share a
+// nonzero sign, else 0.
+__device__ __forceinline__ float minmod3(float a, float b, float c) {
+  if (a > 0.0f && b > 0.0f && c > 0.0f) return fminf(a, fminf(b, c));
+  if (a < 0.0f && b < 0.0f && c < 0.0f) return fmaxf(a, fmaxf(b, c));
+  return 0.0f;
+}
+// FP64 version on the bit patterns (integer pipe; the FP64 pipe is the scarce
+// unit): sign bits must agree and no magnitude may be zero; for finite numbers
+// of one sign the order of the magnitude bits is the order of the magnitudes.
+__device__ __forceinline__ double minmod3(double a, double b, double c) {
+  const unsigned long long ia = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long ib = (unsigned long long)__double_as_longlong(b);
+  const unsigned long long ic = (unsigned long long)__double_as_longlong(c);
+  const unsigned long long mag = 0x7fffffffffffffffull;
+  const unsigned long long ma = ia & mag, mb = ib & mag, mc = ic & mag;
+  if (((ia ^ ib) | (ia ^ ic)) >> 63 || ma == 0ull || mb == 0ull || mc == 0ull) return 0.0;
+  unsigned long long mm = ma < mb ? ma : mb;
+  mm = mm < mc ? mm : mc;
+  return __longlong_as_double((long long)(mm | (ia & ~mag)));
 }
 
+// All admissibility constraints P_k > 0, evaluated exactly (Sec. 2 eq. (uad.form)).
 template <class EQ, typename real>
-__device__ __forceinline__ bool admissible(const real* u, const Mesh& m) {
+__device__ __forceinline__ bool admissible(const real* u, const Phys<real>& ph) {
   bool ok = true;
 #pragma unroll
-  for (int k = 0; k < EQ::K; ++k) ok = ok && (EQ::constraint(u, k, m) > real(0));
+  for (int k = 0; k < EQ::K; ++k) ok = ok && (EQ::constraint(u, k, ph) > real(0));
   return ok;
 }
 
 // Rusanov flux, Sec. 2 eqs. (num.flux.fr), (rusanov.wave.speed).
 template <class EQ, typename real>
 __device__ __forceinline__ void rusanov(const real* uL, const real* uR, int dir, real* out,
-                                        const Mesh& m) {
-  real fL[EQ::M], fR[EQ::M];
-  EQ::flux(uL, dir, fL, m);
-  EQ::flux(uR, dir, fR, m);
-  real lam = fmax(EQ::speed(uL, dir, m), EQ::speed(uR, dir, m));
+                                        const Phys<real>& ph) {
+  real fL[EQ::M], fR[EQ::M], sL, sR;
+  EQ::flux_speed(uL, dir, fL, &sL, ph);
+  EQ::flux_speed(uR, dir, fR, &sR, ph);
+  const real lam = fmax(sL, sR);
 #pragma unroll
   for (int v = 0; v < EQ::M; ++v)
     out[v] = real(0.5) * (fL[v] + fR[v]) - real(0.5) * lam * (uR[v] - uL[v]);
@@ -63,7 +79,7 @@ template <typename real, bool MIXED>
 __device__ __forceinline__ real load_state(const Bufs<real>& b, int ne, int NP, int v, int e,
                                            int k) {
   const real x = b.u[((size_t)v * ne + e) * NP + k];
-  if constexpr (MIXED) return real(b.umean[(size_t)v * ne + e] + double(x));
+  if constexpr (MIXED) return b.umean_f[(size_t)v * ne + e] + x;
   return x;
 }
 
@@ -72,6 +88,38 @@ __device__ __forceinline__ size_t slot_index(int f, int side, int e, int j, int 
                                              int nfn) {
   return (((size_t)f * nside + side) * ne + e) * nfn + j;
 }
+
+// Per-element reductions over the element's threads (shared memory trees).
+// Tree reduction of W quantities per element; buf[(w * epb + el) * NP + k];
+// the result lands in buf[(w * epb + el) * NP].  Called by every thread.
+template <int NP, int W, typename T, class Op>
+__device__ __forceinline__ void elem_tree(T* buf, int epb, int el, int k, Op op) {
+  int s = NP;
+#pragma unroll
+  for (int lev = 0; lev < 6; ++lev) {
+    if (s <= 1) break;
+    const int h = (s + 1) >> 1;
+    __syncthreads();
+    if (k < s - h) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        T* b = buf + (w * epb + el) * NP;
+        b[k] = op(b[k], b[k + h]);
+      }
+    }
+    s = h;
+  }
+  __syncthreads();
+}
+
+struct OpSum {
+  template <typename T>
+  __device__ T operator()(T a, T b) const { return a + b; }
+};
+struct OpMin {
+  template <typename T>
+  __device__ T operator()(T a, T b) const { return fmin(a, b); }
+};
 
 // ===========================================================================
 template <int DIM, int N, class EQ, typename real, bool MIXED>
@@ -86,6 +134,7 @@ __global__ void k_local(const KParams<real> P) {
   constexpr int SPT = (NSLOT + NP - 1) / NP;
   using TB = Tableau<N>;
   const Mesh& m = P.m;
+  const Phys<real>& ph = P.ph;
   const Tab<real>& tb = P.tb;
   const int epb = blockDim.x / NP;
   const int tid = threadIdx.x;
@@ -176,8 +225,8 @@ __global__ void k_local(const KParams<real> P) {
       ui[v] = acc;
     }
     real f[M], g[M], s[M];
-    EQ::flux(ui, 0, f, m);
-    if (DIM == 2) EQ::flux(ui, 1, g, m);
+    if (DIM == 2) EQ::flux_xy(ui, f, g, ph);
+    else EQ::flux(ui, 0, f, ph);
     if (has_src) source_eval<EQ>(ui, dWx, dWy, s);
     else {
 #pragma unroll
@@ -231,7 +280,7 @@ __global__ void k_local(const KParams<real> P) {
             }
             ut[v] = acc;
           }
-          EQ::flux(ut, side >> 1, fn, m);
+          EQ::flux(ut, side >> 1, fn, ph);
 #pragma unroll
           for (int v = 0; v < M; ++v) ea[mm][v] += bi * fn[v];
         }
@@ -280,7 +329,7 @@ __global__ void k_local(const KParams<real> P) {
         ut[v] = a2;
       }
       real* sl_out = P.b.slot;
-      sl_out[slot_index(0, side, e, j, NSIDE, m.ne, NFN)] = EQ::speed(ut, side >> 1, m);
+      sl_out[slot_index(0, side, e, j, NSIDE, m.ne, NFN)] = EQ::speed(ut, side >> 1, ph);
 #pragma unroll
       for (int v = 0; v < M; ++v) {
         sl_out[slot_index(1 + v, side, e, j, NSIDE, m.ne, NFN)] = Ut[v];
@@ -335,11 +384,11 @@ __global__ void k_local(const KParams<real> P) {
         fym[v] = un[v] + sy[v] * tb.dm[q];
         fyp[v] = un[v] + sy[v] * tb.dp[q];
       }
-      EQ::flux(fxm, 0, Fm, m);
-      EQ::flux(fxp, 0, Fp, m);
+      EQ::flux(fxm, 0, Fm, ph);
+      EQ::flux(fxp, 0, Fp, ph);
       if (DIM == 2) {
-        EQ::flux(fym, 1, Gm, m);
-        EQ::flux(fyp, 1, Gp, m);
+        EQ::flux(fym, 1, Gm, ph);
+        EQ::flux(fyp, 1, Gp, ph);
       }
       real ex[M], exm[M], exp_[M], eym[M], eyp[M];
 #pragma unroll
@@ -351,11 +400,11 @@ __global__ void k_local(const KParams<real> P) {
         eym[v] = fym[v] - ex[v];
         eyp[v] = fyp[v] - ex[v];
       }
-      bool ok = admissible<EQ>(fxm, m) && admissible<EQ>(fxp, m) && admissible<EQ>(exm, m) &&
-                admissible<EQ>(exp_, m);
+      bool ok = EQ::admissible_fast(fxm, ph) && EQ::admissible_fast(fxp, ph) &&
+                EQ::admissible_fast(exm, ph) && EQ::admissible_fast(exp_, ph);
       if (DIM == 2)
-        ok = ok && admissible<EQ>(fym, m) && admissible<EQ>(fyp, m) && admissible<EQ>(eym, m) &&
-             admissible<EQ>(eyp, m);
+        ok = ok && EQ::admissible_fast(fym, ph) && EQ::admissible_fast(fyp, ph) &&
+             EQ::admissible_fast(eym, ph) && EQ::admissible_fast(eyp, ph);
       if (ok) {
 #pragma unroll
         for (int v = 0; v < M; ++v) {
@@ -385,7 +434,7 @@ __global__ void k_local(const KParams<real> P) {
         uL[v] = AT(sB, v, k);
         uR[v] = AT(sA, v, k + 1);
       }
-      rusanov<EQ>(uL, uR, 0, fr, m);
+      rusanov<EQ>(uL, uR, 0, fr, ph);
 #pragma unroll
       for (int v = 0; v < M; ++v) AT(sB, v, k) = fr[v];
     }
@@ -396,7 +445,7 @@ __global__ void k_local(const KParams<real> P) {
         uL[v] = AT(sD, v, k);
         uR[v] = AT(sC, v, k + n);
       }
-      rusanov<EQ>(uL, uR, 1, fr, m);
+      rusanov<EQ>(uL, uR, 1, fr, ph);
 #pragma unroll
       for (int v = 0; v < M; ++v) AT(sD, v, k) = fr[v];
     }
@@ -413,7 +462,6 @@ __global__ void k_local(const KParams<real> P) {
     }
     // face-node data for the face kernel: evolved boundary state u* and the
     // candidate base of the flux limiter, u_b -+ c f_adj
-    const double kappa = DIM == 2 ? 0.5 : 1.0;
 #pragma unroll
     for (int mm = 0; mm < SPT; ++mm) {
       const int sl = k + mm * NP;
@@ -426,8 +474,7 @@ __global__ void k_local(const KParams<real> P) {
         else if (side == 1) { nb_node = N + n * j; adj_node = N - 1 + n * j; ust = sB; adj = sB; }
         else if (side == 2) { nb_node = j; adj_node = j; ust = sC; adj = sD; }
         else { nb_node = j + n * N; adj_node = j + n * (N - 1); ust = sD; adj = sD; }
-        const double h = side < 2 ? m.dx : m.dy;
-        const double c = dtd / (kappa * P.td.w[(side & 1) ? N : 0] * h);
+        const double c = dtd * m.cflim[side];
         const double sgn = (side & 1) ? 1.0 : -1.0;
 #pragma unroll
         for (int v = 0; v < M; ++v) {
@@ -449,19 +496,17 @@ __global__ void k_local(const KParams<real> P) {
     }
   }
   if constexpr (MIXED) {
-    // FP64 source contribution to the element mean: sum_k W_k S_k
-    __syncthreads();
+    // source contribution to the FP64 element mean, sum_k W_k S_k (tree sum)
+    if (has_src) {
+      const real W = DIM == 2 ? tb.w[p] * tb.w[q] : tb.w[p];
+      __syncthreads();
 #pragma unroll
-    for (int v = 0; v < M; ++v) AT(sA, v, k) = Sa[v];
-    __syncthreads();
-    for (int v = k; valid && v < M; v += NP) {
-      double acc = 0.0;
-      for (int kk = 0; kk < NP; ++kk) {
-        const int pp = DIM == 2 ? kk % n : kk, qq = DIM == 2 ? kk / n : 0;
-        const double W = DIM == 2 ? P.td.w[pp] * P.td.w[qq] : P.td.w[pp];
-        acc += W * double(sA[v * stride + el * NP + kk]);
-      }
-      P.b.smean[(size_t)v * m.ne + e] = acc;
+      for (int v = 0; v < M; ++v) AT(sA, v, k) = W * Sa[v];
+      elem_tree<NP, M>(sA, epb, el, k, OpSum());
+      for (int v = k; valid && v < M; v += NP)
+        P.b.smean[(size_t)v * m.ne + e] = double(sA[v * stride + el * NP]);
+    } else {
+      for (int v = k; valid && v < M; v += NP) P.b.smean[(size_t)v * m.ne + e] = 0.0;
     }
   }
 #undef AT
@@ -525,7 +570,7 @@ __global__ void k_face(const KParams<real> P) {
         uL[v] = fld(1 + 2 * M + v, sL, eL);
         uR[v] = fld(1 + 2 * M + v, sR, eR);
       }
-      rusanov<EQ>(uL, uR, dir, fLO, m);
+      rusanov<EQ>(uL, uR, dir, fLO, P.ph);
     }
     alpha_f = 0.5 * (P.b.alpha[eL] + P.b.alpha[eR]);
   } else {
@@ -537,7 +582,7 @@ __global__ void k_face(const KParams<real> P) {
       real us[M];
 #pragma unroll
       for (int v = 0; v < M; ++v) us[v] = fld(1 + 2 * M + v, si, ei);
-      EQ::flux(us, dir, fLO, m);
+      EQ::flux(us, dir, fLO, P.ph);
     }
     alpha_f = P.b.alpha[ei];
   }
@@ -547,9 +592,7 @@ __global__ void k_face(const KParams<real> P) {
     F[v] = blend ? (1.0 - alpha_f) * double(FHO[v]) + alpha_f * double(fLO[v]) : double(FHO[v]);
   double theta = 1.0;
   if ((m.limiter & kLimFlux) && EQ::K > 0) {
-    const double kappa = DIM == 2 ? 0.5 : 1.0;
-    const double h = dir == 0 ? m.dx : m.dy;
-    const double cL = dtd / (kappa * P.td.w[N] * h), cR = dtd / (kappa * P.td.w[0] * h);
+    const double cL = dtd * m.cflim[dir == 0 ? 1 : 3], cR = dtd * m.cflim[dir == 0 ? 0 : 2];
     double baseL[M], baseR[M], flo[M];
 #pragma unroll
     for (int v = 0; v < M; ++v) {
@@ -563,13 +606,13 @@ __global__ void k_face(const KParams<real> P) {
       if (eL >= 0) {
 #pragma unroll
         for (int v = 0; v < M; ++v) cand[v] = baseL[v] - cL * flo[v];
-        PlowL = EQ::constraint(cand, kk, m);
+        PlowL = EQ::constraint(cand, kk, P.phd);
         eps = fmin(eps, PlowL);
       }
       if (eR >= 0) {
 #pragma unroll
         for (int v = 0; v < M; ++v) cand[v] = baseR[v] + cR * flo[v];
-        PlowR = EQ::constraint(cand, kk, m);
+        PlowR = EQ::constraint(cand, kk, P.phd);
         eps = fmin(eps, PlowR);
       }
       eps *= 0.1;
@@ -583,13 +626,13 @@ __global__ void k_face(const KParams<real> P) {
       if (eL >= 0) {
 #pragma unroll
         for (int v = 0; v < M; ++v) cand[v] = baseL[v] - cL * Ft[v];
-        const double Pk = EQ::constraint(cand, kk, m);
+        const double Pk = EQ::constraint(cand, kk, P.phd);
         if (Pk < eps) tk = fmin(tk, (PlowL - eps) / (PlowL - Pk));
       }
       if (eR >= 0) {
 #pragma unroll
         for (int v = 0; v < M; ++v) cand[v] = baseR[v] + cR * Ft[v];
-        const double Pk = EQ::constraint(cand, kk, m);
+        const double Pk = EQ::constraint(cand, kk, P.phd);
         if (Pk < eps) tk = fmin(tk, (PlowR - eps) / (PlowR - Pk));
       }
       theta *= tk;
@@ -603,59 +646,60 @@ __global__ void k_face(const KParams<real> P) {
 
 // ===========================================================================
 // Element-level helpers for k_update / k_prologue (one thread per node, EPB
-// elements per block).  sRed: [EPB][NP] doubles.
+// elements per block).  Per-element reductions are trees over the element's
+// threads in shared memory, so that no loop runs on a single lane (a warp
+// instruction costs the FP64 pipe the same with 1 or 32 active lanes).
 
-// smoothness indicator of one element from eps at the nodes (in sE), returns alpha
-// on thread k == 0; uses sT as scratch.  Modal energies: Legendre modes of eps,
-// E = max(top-mode energy fraction, next-to-top fraction), logistic map.
-template <int DIM, int N>
-__device__ void indicator_alpha(const Mesh& m, const Tab<double>& td, double* sE, double* sT,
-                                int el, int k, double* alpha_out) {
+// Smoothness indicator of one element (Hennemann form, see R6 of the readings):
+// eps at the nodes in E[el*NP + k] -> Legendre modes -> energy fractions ->
+// logistic alpha, returned on every thread of the element.  T is the
+// arithmetic type (double in FP64 mode, float in FP32_BULK mode).
+template <int DIM, int N, typename T>
+__device__ T indicator_alpha(const Mesh& m, const Tab<T>& tb, T* E, T* Tm, T* red, int epb, int el,
+                             int k) {
   constexpr int n = N + 1;
   constexpr int NP = DIM == 2 ? n * n : n;
-  double* E = sE + el * NP;
-  double* T = sT + el * NP;
+  T* Ee = E + el * NP;
+  T* Te = Tm + el * NP;
+  T mo;
+  int i, j;
   if (DIM == 2) {
-    const int i = k % n, qq = k / n;
-    double acc = 0.0;
+    i = k % n;
+    j = k / n;
+    T acc = T(0);
 #pragma unroll
-    for (int pp = 0; pp < n; ++pp) acc += td.V[i * n + pp] * E[pp + n * qq];
-    T[k] = acc;
+    for (int pp = 0; pp < n; ++pp) acc += tb.V[i * n + pp] * Ee[pp + n * j];
+    Te[k] = acc;  // row transform, column j
     __syncthreads();
-    const int jj = k / n;
-    double mo = 0.0;
+    mo = T(0);
 #pragma unroll
-    for (int q2 = 0; q2 < n; ++q2) mo += td.V[jj * n + q2] * T[i + n * q2];
-    __syncthreads();
-    E[k] = mo * mo;
-    __syncthreads();
+    for (int q2 = 0; q2 < n; ++q2) mo += tb.V[j * n + q2] * Te[i + n * q2];
   } else {
-    double mo = 0.0;
+    i = k;
+    j = 0;
+    mo = T(0);
 #pragma unroll
-    for (int pp = 0; pp < n; ++pp) mo += td.V[k * n + pp] * E[pp];
-    __syncthreads();
-    E[k] = mo * mo;
-    __syncthreads();
+    for (int pp = 0; pp < n; ++pp) mo += tb.V[k * n + pp] * Ee[pp];
   }
-  if (k == 0) {
-    double tot = 0.0, top = 0.0, low = 0.0, top1 = 0.0;
-    for (int kk = 0; kk < NP; ++kk) {
-      const int i = DIM == 2 ? kk % n : kk, j = DIM == 2 ? kk / n : 0;
-      const int mx = i > j ? i : j;
-      const double e2 = E[kk];
-      tot += e2;
-      if (mx == N) top += e2;
-      if (mx <= N - 1) low += e2;
-      if (mx == N - 1) top1 += e2;
-    }
-    const double r1 = tot > 0.0 ? top / tot : 0.0;
-    const double r2 = (N >= 2 && low > 0.0) ? top1 / low : 0.0;
-    const double Ev = fmax(r1, r2);
-    double al = 1.0 / (1.0 + exp(-m.s_ind / m.T_ind * (Ev - m.T_ind)));
-    if (al < 1e-3) al = 0.0;
-    if (al > 1.0 - 1e-3) al = 1.0;
-    *alpha_out = fmin(al, 1.0);
-  }
+  const T e2 = mo * mo;
+  const int mx = i > j ? i : j;
+  // four sums: total, top (max index N), low (max index <= N-1), next-to-top (N-1)
+  red[(0 * epb + el) * NP + k] = e2;
+  red[(1 * epb + el) * NP + k] = mx == N ? e2 : T(0);
+  red[(2 * epb + el) * NP + k] = mx <= N - 1 ? e2 : T(0);
+  red[(3 * epb + el) * NP + k] = mx == N - 1 ? e2 : T(0);
+  elem_tree<NP, 4>(red, epb, el, k, OpSum());
+  const T tot = red[(0 * epb + el) * NP], top = red[(1 * epb + el) * NP];
+  const T low = red[(2 * epb + el) * NP], top1 = red[(3 * epb + el) * NP];
+  const T r1 = tot > T(0) ? top / tot : T(0);
+  const T r2 = (N >= 2 && low > T(0)) ? top1 / low : T(0);
+  const T Ev = fmax(r1, r2);
+  const T Tt = T(m.T_ind);
+  T al = T(1) / (T(1) + exp(-T(m.s_ind) / Tt * (Ev - Tt)));
+  if (al < T(1e-3)) al = T(0);
+  if (al > T(1) - T(1e-3)) al = T(1);
+  __syncthreads();  // red is reused by the caller
+  return fmin(al, T(1));
 }
 
 // finish the step: block max of the CFL rate, last block publishes the rate,
@@ -679,7 +723,30 @@ __device__ __forceinline__ void finish_block(TimeCtl* ctl, double block_rate, in
   }
 }
 
+// CFL rate sigma_x(u_bar)/dx + sigma_y(u_bar)/dy of each element, block max,
+// then finish_block.  Thread k = 0 of each element evaluates x, k = 1 y.
+template <int DIM, int NP, class EQ, typename T>
+__device__ __forceinline__ void rate_and_finish(const Mesh& m, const Phys<T>& ph, const T* ubar,
+                                                T* rbuf, int epb, int el, int k, bool valid,
+                                                TimeCtl* ctl, int advance, double dtd, int last) {
+  if (k < DIM) {
+    const T r = EQ::speed(ubar, k, ph) * T(k == 0 ? m.invdx : m.invdy);
+    rbuf[el * 2 + k] = valid ? r : T(0);
+  }
+  __syncthreads();
+  double brate = 0.0;
+  if (threadIdx.x == 0)
+    for (int j = 0; j < epb; ++j) {
+      double r = double(rbuf[j * 2]);
+      if (DIM == 2) r += double(rbuf[j * 2 + 1]);
+      brate = fmax(brate, r);
+    }
+  finish_block(ctl, brate, advance, dtd, last);
+}
+
 // ===========================================================================
+// k_update.  Shared memory (doubles): sU [M][epb][NP] node values, sRed
+// [RW][epb][NP] reduction buffer, sEl [epb][16] per-element values.
 template <int DIM, int N, class EQ, typename real, bool MIXED>
 __global__ void k_update(const KParams<real> P) {
   constexpr int n = N + 1;
@@ -689,6 +756,8 @@ __global__ void k_update(const KParams<real> P) {
   constexpr int NFN = DIM == 2 ? n : 1;
   constexpr int NSLOT = NSIDE * NFN;
   constexpr int SPT = (NSLOT + NP - 1) / NP;
+  constexpr int RW = 2 * M > 4 ? 2 * M : 4;
+  constexpr int MU = M > 2 ? M : 2;
   const Mesh& m = P.m;
   const Tab<double>& td = P.td;
   const double dtd = P.b.ctl->dt_step;
@@ -702,185 +771,218 @@ __global__ void k_update(const KParams<real> P) {
   const bool valid = e < m.ne;
   const int ee = valid ? e : m.ne - 1;
   const int ix = ee % m.nx, iy = ee / m.nx;
+  const int stride = epb * NP;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sU = reinterpret_cast<double*>(smem_raw);  // [M][epb][NP]
-  double* sRed = sU + M * epb * NP;                  // [epb][NP]
-  double* sT = sRed + epb * NP;                      // [epb][NP]
-  double* sMean = sT + epb * NP;                     // [epb][M]
-  double* sShift = sMean + epb * M;                  // [epb][M]
-  double* sTh = sShift + epb * M;                    // [epb]
-  const int stride = epb * NP;
+  double* sU = reinterpret_cast<double*>(smem_raw);  // [MU][epb][NP]
+  double* sRed = sU + MU * stride;                   // [RW][epb][NP]
+  double* sEl = sRed + RW * stride;                  // [epb][16]
 #define ATU(v, node) sU[(v) * stride + el * NP + (node)]
+#define RED(w) sRed[((w) * epb + el) * NP + k]
+#define RED0(w) sRed[((w) * epb + el) * NP]
 
+  // ---- node update: partial update + element-face flux terms ------------
   const double alpha = P.b.alpha[ee];
   const bool blend = (m.limiter & kLimBlend) || m.alpha_mode == 1;
   const real a = blend ? real(alpha) : real(0);
   const real dt = real(dtd);
   const real one = real(1);
-  // face indices of this node's x-line and y-line
   const int ixR = m.bcx == 0 ? (ix + 1) % m.nx : ix + 1;
-  real cRx = (one - a) * P.tb.gR[p] + (p == N ? a * P.tb.invw[N] : real(0));
-  real cLx = (one - a) * P.tb.gL[p] - (p == 0 ? a * P.tb.invw[0] : real(0));
+  const int iyT = DIM == 2 ? (m.bcy == 0 ? (iy + 1) % m.ny : iy + 1) : 0;
   const size_t nXf = (size_t)m.ny * m.nfx * NFN;
-  double unew[M];
+  const size_t nYf = DIM == 2 ? (size_t)m.nfy * m.nx * n : 0;
+  const real cRx = (one - a) * P.tb.gR[p] + (p == N ? a * P.tb.invw[N] : real(0));
+  const real cLx = (one - a) * P.tb.gL[p] - (p == 0 ? a * P.tb.invw[0] : real(0));
+  const real cRy = DIM == 2 ? (one - a) * P.tb.gR[q] + (q == N ? a * P.tb.invw[N] : real(0)) : real(0);
+  const real cLy = DIM == 2 ? (one - a) * P.tb.gL[q] - (q == 0 ? a * P.tb.invw[0] : real(0)) : real(0);
+  const real W = DIM == 2 ? P.tb.w[p] * P.tb.w[q] : P.tb.w[p];
+  real val[M];
 #pragma unroll
   for (int v = 0; v < M; ++v) {
     const real FxL = P.b.fx[v * nXf + ((size_t)iy * m.nfx + ix) * NFN + q];
     const real FxR = P.b.fx[v * nXf + ((size_t)iy * m.nfx + ixR) * NFN + q];
-    real val = P.b.P[((size_t)v * m.ne + ee) * NP + k] - dt * real(m.invdx) * (FxR * cRx + FxL * cLx);
+    real x = P.b.P[((size_t)v * m.ne + ee) * NP + k] - dt * real(m.invdx) * (FxR * cRx + FxL * cLx);
+    real GB = real(0), GT = real(0);
     if (DIM == 2) {
-      const int iyT = m.bcy == 0 ? (iy + 1) % m.ny : iy + 1;
-      const size_t nYf = (size_t)m.nfy * m.nx * n;
-      const real cRy = (one - a) * P.tb.gR[q] + (q == N ? a * P.tb.invw[N] : real(0));
-      const real cLy = (one - a) * P.tb.gL[q] - (q == 0 ? a * P.tb.invw[0] : real(0));
-      const real GB = P.b.fy[v * nYf + ((size_t)iy * m.nx + ix) * n + p];
-      const real GT = P.b.fy[v * nYf + ((size_t)iyT * m.nx + ix) * n + p];
-      val -= dt * real(m.invdy) * (GT * cRy + GB * cLy);
+      GB = P.b.fy[v * nYf + ((size_t)iy * m.nx + ix) * n + p];
+      GT = P.b.fy[v * nYf + ((size_t)iyT * m.nx + ix) * n + p];
+      x -= dt * real(m.invdy) * (GT * cRy + GB * cLy);
     }
-    unew[v] = double(val);
-    ATU(v, k) = unew[v];
-  }
-  __syncthreads();
-
-  // element mean: FP64 sum in FP64 mode; in FP32_BULK mode the conservative
-  // FP64 mean update of eq. (upmean) (plus the source mean), and the nodes are
-  // re-centred on it
-  for (int v = k; v < M; v += NP) {
-    double mean;
+    val[v] = x;
     if constexpr (MIXED) {
-      double fxs = 0.0, fys = 0.0;
-      for (int j = 0; j < NFN; ++j) {
-        const double wj = DIM == 2 ? td.w[j] : 1.0;
-        fxs += wj * (double(P.b.fx[v * nXf + ((size_t)iy * m.nfx + ixR) * NFN + j]) -
-                     double(P.b.fx[v * nXf + ((size_t)iy * m.nfx + ix) * NFN + j]));
-      }
+      // conservative FP64 mean change of eq. (upmean): this node's share of the
+      // element-face flux integrals, and the FP32 mean of the nodal update
+      double dmv = 0.0;
+      if (p == N) dmv -= dtd * m.invdx * double(DIM == 2 ? P.tb.w[q] : 1.0f) * double(FxR);
+      if (p == 0) dmv += dtd * m.invdx * double(DIM == 2 ? P.tb.w[q] : 1.0f) * double(FxL);
       if (DIM == 2) {
-        const int iyT = m.bcy == 0 ? (iy + 1) % m.ny : iy + 1;
-        const size_t nYf = (size_t)m.nfy * m.nx * n;
-        for (int j = 0; j < n; ++j)
-          fys += td.w[j] * (double(P.b.fy[v * nYf + ((size_t)iyT * m.nx + ix) * n + j]) -
-                            double(P.b.fy[v * nYf + ((size_t)iy * m.nx + ix) * n + j]));
+        if (q == N) dmv -= dtd * m.invdy * double(P.tb.w[p]) * double(GT);
+        if (q == 0) dmv += dtd * m.invdy * double(P.tb.w[p]) * double(GB);
       }
-      mean = P.b.umean[(size_t)v * m.ne + ee] + dtd * P.b.smean[(size_t)v * m.ne + ee] -
-             dtd * m.invdx * fxs - (DIM == 2 ? dtd * m.invdy * fys : 0.0);
-      double m32 = 0.0;
-      for (int kk = 0; kk < NP; ++kk) {
-        const int pp = DIM == 2 ? kk % n : kk, qq = DIM == 2 ? kk / n : 0;
-        m32 += (DIM == 2 ? td.w[pp] * td.w[qq] : td.w[pp]) * ATU(v, kk);
-      }
-      sShift[el * M + v] = mean - m32;  // shift that re-centres the nodes
+      RED(v) = dmv;
+      RED(M + v) = double(W * x);
     } else {
-      mean = 0.0;
-      for (int kk = 0; kk < NP; ++kk) {
-        const int pp = DIM == 2 ? kk % n : kk, qq = DIM == 2 ? kk / n : 0;
-        mean += (DIM == 2 ? td.w[pp] * td.w[qq] : td.w[pp]) * ATU(v, kk);
-      }
+      RED(v) = double(W) * double(x);
     }
-    sMean[el * M + v] = mean;
   }
-  __syncthreads();
+  elem_tree<NP, (MIXED ? 2 * M : M)>(sRed, epb, el, k, OpSum());
   double ubar[M];
 #pragma unroll
-  for (int v = 0; v < M; ++v) ubar[v] = sMean[el * M + v];
-  if constexpr (MIXED) {
-    double shift[M];
-#pragma unroll
-    for (int v = 0; v < M; ++v) shift[v] = sShift[el * M + v];
-    __syncthreads();
-#pragma unroll
-    for (int v = 0; v < M; ++v) {
-      unew[v] += shift[v];
-      ATU(v, k) = unew[v];
-    }
-    __syncthreads();
+  for (int v = 0; v < M; ++v) {
+    if constexpr (MIXED)
+      ubar[v] = P.b.umean[(size_t)v * m.ne + ee] + RED0(v) + dtd * P.b.smean[(size_t)v * m.ne + ee];
+    else
+      ubar[v] = RED0(v);
   }
+  real m32[M];
+  if constexpr (MIXED) {
+#pragma unroll
+    for (int v = 0; v < M; ++v) m32[v] = real(RED0(M + v));
+  }
+  __syncthreads();
 
-  // ---------------- positivity scaling limiter (FP64 theta) --------------
+  // ---- positivity scaling limiter (FP64 theta) ----------------------------
+  // node value in the kernel's type: FP64 mode the update itself; FP32_BULK the
+  // FP64 mean plus the re-centred FP32 fluctuation
+  real fl[M];
+  real ur[M];
+#pragma unroll
+  for (int v = 0; v < M; ++v) {
+    if constexpr (MIXED) {
+      fl[v] = val[v] - m32[v];
+      ur[v] = real(ubar[v]) + fl[v];
+    } else {
+      ur[v] = val[v];
+    }
+  }
   int bad = 0;
-  const bool mean_ok = admissible<EQ>(ubar, m);
+  if (k == 0) {
+    const double mean_ok = admissible<EQ>(ubar, P.phd) ? 1.0 : 0.0;
+    sEl[el * 16 + 0] = mean_ok;
+    sEl[el * 16 + 1] = EQ::K > 0 ? fmin(1e-12, ubar[0]) : 0.0;                           // eps1
+    sEl[el * 16 + 2] = EQ::K > 0 ? fmin(1e-12, EQ::constraint(ubar, 1, P.phd)) : 0.0;     // eps2
+    sEl[el * 16 + 3] = EQ::K > 0 ? EQ::constraint(ubar, 1, P.phd) : 0.0;                  // P2(u_bar)
+  }
+  __syncthreads();
+  const bool mean_ok = sEl[el * 16 + 0] != 0.0;
   if (EQ::K > 0 && !mean_ok) bad |= kStInadmissible;
   const bool do_scale = (m.limiter & kLimScaling) && EQ::K > 0;
   const bool traces = (m.limiter & kLimTraces) != 0;
-  double pts[1 + SPT][M];
-  int npt = 1;
 #pragma unroll
-  for (int v = 0; v < M; ++v) pts[0][v] = unew[v];
-  if (do_scale && traces) {
-#pragma unroll
-    for (int mm = 0; mm < SPT; ++mm) {
-      const int sl = k + mm * NP;
-      if (sl < NSLOT) {
-        const int side = sl / NFN, j = sl - side * NFN;
-#pragma unroll
-        for (int v = 0; v < M; ++v) {
-          double acc = 0.0;
-#pragma unroll
-          for (int r = 0; r < n; ++r) {
-            const double l = (side & 1) ? td.l1[r] : td.l0[r];
-            acc += l * ATU(v, side < 2 ? r + n * j : j + n * r);
-          }
-          pts[npt][v] = acc;
-        }
-        ++npt;
-      }
-    }
-  }
+  for (int v = 0; v < M; ++v) ATU(v, k) = double(ur[v]);
+  __syncthreads();
   if (do_scale) {
-    // density: theta1 from the smallest density over the checked points
-    double rmin = pts[0][0];
-    for (int t = 1; t < npt; ++t) rmin = fmin(rmin, pts[t][0]);
-    sRed[el * NP + k] = rmin;
-    __syncthreads();
-    if (k == 0) {
-      double r = sRed[el * NP];
-      for (int kk = 1; kk < NP; ++kk) r = fmin(r, sRed[el * NP + kk]);
-      const double eps1 = fmin(1e-12, ubar[0]);
-      sTh[el] = (mean_ok && r < eps1) ? (ubar[0] - eps1) / (ubar[0] - r) : 2.0;  // 2: untouched
-    }
-    __syncthreads();
-    const double th1 = sTh[el];
-    if (th1 <= 1.0)
-      for (int t = 0; t < npt; ++t) pts[t][0] = ubar[0] + th1 * (pts[t][0] - ubar[0]);
-    // second constraint: bisection along the segment from the mean
-    const double eps2 = fmin(1e-12, EQ::constraint(ubar, 1, m));
-    double tmin = 1.0;
-    if (mean_ok)
-      for (int t = 0; t < npt; ++t) {
-        if (EQ::constraint(pts[t], 1, m) >= eps2) continue;
-        double lo = 0.0, hi = 1.0, tmp[M];
-        for (int it = 0; it < 50; ++it) {
-          const double mid = 0.5 * (lo + hi);
+    const double eps1 = sEl[el * 16 + 1], eps2 = sEl[el * 16 + 2], P2bar = sEl[el * 16 + 3];
+    // points this thread checks: its node and its face-trace slots
+    real pr[1 + SPT][M];
+    int npt = 1;
 #pragma unroll
-          for (int v = 0; v < M; ++v) tmp[v] = ubar[v] + mid * (pts[t][v] - ubar[v]);
-          if (EQ::constraint(tmp, 1, m) >= eps2) lo = mid;
-          else hi = mid;
+    for (int v = 0; v < M; ++v) pr[0][v] = ur[v];
+    if (traces) {
+#pragma unroll
+      for (int mm = 0; mm < SPT; ++mm) {
+        const int sl = k + mm * NP;
+        if (sl < NSLOT) {
+          const int side = sl / NFN, j = sl - side * NFN;
+#pragma unroll
+          for (int v = 0; v < M; ++v) {
+            real acc = real(0);
+#pragma unroll
+            for (int r = 0; r < n; ++r) {
+              const real l = (side & 1) ? P.tb.l1[r] : P.tb.l0[r];
+              acc += l * real(ATU(v, side < 2 ? r + n * j : j + n * r));
+            }
+            pr[npt][v] = acc;
+          }
+          ++npt;
         }
-        tmin = fmin(tmin, lo);
       }
-    __syncthreads();
-    sRed[el * NP + k] = tmin;
-    __syncthreads();
-    if (k == 0) {
-      double r = sRed[el * NP];
-      for (int kk = 1; kk < NP; ++kk) r = fmin(r, sRed[el * NP + kk]);
-      sTh[el] = r;
     }
-    __syncthreads();
-    const double th2 = sTh[el];
-    if (th2 < 1.0)
-      for (int t = 0; t < npt; ++t)
+    // does any point of the block need limiting?  FP64 mode: exactly the
+    // oracle's test; FP32_BULK: an FP32 prescreen with a margin, the FP64
+    // solve below decides
+    int need = 0;
+    for (int t = 0; t < npt; ++t) {
+      if constexpr (MIXED) {
+        const real scale = real(EQ::M == 6 ? fabs(double(pr[t][3])) + fabs(double(pr[t][5]))
+                                           : fabs(double(pr[t][M - 1])));
+        const real thr = fmax(fmax(real(1e-3) * real(P2bar), real(1e-5) * scale), real(1e-11));
+        if (!(pr[t][0] > real(1e-3) * real(ubar[0]) && EQ::constraint(pr[t], 1, P.ph) > thr)) need = 1;
+      } else {
+        if (!(pr[t][0] >= eps1 && EQ::constraint(pr[t], 1, P.phd) >= eps2)) need = 1;
+      }
+    }
+    if (__syncthreads_or(need)) {
+      // FP64 path (oracle's limiter): points in FP64
+      double pts[1 + SPT][M];
+      int np2 = 1;
 #pragma unroll
-        for (int v = 0; v < M; ++v) pts[t][v] = ubar[v] + th2 * (pts[t][v] - ubar[v]);
+      for (int v = 0; v < M; ++v) pts[0][v] = ATU(v, k);
+      if (traces) {
 #pragma unroll
-    for (int v = 0; v < M; ++v) unew[v] = pts[0][v];
-    if (mean_ok)
-      for (int t = 0; t < npt; ++t)
-        if (!admissible<EQ>(pts[t], m)) bad |= kStInadmissible;
+        for (int mm = 0; mm < SPT; ++mm) {
+          const int sl = k + mm * NP;
+          if (sl < NSLOT) {
+            const int side = sl / NFN, j = sl - side * NFN;
+#pragma unroll
+            for (int v = 0; v < M; ++v) {
+              double acc = 0.0;
+#pragma unroll
+              for (int r = 0; r < n; ++r) {
+                const double l = (side & 1) ? td.l1[r] : td.l0[r];
+                acc += l * ATU(v, side < 2 ? r + n * j : j + n * r);
+              }
+              pts[np2][v] = acc;
+            }
+            ++np2;
+          }
+        }
+      }
+      double rmin = pts[0][0];
+      for (int t = 1; t < np2; ++t) rmin = fmin(rmin, pts[t][0]);
+      RED(0) = rmin;
+      elem_tree<NP, 1>(sRed, epb, el, k, OpMin());
+      rmin = RED0(0);
+      __syncthreads();
+      if (mean_ok && rmin < eps1) {
+        const double th1 = (ubar[0] - eps1) / (ubar[0] - rmin);
+        for (int t = 0; t < np2; ++t) pts[t][0] = ubar[0] + th1 * (pts[t][0] - ubar[0]);
+      }
+      double tmin = 1.0;
+      if (mean_ok)
+        for (int t = 0; t < np2; ++t) {
+          if (EQ::constraint(pts[t], 1, P.phd) >= eps2) continue;
+          double lo = 0.0, hi = 1.0, tmp[M];
+          for (int it = 0; it < 50; ++it) {
+            const double mid = 0.5 * (lo + hi);
+#pragma unroll
+            for (int v = 0; v < M; ++v) tmp[v] = ubar[v] + mid * (pts[t][v] - ubar[v]);
+            if (EQ::constraint(tmp, 1, P.phd) >= eps2) lo = mid;
+            else hi = mid;
+          }
+          tmin = fmin(tmin, lo);
+        }
+      RED(0) = tmin;
+      elem_tree<NP, 1>(sRed, epb, el, k, OpMin());
+      const double th2 = RED0(0);
+      __syncthreads();
+      if (th2 < 1.0)
+        for (int t = 0; t < np2; ++t)
+#pragma unroll
+          for (int v = 0; v < M; ++v) pts[t][v] = ubar[v] + th2 * (pts[t][v] - ubar[v]);
+      if (mean_ok)
+        for (int t = 0; t < np2; ++t)
+          if (!admissible<EQ>(pts[t], P.phd)) bad |= kStInadmissible;
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        if constexpr (MIXED) fl[v] = real(pts[0][v] - ubar[v]);
+        ur[v] = real(pts[0][v]);
+      }
+    }
   }
 #pragma unroll
   for (int v = 0; v < M; ++v)
-    if (!isfinite(unew[v])) bad |= kStNonFinite;
+    if (!isfinite(ur[v])) bad |= kStNonFinite;
   if (valid && bad) {
     atomicOr(&P.b.ctl->status, bad);
     atomicMin(&P.b.ctl->bad_elem, e);
@@ -889,35 +991,52 @@ __global__ void k_update(const KParams<real> P) {
 #pragma unroll
     for (int v = 0; v < M; ++v) {
       const size_t gi = ((size_t)v * m.ne + e) * NP + k;
-      if constexpr (MIXED) P.b.u[gi] = real(unew[v] - ubar[v]);
-      else P.b.u[gi] = real(unew[v]);
+      if constexpr (MIXED) P.b.u[gi] = fl[v];
+      else P.b.u[gi] = ur[v];
     }
     if constexpr (MIXED) {
-      for (int v = k; v < M; v += NP) P.b.umean[(size_t)v * m.ne + e] = ubar[v];
+      for (int v = k; v < M; v += NP) {
+        P.b.umean[(size_t)v * m.ne + e] = ubar[v];
+        P.b.umean_f[(size_t)v * m.ne + e] = float(ubar[v]);
+      }
     }
   }
 
-  // ---------------- indicator of the new state and the CFL rate ---------
+  // ---- indicator of the new state and the CFL rate -------------------------
   if ((m.limiter & kLimBlend) && m.alpha_mode == 0) {
-    __syncthreads();
-    sRed[el * NP + k] = EQ::indicator_var(unew, m);
-    __syncthreads();
-    double al = 0.0;
-    indicator_alpha<DIM, N>(m, td, sRed, sT, el, k, &al);
-    if (valid && k == 0) P.b.alpha_raw[e] = al;
+    if constexpr (MIXED) {
+      real* rE = reinterpret_cast<real*>(sU);
+      real* rT = rE + stride;
+      real* rR = rT + stride;
+      __syncthreads();
+      rE[el * NP + k] = EQ::indicator_var(ur, P.ph);
+      __syncthreads();
+      const real al = indicator_alpha<DIM, N, real>(m, P.tb, rE, rT, rR, epb, el, k);
+      if (valid && k == 0) P.b.alpha_raw[e] = double(al);
+    } else {
+      double* dE = sU;
+      double* dT = sU + stride;
+      __syncthreads();
+      dE[el * NP + k] = EQ::indicator_var(ur, P.phd);
+      __syncthreads();
+      const double al = indicator_alpha<DIM, N, double>(m, td, dE, dT, sRed, epb, el, k);
+      if (valid && k == 0) P.b.alpha_raw[e] = al;
+    }
   }
   __syncthreads();
-  if (k == 0) {
-    double r = EQ::speed(ubar, 0, m) * m.invdx;
-    if (DIM == 2) r += EQ::speed(ubar, 1, m) * m.invdy;
-    sTh[el] = valid ? r : 0.0;
+  if constexpr (MIXED) {
+    float ubf[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) ubf[v] = float(ubar[v]);
+    rate_and_finish<DIM, NP, EQ, float>(m, P.ph, ubf, reinterpret_cast<float*>(sEl), epb, el, k,
+                                        valid, P.b.ctl, 1, dtd, last_step);
+  } else {
+    rate_and_finish<DIM, NP, EQ, double>(m, P.phd, ubar, sEl, epb, el, k, valid, P.b.ctl, 1, dtd,
+                                         last_step);
   }
-  __syncthreads();
-  double brate = 0.0;
-  if (tid == 0)
-    for (int j = 0; j < epb; ++j) brate = fmax(brate, sTh[j]);
-  finish_block(P.b.ctl, brate, 1, dtd, last_step);
 #undef ATU
+#undef RED
+#undef RED0
 }
 
 // ===========================================================================
@@ -928,72 +1047,56 @@ __global__ void k_prologue(const KParams<real> P) {
   constexpr int n = N + 1;
   constexpr int NP = DIM == 2 ? n * n : n;
   constexpr int M = EQ::M;
+  constexpr int RW = 2 * M > 4 ? 2 * M : 4;
+  constexpr int MU = M > 2 ? M : 2;
   const Mesh& m = P.m;
-  const Tab<double>& td = P.td;
   const int epb = blockDim.x / NP;
   const int tid = threadIdx.x;
   const int el = tid / NP, k = tid - el * NP;
   const int e = blockIdx.x * epb + el;
   const bool valid = e < m.ne;
   const int ee = valid ? e : m.ne - 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sU = reinterpret_cast<double*>(smem_raw);  // [M][epb][NP]
-  double* sRed = sU + M * epb * NP;
-  double* sT = sRed + epb * NP;
-  double* sMean = sT + epb * NP;
-  double* sTh = sMean + 2 * epb * M;
   const int stride = epb * NP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sU = reinterpret_cast<double*>(smem_raw);
+  double* sRed = sU + MU * stride;
+  double* sEl = sRed + RW * stride;
+  const int p = DIM == 2 ? k % n : k, q = DIM == 2 ? k / n : 0;
+  const double W = DIM == 2 ? P.td.w[p] * P.td.w[q] : P.td.w[p];
   double u[M];
   int bad = 0;
 #pragma unroll
   for (int v = 0; v < M; ++v) {
     u[v] = double(P.b.u[((size_t)v * m.ne + ee) * NP + k]);
     if constexpr (MIXED) u[v] += P.b.umean[(size_t)v * m.ne + ee];
-    sU[v * stride + el * NP + k] = u[v];
     if (!isfinite(u[v])) bad = kStInvalidInput;
+    sRed[(v * epb + el) * NP + k] = W * u[v];
   }
-  if (!admissible<EQ>(u, m)) bad = kStInvalidInput;
+  if (!admissible<EQ>(u, P.phd)) bad = kStInvalidInput;
   if (valid && bad) {
     atomicOr(&P.b.ctl->status, bad);
     atomicMin(&P.b.ctl->bad_elem, e);
   }
-  __syncthreads();
-  for (int v = k; v < M; v += NP) {
-    double mean = 0.0;
-    for (int kk = 0; kk < NP; ++kk) {
-      const int pp = DIM == 2 ? kk % n : kk, qq = DIM == 2 ? kk / n : 0;
-      mean += (DIM == 2 ? td.w[pp] * td.w[qq] : td.w[pp]) * sU[v * stride + el * NP + kk];
-    }
-    sMean[el * M + v] = mean;
-  }
+  elem_tree<NP, M>(sRed, epb, el, k, OpSum());
+  double ubar[M];
+#pragma unroll
+  for (int v = 0; v < M; ++v) ubar[v] = sRed[(v * epb + el) * NP];
   __syncthreads();
   if ((m.limiter & kLimBlend) && m.alpha_mode == 0) {
-    sRed[el * NP + k] = EQ::indicator_var(u, m);
+    sU[el * NP + k] = EQ::indicator_var(u, P.phd);
     __syncthreads();
-    double al = 0.0;
-    indicator_alpha<DIM, N>(m, td, sRed, sT, el, k, &al);
+    const double al = indicator_alpha<DIM, N, double>(m, P.td, sU, sU + stride, sRed, epb, el, k);
     if (valid && k == 0) P.b.alpha_raw[e] = al;
   }
   __syncthreads();
-  if (k == 0) {
-    double ubar[M];
-#pragma unroll
-    for (int v = 0; v < M; ++v) ubar[v] = sMean[el * M + v];
-    double r = EQ::speed(ubar, 0, m) * m.invdx;
-    if (DIM == 2) r += EQ::speed(ubar, 1, m) * m.invdy;
-    sTh[el] = valid ? r : 0.0;
-  }
-  __syncthreads();
-  double brate = 0.0;
-  if (tid == 0)
-    for (int j = 0; j < epb; ++j) brate = fmax(brate, sTh[j]);
-  finish_block(P.b.ctl, brate, 0, 0.0, 0);
+  rate_and_finish<DIM, NP, EQ, double>(m, P.phd, ubar, sEl, epb, el, k, valid, P.b.ctl, 0, 0.0, 0);
 }
 
 // FP32_BULK state conversion: FP64 nodal values <-> FP64 mean + FP32 fluctuation.
 template <int DIM, int N, int M>
 __global__ void k_split_state(const double* __restrict__ in, float* __restrict__ fl,
-                              double* __restrict__ mean, int ne, Tab<double> td) {
+                              double* __restrict__ mean, float* __restrict__ mean_f, int ne,
+                              Tab<double> td) {
   constexpr int n = N + 1;
   constexpr int NP = DIM == 2 ? n * n : n;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // one thread per (v, e)
@@ -1005,7 +1108,25 @@ __global__ void k_split_state(const double* __restrict__ in, float* __restrict__
     mu += (DIM == 2 ? td.w[pp] * td.w[qq] : td.w[pp]) * x[kk];
   }
   mean[idx] = mu;
+  mean_f[idx] = float(mu);
   for (int kk = 0; kk < NP; ++kk) fl[(size_t)idx * NP + kk] = float(x[kk] - mu);
+}
+
+// Element means sum_k W_k u_k of an FP64 state [M][Ne][Np] -> [M][Ne].
+template <int DIM, int N, int M>
+__global__ void k_element_means(const double* __restrict__ u, double* __restrict__ mean, int ne,
+                                Tab<double> td) {
+  constexpr int n = N + 1;
+  constexpr int NP = DIM == 2 ? n * n : n;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // one thread per (v, e)
+  if (idx >= M * ne) return;
+  const double* x = u + (size_t)idx * NP;
+  double mu = 0.0;
+  for (int kk = 0; kk < NP; ++kk) {
+    const int pp = DIM == 2 ? kk % n : kk, qq = DIM == 2 ? kk / n : 0;
+    mu += (DIM == 2 ? td.w[pp] * td.w[qq] : td.w[pp]) * x[kk];
+  }
+  mean[idx] = mu;
 }
 
 template <int NP>

@@ -15,6 +15,7 @@ struct KernelSet {
   cudaError_t (*prologue)(const void* params, cudaStream_t s);
   cudaError_t (*split)(const void* params, const double* in, cudaStream_t s);  // FP64 -> state
   cudaError_t (*join)(const void* params, double* out, cudaStream_t s);        // state -> FP64
+  cudaError_t (*means)(const void* params, double* out, cudaStream_t s);       // [M][Ne] FP64
   cudaError_t (*configure)();
 };
 
@@ -29,8 +30,10 @@ struct Impl {
   static constexpr int EPB = (256 / NP) > 0 ? (256 / NP) : 1;
 
   static size_t smem_local(int epb) { return (size_t)5 * M * epb * NP * sizeof(real); }
+  static constexpr int RW = 2 * M > 4 ? 2 * M : 4;
+  static constexpr int MU = M > 2 ? M : 2;
   static size_t smem_update(int epb) {
-    return ((size_t)M * epb * NP + 2 * (size_t)epb * NP + 2 * (size_t)epb * M + epb) * sizeof(double);
+    return ((size_t)(MU + RW) * epb * NP + 16 * (size_t)epb) * sizeof(double);
   }
 
   static cudaError_t configure() {
@@ -82,7 +85,8 @@ struct Impl {
     const size_t nvals = (size_t)M * P.m.ne * NP;
     if constexpr (MIXED) {
       const int nthr = M * P.m.ne;
-      k_split_state<DIM, N, M><<<(nthr + 255) / 256, 256, 0, s>>>(in, P.b.u, P.b.umean, P.m.ne, P.td);
+      k_split_state<DIM, N, M><<<(nthr + 255) / 256, 256, 0, s>>>(in, P.b.u, P.b.umean, P.b.umean_f,
+                                                                 P.m.ne, P.td);
       return cudaGetLastError();
     } else {
       return cudaMemcpyAsync(P.b.u, in, nvals * sizeof(double), cudaMemcpyDefault, s);
@@ -100,11 +104,22 @@ struct Impl {
     }
   }
 
+  static cudaError_t means(const void* pv, double* out, cudaStream_t s) {
+    const KParams<real>& P = *static_cast<const KParams<real>*>(pv);
+    if constexpr (MIXED) {
+      return cudaMemcpyAsync(out, P.b.umean, (size_t)M * P.m.ne * sizeof(double), cudaMemcpyDefault, s);
+    } else {
+      const int nthr = M * P.m.ne;
+      k_element_means<DIM, N, M><<<(nthr + 255) / 256, 256, 0, s>>>(P.b.u, out, P.m.ne, P.td);
+      return cudaGetLastError();
+    }
+  }
+
   static const KernelSet* set() {
     static const KernelSet ks = {DIM, N, M, NP, MIXED ? 1 : 0, 3, &step,
                                  {&launch_local, &launch_face, &launch_update},
                                  {"k_local", "k_face", "k_update"},
-                                 &prologue, &split, &join, &configure};
+                                 &prologue, &split, &join, &means, &configure};
     return &ks;
   }
 };

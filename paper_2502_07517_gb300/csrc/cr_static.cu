@@ -206,11 +206,24 @@ extern "C" cr_status cr_step_static(const cr_mesh_desc* d, const double* u_in, d
   m.src_cy = d->src_cy;
   m.T_ind = 0.5 * std::pow(10.0, -1.8 * std::pow(d->degree + 1.0, 0.25));
   m.s_ind = std::log((1.0 - 1e-4) / 1e-4);
+  P.ph.gamma = d->gamma;
+  P.ph.gm1 = d->gamma - 1.0;
+  P.ph.ax = d->adv[0];
+  P.ph.ay = d->adv[1];
+  P.phd = P.ph;
   static_tables(d->degree, &P.tb);
   P.td = P.tb;
+  {
+    const double kappa = dim == 2 ? 0.5 : 1.0;
+    m.cflim[0] = 1.0 / (kappa * P.td.w[0] * m.dx);
+    m.cflim[1] = 1.0 / (kappa * P.td.w[d->degree] * m.dx);
+    m.cflim[2] = 1.0 / (kappa * P.td.w[0] * m.dy);
+    m.cflim[3] = 1.0 / (kappa * P.td.w[d->degree] * m.dy);
+  }
   P.b.ctl = reinterpret_cast<TimeCtl*>(base + o_ctl);
   P.b.u = u_out;
   P.b.umean = nullptr;
+  P.b.umean_f = nullptr;
   P.b.P = reinterpret_cast<double*>(base + o_P);
   P.b.smean = nullptr;
   P.b.slot = reinterpret_cast<double*>(base + o_slot);
