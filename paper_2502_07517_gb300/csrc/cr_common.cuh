@@ -14,10 +14,11 @@ constexpr int kMaxNodes1 = kMaxN + 1;
 // Status bits kept in TimeCtl::status.
 enum : int { kStInadmissible = 1, kStNonFinite = 2, kStInvalidInput = 4 };
 
-// Time control of one context, resident in device memory.  Every kernel of a
-// step derives the step size from it (step_dt), so a whole run can be
-// enqueued without host round trips; only the last block of the update kernel
-// writes it (t, rate_last), after every other block has finished reading.
+// Time control of one context, resident in device memory.  The step size of
+// the next step is planned once (plan_step) by whoever changed its inputs: the
+// last block of the update/prologue kernel, or the run-setup kernel; the step
+// kernels only read dt_step, so a whole run can be enqueued without host
+// round trips.
 struct TimeCtl {
   double t;                 // current time
   double t_final;           // the run stops here; the last step is clipped to it
@@ -29,23 +30,28 @@ struct TimeCtl {
   int status;               // kSt* bits, sticky until cr_set_state
   int bad_elem;             // smallest element index that set a status bit
   int steps;                // steps taken since cr_set_state
-  double dt_step;           // dt of the step in flight (written by the first kernel of a step)
+  double dt_step;           // dt of the next step (0: nothing to do)
+  float dt_step_f;          // the same in FP32
   int last_step;            // 1 when that step lands on t_final
 };
 
-// dt of the step about to run (0: nothing to do).  Identical arithmetic in
-// every kernel of the step, from the same TimeCtl fields.
-__device__ __forceinline__ double step_dt(const TimeCtl* c, bool* last) {
-  *last = false;
-  if (c->status != 0) return 0.0;
-  double rem = c->t_final - c->t;
-  if (!(rem > 0.0)) return 0.0;
-  double dtc = c->dt_fixed > 0.0 ? c->dt_fixed : c->cfl_factor / c->rate_last;
-  if (dtc >= rem) {
-    *last = true;
-    return rem;
+// Plan the next step from the current time, rate and run limits (one thread).
+__device__ __forceinline__ void plan_step(TimeCtl* c) {
+  double dt = 0.0;
+  int last = 0;
+  const double rem = c->t_final - c->t;
+  if (c->status == 0 && rem > 0.0) {
+    const double dtc = c->dt_fixed > 0.0 ? c->dt_fixed : c->cfl_factor / c->rate_last;
+    if (dtc >= rem) {
+      dt = rem;
+      last = 1;
+    } else {
+      dt = dtc;
+    }
   }
-  return dtc;
+  c->dt_step = dt;
+  c->dt_step_f = float(dt);
+  c->last_step = last;
 }
 
 // Reference-element tables for degree N in the arithmetic type of the kernel
@@ -101,6 +107,7 @@ struct Bufs {
 template <typename real>
 struct Phys {
   real gamma, gm1, ax, ay;
+  real invdx, invdy;  // 1/dx, 1/dy of the mesh
 };
 
 template <typename real>
@@ -365,14 +372,14 @@ struct EqTenMoment {
   }
 };
 
-// Gradient of W = amp exp(-k |x - c|^2) for the ten-moment source (eq. (tenmom.source)).
-template <int DIM>
-__device__ __forceinline__ void source_grad(const Mesh& m, double x, double y, double* dWx,
-                                            double* dWy) {
-  double rx = x - m.src_cx, ry = DIM == 2 ? y - m.src_cy : 0.0;
-  double W = m.src_amp * exp(-m.src_k * (rx * rx + ry * ry));
-  *dWx = -2.0 * m.src_k * rx * W;
-  *dWy = DIM == 2 ? -2.0 * m.src_k * ry * W : 0.0;
+// Gradient of W = amp exp(-k |x - c|^2) for the ten-moment source (eq. (tenmom.source)),
+// from the offsets rx = x - cx, ry = y - cy, in the kernel's arithmetic type.
+template <int DIM, typename real>
+__device__ __forceinline__ void source_grad(const Mesh& m, real rx, real ry, real* dWx, real* dWy) {
+  const real kk = real(m.src_k);
+  const real W = real(m.src_amp) * exp(-kk * (rx * rx + ry * ry));
+  *dWx = real(-2) * kk * rx * W;
+  *dWy = DIM == 2 ? real(-2) * kk * ry * W : real(0);
 }
 
 // s = s^x + s^y of eq. (tenmom.source), linear in u for fixed grad W.

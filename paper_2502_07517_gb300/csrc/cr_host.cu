@@ -257,12 +257,14 @@ __global__ void k_reset_ctl(TimeCtl* c, double cfl_factor) {
   c->bad_elem = INT_MAX;
   c->steps = 0;
   c->dt_step = 0.0;
+  c->dt_step_f = 0.0f;
   c->last_step = 0;
 }
 
 __global__ void k_set_run(TimeCtl* c, double t_final, double dt_fixed) {
   c->t_final = t_final;
   c->dt_fixed = dt_fixed;
+  plan_step(c);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -425,6 +427,10 @@ void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
   P->ph.gm1 = real(d.gamma - 1.0);
   P->ph.ax = real(d.adv[0]);
   P->ph.ay = real(d.adv[1]);
+  P->ph.invdx = real(m.invdx);
+  P->ph.invdy = real(m.invdy);
+  P->phd.invdx = m.invdx;
+  P->phd.invdy = m.invdy;
   P->phd.gamma = d.gamma;
   P->phd.gm1 = d.gamma - 1.0;
   P->phd.ax = d.adv[0];

@@ -145,14 +145,9 @@ __global__ void k_local(const KParams<real> P) {
   const int ee = valid ? e : m.ne - 1;
   const int ix = ee % m.nx, iy = ee / m.nx;
 
-  bool last;
-  const double dtd = step_dt(P.b.ctl, &last);
-  if (blockIdx.x == 0 && tid == 0) {
-    P.b.ctl->dt_step = dtd > 0.0 ? dtd : 0.0;
-    P.b.ctl->last_step = last ? 1 : 0;
-  }
+  const double dtd = P.b.ctl->dt_step;
   if (!(dtd > 0.0)) return;
-  const real dt = real(dtd);
+  const real dt = sizeof(real) == 4 ? real(P.b.ctl->dt_step_f) : real(dtd);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sh = reinterpret_cast<real*>(smem_raw);
@@ -173,32 +168,37 @@ __global__ void k_local(const KParams<real> P) {
   }
 
   // blending coefficient alpha_e, smoothed with the face neighbours
-  double alpha = 0.0;
-  if (m.alpha_mode == 1) {
-    alpha = m.alpha_fixed;
-  } else if (m.limiter & kLimBlend) {
-    alpha = P.b.alpha_raw[ee];
+  // (computed once per element and broadcast through shared memory)
+  double* sAlpha = reinterpret_cast<double*>(
+      smem_raw + (((size_t)5 * M * epb * NP * sizeof(real) + 15) & ~(size_t)15));
+  if (k == 0) {
+    double al = 0.0;
+    if (m.alpha_mode == 1) {
+      al = m.alpha_fixed;
+    } else if (m.limiter & kLimBlend) {
+      al = P.b.alpha_raw[ee];
 #pragma unroll
-    for (int f = 0; f < NSIDE; ++f) {
-      const int nb = neighbour(m, ee, f);
-      if (nb >= 0) alpha = fmax(alpha, 0.5 * P.b.alpha_raw[nb]);
+      for (int f = 0; f < NSIDE; ++f) {
+        const int nb = neighbour(m, ee, f);
+        if (nb >= 0) al = fmax(al, 0.5 * P.b.alpha_raw[nb]);
+      }
     }
+    reinterpret_cast<real*>(sAlpha)[el] = real(al);
+    if (valid) P.b.alpha[e] = al;
   }
-  if (valid && k == 0) P.b.alpha[e] = alpha;
+  __syncthreads();
+  const real alpha = reinterpret_cast<real*>(sAlpha)[el];
   const bool blend = (m.limiter & kLimBlend) || m.alpha_mode == 1;
   const bool need_lo = blend || (m.limiter & kLimFlux);
-  const real a = blend ? real(alpha) : real(0);
+  const real a = blend ? alpha : real(0);
 
   // source: grad W at this node (time independent)
   const bool has_src = (EQ::M == 6) && m.source == 1;
   real dWx = real(0), dWy = real(0);
   if (has_src) {
-    double x = m.x0 + (ix + double(tb.xi[p])) * m.dx;
-    double y = DIM == 2 ? m.y0 + (iy + double(tb.xi[q])) * m.dy : 0.0;
-    double gx, gy;
-    source_grad<DIM>(m, x, y, &gx, &gy);
-    dWx = real(gx);
-    dWy = real(gy);
+    const double x = m.x0 + (ix + double(tb.xi[p])) * m.dx;
+    const double y = DIM == 2 ? m.y0 + (iy + double(tb.xi[q])) * m.dy : 0.0;
+    source_grad<DIM, real>(m, real(x - m.src_cx), real(DIM == 2 ? y - m.src_cy : 0.0), &dWx, &dWy);
   }
 
   // ---------------- local cRK stages -----------------------------------
@@ -211,7 +211,7 @@ __global__ void k_local(const KParams<real> P) {
 #pragma unroll
     for (int mm = 0; mm < SPT; ++mm) ea[mm][v] = real(0);
   }
-  const real invdx = real(m.invdx), invdy = real(m.invdy);
+  const real invdx = ph.invdx, invdy = ph.invdy;
 
 #pragma unroll
   for (int i = 0; i < S; ++i) {
@@ -348,7 +348,7 @@ __global__ void k_local(const KParams<real> P) {
 #pragma unroll
     for (int v = 0; v < M; ++v) xm[v] = xp[v] = ym[v] = yp[v] = un[v];
     if (m.limiter & kLimMH) {
-      const real beta = real(2.0 - alpha);
+      const real beta = real(2) - alpha;
       real um[M], up[M], sx[M], sy[M];
       // x-line neighbours (the neighbour element's node across a face; own node at outflow)
       const int nbL = p == 0 ? neighbour(m, ee, 0) : -1;
@@ -474,14 +474,13 @@ __global__ void k_local(const KParams<real> P) {
         else if (side == 1) { nb_node = N + n * j; adj_node = N - 1 + n * j; ust = sB; adj = sB; }
         else if (side == 2) { nb_node = j; adj_node = j; ust = sC; adj = sD; }
         else { nb_node = j + n * N; adj_node = j + n * (N - 1); ust = sD; adj = sD; }
-        const double c = dtd * m.cflim[side];
-        const double sgn = (side & 1) ? 1.0 : -1.0;
+        const real c = dt * real(m.cflim[side]) * ((side & 1) ? real(1) : real(-1));
 #pragma unroll
         for (int v = 0; v < M; ++v) {
           P.b.slot[slot_index(1 + 2 * M + v, side, e, j, NSIDE, m.ne, NFN)] =
               ust[v * stride + el * NP + nb_node];
           P.b.slot[slot_index(1 + 3 * M + v, side, e, j, NSIDE, m.ne, NFN)] =
-              real(double(AT(s0, v, nb_node)) + sgn * c * double(adj[v * stride + el * NP + adj_node]));
+              AT(s0, v, nb_node) + c * adj[v * stride + el * NP + adj_node];
         }
       }
     }
@@ -591,7 +590,53 @@ __global__ void k_face(const KParams<real> P) {
   for (int v = 0; v < M; ++v)
     F[v] = blend ? (1.0 - alpha_f) * double(FHO[v]) + alpha_f * double(fLO[v]) : double(FHO[v]);
   double theta = 1.0;
-  if ((m.limiter & kLimFlux) && EQ::K > 0) {
+  bool limit = (m.limiter & kLimFlux) && EQ::K > 0;
+  if (limit && sizeof(real) == 4) {
+    // FP32 prescreen: when every candidate with the blended flux clears its
+    // threshold 0.1 min P_k(candidate with f_LO) by a margin above FP32
+    // rounding, the FP64 solve below would return theta = 1; skip it.
+    const real dtf = real(P.b.ctl->dt_step_f);
+    const real cLf = dtf * real(m.cflim[dir == 0 ? 1 : 3]), cRf = dtf * real(m.cflim[dir == 0 ? 0 : 2]);
+    real Ff[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) Ff[v] = real(F[v]);
+    bool safe = true;
+#pragma unroll
+    for (int kk = 0; kk < EQ::K; ++kk) {
+      real lowL = real(0), lowR = real(0), hiL = real(0), hiR = real(0), sc = real(0);
+      real cl[M], ch[M];
+      if (eL >= 0) {
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          const real b = fld(1 + 3 * M + v, sL, eL);
+          cl[v] = b - cLf * fLO[v];
+          ch[v] = b - cLf * Ff[v];
+          sc = fmax(sc, fabs(b));
+        }
+        lowL = EQ::constraint(cl, kk, P.ph);
+        hiL = EQ::constraint(ch, kk, P.ph);
+      }
+      if (eR >= 0) {
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          const real b = fld(1 + 3 * M + v, sR, eR);
+          cl[v] = b + cRf * fLO[v];
+          ch[v] = b + cRf * Ff[v];
+          sc = fmax(sc, fabs(b));
+        }
+        lowR = EQ::constraint(cl, kk, P.ph);
+        hiR = EQ::constraint(ch, kk, P.ph);
+      }
+      const real margin = real(1e-4) * sc + real(1e-11);
+      const real lowmin = eL >= 0 ? (eR >= 0 ? fmin(lowL, lowR) : lowL) : lowR;
+      const real thr = real(0.1) * lowmin + margin;
+      if (!(lowmin > real(20) * margin)) safe = false;
+      if (eL >= 0 && !(hiL > thr)) safe = false;
+      if (eR >= 0 && !(hiR > thr)) safe = false;
+    }
+    if (safe) limit = false;
+  }
+  if (limit) {
     const double cL = dtd * m.cflim[dir == 0 ? 1 : 3], cR = dtd * m.cflim[dir == 0 ? 0 : 2];
     double baseL[M], baseR[M], flo[M];
 #pragma unroll
@@ -652,7 +697,7 @@ __global__ void k_face(const KParams<real> P) {
 
 // Smoothness indicator of one element (Hennemann form, see R6 of the readings):
 // eps at the nodes in E[el*NP + k] -> Legendre modes -> energy fractions ->
-// logistic alpha, returned on every thread of the element.  T is the
+// logistic alpha, returned on thread k = 0 of the element.  T is the
 // arithmetic type (double in FP64 mode, float in FP32_BULK mode).
 template <int DIM, int N, typename T>
 __device__ T indicator_alpha(const Mesh& m, const Tab<T>& tb, T* E, T* Tm, T* red, int epb, int el,
@@ -689,17 +734,21 @@ __device__ T indicator_alpha(const Mesh& m, const Tab<T>& tb, T* E, T* Tm, T* re
   red[(2 * epb + el) * NP + k] = mx <= N - 1 ? e2 : T(0);
   red[(3 * epb + el) * NP + k] = mx == N - 1 ? e2 : T(0);
   elem_tree<NP, 4>(red, epb, el, k, OpSum());
-  const T tot = red[(0 * epb + el) * NP], top = red[(1 * epb + el) * NP];
-  const T low = red[(2 * epb + el) * NP], top1 = red[(3 * epb + el) * NP];
-  const T r1 = tot > T(0) ? top / tot : T(0);
-  const T r2 = (N >= 2 && low > T(0)) ? top1 / low : T(0);
-  const T Ev = fmax(r1, r2);
-  const T Tt = T(m.T_ind);
-  T al = T(1) / (T(1) + exp(-T(m.s_ind) / Tt * (Ev - Tt)));
-  if (al < T(1e-3)) al = T(0);
-  if (al > T(1) - T(1e-3)) al = T(1);
+  T al = T(0);
+  if (k == 0) {
+    const T tot = red[(0 * epb + el) * NP], top = red[(1 * epb + el) * NP];
+    const T low = red[(2 * epb + el) * NP], top1 = red[(3 * epb + el) * NP];
+    const T r1 = tot > T(0) ? top / tot : T(0);
+    const T r2 = (N >= 2 && low > T(0)) ? top1 / low : T(0);
+    const T Ev = fmax(r1, r2);
+    const T Tt = T(m.T_ind);
+    al = T(1) / (T(1) + exp(-T(m.s_ind) / Tt * (Ev - Tt)));
+    if (al < T(1e-3)) al = T(0);
+    if (al > T(1) - T(1e-3)) al = T(1);
+    al = fmin(al, T(1));
+  }
   __syncthreads();  // red is reused by the caller
-  return fmin(al, T(1));
+  return al;  // valid on k == 0
 }
 
 // finish the step: block max of the CFL rate, last block publishes the rate,
@@ -719,6 +768,7 @@ __device__ __forceinline__ void finish_block(TimeCtl* ctl, double block_rate, in
         ctl->t = last_step ? ctl->t_final : ctl->t + dtd;
         ctl->steps += 1;
       }
+      plan_step(ctl);
     }
   }
 }
@@ -745,7 +795,7 @@ __device__ __forceinline__ void rate_and_finish(const Mesh& m, const Phys<T>& ph
 }
 
 // ===========================================================================
-// k_update.  Shared memory (doubles): sU [M][epb][NP] node values, sRed
+// k_update.  Shared memory (doubles): sU [MU][epb][NP] node values, sRed
 // [RW][epb][NP] reduction buffer, sEl [epb][16] per-element values.
 template <int DIM, int N, class EQ, typename real, bool MIXED>
 __global__ void k_update(const KParams<real> P) {
@@ -777,16 +827,24 @@ __global__ void k_update(const KParams<real> P) {
   double* sU = reinterpret_cast<double*>(smem_raw);  // [MU][epb][NP]
   double* sRed = sU + MU * stride;                   // [RW][epb][NP]
   double* sEl = sRed + RW * stride;                  // [epb][16]
+  // per-element area: FP64 values at sEl[el*16 + 0..9] (0..3 limiter scalars, 4..9 the
+  // FP64 mean); values in the kernel's type from double index 10 on: alpha at ER,
+  // the FP32 mean copy at ER + 1 + v
+  real* sElr = reinterpret_cast<real*>(sEl);
+  constexpr int ES = int(16 * sizeof(double) / sizeof(real));
+  constexpr int ER = int(10 * sizeof(double) / sizeof(real));
 #define ATU(v, node) sU[(v) * stride + el * NP + (node)]
 #define RED(w) sRed[((w) * epb + el) * NP + k]
 #define RED0(w) sRed[((w) * epb + el) * NP]
 
   // ---- node update: partial update + element-face flux terms ------------
-  const double alpha = P.b.alpha[ee];
   const bool blend = (m.limiter & kLimBlend) || m.alpha_mode == 1;
-  const real a = blend ? real(alpha) : real(0);
-  const real dt = real(dtd);
+  if (k == 0) sElr[el * ES + ER] = real(P.b.alpha[ee]);
+  __syncthreads();
+  const real a = blend ? sElr[el * ES + ER] : real(0);
+  const real dt = MIXED ? real(P.b.ctl->dt_step_f) : real(dtd);
   const real one = real(1);
+  const real invdx = P.ph.invdx, invdy = P.ph.invdy;
   const int ixR = m.bcx == 0 ? (ix + 1) % m.nx : ix + 1;
   const int iyT = DIM == 2 ? (m.bcy == 0 ? (iy + 1) % m.ny : iy + 1) : 0;
   const size_t nXf = (size_t)m.ny * m.nfx * NFN;
@@ -801,43 +859,72 @@ __global__ void k_update(const KParams<real> P) {
   for (int v = 0; v < M; ++v) {
     const real FxL = P.b.fx[v * nXf + ((size_t)iy * m.nfx + ix) * NFN + q];
     const real FxR = P.b.fx[v * nXf + ((size_t)iy * m.nfx + ixR) * NFN + q];
-    real x = P.b.P[((size_t)v * m.ne + ee) * NP + k] - dt * real(m.invdx) * (FxR * cRx + FxL * cLx);
-    real GB = real(0), GT = real(0);
+    real x = P.b.P[((size_t)v * m.ne + ee) * NP + k] - dt * invdx * (FxR * cRx + FxL * cLx);
     if (DIM == 2) {
-      GB = P.b.fy[v * nYf + ((size_t)iy * m.nx + ix) * n + p];
-      GT = P.b.fy[v * nYf + ((size_t)iyT * m.nx + ix) * n + p];
-      x -= dt * real(m.invdy) * (GT * cRy + GB * cLy);
+      const real GB = P.b.fy[v * nYf + ((size_t)iy * m.nx + ix) * n + p];
+      const real GT = P.b.fy[v * nYf + ((size_t)iyT * m.nx + ix) * n + p];
+      x -= dt * invdy * (GT * cRy + GB * cLy);
     }
     val[v] = x;
-    if constexpr (MIXED) {
-      // conservative FP64 mean change of eq. (upmean): this node's share of the
-      // element-face flux integrals, and the FP32 mean of the nodal update
-      double dmv = 0.0;
-      if (p == N) dmv -= dtd * m.invdx * double(DIM == 2 ? P.tb.w[q] : 1.0f) * double(FxR);
-      if (p == 0) dmv += dtd * m.invdx * double(DIM == 2 ? P.tb.w[q] : 1.0f) * double(FxL);
-      if (DIM == 2) {
-        if (q == N) dmv -= dtd * m.invdy * double(P.tb.w[p]) * double(GT);
-        if (q == 0) dmv += dtd * m.invdy * double(P.tb.w[p]) * double(GB);
-      }
-      RED(v) = dmv;
-      RED(M + v) = double(W * x);
-    } else {
-      RED(v) = double(W) * double(x);
-    }
-  }
-  elem_tree<NP, (MIXED ? 2 * M : M)>(sRed, epb, el, k, OpSum());
-  double ubar[M];
-#pragma unroll
-  for (int v = 0; v < M; ++v) {
-    if constexpr (MIXED)
-      ubar[v] = P.b.umean[(size_t)v * m.ne + ee] + RED0(v) + dtd * P.b.smean[(size_t)v * m.ne + ee];
-    else
-      ubar[v] = RED0(v);
   }
   real m32[M];
+  double ubar[M];
   if constexpr (MIXED) {
+    // FP32 mean of the nodal update (re-centring), tree sum
+    real* fRed = reinterpret_cast<real*>(sRed);
 #pragma unroll
-    for (int v = 0; v < M; ++v) m32[v] = real(RED0(M + v));
+    for (int v = 0; v < M; ++v) fRed[(v * epb + el) * NP + k] = W * val[v];
+    // element-face flux integrals sum_j w_j F_j in FP32, in a fixed order, so
+    // that the two elements of a face obtain the same value (exact telescoping
+    // of the FP64 mean update)
+    real* fI = reinterpret_cast<real*>(sU);  // [epb][NSIDE * M]
+    for (int t = k; t < NSIDE * M; t += NP) {
+      const int side = t / M, v = t - side * M;
+      real acc = real(0);
+      if (side < 2) {
+        const int fxi = side == 0 ? ix : ixR;
+#pragma unroll
+        for (int j = 0; j < NFN; ++j) {
+          const real fv = P.b.fx[v * nXf + ((size_t)iy * m.nfx + fxi) * NFN + j];
+          acc += DIM == 2 ? P.tb.w[j] * fv : fv;
+        }
+      } else {
+        const int fyi = side == 2 ? iy : iyT;
+#pragma unroll
+        for (int j = 0; j < n; ++j)
+          acc += P.tb.w[j] * P.b.fy[v * nYf + ((size_t)fyi * m.nx + ix) * n + j];
+      }
+      fI[el * NSIDE * M + t] = acc;
+    }
+    elem_tree<NP, M>(fRed, epb, el, k, OpSum());
+    // conservative FP64 mean update of eq. (upmean), one thread per variable
+    for (int v = k; v < M; v += NP) {
+      const real* I = fI + el * NSIDE * M;
+      double mv = P.b.umean[(size_t)v * m.ne + ee] + dtd * P.b.smean[(size_t)v * m.ne + ee] -
+                  dtd * m.invdx * (double(I[1 * M + v]) - double(I[0 * M + v]));
+      if (DIM == 2) mv -= dtd * m.invdy * (double(I[3 * M + v]) - double(I[2 * M + v]));
+      sEl[el * 16 + 4 + v] = mv;
+      sElr[el * ES + ER + 1 + v] = real(mv);  // copy in the kernel's type
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) m32[v] = fRed[(v * epb + el) * NP];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < M; ++v) ubar[v] = sEl[el * 16 + 4 + v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < M; ++v) RED(v) = double(W) * double(val[v]);
+    elem_tree<NP, M>(sRed, epb, el, k, OpSum());
+#pragma unroll
+    for (int v = 0; v < M; ++v) ubar[v] = RED0(v);
+  }
+  // per-element limiter scalars: sEl[el*16 + 0..3] = mean_ok, eps1, eps2, P2(u_bar)
+  if (k == 0) {
+    const double P2 = EQ::K > 0 ? EQ::constraint(ubar, 1, P.phd) : 0.0;
+    sEl[el * 16 + 0] = admissible<EQ>(ubar, P.phd) ? 1.0 : 0.0;
+    sEl[el * 16 + 1] = EQ::K > 0 ? fmin(1e-12, ubar[0]) : 0.0;
+    sEl[el * 16 + 2] = EQ::K > 0 ? fmin(1e-12, P2) : 0.0;
+    sEl[el * 16 + 3] = P2;
   }
   __syncthreads();
 
@@ -846,33 +933,30 @@ __global__ void k_update(const KParams<real> P) {
   // FP64 mean plus the re-centred FP32 fluctuation
   real fl[M];
   real ur[M];
+  real ubr[M];  // mean in the kernel's type
 #pragma unroll
   for (int v = 0; v < M; ++v) {
+    if constexpr (MIXED) ubr[v] = sElr[el * ES + ER + 1 + v];
+    else ubr[v] = real(ubar[v]);
     if constexpr (MIXED) {
       fl[v] = val[v] - m32[v];
-      ur[v] = real(ubar[v]) + fl[v];
+      ur[v] = ubr[v] + fl[v];
     } else {
       ur[v] = val[v];
     }
   }
   int bad = 0;
-  if (k == 0) {
-    const double mean_ok = admissible<EQ>(ubar, P.phd) ? 1.0 : 0.0;
-    sEl[el * 16 + 0] = mean_ok;
-    sEl[el * 16 + 1] = EQ::K > 0 ? fmin(1e-12, ubar[0]) : 0.0;                           // eps1
-    sEl[el * 16 + 2] = EQ::K > 0 ? fmin(1e-12, EQ::constraint(ubar, 1, P.phd)) : 0.0;     // eps2
-    sEl[el * 16 + 3] = EQ::K > 0 ? EQ::constraint(ubar, 1, P.phd) : 0.0;                  // P2(u_bar)
-  }
-  __syncthreads();
   const bool mean_ok = sEl[el * 16 + 0] != 0.0;
   if (EQ::K > 0 && !mean_ok) bad |= kStInadmissible;
   const bool do_scale = (m.limiter & kLimScaling) && EQ::K > 0;
   const bool traces = (m.limiter & kLimTraces) != 0;
+  real* sUr = reinterpret_cast<real*>(sU);  // node values in the kernel's type
 #pragma unroll
-  for (int v = 0; v < M; ++v) ATU(v, k) = double(ur[v]);
+  for (int v = 0; v < M; ++v) sUr[v * stride + el * NP + k] = ur[v];
   __syncthreads();
   if (do_scale) {
-    const double eps1 = sEl[el * 16 + 1], eps2 = sEl[el * 16 + 2], P2bar = sEl[el * 16 + 3];
+    const double eps1 = sEl[el * 16 + 1], eps2 = sEl[el * 16 + 2];
+    const real P2r = real(sEl[el * 16 + 3]);
     // points this thread checks: its node and its face-trace slots
     real pr[1 + SPT][M];
     int npt = 1;
@@ -890,7 +974,7 @@ __global__ void k_update(const KParams<real> P) {
 #pragma unroll
             for (int r = 0; r < n; ++r) {
               const real l = (side & 1) ? P.tb.l1[r] : P.tb.l0[r];
-              acc += l * real(ATU(v, side < 2 ? r + n * j : j + n * r));
+              acc += l * sUr[v * stride + el * NP + (side < 2 ? r + n * j : j + n * r)];
             }
             pr[npt][v] = acc;
           }
@@ -904,10 +988,9 @@ __global__ void k_update(const KParams<real> P) {
     int need = 0;
     for (int t = 0; t < npt; ++t) {
       if constexpr (MIXED) {
-        const real scale = real(EQ::M == 6 ? fabs(double(pr[t][3])) + fabs(double(pr[t][5]))
-                                           : fabs(double(pr[t][M - 1])));
-        const real thr = fmax(fmax(real(1e-3) * real(P2bar), real(1e-5) * scale), real(1e-11));
-        if (!(pr[t][0] > real(1e-3) * real(ubar[0]) && EQ::constraint(pr[t], 1, P.ph) > thr)) need = 1;
+        const real scale = EQ::M == 6 ? fabs(pr[t][3]) + fabs(pr[t][5]) : fabs(pr[t][M - 1]);
+        const real thr = fmax(fmax(real(1e-3) * P2r, real(1e-5) * scale), real(1e-11));
+        if (!(pr[t][0] > real(1e-3) * ubr[0] && EQ::constraint(pr[t], 1, P.ph) > thr)) need = 1;
       } else {
         if (!(pr[t][0] >= eps1 && EQ::constraint(pr[t], 1, P.phd) >= eps2)) need = 1;
       }
@@ -916,8 +999,15 @@ __global__ void k_update(const KParams<real> P) {
       // FP64 path (oracle's limiter): points in FP64
       double pts[1 + SPT][M];
       int np2 = 1;
+      __syncthreads();
 #pragma unroll
-      for (int v = 0; v < M; ++v) pts[0][v] = ATU(v, k);
+      for (int v = 0; v < M; ++v) {
+        if constexpr (MIXED) pts[0][v] = ubar[v] + double(fl[v]);
+        else pts[0][v] = double(ur[v]);
+      }
+#pragma unroll
+      for (int v = 0; v < M; ++v) ATU(v, k) = pts[0][v];
+      __syncthreads();
       if (traces) {
 #pragma unroll
         for (int mm = 0; mm < SPT; ++mm) {
@@ -1025,10 +1115,7 @@ __global__ void k_update(const KParams<real> P) {
   }
   __syncthreads();
   if constexpr (MIXED) {
-    float ubf[M];
-#pragma unroll
-    for (int v = 0; v < M; ++v) ubf[v] = float(ubar[v]);
-    rate_and_finish<DIM, NP, EQ, float>(m, P.ph, ubf, reinterpret_cast<float*>(sEl), epb, el, k,
+    rate_and_finish<DIM, NP, EQ, float>(m, P.ph, ubr, reinterpret_cast<float*>(sEl), epb, el, k,
                                         valid, P.b.ctl, 1, dtd, last_step);
   } else {
     rate_and_finish<DIM, NP, EQ, double>(m, P.phd, ubar, sEl, epb, el, k, valid, P.b.ctl, 1, dtd,

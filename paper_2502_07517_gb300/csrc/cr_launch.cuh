@@ -29,7 +29,9 @@ struct Impl {
   // elements per block: about 256 threads per block (at least one element)
   static constexpr int EPB = (256 / NP) > 0 ? (256 / NP) : 1;
 
-  static size_t smem_local(int epb) { return (size_t)5 * M * epb * NP * sizeof(real); }
+  static size_t smem_local(int epb) {
+    return (((size_t)5 * M * epb * NP * sizeof(real) + 15) & ~(size_t)15) + (size_t)epb * sizeof(double);
+  }
   static constexpr int RW = 2 * M > 4 ? 2 * M : 4;
   static constexpr int MU = M > 2 ? M : 2;
   static size_t smem_update(int epb) {

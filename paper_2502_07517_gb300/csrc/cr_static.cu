@@ -51,6 +51,7 @@ __global__ void k_static_reset(TimeCtl* c, double dt) {
   c->bad_elem = INT_MAX;
   c->steps = 0;
   c->dt_step = 0.0;
+  c->dt_step_f = 0.0f;
   c->last_step = 0;
 }
 
@@ -210,6 +211,8 @@ extern "C" cr_status cr_step_static(const cr_mesh_desc* d, const double* u_in, d
   P.ph.gm1 = d->gamma - 1.0;
   P.ph.ax = d->adv[0];
   P.ph.ay = d->adv[1];
+  P.ph.invdx = m.invdx;
+  P.ph.invdy = m.invdy;
   P.phd = P.ph;
   static_tables(d->degree, &P.tb);
   P.td = P.tb;
