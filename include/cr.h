@@ -58,7 +58,13 @@ enum {
   CR_LIM_SCALING = 8, /* Zhang-Shu positivity scaling after the update, Sec. 3.2 */
   CR_LIM_TRACES = 16  /* the scaling limiter also checks the element-face traces */
 };
-enum { CR_ALPHA_INDICATOR = 0, CR_ALPHA_FIXED = 1 };
+enum {
+  CR_ALPHA_INDICATOR = 0, /* smoothness indicator of Sec. 4 (Hennemann form) */
+  CR_ALPHA_FIXED = 1,     /* alpha_e = alpha_fixed everywhere (tests) */
+  CR_ALPHA_MLP = 2        /* learned network on the indicator's modal energies (not in the
+                             paper); the indicator is the fallback when no network is loaded
+                             or its output is not finite */
+};
 enum { CR_FP64 = 0, CR_FP32_BULK = 1 };
 
 typedef struct {
@@ -114,8 +120,10 @@ cr_status cr_get_state(cr_ctx* ctx, double* u, int on_device);
  * (time.step.2d) on the current element means, or is dt_fixed when
  * dt_fixed > 0; the last step is shortened to land exactly on t_final.
  * Synchronises and returns the time reached and the number of steps taken
- * (either pointer may be NULL).  Errors: CR_E_INADMISSIBLE (the step that
- * failed is counted; the state is the failed step's output). */
+ * (either pointer may be NULL).  Steps are enqueued in growing chunks and
+ * launching stops once t_final is reached, so max_steps may be generous.
+ * Errors: CR_E_INADMISSIBLE (the step that failed is counted; the state is
+ * the failed step's output). */
 cr_status cr_step(cr_ctx* ctx, int max_steps, double t_final, double dt_fixed, double* t_out,
                   int* steps_out);
 
@@ -128,6 +136,41 @@ cr_status cr_sync(cr_ctx* ctx, double* t_out, int* steps_out);
 /* alpha_e (after neighbour smoothing) used by the most recent step, [Ne]
  * FP64.  Synchronises when on_device == 0. */
 cr_status cr_get_alpha(cr_ctx* ctx, double* alpha, int on_device);
+
+/* Learned blending coefficient (not in the paper: a small network replaces
+ * the last step of the smoothness indicator, Sec. 4).  Inputs: the element's
+ * normalised modal energies e_k = m_k^2 / sum m^2 of the indicator variable,
+ * k = i + (N+1) j (Np of them), encoded x_k = log10(e_k + 1e-10)/10 + 1;
+ * two hidden layers of 32 ReLU units and a sigmoid output, clipped like the
+ * indicator (< 1e-3 -> 0, > 1 - 1e-3 -> 1) and then smoothed as usual.
+ * Parameter vector (FP32): W1[32][Np], b1[32], W2[32][32], b2[32], w3[32], b3.
+ * cr_mlp_param_count(Np) gives its length (-1 if Np is not 2,3,4,5,9,16,25). */
+int cr_mlp_param_count(int nin);
+
+/* Load network parameters into a context (stored as BF16, evaluated in FP32).
+ * Used when desc.alpha_mode == CR_ALPHA_MLP.  Synchronises.
+ * Errors: CR_E_INVALID_ARG (wrong count, NaN). */
+cr_status cr_mlp_load(cr_ctx* ctx, const float* params, int nparams);
+
+/* Network inputs x[Ne][Np] (FP32) of the current state and the raw alpha
+ * [Ne] (before neighbour smoothing) under the context's alpha mode; either
+ * pointer may be NULL.  Synchronises when on_device == 0. */
+cr_status cr_get_features(cr_ctx* ctx, float* features, double* alpha_raw, int on_device);
+
+/* Mean squared error of the network on samples X[n][nin], targets t[n] and
+ * its gradient (same layout as the parameters), on the GPU.  All pointers are
+ * device pointers; grad and loss are overwritten.  Ordered on stream. */
+cr_status cr_mlp_grad(int nin, const float* params, const float* X, const float* t, int n,
+                      float* grad, float* loss, void* stream);
+
+/* Train the network in place (params: device pointer) with Adam (beta 0.9,
+ * 0.999, eps 1e-8, learning rate lr) on minibatches of size batch from a
+ * seeded shuffle of X[n][nin], t[n] (device), for the given number of epochs.
+ * epoch_loss (host, may be NULL) receives the mean loss of the last epoch.
+ * Allocates its own device scratch; synchronises stream. */
+cr_status cr_mlp_train(int nin, float* params, const float* X, const float* t, int n, int batch,
+                       int epochs, float lr, unsigned long long seed, float* epoch_loss,
+                       void* stream);
 
 /* Element means u_bar_e = sum_k W_k u_{e,k} (Sec. 3.2 eq. (upmean)), FP64
  * [M][Ne].  In CR_FP32_BULK mode these are the FP64 means the scheme updates

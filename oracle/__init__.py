@@ -19,7 +19,7 @@ EQ_LINADV, EQ_EULER, EQ_TENMOMENT = 0, 1, 2
 BC_PERIODIC, BC_OUTFLOW = 0, 1
 LIM_BLEND, LIM_MH, LIM_FLUX, LIM_SCALING, LIM_TRACES = 1, 2, 4, 8, 16
 LIM_ALL = LIM_BLEND | LIM_MH | LIM_FLUX | LIM_SCALING | LIM_TRACES
-ALPHA_INDICATOR, ALPHA_FIXED = 0, 1
+ALPHA_INDICATOR, ALPHA_FIXED, ALPHA_GIVEN = 0, 1, 2
 
 
 class Desc(ctypes.Structure):
@@ -36,6 +36,7 @@ class Desc(ctypes.Structure):
         ("limiter", ctypes.c_int), ("alpha_mode", ctypes.c_int),
         ("alpha_fixed", ctypes.c_double),
         ("cfl", ctypes.c_double), ("cfl_safety", ctypes.c_double),
+        ("alpha_given", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -70,6 +71,8 @@ def lib():
         _lib.or_local_crk.argtypes = [P, D, ctypes.c_double, ctypes.c_int, ctypes.c_int, D, D, D, D]
         _lib.or_indicator.argtypes = [P, D]
         _lib.or_indicator.restype = ctypes.c_double
+        _lib.or_modal_energies.argtypes = [P, D, D]
+        _lib.or_modal_energies.restype = None
         _lib.or_max_rate.argtypes = [P, D]
         _lib.or_max_rate.restype = ctypes.c_double
         _lib.or_dt.argtypes = [P, D]
@@ -92,8 +95,11 @@ def _ptr(a):
 def make_desc(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=BC_PERIODIC,
               bc_y=BC_PERIODIC, degree=3, equation=EQ_LINADV, gamma=1.4, adv=(1.0, 0.0),
               source=0, src_amp=0.0, src_k=0.0, src_cx=0.5, src_cy=0.5, limiter=0,
-              alpha_mode=ALPHA_INDICATOR, alpha_fixed=0.0, cfl=None, cfl_safety=0.98):
-    """Mesh/scheme description; cfl defaults to CFL(degree) from the Fourier analysis."""
+              alpha_mode=ALPHA_INDICATOR, alpha_fixed=0.0, cfl=None, cfl_safety=0.98,
+              alpha_given=None):
+    """Mesh/scheme description; cfl defaults to CFL(degree) from the Fourier analysis.
+    alpha_given: per-element raw alpha array for alpha_mode ALPHA_GIVEN (kept alive on
+    the returned object)."""
     if cfl is None:
         from .cfl import cfl_number
         cfl = cfl_number(degree)
@@ -106,6 +112,11 @@ def make_desc(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=BC_PERIOD
     d.source, d.src_amp, d.src_k, d.src_cx, d.src_cy = source, src_amp, src_k, src_cx, src_cy
     d.limiter, d.alpha_mode, d.alpha_fixed = limiter, alpha_mode, alpha_fixed
     d.cfl, d.cfl_safety = cfl, cfl_safety
+    if alpha_given is not None:
+        arr = np.ascontiguousarray(alpha_given, dtype=np.float64)
+        d._alpha_given_keep = arr
+        d.alpha_given = _ptr(arr)
+        d.alpha_mode = ALPHA_GIVEN
     return d
 
 
@@ -180,6 +191,14 @@ def local_crk(d, ue, dt, ix=0, iy=0):
 def indicator(d, ue):
     ue = np.ascontiguousarray(ue, dtype=np.float64)
     return lib().or_indicator(ctypes.byref(d), _ptr(ue))
+
+
+def modal_energies(d, ue):
+    """Normalised modal energies of one element's indicator variable; ue [Np][M]."""
+    ue = np.ascontiguousarray(ue, dtype=np.float64)
+    e = np.zeros(nodes(d))
+    lib().or_modal_energies(ctypes.byref(d), _ptr(ue), _ptr(e))
+    return e
 
 
 def max_rate(d, u):

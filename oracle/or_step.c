@@ -232,6 +232,29 @@ static double indicator_variable(const or_desc* d, const double* u) {
   return rho * 0.5 * (p11 + p22);
 }
 
+void or_modal_energies(const or_desc* d, const double* ue, double* e) {
+  ctx c;
+  ctx_init(&c, d);
+  const int n = c.n;
+  double eps[NPMAX], m[NPMAX], tot = 0.0;
+  for (int k = 0; k < c.np; ++k) eps[k] = indicator_variable(d, ue + k * c.M);
+  for (int k = 0; k < c.np; ++k) {
+    int i = k % n, j = k / n;
+    double acc = 0.0;
+    if (c.dim == 1) {
+      for (int p = 0; p < n; ++p) acc += c.w[p] * eps[p] * legendre01(i, c.xi[p]);
+      m[k] = (2.0 * i + 1.0) * acc;
+    } else {
+      for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q)
+          acc += c.w[p] * c.w[q] * eps[node(&c, p, q)] * legendre01(i, c.xi[p]) * legendre01(j, c.xi[q]);
+      m[k] = (2.0 * i + 1.0) * (2.0 * j + 1.0) * acc;
+    }
+    tot += m[k] * m[k];
+  }
+  for (int k = 0; k < c.np; ++k) e[k] = tot > 0.0 ? m[k] * m[k] / tot : 0.0;
+}
+
 double or_indicator(const or_desc* d, const double* ue) {
   ctx c;
   ctx_init(&c, d);
@@ -612,8 +635,9 @@ int or_step(const or_desc* d, const double* u_in, double dt, double* u_out, or_d
    *    smoothed as alpha_e <- max(alpha_e, max_neighbour alpha / 2) (reading) */
   for (int e = 0; e < ne; ++e) {
     if (d->alpha_mode == OR_ALPHA_FIXED) alpha_raw[e] = d->alpha_fixed;
-    else if (d->limiter & OR_LIM_BLEND) { gather(&c, u_in, e, ue); alpha_raw[e] = or_indicator(d, ue); }
-    else alpha_raw[e] = 0.0;
+    else if (!(d->limiter & OR_LIM_BLEND)) alpha_raw[e] = 0.0;
+    else if (d->alpha_mode == OR_ALPHA_GIVEN) alpha_raw[e] = d->alpha_given[e];
+    else { gather(&c, u_in, e, ue); alpha_raw[e] = or_indicator(d, ue); }
   }
   for (int e = 0; e < ne; ++e) {
     double a = alpha_raw[e];

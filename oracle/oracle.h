@@ -36,7 +36,7 @@ enum {
   OR_LIM_SCALING = 8,  /* Zhang-Shu positivity scaling, Sec. 3.2 */
   OR_LIM_TRACES = 16   /* scaling limiter also enforces admissibility at face traces */
 };
-enum { OR_ALPHA_INDICATOR = 0, OR_ALPHA_FIXED = 1 };
+enum { OR_ALPHA_INDICATOR = 0, OR_ALPHA_FIXED = 1, OR_ALPHA_GIVEN = 2 };
 
 typedef struct {
   int dim;                 /* 1 or 2 */
@@ -54,6 +54,7 @@ typedef struct {
   double alpha_fixed;      /* alpha_e when alpha_mode == OR_ALPHA_FIXED */
   double cfl;              /* CFL(N) of Sec. 5 eq. (time.step.2d) */
   double cfl_safety;       /* C_s */
+  const double* alpha_given; /* [Ne] raw alpha_e (before smoothing) when alpha_mode == OR_ALPHA_GIVEN */
 } or_desc;
 
 /* Optional outputs of or_step; any pointer may be NULL. */
@@ -94,6 +95,10 @@ void or_local_crk(const or_desc* d, const double* ue, double dt, int ix, int iy,
 
 /* Smoothness indicator alpha of one element from its nodal values [Np][M]. */
 double or_indicator(const or_desc* d, const double* ue);
+/* Normalised modal energies e_k = m_k^2 / sum_j m_j^2 of the indicator variable
+ * of one element (mode k = i + (N+1) j in 2D, k = i in 1D); all zero when the
+ * sum is zero.  These are the inputs of the learned blending coefficient. */
+void or_modal_energies(const or_desc* d, const double* ue, double* e);
 
 /* max_e (sigma_x(mean_e)/dx + sigma_y(mean_e)/dy), Sec. 5 eq. (time.step.2d) */
 double or_max_rate(const or_desc* d, const double* u);

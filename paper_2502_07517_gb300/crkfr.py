@@ -20,14 +20,15 @@ STATUS = {0: "CR_OK", -1: "CR_E_INVALID_ARG", -2: "CR_E_INVALID_STATE", -3: "CR_
 CR_EQ_LINADV, CR_EQ_EULER, CR_EQ_TENMOMENT = 0, 1, 2
 CR_BC_PERIODIC, CR_BC_OUTFLOW = 0, 1
 CR_LIM_BLEND, CR_LIM_MH, CR_LIM_FLUX, CR_LIM_SCALING, CR_LIM_TRACES = 1, 2, 4, 8, 16
-CR_ALPHA_INDICATOR, CR_ALPHA_FIXED = 0, 1
+CR_ALPHA_INDICATOR, CR_ALPHA_FIXED, CR_ALPHA_MLP = 0, 1, 2
 CR_FP64, CR_FP32_BULK = 0, 1
 
 # C symbols declared in include/cr.h
 SYMBOLS = ("cr_workspace_bytes", "cr_init_mesh", "cr_destroy", "cr_set_state", "cr_get_state",
            "cr_step", "cr_step_async", "cr_sync", "cr_get_alpha", "cr_get_means", "cr_next_dt",
            "cr_launches_per_step", "cr_profile_steps", "cr_cfl_number", "cr_reference_tables",
-           "cr_step_static", "cr_last_error")
+           "cr_step_static", "cr_last_error", "cr_mlp_param_count", "cr_mlp_load",
+           "cr_get_features", "cr_mlp_grad", "cr_mlp_train")
 
 
 class CrError(RuntimeError):
@@ -84,6 +85,12 @@ def lib():
         L.cr_cfl_number.argtypes = [I, D]
         L.cr_reference_tables.argtypes = [I, D, D, D]
         L.cr_step_static.argtypes = [P, V, V, ctypes.c_double]
+        F = ctypes.POINTER(ctypes.c_float)
+        L.cr_mlp_param_count.argtypes = [I]
+        L.cr_mlp_load.argtypes = [V, F, I]
+        L.cr_get_features.argtypes = [V, V, V, I]
+        L.cr_mlp_grad.argtypes = [I, V, V, V, I, V, V, V]
+        L.cr_mlp_train.argtypes = [I, V, V, V, I, I, I, ctypes.c_float, ctypes.c_ulonglong, F, V]
         L.cr_last_error.argtypes = [V]
         L.cr_last_error.restype = ctypes.c_char_p
         for s in SYMBOLS:
@@ -240,6 +247,51 @@ def cr_step_static(desc, u_in, u_out, dt):
     st = lib().cr_step_static(ctypes.byref(desc), u_in.data_ptr(), u_out.data_ptr(), float(dt))
     if st != CR_OK:
         raise CrError(st, "cr_step_static")
+
+
+def cr_mlp_param_count(nin):
+    return lib().cr_mlp_param_count(int(nin))
+
+
+def cr_mlp_load(ctx, params):
+    """Load the learned-alpha network (FP32 parameter vector; stored as BF16)."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib().cr_mlp_load(ctx.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size),
+           ctx.handle)
+
+
+def cr_get_features(ctx, ne, npts):
+    """(features [Ne][Np] float32, raw alpha [Ne] float64) of the current state."""
+    f = np.empty((ne, npts), dtype=np.float32)
+    a = np.empty(ne, dtype=np.float64)
+    _check(lib().cr_get_features(ctx.handle, f.ctypes.data, a.ctypes.data, 0), ctx.handle)
+    return f, a
+
+
+def cr_get_features_device(ctx, feat, alpha_raw=None):
+    """Device variant: feat is a float32 CUDA tensor [Ne][Np]; alpha_raw an
+    optional float64 CUDA tensor [Ne]."""
+    _check(lib().cr_get_features(ctx.handle, feat.data_ptr(),
+                                 alpha_raw.data_ptr() if alpha_raw is not None else None, 1),
+           ctx.handle)
+
+
+def cr_mlp_grad(nin, params, X, t, grad, loss, stream=None):
+    """Loss and gradient on device tensors (float32): params [P], X [n][nin], t [n]."""
+    st = lib().cr_mlp_grad(int(nin), params.data_ptr(), X.data_ptr(), t.data_ptr(), int(t.numel()),
+                           grad.data_ptr(), loss.data_ptr(), stream)
+    if st != CR_OK:
+        raise CrError(st, "cr_mlp_grad")
+
+
+def cr_mlp_train(nin, params, X, t, batch, epochs, lr, seed=0, stream=None):
+    """Adam training in place on device tensors; returns the last epoch's mean loss."""
+    out = ctypes.c_float()
+    st = lib().cr_mlp_train(int(nin), params.data_ptr(), X.data_ptr(), t.data_ptr(), int(t.numel()),
+                            int(batch), int(epochs), float(lr), int(seed), ctypes.byref(out), stream)
+    if st != CR_OK:
+        raise CrError(st, "cr_mlp_train")
+    return out.value
 
 
 def cr_last_error(ctx=None):

@@ -74,7 +74,7 @@ struct Mesh {
   int bcx, bcy;              // 0 periodic, 1 outflow
   double x0, y0, dx, dy, invdx, invdy;
   int limiter;               // CR_LIM_* bits
-  int alpha_mode;            // 0 indicator, 1 fixed
+  int alpha_mode;            // 0 indicator, 1 fixed, 2 learned (network, indicator fallback)
   double alpha_fixed;
   double gamma, ax, ay;
   int source;
@@ -100,6 +100,9 @@ struct Bufs {
   double* alpha_raw; // indicator alpha of the current state [Ne]
   double* alpha;     // smoothed alpha used by the last step [Ne]
   TimeCtl* ctl;
+  const int* mlp_flag;              // != 0 once network weights are loaded
+  const unsigned short* mlp_w;      // BF16 network weights (learned alpha)
+  float* feat;                      // when not null, the prologue writes network inputs [Ne][Np]
 };
 
 // Physical constants in the arithmetic type of the kernel (no FP64 work leaks

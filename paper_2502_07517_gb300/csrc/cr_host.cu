@@ -9,6 +9,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/cr.h"
 #include "cr_launch.cuh"
@@ -270,7 +271,7 @@ __global__ void k_set_run(TimeCtl* c, double t_final, double dt_fixed) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t ctl, u, umean, umean_f, P, smean, slot, fx, fy, alpha_raw, alpha, staging, total;
+  size_t ctl, u, umean, umean_f, P, smean, slot, fx, fy, alpha_raw, alpha, mlp, staging, total;
 };
 
 int nvars_of(const cr_mesh_desc* d) {
@@ -306,6 +307,7 @@ Layout layout_of(const cr_mesh_desc* d) {
   L.fy = take(dim == 2 ? M * nfy * nx * n * rs : 0);
   L.alpha_raw = take(ne * sizeof(double));
   L.alpha = take(ne * sizeof(double));
+  L.mlp = take(16 + 2 * (size_t)(32 * np + 32 + 32 * 32 + 32 + 32 + 1));  // flag + BF16 weights
   L.staging = take(mixed ? M * ne * np * sizeof(double) : 0);
   L.total = off;
   return L;
@@ -333,7 +335,8 @@ const char* check_desc(const cr_mesh_desc* d) {
   if (d->equation < 0 || d->equation > 2) return "unknown equation";
   if (d->equation == CR_EQ_EULER && !(d->gamma > 1.0)) return "gamma must be > 1";
   if (d->precision != CR_FP64 && d->precision != CR_FP32_BULK) return "unknown precision";
-  if (d->alpha_mode != CR_ALPHA_INDICATOR && d->alpha_mode != CR_ALPHA_FIXED)
+  if (d->alpha_mode != CR_ALPHA_INDICATOR && d->alpha_mode != CR_ALPHA_FIXED &&
+      d->alpha_mode != CR_ALPHA_MLP)
     return "unknown alpha mode";
   if (d->alpha_mode == CR_ALPHA_FIXED && !(d->alpha_fixed >= 0.0 && d->alpha_fixed <= 1.0))
     return "alpha_fixed must be in [0,1]";
@@ -450,6 +453,9 @@ void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
   b.fy = reinterpret_cast<real*>(w + c->L.fy);
   b.alpha_raw = reinterpret_cast<double*>(w + c->L.alpha_raw);
   b.alpha = reinterpret_cast<double*>(w + c->L.alpha);
+  b.mlp_flag = reinterpret_cast<const int*>(w + c->L.mlp);
+  b.mlp_w = reinterpret_cast<const unsigned short*>(w + c->L.mlp + 16);
+  b.feat = nullptr;
 }
 
 cr_status read_ctl(cr_ctx* c) {
@@ -483,6 +489,24 @@ cr_status build_graphs(cr_ctx* c) {
       return CR_OK;
     }
     (which == 0 ? c->g1 : c->g8) = ex;
+  }
+  return CR_OK;
+}
+
+// Enqueue n steps (graphs of 8 and 1 steps; direct launches if capture failed).
+// A step whose planned dt is 0 (run finished or failed) does no work.
+cr_status launch_steps(cr_ctx* c, int n) {
+  while (n > 0) {
+    if (n >= 8 && c->g8) {
+      CR_CUDA(c, cudaGraphLaunch(c->g8, c->stream));
+      n -= 8;
+    } else if (c->g1) {
+      CR_CUDA(c, cudaGraphLaunch(c->g1, c->stream));
+      n -= 1;
+    } else {
+      CR_CUDA(c, c->ks->step(c->params, c->stream));
+      n -= 1;
+    }
   }
   return CR_OK;
 }
@@ -574,6 +598,8 @@ cr_status cr_init_mesh(const cr_mesh_desc* desc, void* workspace, size_t workspa
   k_reset_ctl<<<1, 1, 0, c->stream>>>(c->d_ctl, c->d.cfl_safety * c->cfl);
   e = cudaGetLastError();
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "k_reset_ctl"));
+  e = cudaMemsetAsync(c->ws + c->L.mlp, 0, 16, c->stream);  // no network loaded
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemsetAsync"));
   *out = c;
   return CR_OK;
 }
@@ -636,20 +662,7 @@ cr_status cr_step_async(cr_ctx* c, int max_steps, double t_final, double dt_fixe
   }
   k_set_run<<<1, 1, 0, c->stream>>>(c->d_ctl, t_final, dt_fixed);
   CR_CUDA(c, cudaGetLastError());
-  int left = max_steps;
-  while (left > 0) {
-    if (left >= 8 && c->g8) {
-      CR_CUDA(c, cudaGraphLaunch(c->g8, c->stream));
-      left -= 8;
-    } else if (c->g1) {
-      CR_CUDA(c, cudaGraphLaunch(c->g1, c->stream));
-      left -= 1;
-    } else {
-      CR_CUDA(c, c->ks->step(c->params, c->stream));
-      left -= 1;
-    }
-  }
-  return CR_OK;
+  return launch_steps(c, max_steps);
 }
 
 cr_status cr_profile_steps(cr_ctx* c, int max_steps, double t_final, double dt_fixed,
@@ -693,8 +706,23 @@ cr_status cr_sync(cr_ctx* c, double* t_out, int* steps_out) {
 
 cr_status cr_step(cr_ctx* c, int max_steps, double t_final, double dt_fixed, double* t_out,
                   int* steps_out) {
-  cr_status st = cr_step_async(c, max_steps, t_final, dt_fixed);
+  // Steps go out in chunks of 64, 128, ... 4096; between chunks the time
+  // record is read back, and launching stops once the run has reached
+  // t_final or failed, so a generous max_steps costs nothing extra.
+  const int first = max_steps < 64 ? max_steps : 64;
+  cr_status st = cr_step_async(c, first, t_final, dt_fixed);
   if (st != CR_OK) return st;
+  int left = max_steps - first, chunk = 64;
+  while (left > 0) {
+    st = read_ctl(c);
+    if (st != CR_OK) return st;
+    if (c->h_ctl->status != 0 || !(c->h_ctl->dt_step > 0.0)) break;
+    chunk = chunk < 4096 ? 2 * chunk : chunk;
+    const int n = left < chunk ? left : chunk;
+    st = launch_steps(c, n);
+    if (st != CR_OK) return st;
+    left -= n;
+  }
   return cr_sync(c, t_out, steps_out);
 }
 
@@ -703,6 +731,51 @@ cr_status cr_get_alpha(cr_ctx* c, double* alpha, int on_device) {
   const size_t ne = (size_t)c->d.nx * (c->d.dim == 2 ? c->d.ny : 1);
   CR_CUDA(c, cudaMemcpyAsync(alpha, c->ws + c->L.alpha, ne * sizeof(double), cudaMemcpyDefault,
                              c->stream));
+  if (!on_device) CR_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CR_OK;
+}
+
+cr_status cr_mlp_load(cr_ctx* c, const float* params, int nparams) {
+  if (!c || !params) return fail(c, CR_E_INVALID_ARG, "NULL argument");
+  const int np = c->ks->nodes;
+  const int want = 32 * np + 32 + 32 * 32 + 32 + 32 + 1;
+  if (nparams != want)
+    return fail(c, CR_E_INVALID_ARG, "expected " + std::to_string(want) + " network parameters");
+  std::vector<unsigned short> h(nparams);
+  for (int i = 0; i < nparams; ++i) {  // FP32 -> BF16, round to nearest even
+    uint32_t b;
+    memcpy(&b, &params[i], 4);
+    if ((b & 0x7f800000u) == 0x7f800000u && (b & 0x007fffffu)) return fail(c, CR_E_INVALID_ARG, "NaN parameter");
+    b += 0x7fffu + ((b >> 16) & 1u);
+    h[i] = (unsigned short)(b >> 16);
+  }
+  const int one = 1;
+  CR_CUDA(c, cudaMemcpyAsync(c->ws + c->L.mlp + 16, h.data(), h.size() * 2, cudaMemcpyHostToDevice, c->stream));
+  CR_CUDA(c, cudaMemcpyAsync(c->ws + c->L.mlp, &one, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CR_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CR_OK;
+}
+
+cr_status cr_get_features(cr_ctx* c, float* features, double* alpha_raw, int on_device) {
+  if (!c || (!features && !alpha_raw)) return fail(c, CR_E_INVALID_ARG, "NULL argument");
+  const size_t ne = (size_t)c->d.nx * (c->d.dim == 2 ? c->d.ny : 1);
+  const size_t nf = ne * c->ks->nodes;
+  float* staging = reinterpret_cast<float*>(c->ws + c->L.P);  // P is free between steps
+  cudaError_t e;
+  if (c->ks->mixed) {
+    KParams<float> P = c->pf;
+    P.b.feat = staging;
+    e = c->ks->prologue(&P, c->stream);
+  } else {
+    KParams<double> P = c->pd;
+    P.b.feat = staging;
+    e = c->ks->prologue(&P, c->stream);
+  }
+  CR_CUDA(c, e);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (features) CR_CUDA(c, cudaMemcpyAsync(features, staging, nf * sizeof(float), kind, c->stream));
+  if (alpha_raw)
+    CR_CUDA(c, cudaMemcpyAsync(alpha_raw, c->ws + c->L.alpha_raw, ne * sizeof(double), kind, c->stream));
   if (!on_device) CR_CUDA(c, cudaStreamSynchronize(c->stream));
   return CR_OK;
 }

@@ -585,10 +585,11 @@ __global__ void k_face(const KParams<real> P) {
     }
     alpha_f = P.b.alpha[ei];
   }
-  double F[M];
+  // blended flux of eq. (Fblend) in the kernel's type
+  const real af = real(alpha_f);
+  real Fr[M];
 #pragma unroll
-  for (int v = 0; v < M; ++v)
-    F[v] = blend ? (1.0 - alpha_f) * double(FHO[v]) + alpha_f * double(fLO[v]) : double(FHO[v]);
+  for (int v = 0; v < M; ++v) Fr[v] = blend ? (real(1) - af) * FHO[v] + af * fLO[v] : FHO[v];
   double theta = 1.0;
   bool limit = (m.limiter & kLimFlux) && EQ::K > 0;
   if (limit && sizeof(real) == 4) {
@@ -597,9 +598,7 @@ __global__ void k_face(const KParams<real> P) {
     // rounding, the FP64 solve below would return theta = 1; skip it.
     const real dtf = real(P.b.ctl->dt_step_f);
     const real cLf = dtf * real(m.cflim[dir == 0 ? 1 : 3]), cRf = dtf * real(m.cflim[dir == 0 ? 0 : 2]);
-    real Ff[M];
-#pragma unroll
-    for (int v = 0; v < M; ++v) Ff[v] = real(F[v]);
+    const real* Ff = Fr;
     bool safe = true;
 #pragma unroll
     for (int kk = 0; kk < EQ::K; ++kk) {
@@ -638,7 +637,9 @@ __global__ void k_face(const KParams<real> P) {
   }
   if (limit) {
     const double cL = dtd * m.cflim[dir == 0 ? 1 : 3], cR = dtd * m.cflim[dir == 0 ? 0 : 2];
-    double baseL[M], baseR[M], flo[M];
+    double baseL[M], baseR[M], flo[M], F[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) F[v] = double(Fr[v]);
 #pragma unroll
     for (int v = 0; v < M; ++v) {
       baseL[v] = eL >= 0 ? double(fld(1 + 3 * M + v, sL, eL)) : 0.0;
@@ -683,10 +684,10 @@ __global__ void k_face(const KParams<real> P) {
       theta *= tk;
     }
 #pragma unroll
-    for (int v = 0; v < M; ++v) F[v] = theta * F[v] + (1.0 - theta) * flo[v];
+    for (int v = 0; v < M; ++v) Fr[v] = real(theta * F[v] + (1.0 - theta) * flo[v]);
   }
 #pragma unroll
-  for (int v = 0; v < M; ++v) out[v * vstride + out_idx] = real(F[v]);
+  for (int v = 0; v < M; ++v) out[v * vstride + out_idx] = Fr[v];
 }
 
 // ===========================================================================
@@ -699,9 +700,62 @@ __global__ void k_face(const KParams<real> P) {
 // eps at the nodes in E[el*NP + k] -> Legendre modes -> energy fractions ->
 // logistic alpha, returned on thread k = 0 of the element.  T is the
 // arithmetic type (double in FP64 mode, float in FP32_BULK mode).
+// With alpha mode 2 the learned network replaces the logistic map (see
+// mlp_alpha); the indicator's alpha is the fallback when the network is not
+// loaded or returns a non-finite value.  When feat is not null the network
+// inputs of element e are written to feat[e * NP + k].
+__device__ __forceinline__ float bf16_to_float(unsigned short h) {
+  return __uint_as_float(((unsigned int)h) << 16);
+}
+
+constexpr int kMlpH = 32;
+
+// Learned alpha: x_k = log10(e_k + 1e-10)/10 + 1 from the normalised modal
+// energies e_k; two hidden layers of 32 ReLU units, sigmoid output; BF16
+// weights, FP32 arithmetic.  Weight layout W1[32][NP], b1, W2[32][32], b2, w3, b3.
+template <int NP>
+__device__ float mlp_alpha(const unsigned short* w, float x, float* fb, int k) {
+  float* X = fb;            // [NP]
+  float* H = fb + NP;       // [32] hidden layer 1
+  float* Z = fb + NP + kMlpH;  // [NP] partial sums of the output
+  const unsigned short* W1 = w;
+  const unsigned short* B1 = W1 + kMlpH * NP;
+  const unsigned short* W2 = B1 + kMlpH;
+  const unsigned short* B2 = W2 + kMlpH * kMlpH;
+  const unsigned short* W3 = B2 + kMlpH;
+  const unsigned short* B3 = W3 + kMlpH;
+  X[k] = x;
+  __syncthreads();
+  for (int j = k; j < kMlpH; j += NP) {
+    float acc = bf16_to_float(B1[j]);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) acc += bf16_to_float(W1[j * NP + i]) * X[i];
+    H[j] = fmaxf(acc, 0.0f);
+  }
+  __syncthreads();
+  float zp = 0.0f;
+  for (int j = k; j < kMlpH; j += NP) {
+    float acc = bf16_to_float(B2[j]);
+#pragma unroll 8
+    for (int i = 0; i < kMlpH; ++i) acc += bf16_to_float(W2[j * kMlpH + i]) * H[i];
+    zp += bf16_to_float(W3[j]) * fmaxf(acc, 0.0f);
+  }
+  Z[k] = zp;
+  __syncthreads();
+  float y = 0.0f;
+  if (k == 0) {
+    float z = bf16_to_float(B3[0]);
+    for (int i = 0; i < NP; ++i) z += Z[i];
+    y = 1.0f / (1.0f + expf(-z));
+  }
+  __syncthreads();
+  return y;  // valid on k == 0
+}
+
 template <int DIM, int N, typename T>
 __device__ T indicator_alpha(const Mesh& m, const Tab<T>& tb, T* E, T* Tm, T* red, int epb, int el,
-                             int k) {
+                             int k, const int* mlp_flag, const unsigned short* mlp_w, float* fbuf,
+                             float* feat, int e_out) {
   constexpr int n = N + 1;
   constexpr int NP = DIM == 2 ? n * n : n;
   T* Ee = E + el * NP;
@@ -734,9 +788,10 @@ __device__ T indicator_alpha(const Mesh& m, const Tab<T>& tb, T* E, T* Tm, T* re
   red[(2 * epb + el) * NP + k] = mx <= N - 1 ? e2 : T(0);
   red[(3 * epb + el) * NP + k] = mx == N - 1 ? e2 : T(0);
   elem_tree<NP, 4>(red, epb, el, k, OpSum());
+  const T tot = red[(0 * epb + el) * NP];
   T al = T(0);
   if (k == 0) {
-    const T tot = red[(0 * epb + el) * NP], top = red[(1 * epb + el) * NP];
+    const T top = red[(1 * epb + el) * NP];
     const T low = red[(2 * epb + el) * NP], top1 = red[(3 * epb + el) * NP];
     const T r1 = tot > T(0) ? top / tot : T(0);
     const T r2 = (N >= 2 && low > T(0)) ? top1 / low : T(0);
@@ -746,6 +801,20 @@ __device__ T indicator_alpha(const Mesh& m, const Tab<T>& tb, T* E, T* Tm, T* re
     if (al < T(1e-3)) al = T(0);
     if (al > T(1) - T(1e-3)) al = T(1);
     al = fmin(al, T(1));
+  }
+  if (m.alpha_mode == 2 || feat) {
+    const float ek = tot > T(0) ? float(e2 / tot) : 0.0f;
+    const float x = log10f(ek + 1e-10f) * 0.1f + 1.0f;
+    if (feat && e_out >= 0) feat[(size_t)e_out * NP + k] = x;
+    if (m.alpha_mode == 2 && mlp_flag && *mlp_flag) {
+      const float y = mlp_alpha<NP>(mlp_w, x, fbuf + el * (2 * NP + kMlpH), k);
+      if (k == 0 && isfinite(y)) {
+        float ya = y;
+        if (ya < 1e-3f) ya = 0.0f;
+        if (ya > 1.0f - 1e-3f) ya = 1.0f;
+        al = T(fminf(ya, 1.0f));
+      }
+    }
   }
   __syncthreads();  // red is reused by the caller
   return al;  // valid on k == 0
@@ -827,6 +896,7 @@ __global__ void k_update(const KParams<real> P) {
   double* sU = reinterpret_cast<double*>(smem_raw);  // [MU][epb][NP]
   double* sRed = sU + MU * stride;                   // [RW][epb][NP]
   double* sEl = sRed + RW * stride;                  // [epb][16]
+  float* sMlp = reinterpret_cast<float*>(sEl + 16 * epb);  // [epb][2 NP + 32] network scratch
   // per-element area: FP64 values at sEl[el*16 + 0..9] (0..3 limiter scalars, 4..9 the
   // FP64 mean); values in the kernel's type from double index 10 on: alpha at ER,
   // the FP32 mean copy at ER + 1 + v
@@ -918,13 +988,34 @@ __global__ void k_update(const KParams<real> P) {
 #pragma unroll
     for (int v = 0; v < M; ++v) ubar[v] = RED0(v);
   }
-  // per-element limiter scalars: sEl[el*16 + 0..3] = mean_ok, eps1, eps2, P2(u_bar)
+  // per-element limiter scalars: sEl[el*16 + 0..3] = mean_ok, eps1, eps2, P2(u_bar).
+  // FP32_BULK: when the FP32 copy of the mean is clearly admissible the FP64
+  // values are known without FP64 work (eps = 1e-12); otherwise FP64.
   if (k == 0) {
-    const double P2 = EQ::K > 0 ? EQ::constraint(ubar, 1, P.phd) : 0.0;
-    sEl[el * 16 + 0] = admissible<EQ>(ubar, P.phd) ? 1.0 : 0.0;
-    sEl[el * 16 + 1] = EQ::K > 0 ? fmin(1e-12, ubar[0]) : 0.0;
-    sEl[el * 16 + 2] = EQ::K > 0 ? fmin(1e-12, P2) : 0.0;
-    sEl[el * 16 + 3] = P2;
+    bool done = false;
+    if constexpr (MIXED) {
+      if (EQ::K > 0) {
+        real ub[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) ub[v] = sElr[el * ES + ER + 1 + v];
+        const real scale = EQ::M == 6 ? fabs(ub[3]) + fabs(ub[5]) : fabs(ub[M - 1]);
+        const real P2f = EQ::constraint(ub, 1, P.ph);
+        if (ub[0] > real(1e-9) && P2f > real(1e-5) * scale + real(1e-9)) {
+          sEl[el * 16 + 0] = 1.0;
+          sEl[el * 16 + 1] = 1e-12;
+          sEl[el * 16 + 2] = 1e-12;
+          sEl[el * 16 + 3] = double(P2f);
+          done = true;
+        }
+      }
+    }
+    if (!done) {
+      const double P2 = EQ::K > 0 ? EQ::constraint(ubar, 1, P.phd) : 0.0;
+      sEl[el * 16 + 0] = admissible<EQ>(ubar, P.phd) ? 1.0 : 0.0;
+      sEl[el * 16 + 1] = EQ::K > 0 ? fmin(1e-12, ubar[0]) : 0.0;
+      sEl[el * 16 + 2] = EQ::K > 0 ? fmin(1e-12, P2) : 0.0;
+      sEl[el * 16 + 3] = P2;
+    }
   }
   __syncthreads();
 
@@ -1093,7 +1184,7 @@ __global__ void k_update(const KParams<real> P) {
   }
 
   // ---- indicator of the new state and the CFL rate -------------------------
-  if ((m.limiter & kLimBlend) && m.alpha_mode == 0) {
+  if ((m.limiter & kLimBlend) && (m.alpha_mode == 0 || m.alpha_mode == 2)) {
     if constexpr (MIXED) {
       real* rE = reinterpret_cast<real*>(sU);
       real* rT = rE + stride;
@@ -1101,7 +1192,8 @@ __global__ void k_update(const KParams<real> P) {
       __syncthreads();
       rE[el * NP + k] = EQ::indicator_var(ur, P.ph);
       __syncthreads();
-      const real al = indicator_alpha<DIM, N, real>(m, P.tb, rE, rT, rR, epb, el, k);
+      const real al = indicator_alpha<DIM, N, real>(m, P.tb, rE, rT, rR, epb, el, k, P.b.mlp_flag,
+                                                    P.b.mlp_w, sMlp, nullptr, -1);
       if (valid && k == 0) P.b.alpha_raw[e] = double(al);
     } else {
       double* dE = sU;
@@ -1109,7 +1201,8 @@ __global__ void k_update(const KParams<real> P) {
       __syncthreads();
       dE[el * NP + k] = EQ::indicator_var(ur, P.phd);
       __syncthreads();
-      const double al = indicator_alpha<DIM, N, double>(m, td, dE, dT, sRed, epb, el, k);
+      const double al = indicator_alpha<DIM, N, double>(m, td, dE, dT, sRed, epb, el, k,
+                                                        P.b.mlp_flag, P.b.mlp_w, sMlp, nullptr, -1);
       if (valid && k == 0) P.b.alpha_raw[e] = al;
     }
   }
@@ -1148,6 +1241,7 @@ __global__ void k_prologue(const KParams<real> P) {
   double* sU = reinterpret_cast<double*>(smem_raw);
   double* sRed = sU + MU * stride;
   double* sEl = sRed + RW * stride;
+  float* sMlp = reinterpret_cast<float*>(sEl + 16 * epb);
   const int p = DIM == 2 ? k % n : k, q = DIM == 2 ? k / n : 0;
   const double W = DIM == 2 ? P.td.w[p] * P.td.w[q] : P.td.w[p];
   double u[M];
@@ -1169,10 +1263,12 @@ __global__ void k_prologue(const KParams<real> P) {
 #pragma unroll
   for (int v = 0; v < M; ++v) ubar[v] = sRed[(v * epb + el) * NP];
   __syncthreads();
-  if ((m.limiter & kLimBlend) && m.alpha_mode == 0) {
+  if (((m.limiter & kLimBlend) && (m.alpha_mode == 0 || m.alpha_mode == 2)) || P.b.feat) {
     sU[el * NP + k] = EQ::indicator_var(u, P.phd);
     __syncthreads();
-    const double al = indicator_alpha<DIM, N, double>(m, P.td, sU, sU + stride, sRed, epb, el, k);
+    const double al = indicator_alpha<DIM, N, double>(m, P.td, sU, sU + stride, sRed, epb, el, k,
+                                                      P.b.mlp_flag, P.b.mlp_w, sMlp, P.b.feat,
+                                                      valid ? e : -1);
     if (valid && k == 0) P.b.alpha_raw[e] = al;
   }
   __syncthreads();

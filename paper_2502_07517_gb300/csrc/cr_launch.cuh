@@ -35,7 +35,8 @@ struct Impl {
   static constexpr int RW = 2 * M > 4 ? 2 * M : 4;
   static constexpr int MU = M > 2 ? M : 2;
   static size_t smem_update(int epb) {
-    return ((size_t)(MU + RW) * epb * NP + 16 * (size_t)epb) * sizeof(double);
+    return ((size_t)(MU + RW) * epb * NP + 16 * (size_t)epb) * sizeof(double) +
+           (size_t)epb * (2 * NP + 32) * sizeof(float);
   }
 
   static cudaError_t configure() {
