@@ -161,6 +161,111 @@ def cpu_baseline(target_s=10.0, nx=256):
                       % (nx, nx, steps, el)}
 
 
+def train_alpha_network(degree, stream, seeds=range(1000, 1008), nx=96, snaps=(0, 10, 40),
+                        epochs=15):
+    """Learned blending coefficient for this degree: network inputs and the
+    indicator's raw alpha harvested along GPU runs of the vortex-plus-Riemann
+    recipe (shocks and smooth flow), then Adam on the GPU (cr_mlp_train)."""
+    import torch
+    from paper_2502_07517_gb300 import crkfr
+    X, T = [], []
+    for seed in seeds:
+        prob, u = wl.euler2d_vortex_riemann(nx=nx, degree=degree, seed=seed)
+        ctx = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, stream=stream))
+        crkfr.cr_set_state(ctx, u)
+        done = 0
+        for s in snaps:
+            if s > done:
+                crkfr.cr_step(ctx, s - done, 1e300)
+                done = s
+            f, a = crkfr.cr_get_features(ctx, u.shape[1], u.shape[2])
+            X.append(f)
+            T.append(a)
+        crkfr.cr_destroy(ctx)
+    X, T = np.concatenate(X), np.concatenate(T).astype(np.float32)
+    nin = X.shape[1]
+    rng = np.random.default_rng(0)
+    p = torch.from_numpy(rng.normal(0.0, 0.2, crkfr.cr_mlp_param_count(nin)).astype(np.float32)).cuda()
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    crkfr.cr_mlp_train(nin, p, Xd, Td, batch=512, epochs=epochs, lr=3e-3, seed=1)
+    train_s = time.perf_counter() - t0
+    g, loss = torch.empty_like(p), torch.empty(1, device="cuda")
+    crkfr.cr_mlp_grad(nin, p, Xd, Td, g, loss)
+    params = p.cpu().numpy()
+    # served by the fused inference kernel on a held-out seed: |alpha_net - alpha_indicator|
+    prob, u = wl.euler2d_vortex_riemann(nx=nx, degree=degree, seed=max(seeds) + 1)
+    ctx = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, stream=stream))
+    crkfr.cr_set_state(ctx, u)
+    crkfr.cr_step(ctx, 20, 1e300)
+    _, a_ind = crkfr.cr_get_features(ctx, u.shape[1], u.shape[2])
+    ctx2 = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, stream=stream, alpha_mode=crkfr.CR_ALPHA_MLP))
+    crkfr.cr_mlp_load(ctx2, params)
+    crkfr.cr_set_state(ctx2, crkfr.cr_get_state(ctx, shape=u.shape))
+    _, a_net = crkfr.cr_get_features(ctx2, u.shape[1], u.shape[2])
+    info = {"samples": int(T.size), "inputs": nin, "epochs": epochs, "train_s": train_s,
+            "cross_entropy": float(loss.item()), "target_mean": float(T.mean()),
+            "heldout_mean_abs_alpha_err": float(np.abs(a_net - a_ind).mean()),
+            "heldout_max_abs_alpha_err": float(np.abs(a_net - a_ind).max()),
+            "data": "vortex + planar Riemann jump, %dx%d, N=%d, %d seeds, steps %s"
+                    % (nx, nx, degree, len(seeds), list(snaps))}
+    return params, info
+
+
+def timed_steps(ctx, steps, warmup, stream):
+    import torch
+    from paper_2502_07517_gb300 import crkfr
+    crkfr.cr_step_async(ctx, warmup, 1e300)
+    crkfr.cr_sync(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    crkfr.cr_step_async(ctx, steps, 1e300)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    crkfr.cr_sync(ctx)
+    return e0.elapsed_time(e1) / steps
+
+
+def l1_rel(g, ref):
+    return [float(np.abs(g[v] - ref[v]).sum() / max(np.abs(ref[v]).sum(), 1e-300))
+            for v in range(ref.shape[0])]
+
+
+def fp32_variants(prob, u, ctx64, steps, warmup, stream, fp64_ms):
+    """FP32 bulk with the indicator's alpha and with the learned alpha: device
+    time per step on the same workload, and the normalised L1 difference per
+    variable from the FP64 path (parity-checked against the FP64 oracle) after
+    the same number of steps at the same fixed dt."""
+    from paper_2502_07517_gb300 import crkfr
+    params, train = train_alpha_network(prob["degree"], stream.cuda_stream)
+    nodes = u.shape[1] * u.shape[2]
+    crkfr.cr_set_state(ctx64, u)
+    dt0 = crkfr.cr_next_dt(ctx64)
+    crkfr.cr_step(ctx64, steps, 1e300, dt0)
+    ref = crkfr.cr_get_state(ctx64, shape=u.shape)
+    out = {"alpha_network": train, "l1_reference": "FP64 path after %d steps at dt %.6g" % (steps, dt0)}
+    for name, mode in (("fp32_indicator", crkfr.CR_ALPHA_INDICATOR),
+                       ("fp32_learned_alpha", crkfr.CR_ALPHA_MLP)):
+        d = crkfr.desc_from_problem(prob, precision=crkfr.CR_FP32_BULK, alpha_mode=mode,
+                                    stream=stream.cuda_stream)
+        ctx = crkfr.cr_init_mesh(d)
+        if mode == crkfr.CR_ALPHA_MLP:
+            crkfr.cr_mlp_load(ctx, params)
+        crkfr.cr_set_state(ctx, u)
+        ms = timed_steps(ctx, steps, warmup, stream)
+        crkfr.cr_set_state(ctx, u)
+        crkfr.cr_step(ctx, steps, 1e300, dt0)
+        g = crkfr.cr_get_state(ctx, shape=u.shape)
+        a = crkfr.cr_get_alpha(ctx, u.shape[1])
+        out[name] = {"value": nodes / (ms * 1e-3), "unit": "DOF-updates/s", "ms_per_step": ms,
+                     "speedup_vs_fp64": fp64_ms / ms, "l1_rel_vs_fp64": l1_rel(g, ref),
+                     "alpha_mean": float(a.mean()), "alpha_max": float(a.max())}
+        crkfr.cr_destroy(ctx)
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -246,6 +351,17 @@ def run_ours(args):
                 "kernel_ms": {nm: float(x) for nm, x in zip(names, kms)},
                 "step_tflops": sum(flops) * nodes / (ms_per_step * 1e-3) / 1e12}
 
+    # ---- HBM view: the method's own bytes (read u^n, write u^{n+1}) per step ----
+    state_bytes = u.size * (4 if mixed else 8) + (2 * M * ne * 8 if mixed else 0)
+    hbm_peak = json.load(open(MEASURED_PEAKS))["hbm_gbs"] if os.path.exists(MEASURED_PEAKS) else 6800.0
+    hbm = {"algorithmic_bytes_per_step": 2 * state_bytes,
+           "achieved_GBs": 2 * state_bytes / (ms_per_step * 1e-3) / 1e9, "peak_GBs": hbm_peak}
+    hbm["frac"] = hbm["achieved_GBs"] / hbm_peak
+
+    variants = None
+    if not mixed and not args.quick and not args.no_variants:
+        variants = fp32_variants(prob, u, ctx, args.steps, args.warmup, stream, ms_per_step)
+
     # ---- end to end through the public API with host buffers ----
     if args.quick:
         print(json.dumps({"quick": True, "mode": args.mode, "nx": args.nx, "ms_per_step": ms_per_step,
@@ -283,7 +399,8 @@ def run_ours(args):
                    "limiters": "blend+MUSCL-Hancock+flux+scaling",
                    "l2": "inputs larger than L2 (state %.0f MB)" % (u.size * (4 if mixed else 8) / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
+        "roofline": roofline, "hbm_roofline": hbm, "variants": variants,
+        "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches * args.steps, "t_reached": t_s, "steps_run": n_s,
     }
     print(json.dumps(line))
@@ -301,6 +418,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--nx", type=int, default=WORKLOAD["nx"],
                     help="elements per direction (smaller meshes of the same recipe for profiling)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP32 bulk / learned-alpha comparison legs")
     ap.add_argument("--quick", action="store_true",
                     help="device timing only (no CPU baseline, no end-to-end leg)")
     args = ap.parse_args()

@@ -157,8 +157,10 @@ cr_status cr_mlp_load(cr_ctx* ctx, const float* params, int nparams);
  * pointer may be NULL.  Synchronises when on_device == 0. */
 cr_status cr_get_features(cr_ctx* ctx, float* features, double* alpha_raw, int on_device);
 
-/* Mean squared error of the network on samples X[n][nin], targets t[n] and
- * its gradient (same layout as the parameters), on the GPU.  All pointers are
+/* Cross-entropy loss -mean(t log y + (1 - t) log(1 - y)) of the network on
+ * samples X[n][nin] with targets t[n] in [0, 1] (the indicator's alpha taken
+ * as a probability) and its gradient (same layout as the parameters), on the
+ * GPU.  All pointers are
  * device pointers; grad and loss are overwritten.  Ordered on stream. */
 cr_status cr_mlp_grad(int nin, const float* params, const float* X, const float* t, int n,
                       float* grad, float* loss, void* stream);

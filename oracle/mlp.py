@@ -8,8 +8,11 @@ variant replaces the indicator's last step by a small network: inputs are the
 element's normalised modal energies e_k = m_k^2 / sum m^2 (the indicator's
 own modes), encoded as x_k = log10(e_k + 1e-10) / 10 + 1; two hidden layers
 of 32 ReLU units; a sigmoid output.  It is trained on the indicator's alpha
-with the mean squared error.  This module is the plain definition: forward
-pass, loss and the hand-derived backward pass, in FP64.
+with the cross-entropy loss -mean(t log y + (1 - t) log(1 - y)), alpha in
+[0, 1] taken as a probability: unlike the squared error, its gradient with
+respect to the output logit, (y - t)/n, does not vanish where y saturates,
+so alpha = 1 regions (shocks) are learned as 1.  This module is the plain
+definition: forward pass, loss and the hand-derived backward pass, in FP64.
 
 Pinned (tests/test_oracle_mlp.py) by central finite differences of the loss
 (the backward pass against the forward pass), hand-built networks with a
@@ -59,18 +62,32 @@ def forward(params, X):
     return y, (X, a1, h1, a2, h2, y)
 
 
+def _softplus(z):
+    return np.maximum(z, 0.0) + np.log1p(np.exp(-np.abs(z)))
+
+
+def logits(params, X):
+    """Output before the sigmoid."""
+    X = np.asarray(X, dtype=np.float64)
+    W1, b1, W2, b2, w3, b3 = unpack(params, X.shape[1])
+    h1 = np.maximum(X @ W1.T + b1, 0.0)
+    h2 = np.maximum(h1 @ W2.T + b2, 0.0)
+    return h2 @ w3 + b3
+
+
 def loss(params, X, t):
-    y, _ = forward(params, X)
-    return float(np.mean((y - np.asarray(t, dtype=np.float64)) ** 2))
+    """Cross-entropy, with log y = -softplus(-z) and log(1 - y) = -softplus(z)."""
+    z = logits(params, X)
+    t = np.asarray(t, dtype=np.float64)
+    return float(np.mean(t * _softplus(-z) + (1.0 - t) * _softplus(z)))
 
 
 def grad(params, X, t):
-    """Gradient of the mean squared error, same layout as params."""
+    """Gradient of the cross-entropy loss, same layout as params."""
     y, (X, a1, h1, a2, h2, y) = forward(params, X)
     W1, b1, W2, b2, w3, b3 = unpack(params, X.shape[1])
     B = X.shape[0]
-    dy = 2.0 * (y - np.asarray(t, dtype=np.float64)) / B
-    dz = dy * y * (1.0 - y)
+    dz = (y - np.asarray(t, dtype=np.float64)) / B
     dw3 = h2.T @ dz
     db3 = dz.sum()
     da2 = np.outer(dz, w3) * (a2 > 0.0)

@@ -741,10 +741,20 @@ cr_status cr_mlp_load(cr_ctx* c, const float* params, int nparams) {
   const int want = 32 * np + 32 + 32 * 32 + 32 + 32 + 1;
   if (nparams != want)
     return fail(c, CR_E_INVALID_ARG, "expected " + std::to_string(want) + " network parameters");
+  // Device layout: the weight matrices transposed (W1T[Np][32], W2T[32][32])
+  // so that the 32 lanes of a warp read 32 consecutive entries.
+  const int H = 32;
+  std::vector<int> src(nparams);
+  for (int i = 0; i < nparams; ++i) src[i] = i;
+  for (int j = 0; j < H; ++j)
+    for (int i = 0; i < np; ++i) src[i * H + j] = j * np + i;
+  const int o2 = H * np + H;
+  for (int j = 0; j < H; ++j)
+    for (int i = 0; i < H; ++i) src[o2 + i * H + j] = o2 + j * H + i;
   std::vector<unsigned short> h(nparams);
   for (int i = 0; i < nparams; ++i) {  // FP32 -> BF16, round to nearest even
     uint32_t b;
-    memcpy(&b, &params[i], 4);
+    memcpy(&b, &params[src[i]], 4);
     if ((b & 0x7f800000u) == 0x7f800000u && (b & 0x007fffffu)) return fail(c, CR_E_INVALID_ARG, "NaN parameter");
     b += 0x7fffu + ((b >> 16) & 1u);
     h[i] = (unsigned short)(b >> 16);

@@ -712,44 +712,46 @@ constexpr int kMlpH = 32;
 
 // Learned alpha: x_k = log10(e_k + 1e-10)/10 + 1 from the normalised modal
 // energies e_k; two hidden layers of 32 ReLU units, sigmoid output; BF16
-// weights, FP32 arithmetic.  Weight layout W1[32][NP], b1, W2[32][32], b2, w3, b3.
+// weights, FP32 arithmetic.  Device weight layout (transposed by cr_mlp_load
+// so that lane j of a warp reads entry j of 32 consecutive ones):
+// W1T[NP][32], b1[32], W2T[32][32] (W2T[i][j] = W2[j][i]), b2[32], w3[32], b3.
+// Every thread of the block calls this with its element's input x (thread k
+// of element el); each full warp then evaluates whole elements, lane j being
+// hidden unit j, and the output of element el is returned to all its threads.
+// fbuf: shared memory for epb * (NP + 1) floats.
 template <int NP>
-__device__ float mlp_alpha(const unsigned short* w, float x, float* fb, int k) {
-  float* X = fb;            // [NP]
-  float* H = fb + NP;       // [32] hidden layer 1
-  float* Z = fb + NP + kMlpH;  // [NP] partial sums of the output
+__device__ float mlp_alpha(const unsigned short* __restrict__ w, float x, float* fbuf, int epb,
+                           int el, int k) {
+  float* X = fbuf;            // [epb][NP] inputs
+  float* Y = fbuf + epb * NP; // [epb] outputs
+  X[el * NP + k] = x;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const unsigned short* W1 = w;
-  const unsigned short* B1 = W1 + kMlpH * NP;
+  const unsigned short* B1 = W1 + NP * kMlpH;
   const unsigned short* W2 = B1 + kMlpH;
   const unsigned short* B2 = W2 + kMlpH * kMlpH;
   const unsigned short* W3 = B2 + kMlpH;
   const unsigned short* B3 = W3 + kMlpH;
-  X[k] = x;
-  __syncthreads();
-  for (int j = k; j < kMlpH; j += NP) {
-    float acc = bf16_to_float(B1[j]);
+  if (warp < nw) {  // full warps only (blockDim need not be a multiple of 32)
+    for (int e2 = warp; e2 < epb; e2 += nw) {
+      const float* xe = X + e2 * NP;
+      float h = bf16_to_float(B1[lane]);
 #pragma unroll
-    for (int i = 0; i < NP; ++i) acc += bf16_to_float(W1[j * NP + i]) * X[i];
-    H[j] = fmaxf(acc, 0.0f);
+      for (int i = 0; i < NP; ++i) h = fmaf(bf16_to_float(W1[i * kMlpH + lane]), xe[i], h);
+      h = fmaxf(h, 0.0f);
+      float a = bf16_to_float(B2[lane]);
+#pragma unroll
+      for (int i = 0; i < kMlpH; ++i)
+        a = fmaf(bf16_to_float(W2[i * kMlpH + lane]), __shfl_sync(0xffffffffu, h, i), a);
+      float z = bf16_to_float(W3[lane]) * fmaxf(a, 0.0f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+      if (lane == 0) Y[e2] = 1.0f / (1.0f + expf(-(z + bf16_to_float(B3[0]))));
+    }
   }
   __syncthreads();
-  float zp = 0.0f;
-  for (int j = k; j < kMlpH; j += NP) {
-    float acc = bf16_to_float(B2[j]);
-#pragma unroll 8
-    for (int i = 0; i < kMlpH; ++i) acc += bf16_to_float(W2[j * kMlpH + i]) * H[i];
-    zp += bf16_to_float(W3[j]) * fmaxf(acc, 0.0f);
-  }
-  Z[k] = zp;
-  __syncthreads();
-  float y = 0.0f;
-  if (k == 0) {
-    float z = bf16_to_float(B3[0]);
-    for (int i = 0; i < NP; ++i) z += Z[i];
-    y = 1.0f / (1.0f + expf(-z));
-  }
-  __syncthreads();
-  return y;  // valid on k == 0
+  return Y[el];
 }
 
 template <int DIM, int N, typename T>
@@ -807,7 +809,7 @@ __device__ T indicator_alpha(const Mesh& m, const Tab<T>& tb, T* E, T* Tm, T* re
     const float x = log10f(ek + 1e-10f) * 0.1f + 1.0f;
     if (feat && e_out >= 0) feat[(size_t)e_out * NP + k] = x;
     if (m.alpha_mode == 2 && mlp_flag && *mlp_flag) {
-      const float y = mlp_alpha<NP>(mlp_w, x, fbuf + el * (2 * NP + kMlpH), k);
+      const float y = mlp_alpha<NP>(mlp_w, x, fbuf, epb, el, k);
       if (k == 0 && isfinite(y)) {
         float ya = y;
         if (ya < 1e-3f) ya = 0.0f;
@@ -896,7 +898,7 @@ __global__ void k_update(const KParams<real> P) {
   double* sU = reinterpret_cast<double*>(smem_raw);  // [MU][epb][NP]
   double* sRed = sU + MU * stride;                   // [RW][epb][NP]
   double* sEl = sRed + RW * stride;                  // [epb][16]
-  float* sMlp = reinterpret_cast<float*>(sEl + 16 * epb);  // [epb][2 NP + 32] network scratch
+  float* sMlp = reinterpret_cast<float*>(sEl + 16 * epb);  // [epb][NP + 1] network scratch
   // per-element area: FP64 values at sEl[el*16 + 0..9] (0..3 limiter scalars, 4..9 the
   // FP64 mean); values in the kernel's type from double index 10 on: alpha at ER,
   // the FP32 mean copy at ER + 1 + v

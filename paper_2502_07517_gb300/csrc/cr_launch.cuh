@@ -36,7 +36,7 @@ struct Impl {
   static constexpr int MU = M > 2 ? M : 2;
   static size_t smem_update(int epb) {
     return ((size_t)(MU + RW) * epb * NP + 16 * (size_t)epb) * sizeof(double) +
-           (size_t)epb * (2 * NP + 32) * sizeof(float);
+           (size_t)epb * (NP + 1) * sizeof(float);
   }
 
   static cudaError_t configure() {

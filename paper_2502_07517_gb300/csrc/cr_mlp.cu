@@ -1,7 +1,8 @@
 // Training of the learned blending coefficient on the GPU: the network maps
 // an element's normalised modal energies (encoded, nin inputs) through two
-// hidden layers of 32 ReLU units to a sigmoid output; the loss is the mean
-// squared error against the smoothness indicator's alpha.  Forward and
+// hidden layers of 32 ReLU units to a sigmoid output; the loss is the
+// cross-entropy against the smoothness indicator's alpha (in [0, 1], taken as
+// a probability), whose gradient in the output logit is (y - t) / n.  Forward and
 // backward passes, Adam, and the epoch loop are this file's kernels.
 #include <cstdint>
 #include <cstring>
@@ -20,9 +21,9 @@ __host__ __device__ constexpr int param_count(int nin) {
   return kH * nin + kH + kH * kH + kH + kH + 1;
 }
 
-// Gradient of the mean squared error over samples [0, n) (indices through
-// idx when given), accumulated into grad (same layout as the parameters);
-// loss accumulates sum (y - t)^2 * inv_n.  One block handles chunks of 64
+// Gradient of the cross-entropy over samples [0, n) (indices through idx
+// when given), accumulated into grad (same layout as the parameters); loss
+// accumulates (t softplus(-z) + (1 - t) softplus(z)) * inv_n.  One block handles chunks of 64
 // samples: threads 0..63 run forward and backward for one sample each into
 // shared memory, then all threads reduce their share of the gradient entries.
 template <int NIN>
@@ -77,9 +78,10 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const float* __restrict__
         z += W3[j] * fmaxf(a, 0.0f);
       }
       const float y = 1.0f / (1.0f + expf(-z));
-      const float diff = y - T[s];
-      lsum += diff * diff * inv_n;
-      const float dz = 2.0f * diff * inv_n * y * (1.0f - y);
+      const float t = T[s];
+      const float sp = log1pf(expf(-fabsf(z)));  // softplus(z) = max(z, 0) + sp
+      lsum += (t * (fmaxf(-z, 0.0f) + sp) + (1.0f - t) * (fmaxf(z, 0.0f) + sp)) * inv_n;
+      const float dz = (y - t) * inv_n;
       R[REC - 1] = dz;
       for (int j = 0; j < kH; ++j) d2[j] = h2[j] > 0.0f ? dz * W3[j] : 0.0f;
       for (int i = 0; i < kH; ++i) {

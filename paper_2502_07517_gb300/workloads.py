@@ -160,6 +160,33 @@ def euler2d_vortex(nx=512, ny=None, degree=4, seed=0, perturb=0.01, limiter=LIMI
     return prob, euler_conservative(rho, v1, v2, p, prob["gamma"], 2)
 
 
+def euler2d_vortex_riemann(nx=128, ny=None, degree=4, seed=0, limiter=LIMITER_ALL, steps=100):
+    """2D Euler on [-5,5]^2 periodic: the isentropic vortex (as euler2d_vortex,
+    unperturbed) with a seeded planar Riemann jump: a stripe of half the domain,
+    normal to x or to y, bounded by element faces, where density and pressure
+    are multiplied by (rho_R, p_R) and elsewhere by (rho_L, p_L); rho uniform
+    in [0.5, 5], p uniform in [0.1, 10]."""
+    ny = nx if ny is None else ny
+    prob = base_problem(dim=2, nx=nx, ny=ny, x0=-5.0, x1=5.0, y0=-5.0, y1=5.0, degree=degree,
+                        equation="euler", limiter=frozenset(limiter), steps=steps, t_final=1e9)
+    rng = np.random.default_rng(seed)
+    rho_s = rng.uniform(0.5, 5.0, 2)
+    p_s = rng.uniform(0.1, 10.0, 2)
+    along_x = bool(rng.integers(0, 2))
+    n_dir = nx if along_x else ny
+    lo = int(rng.integers(n_dir // 8, 3 * n_dir // 8 + 1))
+    hi = lo + n_dir // 2
+    x, y = node_coords(prob)
+    rho, v1, v2, p = isentropic_vortex(x, y, prob["gamma"])
+    e = np.arange(nx * ny)
+    idx = (e % nx) if along_x else (e // nx)
+    inside = ((idx >= lo) & (idx < hi))[:, None]
+    rho = rho * np.where(inside, rho_s[1], rho_s[0])
+    p = p * np.where(inside, p_s[1], p_s[0])
+    prob["riemann2d"] = dict(rho=rho_s.tolist(), p=p_s.tolist(), along_x=along_x, lo=lo, hi=hi)
+    return prob, euler_conservative(rho, v1, v2, p, prob["gamma"], 2)
+
+
 def tenmoment2d_voronoi(nx=256, ny=None, degree=3, seed=0, ncells=16, limiter=LIMITER_ALL,
                         steps=200, source=True):
     """2D ten-moment on [0,1]^2 periodic with the Gaussian source

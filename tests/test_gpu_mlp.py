@@ -8,8 +8,9 @@ reference (oracle/mlp.py, oracle.modal_energies):
 * one whole cRKFR step with the learned alpha against the oracle step given
   the same raw alpha (1e-12 relative, as every FP64 step);
 * the fallbacks to the indicator (no network loaded, a non-finite output);
-* the training kernels: loss and gradient against the hand-derived FP64
-  backward pass, and Adam training that fits the indicator's alpha.
+* the training kernels: cross-entropy loss and gradient against the
+  hand-derived FP64 backward pass, and Adam training that fits the
+  indicator's alpha.
 """
 import numpy as np
 import pytest
@@ -216,12 +217,15 @@ def test_training_fits_the_indicator():
     Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T.astype(np.float32)).cuda()
     g, l0 = torch.empty_like(p), torch.empty(1, device="cuda")
     crkfr.cr_mlp_grad(nin, p, Xd, Td, g, l0)
+    first = l0.item()
     loss = crkfr.cr_mlp_train(nin, p, Xd, Td, batch=256, epochs=30, lr=3e-3, seed=1)
     crkfr.cr_mlp_grad(nin, p, Xd, Td, g, l0)
-    final = l0.item()
-    var = T.var()
-    print("samples", T.size, "target var %.4f final mse %.5f (last epoch %.5f)" % (var, final, loss))
-    assert final < 0.1 * var
+    assert l0.item() < first
+    y, _ = mlp.forward(p.cpu().numpy().astype(np.float64), X.astype(np.float64))
+    mse, var = float(np.mean((y - T) ** 2)), T.var()
+    print("samples", T.size, "target var %.4f, trained mse %.5f (cross-entropy %.4f -> %.4f, last epoch %.4f)"
+          % (var, mse, first, l0.item(), loss))
+    assert mse < 0.1 * var
     # served by the fused inference kernel on an unseen seed
     Xv, Tv = _indicator_samples([11], steps=(0, 8))
     prob, u = wl.tenmoment2d_voronoi(nx=48, ny=48, degree=3, seed=11)

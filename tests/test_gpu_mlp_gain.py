@@ -12,9 +12,11 @@ Riemann solution is compared for
 
 The network is trained to imitate the indicator, so it cannot beat it on
 accuracy; what it offers over the method without it (no blending) is the
-indicator's shock capturing with the indicator kept as fallback.  The test
-asserts that the learned alpha stays within 25% of the indicator's error and
-below the unblended scheme's error, and prints all three.
+indicator's shock capturing with the indicator kept as fallback.  A run whose
+step turns out inadmissible stops there and is counted as failed.  The test
+asserts that the learned alpha fails no more often than the indicator, stays
+within 25% of its error, and beats the unblended scheme (which either fails
+or is less accurate), and prints all of it.
 """
 import json
 import os
@@ -29,7 +31,7 @@ from tests import _riemann_exact as rx
 pytestmark = pytest.mark.gpu
 
 NX, N = 400, 4
-TRAIN_SEEDS = range(100, 124)
+TRAIN_SEEDS = range(100, 148)
 TEST_SEEDS = range(0, 10)
 
 
@@ -68,7 +70,7 @@ def _train():
         ctx = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob))
         crkfr.cr_set_state(ctx, u)
         t_end = _t_end(prob)
-        for frac in (0.0, 0.05, 0.3, 1.0):
+        for frac in (0.0, 0.02, 0.05, 0.1, 0.2, 0.35, 0.5, 0.75, 1.0):
             if frac > 0:
                 crkfr.cr_step(ctx, 10 ** 7, frac * t_end)
             f, a = crkfr.cr_get_features(ctx, NX, N + 1)
@@ -79,7 +81,7 @@ def _train():
     p = torch.from_numpy(np.random.default_rng(0).normal(0, 0.2, crkfr.cr_mlp_param_count(nin))
                          .astype(np.float32)).cuda()
     crkfr.cr_mlp_train(nin, p, torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), batch=256,
-                       epochs=40, lr=3e-3, seed=3)
+                       epochs=60, lr=3e-3, seed=3)
     return p.cpu().numpy(), X.shape[0]
 
 
@@ -113,21 +115,44 @@ def test_learned_alpha_gain_on_exact_riemann_solutions():
             crkfr.cr_set_state(ctx, u)
             if name == "learned":
                 crkfr.cr_mlp_load(ctx, params)
-            t, n = crkfr.cr_step(ctx, 10 ** 7, t_end)   # raises if a step is inadmissible
+            try:
+                t, n = crkfr.cr_step(ctx, 10 ** 7, t_end)
+            except crkfr.CrError as err:     # a step produced an inadmissible state
+                assert err.status == -3
+                res[name] = None
+                res[name + "_failed_at_t"] = _time_reached(ctx)
+                continue
             assert t == t_end
             g = crkfr.cr_get_state(ctx, shape=u.shape)
             assert np.all(np.isfinite(g))
             res[name] = _l1_rho(prob, g, t_end)
             res[name + "_steps"] = n
         rows.append(dict(seed=seed, **res))
-    mean = {k: float(np.mean([r[k] for r in rows])) for k in ("indicator", "learned", "no_blend")}
-    print("\ntrained on %d samples; mean L1(rho) over %d problems: %s" % (nsamples, len(rows), mean))
+    names = ("indicator", "learned", "no_blend")
+    failed = {k: sum(r[k] is None for r in rows) for k in names}
+    both = [r for r in rows if r["indicator"] is not None and r["learned"] is not None]
+    mean = {k: float(np.mean([r[k] for r in both])) for k in ("indicator", "learned")}
+    nb = [r for r in both if r["no_blend"] is not None]
+    mean_nb = {k: float(np.mean([r[k] for r in nb])) for k in names} if nb else None
+    print("\ntrained on %d samples; %d problems; failed runs %s" % (nsamples, len(rows), failed))
+    print("mean L1(rho), indicator vs learned over %d problems: %s" % (len(both), mean))
+    print("mean L1(rho) where the unblended scheme finished (%d): %s" % (len(nb), mean_nb))
     for r in rows:
         print(r)
     out = os.environ.get("CR_GAIN_JSON")
     if out:
         with open(out, "w") as fh:
-            json.dump({"samples": nsamples, "mean": mean, "rows": rows}, fh, indent=1)
+            json.dump({"samples": nsamples, "failed": failed, "mean": mean, "mean_where_no_blend_ran": mean_nb,
+                       "rows": rows}, fh, indent=1)
     assert len(rows) >= 6
+    assert failed["learned"] <= failed["indicator"]
     assert mean["learned"] <= 1.25 * mean["indicator"]
-    assert mean["learned"] < mean["no_blend"]
+    # what it gains over the method without it: the unblended scheme fails, or is less accurate
+    assert failed["no_blend"] > 0 or mean_nb["learned"] < mean_nb["no_blend"]
+
+
+def _time_reached(ctx):
+    import ctypes
+    t, n = ctypes.c_double(), ctypes.c_int()
+    crkfr.lib().cr_sync(ctx.handle, ctypes.byref(t), ctypes.byref(n))
+    return t.value

@@ -40,6 +40,19 @@ def test_zero_network_is_sigmoid_of_output_bias():
     np.testing.assert_allclose(y, 1.0 / (1.0 + math.exp(-0.7)), rtol=1e-15)
 
 
+def test_cross_entropy_of_a_constant_output():
+    """Zero weights and output bias b: y = 1/(1 + e^-b) for every sample, so the
+    loss is -(t log y + (1 - t) log(1 - y)) averaged over the targets."""
+    p = np.zeros(mlp.param_count(5))
+    p[-1] = -1.3
+    t = np.array([0.0, 1.0, 0.25, 0.9])
+    y = 1.0 / (1.0 + math.exp(1.3))
+    ref = -np.mean(t * math.log(y) + (1 - t) * math.log(1 - y))
+    assert abs(mlp.loss(p, np.ones((4, 5)), t) - ref) < 1e-15
+    # and the output-bias gradient is mean(y - t)
+    assert abs(mlp.grad(p, np.ones((4, 5)), t)[-1] - np.mean(y - t)) < 1e-15
+
+
 def test_hand_built_network():
     """Hidden unit j of layer 1 reads input (3j mod nin) with weight j+1 and bias
     -0.25; layer 2 is the identity; the output sums the units with weights
