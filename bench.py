@@ -36,6 +36,10 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # ALU peaks from the unit counts and the maximum SM clock: 152 SMs; FP64 2 FMA
 # lanes per SM per clock (1.25 TFLOP/s nominal), FP32 128 FMA lanes per SM.
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+# DRAM bytes (read + write) per element of the dominant kernel, from one ncu
+# capture of the current kernel (profiles/k_local_euler2d_384x384_N4_fp64.md:
+# 585.0 MB at 147,456 elements; the traffic scales with the element count).
+NCU_TRAFFIC_PER_ELEMENT = {("fp64", "k_local"): 585.0e6 / 147456}
 PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -344,7 +348,9 @@ def run_ours(args):
     achieved = flops[dom] * nodes / (kms[dom] * 1e-3) / 1e12
     peak = PEAK_FP32_TFLOPS if mixed else PEAK_FP64_TFLOPS
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": names[dom],
+                "frac": achieved / peak, "kernel": names[dom],
+                "traffic": (NCU_TRAFFIC_PER_ELEMENT[(args.mode, names[dom])] * ne
+                            if (args.mode, names[dom]) in NCU_TRAFFIC_PER_ELEMENT else None),
                 "peak_source": "derived: 152 SMs x %s FMA lanes x 2 x 2070 MHz"
                                % ("128 FP32" if mixed else "2 FP64"),
                 "algorithmic_flops_per_point": flops[dom],
