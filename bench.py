@@ -270,6 +270,77 @@ def fp32_variants(prob, u, ctx64, steps, warmup, stream, fp64_ms):
     return out
 
 
+def ensemble_leg(steps, warmup, nprob=96, seed=0, config=None, learned=True):
+    """Batched ensemble: nprob independent 2D Euler problems (sides uniform in
+    32..512, N in {3, 4}, vortex plus planar Riemann jump), FP32 bulk with the
+    learned alpha, advanced by one batch (autotuned threads per block and
+    mode, CUDA graphs); against the same problems stepped one at a time."""
+    import torch
+    from paper_2502_07517_gb300 import crkfr
+    t0 = time.perf_counter()
+    probs = wl.euler2d_ensemble(nprob=nprob, seed=seed)
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    nets = {N: train_alpha_network(N, stream.cuda_stream) for N in (3, 4)} if learned else None
+    ctxs = []
+    for prob, u in probs:
+        d = crkfr.desc_from_problem(prob, precision=crkfr.CR_FP32_BULK,
+                                    alpha_mode=crkfr.CR_ALPHA_MLP if learned else crkfr.CR_ALPHA_INDICATOR,
+                                    stream=stream.cuda_stream)
+        c = crkfr.cr_init_mesh(d)
+        if learned:
+            crkfr.cr_mlp_load(c, nets[prob["degree"]][0])
+        crkfr.cr_set_state(c, u)
+        ctxs.append(c)
+    nodes = sum(u.shape[1] * u.shape[2] for _, u in probs)
+    b = crkfr.cr_batch_init(ctxs)
+    if config:  # "threads/mode", e.g. "256/fused": fixed instead of tuned
+        threads, mode = int(config.split("/")[0]), int(config.split("/")[1] == "fused")
+        crkfr.cr_batch_config(b, threads, mode)
+        cand = np.full(4, np.nan)
+    else:
+        threads, mode, cand = crkfr.cr_batch_autotune(b, 2)
+
+    def reset():
+        for (prob, u), c in zip(probs, ctxs):
+            crkfr.cr_set_state(c, u)
+        torch.cuda.synchronize()
+
+    reset()
+    crkfr.cr_batch_step(b, warmup)
+    reset()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    crkfr.cr_batch_step_async(b, steps)
+    e1.record(stream)
+    crkfr.cr_batch_sync(b)
+    batch_ms = e0.elapsed_time(e1)
+    # the same problems, one problem's steps at a time (its own launches, then the next)
+    reset()
+    for c in ctxs:
+        crkfr.cr_step(c, warmup, 1e300)
+    reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in ctxs:
+        crkfr.cr_step(c, steps, 1e300)
+    seq_s = time.perf_counter() - t0
+    a = np.concatenate([crkfr.cr_get_alpha(c, u.shape[1]) for (prob, u), c in zip(probs, ctxs)])
+    names = ["128/phases", "128/fused", "256/phases", "256/fused"]
+    return {"problems": nprob, "elements": int(sum(u.shape[1] for _, u in probs)), "dofs": int(nodes),
+            "degrees": {"3": sum(p["degree"] == 3 for p, _ in probs), "4": sum(p["degree"] == 4 for p, _ in probs)},
+            "steps": steps, "value": nodes * steps / (batch_ms * 1e-3), "unit": "DOF-updates/s",
+            "ms_per_step": batch_ms / steps,
+            "sequential_value": nodes * steps / seq_s, "sequential_ms_per_step": seq_s * 1e3 / steps,
+            "speedup_vs_sequential": seq_s * 1e3 / batch_ms,
+            "autotune": {"chosen": "%d/%s" % (threads, "fused" if mode else "phases"),
+                         "ms_per_step": {nm: float(x) for nm, x in zip(names, cand)}},
+            "alpha_networks": {str(N): nets[N][1] for N in (3, 4)} if learned else None,
+            "alpha_mean": float(a.mean()), "generate_s": gen_s,
+            "precision": "FP32 bulk + FP64 means/limiter theta, " +
+                         ("learned alpha (BF16 weights)" if learned else "indicator alpha")}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -367,6 +438,9 @@ def run_ours(args):
     variants = None
     if not mixed and not args.quick and not args.no_variants:
         variants = fp32_variants(prob, u, ctx, args.steps, args.warmup, stream, ms_per_step)
+    ensemble = None
+    if not args.quick and not args.no_ensemble:
+        ensemble = ensemble_leg(args.steps, args.warmup, seed=rank)
 
     # ---- end to end through the public API with host buffers ----
     if args.quick:
@@ -405,7 +479,7 @@ def run_ours(args):
                    "limiters": "blend+MUSCL-Hancock+flux+scaling",
                    "l2": "inputs larger than L2 (state %.0f MB)" % (u.size * (4 if mixed else 8) / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": roofline, "hbm_roofline": hbm, "variants": variants,
+        "roofline": roofline, "hbm_roofline": hbm, "variants": variants, "ensemble": ensemble,
         "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches * args.steps, "t_reached": t_s, "steps_run": n_s,
     }
@@ -424,12 +498,28 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--nx", type=int, default=WORKLOAD["nx"],
                     help="elements per direction (smaller meshes of the same recipe for profiling)")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the batched-ensemble leg (96 problems in one batch)")
+    ap.add_argument("--ensemble-only", action="store_true",
+                    help="run only the batched-ensemble leg and print it")
+    ap.add_argument("--ens-problems", type=int, default=96, help="problems in the ensemble leg")
+    ap.add_argument("--ens-config", default=None,
+                    help="fixed batch configuration threads/mode (128|256 / phases|fused) instead of autotuning")
+    ap.add_argument("--ens-indicator", action="store_true",
+                    help="ensemble leg with the indicator's alpha (no network training)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32 bulk / learned-alpha comparison legs")
     ap.add_argument("--quick", action="store_true",
                     help="device timing only (no CPU baseline, no end-to-end leg)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.ensemble_only:
+        import torch
+        from paper_2502_07517_gb300 import build as lib_build
+        lib_build.build()
+        torch.cuda.set_device(0)
+        print(json.dumps(ensemble_leg(args.steps, args.warmup, nprob=args.ens_problems,
+                                      config=args.ens_config, learned=not args.ens_indicator)))
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -160,8 +160,10 @@ cr_status cr_get_features(cr_ctx* ctx, float* features, double* alpha_raw, int o
 /* Cross-entropy loss -mean(t log y + (1 - t) log(1 - y)) of the network on
  * samples X[n][nin] with targets t[n] in [0, 1] (the indicator's alpha taken
  * as a probability) and its gradient (same layout as the parameters), on the
- * GPU.  All pointers are
- * device pointers; grad and loss are overwritten.  Ordered on stream. */
+ * GPU.  All pointers are device pointers; grad and loss are overwritten.
+ * Per-block partial sums are added in a fixed order, so the result is the
+ * same on every run.  Ordered on stream; takes a small stream-ordered scratch
+ * allocation (cudaMallocAsync) for the partial sums. */
 cr_status cr_mlp_grad(int nin, const float* params, const float* X, const float* t, int n,
                       float* grad, float* loss, void* stream);
 
@@ -169,6 +171,7 @@ cr_status cr_mlp_grad(int nin, const float* params, const float* X, const float*
  * 0.999, eps 1e-8, learning rate lr) on minibatches of size batch from a
  * seeded shuffle of X[n][nin], t[n] (device), for the given number of epochs.
  * epoch_loss (host, may be NULL) receives the mean loss of the last epoch.
+ * Deterministic: the same inputs and seed give the same parameters.
  * Allocates its own device scratch; synchronises stream. */
 cr_status cr_mlp_train(int nin, float* params, const float* X, const float* t, int n, int batch,
                        int epochs, float lr, unsigned long long seed, float* epoch_loss,
@@ -227,6 +230,58 @@ cr_status cr_step_static(const cr_mesh_desc* desc, const double* u_in, double* u
 
 /* Last error message of ctx (or of the last failed cr_init_mesh when ctx is NULL). */
 const char* cr_last_error(const cr_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many independent problems advanced together.  The paper treats one
+ * problem at a time; a batch runs the same step (Sec. 3 eq. (crkfr.avg) with
+ * the limiters of Sec. 4 and the time step of eq. (time.step.2d), each problem
+ * with its own dt) for every problem of a set of contexts, in one launch per
+ * phase or in one persistent launch, so many small meshes fill the GPU.  A
+ * batched step computes exactly what cr_step computes on each context.
+ * Supported: 2D Euler, degree 3 or 4 (mixed in one batch), all contexts in the
+ * same precision.  The contexts keep their state and remain usable with
+ * cr_set_state / cr_get_state / cr_get_alpha / cr_mlp_load. */
+typedef struct cr_batch cr_batch;
+enum {
+  CR_BATCH_PHASES = 0, /* three launches per step (local, face, update) over all problems */
+  CR_BATCH_FUSED = 1   /* one cooperative persistent launch for all phases of up to 8 steps,
+                          with a grid barrier (bounded wait) between phases */
+};
+
+/* Group n contexts (pointers owned by the caller; they must outlive the
+ * batch).  Allocates the batch's small device tables (parameters, tiles).
+ * Default configuration: 256 threads per block, CR_BATCH_FUSED.  Synchronises
+ * the contexts' streams.  Errors: CR_E_INVALID_ARG, CR_E_UNSUPPORTED,
+ * CR_E_NOMEM, CR_E_CUDA. */
+cr_status cr_batch_init(cr_ctx* const* ctxs, int n, cr_batch** out);
+void cr_batch_destroy(cr_batch* batch);
+
+/* Threads per block (128 or 256: elements per block = threads / (N+1)^2) and
+ * mode (CR_BATCH_PHASES or CR_BATCH_FUSED). */
+cr_status cr_batch_config(cr_batch* batch, int threads, int mode);
+
+/* Autotuner: times one step of each (threads, mode) candidate in turn, for
+ * trial_steps rounds after one warm-up round, on the batch's own problems
+ * (CUDA events), and keeps the candidate with the fastest step.  The problems
+ * advance by 4 * (trial_steps + 1) steps: tune before setting the state of
+ * the real run.  ms_per_step (host, may be NULL) receives each candidate's
+ * fastest step, in the order (128, PHASES), (128, FUSED), (256, PHASES),
+ * (256, FUSED). */
+cr_status cr_batch_autotune(cr_batch* batch, int trial_steps, int* threads, int* mode,
+                            double* ms_per_step);
+
+/* Advance every problem by up to nsteps steps (each stops at t_final, the
+ * last step clipped to land on it).  Ordered after work already queued on the
+ * contexts' streams; enqueued on the first context's stream.  Call
+ * cr_batch_sync before using a context on its own again. */
+cr_status cr_batch_step_async(cr_batch* batch, int nsteps, double t_final);
+/* Wait for the batch; CR_E_TIMEOUT if a grid barrier gave up (the fused
+ * kernel then returned early), CR_E_INADMISSIBLE naming the first problem
+ * whose step produced an inadmissible state. */
+cr_status cr_batch_sync(cr_batch* batch);
+/* cr_batch_step_async followed by cr_batch_sync. */
+cr_status cr_batch_step(cr_batch* batch, int nsteps, double t_final);
+const char* cr_batch_last_error(const cr_batch* batch);
 
 #ifdef __cplusplus
 }

@@ -22,13 +22,16 @@ CR_BC_PERIODIC, CR_BC_OUTFLOW = 0, 1
 CR_LIM_BLEND, CR_LIM_MH, CR_LIM_FLUX, CR_LIM_SCALING, CR_LIM_TRACES = 1, 2, 4, 8, 16
 CR_ALPHA_INDICATOR, CR_ALPHA_FIXED, CR_ALPHA_MLP = 0, 1, 2
 CR_FP64, CR_FP32_BULK = 0, 1
+CR_BATCH_PHASES, CR_BATCH_FUSED = 0, 1
 
 # C symbols declared in include/cr.h
 SYMBOLS = ("cr_workspace_bytes", "cr_init_mesh", "cr_destroy", "cr_set_state", "cr_get_state",
            "cr_step", "cr_step_async", "cr_sync", "cr_get_alpha", "cr_get_means", "cr_next_dt",
            "cr_launches_per_step", "cr_profile_steps", "cr_cfl_number", "cr_reference_tables",
            "cr_step_static", "cr_last_error", "cr_mlp_param_count", "cr_mlp_load",
-           "cr_get_features", "cr_mlp_grad", "cr_mlp_train")
+           "cr_get_features", "cr_mlp_grad", "cr_mlp_train", "cr_batch_init", "cr_batch_destroy",
+           "cr_batch_config", "cr_batch_autotune", "cr_batch_step_async", "cr_batch_sync",
+           "cr_batch_step", "cr_batch_last_error")
 
 
 class CrError(RuntimeError):
@@ -93,8 +96,18 @@ def lib():
         L.cr_mlp_train.argtypes = [I, V, V, V, I, I, I, ctypes.c_float, ctypes.c_ulonglong, F, V]
         L.cr_last_error.argtypes = [V]
         L.cr_last_error.restype = ctypes.c_char_p
+        L.cr_batch_init.argtypes = [ctypes.POINTER(V), I, ctypes.POINTER(V)]
+        L.cr_batch_destroy.argtypes = [V]
+        L.cr_batch_destroy.restype = None
+        L.cr_batch_config.argtypes = [V, I, I]
+        L.cr_batch_autotune.argtypes = [V, I, ctypes.POINTER(I), ctypes.POINTER(I), D]
+        L.cr_batch_step_async.argtypes = [V, I, ctypes.c_double]
+        L.cr_batch_sync.argtypes = [V]
+        L.cr_batch_step.argtypes = [V, I, ctypes.c_double]
+        L.cr_batch_last_error.argtypes = [V]
+        L.cr_batch_last_error.restype = ctypes.c_char_p
         for s in SYMBOLS:
-            if s not in ("cr_destroy", "cr_last_error"):
+            if s not in ("cr_destroy", "cr_last_error", "cr_batch_destroy", "cr_batch_last_error"):
                 getattr(L, s).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -292,6 +305,69 @@ def cr_mlp_train(nin, params, X, t, batch, epochs, lr, seed=0, stream=None):
     if st != CR_OK:
         raise CrError(st, "cr_mlp_train")
     return out.value
+
+
+class Batch:
+    """Owns a cr_batch; keeps its contexts alive."""
+
+    def __init__(self, handle, ctxs):
+        self.handle = handle
+        self.ctxs = list(ctxs)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().cr_batch_destroy(self.handle)
+            self.handle = None
+
+
+def _bcheck(st, b=None):
+    if st != CR_OK:
+        msg = lib().cr_batch_last_error(b.handle if b is not None else None)
+        raise CrError(st, msg.decode() if msg else "")
+
+
+def cr_batch_init(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.handle.value if isinstance(c.handle, ctypes.c_void_p)
+                                          else c.handle for c in ctxs])
+    out = ctypes.c_void_p()
+    _bcheck(lib().cr_batch_init(arr, len(ctxs), ctypes.byref(out)))
+    return Batch(out, ctxs)
+
+
+def cr_batch_destroy(b):
+    if b.handle:
+        lib().cr_batch_destroy(b.handle)
+        b.handle = None
+
+
+def cr_batch_config(b, threads, mode):
+    _bcheck(lib().cr_batch_config(b.handle, int(threads), int(mode)), b)
+
+
+def cr_batch_autotune(b, trial_steps=3):
+    """Returns (threads, mode, ms per step of the 4 candidates)."""
+    t, m = ctypes.c_int(), ctypes.c_int()
+    ms = np.zeros(4)
+    _bcheck(lib().cr_batch_autotune(b.handle, int(trial_steps), ctypes.byref(t), ctypes.byref(m),
+                                    _dptr(ms)), b)
+    return t.value, m.value, ms
+
+
+def cr_batch_step_async(b, nsteps, t_final=1e300):
+    _bcheck(lib().cr_batch_step_async(b.handle, int(nsteps), float(t_final)), b)
+
+
+def cr_batch_sync(b):
+    _bcheck(lib().cr_batch_sync(b.handle), b)
+
+
+def cr_batch_step(b, nsteps, t_final=1e300):
+    _bcheck(lib().cr_batch_step(b.handle, int(nsteps), float(t_final)), b)
+
+
+def cr_batch_last_error(b=None):
+    msg = lib().cr_batch_last_error(b.handle if b is not None else None)
+    return msg.decode() if msg else ""
 
 
 def cr_last_error(ctx=None):

@@ -1,0 +1,50 @@
+// Batched stepping of many independent 2D Euler problems (degrees 3 and 4) in
+// one launch per phase, or in one persistent launch for all phases and steps.
+// The kernels run the same per-block bodies as the single-problem kernels
+// (local_body, face_body, update_body), so a batched step computes exactly
+// what the single-problem step computes.  Interface between cr_batch.cu (the
+// kernels) and cr_host.cu (the C ABI).
+#pragma once
+#include "cr_common.cuh"
+
+namespace crk {
+
+// One unit of work: block blk of problem prob.
+struct BatchTile {
+  int prob, blk;
+};
+
+template <typename real>
+struct BatchArgs {
+  Tab<real> tb[2];              // tables of degree 3 and 4 in the bulk type (kernel parameters,
+  Tab<double> td[2];            // like the single-problem kernels'), and in FP64
+  const KParams<real>* P;       // [nprob] parameters of every problem (device)
+  const int* deg;               // [nprob] degree, 3 or 4
+  const int* nblk_el;           // [nprob] element blocks of the problem (update phase count)
+  const BatchTile* t_el;        // element tiles (local and update phases), all problems
+  int n_el;
+  const BatchTile* t_face;      // face-node tiles, all problems
+  int n_face;
+  unsigned* bar;                // [2] grid barrier: arrivals, generation (fused launch)
+  int* err;                     // set when a grid barrier gave up waiting
+  int nsteps;                   // steps per fused launch
+};
+
+// Threads per block the batched kernels are built for.
+constexpr int kBatchThreadChoices[2] = {128, 256};
+
+// Shared memory (bytes) of the largest body for a block of `threads` threads.
+size_t batch_smem(int threads, bool fp32);
+// Set the kernels' shared-memory limits; returns the first error.
+cudaError_t batch_configure(int threads, bool fp32);
+// Blocks of the fused kernel that fit on the device at once (cooperative grid).
+cudaError_t batch_fused_max_blocks(int threads, bool fp32, int* blocks);
+// phase 0 local, 1 face, 2 update: one launch over all tiles of the phase.
+cudaError_t batch_launch_phase(int threads, int phase, const void* args, bool fp32,
+                               cudaStream_t s);
+// Start a run on every problem (t_final, CFL time step; plans the first step).
+cudaError_t batch_set_run(const void* P, int n, double t_final, bool fp32, cudaStream_t s);
+// All phases of A.nsteps steps in one cooperative launch of `grid` blocks.
+cudaError_t batch_launch_fused(int threads, int grid, const void* args, bool fp32, cudaStream_t s);
+
+}  // namespace crk

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/cr.h"
+#include "cr_batch.cuh"
 #include "cr_launch.cuh"
 
 using namespace crk;
@@ -823,5 +824,350 @@ cr_status cr_launches_per_step(cr_ctx* c, int* launches) {
 const char* cr_last_error(const cr_ctx* c) {
   return c ? c->err.c_str() : g_init_error.c_str();
 }
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches: many contexts advanced together by the kernels of cr_batch.cu.
+struct cr_batch {
+  std::vector<cr_ctx*> ctx;
+  bool fp32 = false;
+  cudaStream_t stream = nullptr;
+  int threads = 256, mode = CR_BATCH_FUSED;
+  int fused_grid = 0;
+  unsigned char* dmem = nullptr;     // parameters, degrees, block counts, tiles, barrier
+  size_t params_off = 0, deg_off = 0, nblk_off = 0, tel_off = 0, tface_off = 0, bar_off = 0;
+  size_t max_el = 0, max_face = 0;   // tile capacity (the smallest block size)
+  BatchArgs<float> af{};
+  BatchArgs<double> ad{};
+  cudaGraphExec_t g1 = nullptr, g8 = nullptr;
+  std::vector<cudaEvent_t> ev;       // one per context stream (ordering before a step)
+  int* h_err = nullptr;              // pinned copy of the barrier error flag
+  std::string err;
+};
+
+namespace {
+
+cr_status bfail(cr_batch* b, cr_status st, const std::string& msg) {
+  if (b) b->err = msg;
+  else g_init_error = msg;
+  return st;
+}
+
+#define CR_BCUDA(b, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t _e = (call);                                                               \
+    if (_e != cudaSuccess) return bfail((b), CR_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+// Element and face-node tile counts of one problem for a block of `threads`.
+void tile_counts(const cr_ctx* c, int threads, int* nel, int* nface) {
+  const int n = c->d.degree + 1, np = n * n;
+  const int epr = threads / np;
+  const int nx = c->d.nx, ny = c->d.ny;
+  const int ne = nx * ny;
+  const int nfx = c->d.bc_x == CR_BC_PERIODIC ? nx : nx + 1;
+  const int nfy = c->d.bc_y == CR_BC_PERIODIC ? ny : ny + 1;
+  const long long fnodes = (long long)ny * nfx * n + (long long)nfy * nx * n;
+  *nel = (ne + epr - 1) / epr;
+  *nface = (int)((fnodes + threads - 1) / threads);
+}
+
+void destroy_graphs(cr_batch* b) {
+  if (b->g1) cudaGraphExecDestroy(b->g1);
+  if (b->g8) cudaGraphExecDestroy(b->g8);
+  b->g1 = b->g8 = nullptr;
+}
+
+// Tiles, block counts and launch arguments for b->threads; graphs of 1 and 8
+// steps in b->mode.
+cr_status batch_build(cr_batch* b) {
+  destroy_graphs(b);
+  const int nprob = (int)b->ctx.size();
+  std::vector<BatchTile> tel, tface;
+  std::vector<int> nblk(nprob);
+  for (int i = 0; i < nprob; ++i) {
+    int nel, nface;
+    tile_counts(b->ctx[i], b->threads, &nel, &nface);
+    nblk[i] = nel;
+    for (int k = 0; k < nel; ++k) tel.push_back({i, k});
+    for (int k = 0; k < nface; ++k) tface.push_back({i, k});
+  }
+  if (tel.size() > b->max_el || tface.size() > b->max_face)
+    return bfail(b, CR_E_INVALID_ARG, "tile capacity exceeded");
+  unsigned char* d = b->dmem;
+  CR_BCUDA(b, cudaMemcpyAsync(d + b->nblk_off, nblk.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  CR_BCUDA(b, cudaMemcpyAsync(d + b->tel_off, tel.data(), tel.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
+  CR_BCUDA(b, cudaMemcpyAsync(d + b->tface_off, tface.data(), tface.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
+  CR_BCUDA(b, cudaStreamSynchronize(b->stream));
+  auto fill = [&](auto& A, auto* P) {
+    A.P = P;
+    A.deg = reinterpret_cast<const int*>(d + b->deg_off);
+    A.nblk_el = reinterpret_cast<const int*>(d + b->nblk_off);
+    A.t_el = reinterpret_cast<const BatchTile*>(d + b->tel_off);
+    A.n_el = (int)tel.size();
+    A.t_face = reinterpret_cast<const BatchTile*>(d + b->tface_off);
+    A.n_face = (int)tface.size();
+    A.bar = reinterpret_cast<unsigned*>(d + b->bar_off);
+    A.err = reinterpret_cast<int*>(d + b->bar_off + 8);
+  };
+  fill(b->af, reinterpret_cast<const KParams<float>*>(d + b->params_off));
+  fill(b->ad, reinterpret_cast<const KParams<double>*>(d + b->params_off));
+  for (cr_ctx* c : b->ctx) {  // the tables depend only on the degree
+    const int i = c->d.degree - 3;
+    b->af.tb[i] = c->pf.tb;
+    b->af.td[i] = c->pf.td;
+    b->ad.tb[i] = c->pd.tb;
+    b->ad.td[i] = c->pd.td;
+  }
+  CR_BCUDA(b, batch_configure(b->threads, b->fp32));
+  if (b->mode == CR_BATCH_FUSED) {
+    int maxb = 0;
+    CR_BCUDA(b, batch_fused_max_blocks(b->threads, b->fp32, &maxb));
+    if (maxb < 1) return bfail(b, CR_E_CUDA, "the fused batch kernel does not fit on an SM");
+    const int want = b->af.n_el > b->af.n_face ? b->af.n_el : b->af.n_face;
+    b->fused_grid = want < maxb ? want : maxb;
+  }
+  // graphs of 1 and 8 steps (direct launches if capture is refused)
+  for (int which = 0; which < 2; ++which) {
+    const int nsteps = which == 0 ? 1 : 8;
+    b->af.nsteps = b->ad.nsteps = nsteps;
+    const void* args = b->fp32 ? static_cast<const void*>(&b->af) : static_cast<const void*>(&b->ad);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
+    cudaError_t e = cudaSuccess;
+    if (b->mode == CR_BATCH_FUSED) {
+      e = batch_launch_fused(b->threads, b->fused_grid, args, b->fp32, b->stream);
+    } else {
+      for (int s = 0; s < nsteps && e == cudaSuccess; ++s)
+        for (int ph = 0; ph < 3 && e == cudaSuccess; ++ph)
+          e = batch_launch_phase(b->threads, ph, args, b->fp32, b->stream);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess && e2 == cudaSuccess && g) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !ex) {
+      cudaGetLastError();
+      destroy_graphs(b);
+      break;
+    }
+    (which == 0 ? b->g1 : b->g8) = ex;
+  }
+  return CR_OK;
+}
+
+cr_status batch_launch_steps(cr_batch* b, int nsteps) {
+  const void* args = b->fp32 ? static_cast<const void*>(&b->af) : static_cast<const void*>(&b->ad);
+  while (nsteps > 0) {
+    const int k = nsteps >= 8 ? 8 : 1;
+    cudaGraphExec_t g = k == 8 ? b->g8 : b->g1;
+    if (g) {
+      CR_BCUDA(b, cudaGraphLaunch(g, b->stream));
+    } else {
+      b->af.nsteps = b->ad.nsteps = k;
+      if (b->mode == CR_BATCH_FUSED) {
+        CR_BCUDA(b, batch_launch_fused(b->threads, b->fused_grid, args, b->fp32, b->stream));
+      } else {
+        for (int s = 0; s < k; ++s)
+          for (int ph = 0; ph < 3; ++ph) CR_BCUDA(b, batch_launch_phase(b->threads, ph, args, b->fp32, b->stream));
+      }
+    }
+    nsteps -= k;
+  }
+  return CR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cr_status cr_batch_init(cr_ctx* const* ctxs, int n, cr_batch** out) {
+  if (!ctxs || n < 1 || !out) return bfail(nullptr, CR_E_INVALID_ARG, "cr_batch_init: bad arguments");
+  *out = nullptr;
+  cr_batch* b = new (std::nothrow) cr_batch();
+  if (!b) return bfail(nullptr, CR_E_NOMEM, "cr_batch_init: out of host memory");
+  auto bail = [&](cr_status st) {
+    if (st != CR_OK) g_init_error = b->err;
+    cr_batch_destroy(b);
+    return st;
+  };
+  for (int i = 0; i < n; ++i) {
+    cr_ctx* c = ctxs[i];
+    if (!c) return bail(bfail(b, CR_E_INVALID_ARG, "cr_batch_init: NULL context"));
+    const cr_mesh_desc& d = c->d;
+    if (d.dim != 2 || d.equation != CR_EQ_EULER || (d.degree != 3 && d.degree != 4))
+      return bail(bfail(b, CR_E_UNSUPPORTED, "cr_batch_init: batches hold 2D Euler problems of degree 3 or 4"));
+    if (i > 0 && d.precision != ctxs[0]->d.precision)
+      return bail(bfail(b, CR_E_INVALID_ARG, "cr_batch_init: mixed precisions"));
+    b->ctx.push_back(c);
+  }
+  b->fp32 = ctxs[0]->d.precision == CR_FP32_BULK;
+  b->stream = ctxs[0]->stream;
+  // capacity for the smallest block size
+  size_t mel = 0, mface = 0;
+  for (cr_ctx* c : b->ctx) {
+    int nel, nface;
+    tile_counts(c, kBatchThreadChoices[0], &nel, &nface);
+    mel += nel;
+    mface += nface;
+  }
+  b->max_el = mel;
+  b->max_face = mface;
+  const size_t psz = b->fp32 ? sizeof(KParams<float>) : sizeof(KParams<double>);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off += align256(bytes); return o; };
+  b->params_off = take(psz * n);
+  b->deg_off = take(sizeof(int) * n);
+  b->nblk_off = take(sizeof(int) * n);
+  b->tel_off = take(sizeof(BatchTile) * mel);
+  b->tface_off = take(sizeof(BatchTile) * mface);
+  b->bar_off = take(16);
+  cudaError_t e = cudaMalloc(&b->dmem, off);
+  if (e != cudaSuccess) return bail(bfail(b, CR_E_NOMEM, "cr_batch_init: cudaMalloc failed"));
+  e = cudaMallocHost(&b->h_err, sizeof(int));
+  if (e != cudaSuccess) return bail(bfail(b, CR_E_NOMEM, "cr_batch_init: cudaMallocHost failed"));
+  std::vector<unsigned char> hp(psz * n);
+  std::vector<int> deg(n);
+  for (int i = 0; i < n; ++i) {
+    memcpy(hp.data() + psz * i, b->fp32 ? static_cast<const void*>(&b->ctx[i]->pf)
+                                        : static_cast<const void*>(&b->ctx[i]->pd), psz);
+    deg[i] = b->ctx[i]->d.degree;
+  }
+  for (cr_ctx* c : b->ctx)  // the contexts' queued work (cr_set_state) comes first
+    if (c->stream != b->stream && cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return bail(bfail(b, CR_E_CUDA, "cr_batch_init: a context stream failed"));
+  e = cudaMemcpyAsync(b->dmem + b->params_off, hp.data(), hp.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->dmem + b->deg_off, deg.data(), n * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->dmem + b->bar_off, 0, 16, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bail(bfail(b, CR_E_CUDA, std::string("cr_batch_init: ") + cudaGetErrorString(e)));
+  for (cr_ctx* c : b->ctx) {
+    if (c->stream == b->stream) continue;
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+      return bail(bfail(b, CR_E_CUDA, "cr_batch_init: cudaEventCreate failed"));
+    b->ev.push_back(ev);
+  }
+  cr_status st = batch_build(b);
+  if (st != CR_OK) return bail(st);
+  *out = b;
+  return CR_OK;
+}
+
+void cr_batch_destroy(cr_batch* b) {
+  if (!b) return;
+  destroy_graphs(b);
+  for (cudaEvent_t ev : b->ev) cudaEventDestroy(ev);
+  if (b->dmem) cudaFree(b->dmem);
+  if (b->h_err) cudaFreeHost(b->h_err);
+  delete b;
+}
+
+cr_status cr_batch_config(cr_batch* b, int threads, int mode) {
+  if (!b) return bfail(nullptr, CR_E_INVALID_ARG, "NULL batch");
+  if ((threads != kBatchThreadChoices[0] && threads != kBatchThreadChoices[1]) ||
+      (mode != CR_BATCH_PHASES && mode != CR_BATCH_FUSED))
+    return bfail(b, CR_E_INVALID_ARG, "cr_batch_config: threads must be 128 or 256, mode PHASES or FUSED");
+  b->threads = threads;
+  b->mode = mode;
+  return batch_build(b);
+}
+
+cr_status cr_batch_step_async(cr_batch* b, int nsteps, double t_final) {
+  if (!b) return bfail(nullptr, CR_E_INVALID_ARG, "NULL batch");
+  if (nsteps < 0 || !(t_final == t_final)) return bfail(b, CR_E_INVALID_ARG, "bad nsteps or t_final");
+  size_t k = 0;
+  for (cr_ctx* c : b->ctx) {  // work queued on the contexts' own streams comes first
+    if (c->stream == b->stream) continue;
+    CR_BCUDA(b, cudaEventRecord(b->ev[k], c->stream));
+    CR_BCUDA(b, cudaStreamWaitEvent(b->stream, b->ev[k], 0));
+    ++k;
+  }
+  const void* P = b->dmem + b->params_off;
+  CR_BCUDA(b, batch_set_run(P, (int)b->ctx.size(), t_final, b->fp32, b->stream));
+  return batch_launch_steps(b, nsteps);
+}
+
+cr_status cr_batch_sync(cr_batch* b) {
+  if (!b) return bfail(nullptr, CR_E_INVALID_ARG, "NULL batch");
+  CR_BCUDA(b, cudaMemcpyAsync(b->h_err, b->dmem + b->bar_off + 8, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  CR_BCUDA(b, cudaStreamSynchronize(b->stream));
+  if (*b->h_err) return bfail(b, CR_E_TIMEOUT, "cr_batch_sync: a grid barrier of the fused kernel gave up waiting");
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    cr_ctx* c = b->ctx[i];
+    cr_status st = read_ctl(c);
+    if (st != CR_OK) return bfail(b, st, "cr_batch_sync: problem " + std::to_string(i) + ": " + c->err);
+    if (c->h_ctl->status & (kStInadmissible | kStNonFinite))
+      return bfail(b, CR_E_INADMISSIBLE, "problem " + std::to_string(i) +
+                                             ": inadmissible or non-finite state after a step, element " +
+                                             std::to_string(c->h_ctl->bad_elem));
+  }
+  return CR_OK;
+}
+
+cr_status cr_batch_step(cr_batch* b, int nsteps, double t_final) {
+  cr_status st = cr_batch_step_async(b, nsteps, t_final);
+  if (st != CR_OK) return st;
+  return cr_batch_sync(b);
+}
+
+cr_status cr_batch_autotune(cr_batch* b, int trial_steps, int* threads_out, int* mode_out,
+                            double* ms_per_step) {
+  if (!b || trial_steps < 1) return bfail(b, CR_E_INVALID_ARG, "cr_batch_autotune: bad arguments");
+  const int cand_t[4] = {kBatchThreadChoices[0], kBatchThreadChoices[0], kBatchThreadChoices[1],
+                         kBatchThreadChoices[1]};
+  const int cand_m[4] = {CR_BATCH_PHASES, CR_BATCH_FUSED, CR_BATCH_PHASES, CR_BATCH_FUSED};
+  double best_ms[4] = {1e300, 1e300, 1e300, 1e300};
+  cudaEvent_t e0, e1;
+  CR_BCUDA(b, cudaEventCreate(&e0));
+  CR_BCUDA(b, cudaEventCreate(&e1));
+  const void* P = b->dmem + b->params_off;
+  cr_status st = CR_OK;
+  // Round 0 warms every candidate up (graph upload, first launch); rounds
+  // 1..trial_steps time one step of each candidate in turn, so the state the
+  // problems reach as they advance is shared fairly between the candidates;
+  // each candidate keeps its fastest step.
+  for (int r = 0; r <= trial_steps && st == CR_OK; ++r) {
+    for (int i = 0; i < 4 && st == CR_OK; ++i) {
+      b->threads = cand_t[i];
+      b->mode = cand_m[i];
+      st = batch_build(b);
+      if (st != CR_OK) break;
+      if (batch_set_run(P, (int)b->ctx.size(), 1e300, b->fp32, b->stream) != cudaSuccess) {
+        st = bfail(b, CR_E_CUDA, "cr_batch_autotune: launch failed");
+        break;
+      }
+      cudaEventRecord(e0, b->stream);
+      st = batch_launch_steps(b, 1);
+      cudaEventRecord(e1, b->stream);
+      if (st == CR_OK) st = cr_batch_sync(b);
+      float ms = 0.0f;
+      if (st == CR_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        st = bfail(b, CR_E_CUDA, "cr_batch_autotune: event timing");
+      if (st == CR_OK && r > 0 && ms < best_ms[i]) best_ms[i] = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != CR_OK) return st;
+  int bi = 0;
+  for (int i = 1; i < 4; ++i)
+    if (best_ms[i] < best_ms[bi]) bi = i;
+  if (ms_per_step)
+    for (int i = 0; i < 4; ++i) ms_per_step[i] = best_ms[i];
+  b->threads = cand_t[bi];
+  b->mode = cand_m[bi];
+  st = batch_build(b);
+  if (threads_out) *threads_out = cand_t[bi];
+  if (mode_out) *mode_out = cand_m[bi];
+  return st;
+}
+
+const char* cr_batch_last_error(const cr_batch* b) { return b ? b->err.c_str() : g_init_error.c_str(); }
 
 }  // extern "C"

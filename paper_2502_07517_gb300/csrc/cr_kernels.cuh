@@ -122,8 +122,12 @@ struct OpMin {
 };
 
 // ===========================================================================
+// Body of k_local for block blk of a problem (the standalone kernel and the
+// batched kernels of cr_batch.cu call it).  Threads past the block's last whole
+// element form an invalid "ghost" slot, so any block size works.
 template <int DIM, int N, class EQ, typename real, bool MIXED>
-__global__ void k_local(const KParams<real> P) {
+__device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<real>& tb,
+                                           const int blk) {
   constexpr int n = N + 1;
   constexpr int NP = DIM == 2 ? n * n : n;
   constexpr int M = EQ::M;
@@ -135,13 +139,13 @@ __global__ void k_local(const KParams<real> P) {
   using TB = Tableau<N>;
   const Mesh& m = P.m;
   const Phys<real>& ph = P.ph;
-  const Tab<real>& tb = P.tb;
-  const int epb = blockDim.x / NP;
+  const int epb = (blockDim.x + NP - 1) / NP;  // element slots in shared memory
+  const int epr = blockDim.x / NP;             // whole elements of the block
   const int tid = threadIdx.x;
   const int el = tid / NP, k = tid - el * NP;
   const int p = DIM == 2 ? k % n : k, q = DIM == 2 ? k / n : 0;
-  const int e = blockIdx.x * epb + el;
-  const bool valid = e < m.ne;
+  const int e = blk * epr + el;
+  const bool valid = el < epr && e < m.ne;
   const int ee = valid ? e : m.ne - 1;
   const int ix = ee % m.nx, iy = ee / m.nx;
 
@@ -511,9 +515,14 @@ __global__ void k_local(const KParams<real> P) {
 #undef AT
 }
 
+template <int DIM, int N, class EQ, typename real, bool MIXED>
+__global__ void k_local(const __grid_constant__ KParams<real> P) {
+  local_body<DIM, N, EQ, real, MIXED>(P, P.tb, blockIdx.x);
+}
+
 // ===========================================================================
 template <int DIM, int N, class EQ, typename real>
-__global__ void k_face(const KParams<real> P) {
+__device__ __forceinline__ void face_body(const KParams<real>& P, const int blk) {
   constexpr int n = N + 1;
   constexpr int M = EQ::M;
   constexpr int NSIDE = DIM == 2 ? 4 : 2;
@@ -523,7 +532,7 @@ __global__ void k_face(const KParams<real> P) {
   if (!(dtd > 0.0)) return;
   const int nX = m.ny * m.nfx * NFN;
   const int nY = DIM == 2 ? m.nfy * m.nx * n : 0;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = blk * blockDim.x + threadIdx.x;
   if (idx >= nX + nY) return;
   int dir, j, eL, eR;
   size_t out_idx, vstride;
@@ -690,6 +699,11 @@ __global__ void k_face(const KParams<real> P) {
   for (int v = 0; v < M; ++v) out[v * vstride + out_idx] = Fr[v];
 }
 
+template <int DIM, int N, class EQ, typename real>
+__global__ void k_face(const __grid_constant__ KParams<real> P) {
+  face_body<DIM, N, EQ, real>(P, blockIdx.x);
+}
+
 // ===========================================================================
 // Element-level helpers for k_update / k_prologue (one thread per node, EPB
 // elements per block).  Per-element reductions are trees over the element's
@@ -825,12 +839,12 @@ __device__ T indicator_alpha(const Mesh& m, const Tab<T>& tb, T* E, T* Tm, T* re
 // finish the step: block max of the CFL rate, last block publishes the rate,
 // advances time when advance != 0, and resets the accumulators.
 __device__ __forceinline__ void finish_block(TimeCtl* ctl, double block_rate, int advance,
-                                             double dtd, int last_step) {
+                                             double dtd, int last_step, int nblk) {
   if (threadIdx.x == 0) {
     atomicMax(&ctl->rate_acc, (unsigned long long)__double_as_longlong(block_rate));
     __threadfence();
     const unsigned prev = atomicAdd(&ctl->blocks_done, 1u);
-    if (prev == gridDim.x - 1) {
+    if (prev == unsigned(nblk) - 1u) {
       __threadfence();
       const unsigned long long bits = atomicExch(&ctl->rate_acc, 0ull);
       ctl->rate_last = __longlong_as_double((long long)bits);
@@ -849,7 +863,8 @@ __device__ __forceinline__ void finish_block(TimeCtl* ctl, double block_rate, in
 template <int DIM, int NP, class EQ, typename T>
 __device__ __forceinline__ void rate_and_finish(const Mesh& m, const Phys<T>& ph, const T* ubar,
                                                 T* rbuf, int epb, int el, int k, bool valid,
-                                                TimeCtl* ctl, int advance, double dtd, int last) {
+                                                TimeCtl* ctl, int advance, double dtd, int last,
+                                                int nblk) {
   if (k < DIM) {
     const T r = EQ::speed(ubar, k, ph) * T(k == 0 ? m.invdx : m.invdy);
     rbuf[el * 2 + k] = valid ? r : T(0);
@@ -862,14 +877,15 @@ __device__ __forceinline__ void rate_and_finish(const Mesh& m, const Phys<T>& ph
       if (DIM == 2) r += double(rbuf[j * 2 + 1]);
       brate = fmax(brate, r);
     }
-  finish_block(ctl, brate, advance, dtd, last);
+  finish_block(ctl, brate, advance, dtd, last, nblk);
 }
 
 // ===========================================================================
 // k_update.  Shared memory (doubles): sU [MU][epb][NP] node values, sRed
 // [RW][epb][NP] reduction buffer, sEl [epb][16] per-element values.
 template <int DIM, int N, class EQ, typename real, bool MIXED>
-__global__ void k_update(const KParams<real> P) {
+__device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<real>& tb,
+                                            const Tab<double>& td, const int blk, const int nblk) {
   constexpr int n = N + 1;
   constexpr int NP = DIM == 2 ? n * n : n;
   constexpr int M = EQ::M;
@@ -880,16 +896,16 @@ __global__ void k_update(const KParams<real> P) {
   constexpr int RW = 2 * M > 4 ? 2 * M : 4;
   constexpr int MU = M > 2 ? M : 2;
   const Mesh& m = P.m;
-  const Tab<double>& td = P.td;
   const double dtd = P.b.ctl->dt_step;
   const int last_step = P.b.ctl->last_step;
   if (!(dtd > 0.0)) return;
-  const int epb = blockDim.x / NP;
+  const int epb = (blockDim.x + NP - 1) / NP;  // element slots in shared memory
+  const int epr = blockDim.x / NP;             // whole elements of the block
   const int tid = threadIdx.x;
   const int el = tid / NP, k = tid - el * NP;
   const int p = DIM == 2 ? k % n : k, q = DIM == 2 ? k / n : 0;
-  const int e = blockIdx.x * epb + el;
-  const bool valid = e < m.ne;
+  const int e = blk * epr + el;
+  const bool valid = el < epr && e < m.ne;
   const int ee = valid ? e : m.ne - 1;
   const int ix = ee % m.nx, iy = ee / m.nx;
   const int stride = epb * NP;
@@ -921,11 +937,11 @@ __global__ void k_update(const KParams<real> P) {
   const int iyT = DIM == 2 ? (m.bcy == 0 ? (iy + 1) % m.ny : iy + 1) : 0;
   const size_t nXf = (size_t)m.ny * m.nfx * NFN;
   const size_t nYf = DIM == 2 ? (size_t)m.nfy * m.nx * n : 0;
-  const real cRx = (one - a) * P.tb.gR[p] + (p == N ? a * P.tb.invw[N] : real(0));
-  const real cLx = (one - a) * P.tb.gL[p] - (p == 0 ? a * P.tb.invw[0] : real(0));
-  const real cRy = DIM == 2 ? (one - a) * P.tb.gR[q] + (q == N ? a * P.tb.invw[N] : real(0)) : real(0);
-  const real cLy = DIM == 2 ? (one - a) * P.tb.gL[q] - (q == 0 ? a * P.tb.invw[0] : real(0)) : real(0);
-  const real W = DIM == 2 ? P.tb.w[p] * P.tb.w[q] : P.tb.w[p];
+  const real cRx = (one - a) * tb.gR[p] + (p == N ? a * tb.invw[N] : real(0));
+  const real cLx = (one - a) * tb.gL[p] - (p == 0 ? a * tb.invw[0] : real(0));
+  const real cRy = DIM == 2 ? (one - a) * tb.gR[q] + (q == N ? a * tb.invw[N] : real(0)) : real(0);
+  const real cLy = DIM == 2 ? (one - a) * tb.gL[q] - (q == 0 ? a * tb.invw[0] : real(0)) : real(0);
+  const real W = DIM == 2 ? tb.w[p] * tb.w[q] : tb.w[p];
   real val[M];
 #pragma unroll
   for (int v = 0; v < M; ++v) {
@@ -958,13 +974,13 @@ __global__ void k_update(const KParams<real> P) {
 #pragma unroll
         for (int j = 0; j < NFN; ++j) {
           const real fv = P.b.fx[v * nXf + ((size_t)iy * m.nfx + fxi) * NFN + j];
-          acc += DIM == 2 ? P.tb.w[j] * fv : fv;
+          acc += DIM == 2 ? tb.w[j] * fv : fv;
         }
       } else {
         const int fyi = side == 2 ? iy : iyT;
 #pragma unroll
         for (int j = 0; j < n; ++j)
-          acc += P.tb.w[j] * P.b.fy[v * nYf + ((size_t)fyi * m.nx + ix) * n + j];
+          acc += tb.w[j] * P.b.fy[v * nYf + ((size_t)fyi * m.nx + ix) * n + j];
       }
       fI[el * NSIDE * M + t] = acc;
     }
@@ -1066,7 +1082,7 @@ __global__ void k_update(const KParams<real> P) {
             real acc = real(0);
 #pragma unroll
             for (int r = 0; r < n; ++r) {
-              const real l = (side & 1) ? P.tb.l1[r] : P.tb.l0[r];
+              const real l = (side & 1) ? tb.l1[r] : tb.l0[r];
               acc += l * sUr[v * stride + el * NP + (side < 2 ? r + n * j : j + n * r)];
             }
             pr[npt][v] = acc;
@@ -1088,10 +1104,18 @@ __global__ void k_update(const KParams<real> P) {
         if (!(pr[t][0] >= eps1 && EQ::constraint(pr[t], 1, P.phd) >= eps2)) need = 1;
       }
     }
-    if (__syncthreads_or(need)) {
+    // Only real elements vote (a ghost slot of a block whose size is not a
+    // multiple of the element size holds partial data), and only an element
+    // with a failing point takes the FP64 result below: the others keep their
+    // values bit for bit, whichever elements share their block.
+    if (__syncthreads_or(valid && need)) {
       // FP64 path (oracle's limiter): points in FP64
       double pts[1 + SPT][M];
       int np2 = 1;
+      __syncthreads();
+      RED(0) = need ? 0.0 : 1.0;
+      elem_tree<NP, 1>(sRed, epb, el, k, OpMin());
+      const bool elem_need = RED0(0) == 0.0;
       __syncthreads();
 #pragma unroll
       for (int v = 0; v < M; ++v) {
@@ -1153,13 +1177,15 @@ __global__ void k_update(const KParams<real> P) {
         for (int t = 0; t < np2; ++t)
 #pragma unroll
           for (int v = 0; v < M; ++v) pts[t][v] = ubar[v] + th2 * (pts[t][v] - ubar[v]);
-      if (mean_ok)
-        for (int t = 0; t < np2; ++t)
-          if (!admissible<EQ>(pts[t], P.phd)) bad |= kStInadmissible;
+      if (elem_need) {
+        if (mean_ok)
+          for (int t = 0; t < np2; ++t)
+            if (!admissible<EQ>(pts[t], P.phd)) bad |= kStInadmissible;
 #pragma unroll
-      for (int v = 0; v < M; ++v) {
-        if constexpr (MIXED) fl[v] = real(pts[0][v] - ubar[v]);
-        ur[v] = real(pts[0][v]);
+        for (int v = 0; v < M; ++v) {
+          if constexpr (MIXED) fl[v] = real(pts[0][v] - ubar[v]);
+          ur[v] = real(pts[0][v]);
+        }
       }
     }
   }
@@ -1194,7 +1220,7 @@ __global__ void k_update(const KParams<real> P) {
       __syncthreads();
       rE[el * NP + k] = EQ::indicator_var(ur, P.ph);
       __syncthreads();
-      const real al = indicator_alpha<DIM, N, real>(m, P.tb, rE, rT, rR, epb, el, k, P.b.mlp_flag,
+      const real al = indicator_alpha<DIM, N, real>(m, tb, rE, rT, rR, epb, el, k, P.b.mlp_flag,
                                                     P.b.mlp_w, sMlp, nullptr, -1);
       if (valid && k == 0) P.b.alpha_raw[e] = double(al);
     } else {
@@ -1211,32 +1237,38 @@ __global__ void k_update(const KParams<real> P) {
   __syncthreads();
   if constexpr (MIXED) {
     rate_and_finish<DIM, NP, EQ, float>(m, P.ph, ubr, reinterpret_cast<float*>(sEl), epb, el, k,
-                                        valid, P.b.ctl, 1, dtd, last_step);
+                                        valid, P.b.ctl, 1, dtd, last_step, nblk);
   } else {
     rate_and_finish<DIM, NP, EQ, double>(m, P.phd, ubar, sEl, epb, el, k, valid, P.b.ctl, 1, dtd,
-                                         last_step);
+                                         last_step, nblk);
   }
 #undef ATU
 #undef RED
 #undef RED0
 }
 
+template <int DIM, int N, class EQ, typename real, bool MIXED>
+__global__ void k_update(const __grid_constant__ KParams<real> P) {
+  update_body<DIM, N, EQ, real, MIXED>(P, P.tb, P.td, blockIdx.x, gridDim.x);
+}
+
 // ===========================================================================
 // After cr_set_state: validate the input, compute the indicator of the state
 // and the CFL rate of eq. (time.step.2d) (no time advance).
 template <int DIM, int N, class EQ, typename real, bool MIXED>
-__global__ void k_prologue(const KParams<real> P) {
+__global__ void k_prologue(const __grid_constant__ KParams<real> P) {
   constexpr int n = N + 1;
   constexpr int NP = DIM == 2 ? n * n : n;
   constexpr int M = EQ::M;
   constexpr int RW = 2 * M > 4 ? 2 * M : 4;
   constexpr int MU = M > 2 ? M : 2;
   const Mesh& m = P.m;
-  const int epb = blockDim.x / NP;
+  const int epb = (blockDim.x + NP - 1) / NP;  // element slots in shared memory
+  const int epr = blockDim.x / NP;             // whole elements of the block
   const int tid = threadIdx.x;
   const int el = tid / NP, k = tid - el * NP;
-  const int e = blockIdx.x * epb + el;
-  const bool valid = e < m.ne;
+  const int e = blockIdx.x * epr + el;
+  const bool valid = el < epr && e < m.ne;
   const int ee = valid ? e : m.ne - 1;
   const int stride = epb * NP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1274,7 +1306,8 @@ __global__ void k_prologue(const KParams<real> P) {
     if (valid && k == 0) P.b.alpha_raw[e] = al;
   }
   __syncthreads();
-  rate_and_finish<DIM, NP, EQ, double>(m, P.phd, ubar, sEl, epb, el, k, valid, P.b.ctl, 0, 0.0, 0);
+  rate_and_finish<DIM, NP, EQ, double>(m, P.phd, ubar, sEl, epb, el, k, valid, P.b.ctl, 0, 0.0, 0,
+                                       gridDim.x);
 }
 
 // FP32_BULK state conversion: FP64 nodal values <-> FP64 mean + FP32 fluctuation.

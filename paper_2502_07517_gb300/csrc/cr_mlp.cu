@@ -22,17 +22,18 @@ __host__ __device__ constexpr int param_count(int nin) {
 }
 
 // Gradient of the cross-entropy over samples [0, n) (indices through idx
-// when given), accumulated into grad (same layout as the parameters); loss
-// accumulates (t softplus(-z) + (1 - t) softplus(z)) * inv_n.  One block handles chunks of 64
-// samples: threads 0..63 run forward and backward for one sample each into
-// shared memory, then all threads reduce their share of the gradient entries.
+// when given) and the loss (t softplus(-z) + (1 - t) softplus(z)) * inv_n.
+// One block handles chunks of 64 samples: threads 0..63 run forward and
+// backward for one sample each into shared memory, then all threads reduce
+// their share of the gradient entries.  Block b writes its partial sums to
+// part[b][0..P) and its loss to part[b][P]; k_mlp_reduce adds the blocks in a
+// fixed order, so the result does not depend on block scheduling.
 template <int NIN>
 __global__ void __launch_bounds__(kThreads) k_mlp_grad(const float* __restrict__ prm,
                                                         const float* __restrict__ X,
                                                         const float* __restrict__ T,
                                                         const int* __restrict__ idx, int n,
-                                                        float inv_n, float* __restrict__ grad,
-                                                        float* __restrict__ loss) {
+                                                        float inv_n, float* __restrict__ part) {
   constexpr int P = param_count(NIN);
   constexpr int PER = (P + kThreads - 1) / kThreads;
   constexpr int REC = NIN + 4 * kH + 1;  // x, h1, da1, h2, da2, dz per sample
@@ -122,12 +123,32 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const float* __restrict__
     }
     __syncthreads();
   }
+  float* out = part + (size_t)blockIdx.x * (P + 1);
 #pragma unroll
   for (int r = 0; r < PER; ++r) {
     const int g = tid + r * kThreads;
-    if (g < P) atomicAdd(&grad[g], acc[r]);
+    if (g < P) out[g] = acc[r];
   }
-  if (lsum != 0.0f) atomicAdd(loss, lsum);
+  // block sum of the per-sample losses (threads >= 64 hold 0), fixed order
+  __syncthreads();
+  sr[tid] = lsum;
+  __syncthreads();
+  if (tid == 0) {
+    float l = 0.0f;
+    for (int i = 0; i < kThreads; ++i) l += sr[i];
+    out[P] = l;
+  }
+}
+
+// grad[g] = sum over blocks b = 0, 1, ... of part[b][g]; loss likewise (g = P).
+__global__ void k_mlp_reduce(const float* __restrict__ part, int nblocks, int P,
+                             float* __restrict__ grad, float* __restrict__ loss) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g > P) return;
+  float a = 0.0f;
+  for (int b = 0; b < nblocks; ++b) a += part[(size_t)b * (P + 1) + g];
+  if (g < P) grad[g] = a;
+  else *loss = a;
 }
 
 __global__ void k_mlp_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -144,31 +165,40 @@ __global__ void k_mlp_adam(float* __restrict__ p, const float* __restrict__ g, f
 
 __global__ void k_accumulate(float* dst, const float* src) { *dst += *src; }
 
+constexpr int kMaxGradBlocks = 304;  // two blocks per SM
+
+int grad_blocks(int n) {
+  int blocks = (n + kChunk - 1) / kChunk;
+  if (blocks > kMaxGradBlocks) blocks = kMaxGradBlocks;
+  return blocks < 1 ? 1 : blocks;
+}
+
+// Loss and gradient of samples [0, n) into grad and loss (overwritten); part
+// is scratch of grad_blocks(n) * (P + 1) floats.
 template <int NIN>
 cudaError_t launch_grad(const float* prm, const float* X, const float* T, const int* idx, int n,
-                        float* grad, float* loss, cudaStream_t s) {
+                        float* part, float* grad, float* loss, cudaStream_t s) {
   constexpr int P = param_count(NIN);
   const size_t smem = (size_t)(P + kChunk * (NIN + 4 * kH + 1)) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_mlp_grad<NIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  int blocks = (n + kChunk - 1) / kChunk;
-  if (blocks > 608) blocks = 608;
-  if (blocks < 1) blocks = 1;
-  k_mlp_grad<NIN><<<blocks, kThreads, smem, s>>>(prm, X, T, idx, n, 1.0f / float(n), grad, loss);
+  const int blocks = grad_blocks(n);
+  k_mlp_grad<NIN><<<blocks, kThreads, smem, s>>>(prm, X, T, idx, n, 1.0f / float(n), part);
+  k_mlp_reduce<<<(P + 1 + 255) / 256, 256, 0, s>>>(part, blocks, P, grad, loss);
   return cudaGetLastError();
 }
 
 cudaError_t dispatch_grad(int nin, const float* prm, const float* X, const float* T, const int* idx,
-                          int n, float* grad, float* loss, cudaStream_t s) {
+                          int n, float* part, float* grad, float* loss, cudaStream_t s) {
   switch (nin) {
-    case 2: return launch_grad<2>(prm, X, T, idx, n, grad, loss, s);
-    case 3: return launch_grad<3>(prm, X, T, idx, n, grad, loss, s);
-    case 4: return launch_grad<4>(prm, X, T, idx, n, grad, loss, s);
-    case 5: return launch_grad<5>(prm, X, T, idx, n, grad, loss, s);
-    case 9: return launch_grad<9>(prm, X, T, idx, n, grad, loss, s);
-    case 16: return launch_grad<16>(prm, X, T, idx, n, grad, loss, s);
-    case 25: return launch_grad<25>(prm, X, T, idx, n, grad, loss, s);
+    case 2: return launch_grad<2>(prm, X, T, idx, n, part, grad, loss, s);
+    case 3: return launch_grad<3>(prm, X, T, idx, n, part, grad, loss, s);
+    case 4: return launch_grad<4>(prm, X, T, idx, n, part, grad, loss, s);
+    case 5: return launch_grad<5>(prm, X, T, idx, n, part, grad, loss, s);
+    case 9: return launch_grad<9>(prm, X, T, idx, n, part, grad, loss, s);
+    case 16: return launch_grad<16>(prm, X, T, idx, n, part, grad, loss, s);
+    case 25: return launch_grad<25>(prm, X, T, idx, n, part, grad, loss, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -194,9 +224,13 @@ cr_status cr_mlp_grad(int nin, const float* params, const float* X, const float*
                       float* grad, float* loss, void* stream) {
   if (!nin_supported(nin) || !params || !X || !t || !grad || !loss || n < 1) return CR_E_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(grad, 0, sizeof(float) * param_count(nin), s) != cudaSuccess) return CR_E_CUDA;
-  if (cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return CR_E_CUDA;
-  return dispatch_grad(nin, params, X, t, nullptr, n, grad, loss, s) == cudaSuccess ? CR_OK : CR_E_CUDA;
+  float* part = nullptr;  // per-block partial sums, stream-ordered allocation
+  const size_t bytes = sizeof(float) * (size_t)grad_blocks(n) * (param_count(nin) + 1);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&part), bytes, s);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? CR_E_NOMEM : CR_E_CUDA;
+  e = dispatch_grad(nin, params, X, t, nullptr, n, part, grad, loss, s);
+  const cudaError_t e2 = cudaFreeAsync(part, s);
+  return (e == cudaSuccess && e2 == cudaSuccess) ? CR_OK : CR_E_CUDA;
 }
 
 cr_status cr_mlp_train(int nin, float* params, const float* X, const float* t, int n, int batch,
@@ -206,7 +240,7 @@ cr_status cr_mlp_train(int nin, float* params, const float* X, const float* t, i
     return CR_E_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int P = param_count(nin);
-  float *grad = nullptr, *mom = nullptr, *var = nullptr, *bl = nullptr, *el = nullptr;
+  float *grad = nullptr, *mom = nullptr, *var = nullptr, *bl = nullptr, *el = nullptr, *part = nullptr;
   int* idx = nullptr;
   cr_status st = CR_OK;
   auto ok = [&](cudaError_t e) {
@@ -219,6 +253,7 @@ cr_status cr_mlp_train(int nin, float* params, const float* X, const float* t, i
   ok(cudaMalloc(&bl, sizeof(float)));
   ok(cudaMalloc(&el, sizeof(float)));
   ok(cudaMalloc(&idx, sizeof(int) * n));
+  ok(cudaMalloc(&part, sizeof(float) * (size_t)grad_blocks(batch < n ? batch : n) * (P + 1)));
   if (st == CR_OK) {
     ok(cudaMemsetAsync(mom, 0, sizeof(float) * P, s));
     ok(cudaMemsetAsync(var, 0, sizeof(float) * P, s));
@@ -240,9 +275,7 @@ cr_status cr_mlp_train(int nin, float* params, const float* X, const float* t, i
     int nb = 0;
     for (int b0 = 0; b0 < n && st == CR_OK; b0 += batch, ++nb) {
       const int cnt = b0 + batch <= n ? batch : n - b0;
-      ok(cudaMemsetAsync(grad, 0, sizeof(float) * P, s));
-      ok(cudaMemsetAsync(bl, 0, sizeof(float), s));
-      ok(dispatch_grad(nin, params, X, t, idx + b0, cnt, grad, bl, s));
+      ok(dispatch_grad(nin, params, X, t, idx + b0, cnt, part, grad, bl, s));
       ++step;
       const float c1 = 1.0f - powf(0.9f, float(step)), c2 = 1.0f - powf(0.999f, float(step));
       k_mlp_adam<<<(P + 255) / 256, 256, 0, s>>>(params, grad, mom, var, P, lr, c1, c2);
@@ -262,6 +295,7 @@ cr_status cr_mlp_train(int nin, float* params, const float* X, const float* t, i
   cudaFree(bl);
   cudaFree(el);
   cudaFree(idx);
+  cudaFree(part);
   return st;
 }
 

@@ -187,6 +187,18 @@ def euler2d_vortex_riemann(nx=128, ny=None, degree=4, seed=0, limiter=LIMITER_AL
     return prob, euler_conservative(rho, v1, v2, p, prob["gamma"], 2)
 
 
+def euler2d_ensemble(nprob=96, seed=0, nmin=32, nmax=512, limiter=LIMITER_ALL):
+    """Independent 2D Euler problems for batched runs: side n uniform integer in
+    [nmin, nmax] (n x n elements), degree uniform in {3, 4}, each with the
+    vortex-plus-Riemann data of euler2d_vortex_riemann (its own seed).
+    Returns a list of (problem, state)."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(nmin, nmax + 1, nprob)
+    degs = rng.integers(3, 5, nprob)
+    return [euler2d_vortex_riemann(nx=int(n), degree=int(N), seed=seed * 1000 + i, limiter=limiter)
+            for i, (n, N) in enumerate(zip(sides, degs))]
+
+
 def tenmoment2d_voronoi(nx=256, ny=None, degree=3, seed=0, ncells=16, limiter=LIMITER_ALL,
                         steps=200, source=True):
     """2D ten-moment on [0,1]^2 periodic with the Gaussian source

