@@ -140,8 +140,8 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
-def make_workload(seed, nx=None):
-    prob, u = wl.euler2d_vortex(nx=nx or WORKLOAD["nx"], degree=WORKLOAD["degree"], seed=seed)
+def make_workload(seed, nx=None, degree=None):
+    prob, u = wl.euler2d_vortex(nx=nx or WORKLOAD["nx"], degree=degree or WORKLOAD["degree"], seed=seed)
     return prob, u
 
 
@@ -166,21 +166,28 @@ def cpu_baseline(target_s=10.0, nx=256):
 
 
 def train_alpha_network(degree, stream, seeds=range(1000, 1008), nx=96, snaps=(0, 10, 40),
-                        epochs=15):
+                        epochs=15, make=None, label=None):
     """Learned blending coefficient for this degree: network inputs and the
-    indicator's raw alpha harvested along GPU runs of the vortex-plus-Riemann
-    recipe (shocks and smooth flow), then Adam on the GPU (cr_mlp_train)."""
+    indicator's raw alpha harvested along GPU runs of a workload recipe (by
+    default the vortex-plus-Riemann recipe: shocks and smooth flow), then Adam
+    on the GPU (cr_mlp_train)."""
     import torch
     from paper_2502_07517_gb300 import crkfr
+    if make is None:
+        make = lambda seed: wl.euler2d_vortex_riemann(nx=nx, degree=degree, seed=seed)
+        label = "vortex + planar Riemann jump, %dx%d, N=%d" % (nx, nx, degree)
     X, T = [], []
     for seed in seeds:
-        prob, u = wl.euler2d_vortex_riemann(nx=nx, degree=degree, seed=seed)
+        prob, u = make(seed)
         ctx = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, stream=stream))
         crkfr.cr_set_state(ctx, u)
         done = 0
         for s in snaps:
             if s > done:
-                crkfr.cr_step(ctx, s - done, 1e300)
+                try:
+                    crkfr.cr_step(ctx, s - done, 1e300)
+                except crkfr.CrError:  # data that reach an inadmissible state: stop harvesting
+                    break
                 done = s
             f, a = crkfr.cr_get_features(ctx, u.shape[1], u.shape[2])
             X.append(f)
@@ -199,7 +206,7 @@ def train_alpha_network(degree, stream, seeds=range(1000, 1008), nx=96, snaps=(0
     crkfr.cr_mlp_grad(nin, p, Xd, Td, g, loss)
     params = p.cpu().numpy()
     # served by the fused inference kernel on a held-out seed: |alpha_net - alpha_indicator|
-    prob, u = wl.euler2d_vortex_riemann(nx=nx, degree=degree, seed=max(seeds) + 1)
+    prob, u = make(max(seeds) + 1)
     ctx = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, stream=stream))
     crkfr.cr_set_state(ctx, u)
     crkfr.cr_step(ctx, 20, 1e300)
@@ -212,8 +219,7 @@ def train_alpha_network(degree, stream, seeds=range(1000, 1008), nx=96, snaps=(0
             "cross_entropy": float(loss.item()), "target_mean": float(T.mean()),
             "heldout_mean_abs_alpha_err": float(np.abs(a_net - a_ind).mean()),
             "heldout_max_abs_alpha_err": float(np.abs(a_net - a_ind).max()),
-            "data": "vortex + planar Riemann jump, %dx%d, N=%d, %d seeds, steps %s"
-                    % (nx, nx, degree, len(seeds), list(snaps))}
+            "data": "%s, %d seeds, steps %s" % (label, len(seeds), list(snaps))}
     return params, info
 
 
@@ -267,6 +273,74 @@ def fp32_variants(prob, u, ctx64, steps, warmup, stream, fp64_ms):
                      "speedup_vs_fp64": fp64_ms / ms, "l1_rel_vs_fp64": l1_rel(g, ref),
                      "alpha_mean": float(a.mean()), "alpha_max": float(a.max())}
         crkfr.cr_destroy(ctx)
+    return out
+
+
+def config_legs(steps, warmup):
+    """The other workloads: 1D linear advection to t = 1 (error against the
+    exact solution), 1D Euler Riemann problems (4000 elements, N = 4) and 2D
+    ten-moment with the Gaussian source (256x256, N = 3), each in FP64 (plain,
+    indicator alpha) and FP32 bulk with the learned alpha (a network trained
+    for that workload on the GPU): device time per step, DOF-updates/s and the
+    normalised L1 difference from the FP64 path after the same steps at the
+    same fixed dt."""
+    import torch
+    from paper_2502_07517_gb300 import crkfr
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    out = {}
+    # linear advection, N = 3, 64 elements, CFL step to t = 1
+    prob, u = wl.linadv_sine(nx=64, degree=3, t_final=1.0)
+    ctx = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, stream=sp))
+    crkfr.cr_set_state(ctx, u)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t, n = crkfr.cr_step(ctx, 10 ** 6, 1.0)
+    wall = time.perf_counter() - t0
+    g = crkfr.cr_get_state(ctx, shape=u.shape)
+    x, _ = wl.node_coords(prob)
+    _, w = wl.gl_nodes01(3)
+    out["linadv1d_sine_64_N3"] = {
+        "steps_to_t1": n, "t": t, "wall_s": wall, "value": u.size * n / wall, "unit": "DOF-updates/s",
+        "l1_error_vs_exact": float((np.abs(g[0] - np.sin(2 * np.pi * (x - 1.0))) * w).sum() / 64),
+        "note": "256 DOF: launch-bound; the value is whole-run throughput including the host loop"}
+
+    def leg(name, prob, u, make, nin_label, seeds, snaps):
+        nodes = u.shape[1] * u.shape[2]
+        c64 = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, stream=sp))
+        crkfr.cr_set_state(c64, u)
+        ms64 = timed_steps(c64, steps, warmup, stream)
+        crkfr.cr_set_state(c64, u)
+        dt0 = crkfr.cr_next_dt(c64)
+        crkfr.cr_step(c64, steps, 1e300, dt0)
+        ref = crkfr.cr_get_state(c64, shape=u.shape)
+        params, info = train_alpha_network(prob["degree"], sp, seeds=seeds, snaps=snaps, make=make,
+                                           label=nin_label)
+        c32 = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, precision=crkfr.CR_FP32_BULK,
+                                                         alpha_mode=crkfr.CR_ALPHA_MLP, stream=sp))
+        crkfr.cr_mlp_load(c32, params)
+        crkfr.cr_set_state(c32, u)
+        ms32 = timed_steps(c32, steps, warmup, stream)
+        crkfr.cr_set_state(c32, u)
+        crkfr.cr_step(c32, steps, 1e300, dt0)
+        g = crkfr.cr_get_state(c32, shape=u.shape)
+        out[name] = {"dofs": nodes, "steps": steps,
+                     "fp64": {"value": nodes / (ms64 * 1e-3), "ms_per_step": ms64},
+                     "fp32_learned_alpha": {"value": nodes / (ms32 * 1e-3), "ms_per_step": ms32,
+                                            "speedup_vs_fp64": ms64 / ms32,
+                                            "l1_rel_vs_fp64": l1_rel(g, ref)},
+                     "alpha_network": info, "unit": "DOF-updates/s"}
+        for c in (c64, c32):
+            crkfr.cr_destroy(c)
+
+    prob, u = wl.euler1d_riemann(nx=4000, degree=4, seed=0)
+    leg("euler1d_riemann_4000_N4", prob, u,
+        lambda seed: wl.euler1d_riemann(nx=4000, degree=4, seed=seed),
+        "1D Euler Riemann problems, 4000 elements, N=4", range(1000, 1024), (0, 50, 200, 800))
+    prob, u = wl.tenmoment2d_voronoi(nx=256, degree=3, seed=0)
+    leg("tenmoment2d_voronoi_256x256_N3", prob, u,
+        lambda seed: wl.tenmoment2d_voronoi(nx=128, degree=3, seed=seed),
+        "ten-moment Voronoi states with source, 128x128, N=3", range(1000, 1020), (0, 5, 20))
     return out
 
 
@@ -378,7 +452,7 @@ def run_ours(args):
     from paper_2502_07517_gb300 import crkfr
 
     mixed = args.mode == "fp32"
-    prob, u = make_workload(seed=rank, nx=args.nx)
+    prob, u = make_workload(seed=rank, nx=args.nx, degree=args.degree)
     M, ne, npn = u.shape
     nodes = ne * npn
     stream = torch.cuda.Stream()
@@ -415,7 +489,7 @@ def run_ours(args):
     kms = crkfr.cr_profile_steps(ctx, args.steps, 1e300) / args.steps
     names = ["k_local", "k_face", "k_update"]
     dom = int(np.argmax(kms))
-    flops = flop_model(2, WORKLOAD["degree"], "euler2d")
+    flops = flop_model(2, prob["degree"], "euler2d")
     achieved = flops[dom] * nodes / (kms[dom] * 1e-3) / 1e12
     peak = PEAK_FP32_TFLOPS if mixed else PEAK_FP64_TFLOPS
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -441,6 +515,9 @@ def run_ours(args):
     ensemble = None
     if not args.quick and not args.no_ensemble:
         ensemble = ensemble_leg(args.steps, args.warmup, seed=rank)
+    configs = None
+    if not args.quick and not args.no_configs:
+        configs = config_legs(args.steps, args.warmup)
 
     # ---- end to end through the public API with host buffers ----
     if args.quick:
@@ -473,13 +550,15 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"] if args.nx == WORKLOAD["nx"] else
-                   "euler2d_vortex_%dx%d_N4" % (args.nx, args.nx), "elements": ne, "points_per_element": npn,
+        "config": {"workload": WORKLOAD["name"] if (args.nx, args.degree) == (WORKLOAD["nx"], WORKLOAD["degree"])
+                   else "euler2d_vortex_%dx%d_N%d" % (args.nx, args.nx, args.degree),
+                   "elements": ne, "points_per_element": npn,
                    "variables": M, "mode": args.mode,
                    "limiters": "blend+MUSCL-Hancock+flux+scaling",
                    "l2": "inputs larger than L2 (state %.0f MB)" % (u.size * (4 if mixed else 8) / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roofline, "hbm_roofline": hbm, "variants": variants, "ensemble": ensemble,
+        "other_workloads": configs,
         "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches * args.steps, "t_reached": t_s, "steps_run": n_s,
     }
@@ -502,6 +581,9 @@ def main():
                     help="skip the batched-ensemble leg (96 problems in one batch)")
     ap.add_argument("--ensemble-only", action="store_true",
                     help="run only the batched-ensemble leg and print it")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the legs of the other workloads (1D linear advection, 1D Euler, ten-moment)")
+    ap.add_argument("--configs-only", action="store_true", help="run only those legs and print them")
     ap.add_argument("--ens-problems", type=int, default=96, help="problems in the ensemble leg")
     ap.add_argument("--ens-config", default=None,
                     help="fixed batch configuration threads/mode (128|256 / phases|fused) instead of autotuning")
@@ -509,10 +591,18 @@ def main():
                     help="ensemble leg with the indicator's alpha (no network training)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32 bulk / learned-alpha comparison legs")
+    ap.add_argument("--degree", type=int, default=WORKLOAD["degree"],
+                    help="degree N of the same recipe (profiling; the bench workload is N = 4)")
     ap.add_argument("--quick", action="store_true",
                     help="device timing only (no CPU baseline, no end-to-end leg)")
     args = ap.parse_args()
-    if args.ensemble_only:
+    if args.configs_only:
+        import torch
+        from paper_2502_07517_gb300 import build as lib_build
+        lib_build.build()
+        torch.cuda.set_device(0)
+        print(json.dumps(config_legs(args.steps, args.warmup)))
+    elif args.ensemble_only:
         import torch
         from paper_2502_07517_gb300 import build as lib_build
         lib_build.build()

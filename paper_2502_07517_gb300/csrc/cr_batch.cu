@@ -98,15 +98,24 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
   return *reinterpret_cast<volatile int*>(err) == 0;
 }
 
+// Resident blocks per SM: as the single-problem kernels (MinBlocks), scaled
+// from 256-thread blocks to T threads.
+template <typename real, int T, int PHASE>
+struct BatchMinBlocks {
+  static constexpr bool MIXED = sizeof(real) == 4;
+  static constexpr int per256 = PHASE == 0 ? MinBlocks<MIXED>::local : MinBlocks<MIXED>::update;
+  static constexpr int value = per256 * 256 / T;
+};
+
 template <typename real, int T>
-__global__ void __launch_bounds__(T) k_batch_local(const __grid_constant__ BatchArgs<real> A) {
+__global__ void __launch_bounds__(T, (BatchMinBlocks<real, T, 0>::value)) k_batch_local(const __grid_constant__ BatchArgs<real> A) {
   __shared__ __align__(16) KParams<real> sP;
   int cur = -1;
   el_tile<real, 0>(A, &sP, blockIdx.x, cur);
 }
 
 template <typename real, int T>
-__global__ void __launch_bounds__(T) k_batch_update(const __grid_constant__ BatchArgs<real> A) {
+__global__ void __launch_bounds__(T, (BatchMinBlocks<real, T, 2>::value)) k_batch_update(const __grid_constant__ BatchArgs<real> A) {
   __shared__ __align__(16) KParams<real> sP;
   int cur = -1;
   el_tile<real, 2>(A, &sP, blockIdx.x, cur);

@@ -515,8 +515,17 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
 #undef AT
 }
 
+// Resident blocks per SM the step kernels ask for (measured on GB300,
+// 2D Euler N = 4, 512x512): FP32_BULK blocks are latency bound and gain from
+// four 256-thread blocks per SM (64 registers; k_local 1.39 -> 1.05 ms,
+// k_update 0.91 -> 0.60 ms); the FP64 k_local is bound by the FP64 pipe and
+// gains 3% from two blocks (128 registers instead of 130).
+template <bool MIXED> struct MinBlocks {
+  static constexpr int local = MIXED ? 4 : 2, update = MIXED ? 4 : 1;
+};
+
 template <int DIM, int N, class EQ, typename real, bool MIXED>
-__global__ void k_local(const __grid_constant__ KParams<real> P) {
+__global__ void __launch_bounds__(256, MinBlocks<MIXED>::local) k_local(const __grid_constant__ KParams<real> P) {
   local_body<DIM, N, EQ, real, MIXED>(P, P.tb, blockIdx.x);
 }
 
@@ -1248,7 +1257,7 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
 }
 
 template <int DIM, int N, class EQ, typename real, bool MIXED>
-__global__ void k_update(const __grid_constant__ KParams<real> P) {
+__global__ void __launch_bounds__(256, MinBlocks<MIXED>::update) k_update(const __grid_constant__ KParams<real> P) {
   update_body<DIM, N, EQ, real, MIXED>(P, P.tb, P.td, blockIdx.x, gridDim.x);
 }
 
