@@ -13,6 +13,14 @@
  * no blocking, fusion or reordering.  Where the paper defers a detail to
  * another paper, the reading taken is stated beside the code.
  *
+ * Pins (tests/test_oracle_pins.py, tests/test_oracle_mlp.py): closed forms,
+ * exact solutions, invariants and brute force for every step of the scheme.
+ * The smoothness indicator (or_indicator) follows a method the paper cites
+ * without printing it; its constants are readings.  It is pinned only by
+ * special cases (constant and linear data give 0, a jump gives 1) and its
+ * modal energies (or_modal_energies) by pure Legendre modes: beyond these,
+ * parity unpinned.
+ *
  * Layout of a state vector: u[(v * Ne + e) * Np + k], variable v, element
  * e = ix + nx * iy, node k = p + (N + 1) * q (p along x, q along y).
  */
