@@ -135,6 +135,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_timing(ms, nodes, steps, world, tdist=None, device="cpu"):
+    """Replicas: every rank timed its own workload of `nodes` solution points for
+    `steps` steps; the job's time is the slowest rank's and its throughput counts
+    the points of all ranks.  Returns (ms_max, DOF-updates/s)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * nodes * steps / (ms * 1e-3)
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
         int(os.environ.get("LOCAL_RANK", 0))
@@ -478,12 +490,8 @@ def run_ours(args):
     if world > 1:
         tdist.barrier()
     ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms, value = aggregate_timing(ms, nodes, args.steps, world, tdist if world > 1 else None, "cuda")
     ms_per_step = ms / args.steps
-    value = world * nodes * args.steps / (ms * 1e-3)
 
     # ---- per-kernel device times (same workload, every kernel between events) ----
     kms = crkfr.cr_profile_steps(ctx, args.steps, 1e300) / args.steps

@@ -283,6 +283,17 @@ cr_status cr_batch_sync(cr_batch* batch);
 cr_status cr_batch_step(cr_batch* batch, int nsteps, double t_final);
 const char* cr_batch_last_error(const cr_batch* batch);
 
+/* Fault injection for tests of the fused kernel's timeout path (no
+ * counterpart in the paper).  Sets the grid barrier's wait budget to `polls`
+ * polls of at least 64 ns each (0 restores the default, 2^26, at least 4 s) and
+ * makes every barrier wait for `phantom` further blocks that never arrive.
+ * With phantom > 0 each block's wait runs out after its budget, the block sets
+ * the batch's error flag and returns; no block traps or hangs.  The next
+ * cr_batch_sync then returns CR_E_TIMEOUT and clears the flag and the barrier;
+ * the problems' states are undefined until they are set again.  No effect in
+ * CR_BATCH_PHASES mode (no grid barrier). */
+cr_status cr_batch_barrier_test(cr_batch* batch, unsigned long long polls, int phantom);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,7 @@ SYMBOLS = ("cr_workspace_bytes", "cr_init_mesh", "cr_destroy", "cr_set_state", "
            "cr_step_static", "cr_last_error", "cr_mlp_param_count", "cr_mlp_load",
            "cr_get_features", "cr_mlp_grad", "cr_mlp_train", "cr_batch_init", "cr_batch_destroy",
            "cr_batch_config", "cr_batch_autotune", "cr_batch_step_async", "cr_batch_sync",
-           "cr_batch_step", "cr_batch_last_error")
+           "cr_batch_step", "cr_batch_last_error", "cr_batch_barrier_test")
 
 
 class CrError(RuntimeError):
@@ -104,6 +104,7 @@ def lib():
         L.cr_batch_step_async.argtypes = [V, I, ctypes.c_double]
         L.cr_batch_sync.argtypes = [V]
         L.cr_batch_step.argtypes = [V, I, ctypes.c_double]
+        L.cr_batch_barrier_test.argtypes = [V, ctypes.c_ulonglong, I]
         L.cr_batch_last_error.argtypes = [V]
         L.cr_batch_last_error.restype = ctypes.c_char_p
         for s in SYMBOLS:
@@ -363,6 +364,11 @@ def cr_batch_sync(b):
 
 def cr_batch_step(b, nsteps, t_final=1e300):
     _bcheck(lib().cr_batch_step(b.handle, int(nsteps), float(t_final)), b)
+
+
+def cr_batch_barrier_test(b, polls, phantom):
+    """Fault injection for the fused kernel's timeout path (tests)."""
+    _bcheck(lib().cr_batch_barrier_test(b.handle, int(polls), int(phantom)), b)
 
 
 def cr_batch_last_error(b=None):

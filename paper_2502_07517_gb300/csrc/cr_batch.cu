@@ -10,7 +10,7 @@
 //       the tiles of every problem (three launches per step for the batch).
 //   k_batch_fused : one cooperative, persistent launch for all phases of
 //       nsteps steps; blocks stride over the tiles and meet at a grid barrier
-//       between phases.  The barrier's wait is bounded: after kBarrierSpins
+//       between phases.  The barrier's wait is bounded: after A.spin_limit
 //       polls it sets the error flag and every block returns.
 #include <cstdint>
 
@@ -21,7 +21,6 @@ namespace crk {
 namespace {
 
 using Eq2 = EqEuler<2>;
-constexpr unsigned long long kBarrierSpins = 1ull << 26;  // >= 4 s of 64 ns sleeps
 
 template <typename real>
 struct SharedParams {
@@ -70,22 +69,23 @@ __device__ __forceinline__ void face_tile(const BatchArgs<real>& A, KParams<real
 }
 
 // Grid-wide barrier of a cooperative launch (all blocks resident).  Thread 0
-// of each block arrives on bar[0]; the last arrival resets it and advances the
-// generation bar[1]; the others poll the generation with a bounded wait.
-__device__ bool grid_barrier(unsigned* bar, int* err) {
+// of each block arrives on bar[0]; the last of gridDim.x + phantom arrivals
+// resets it and advances the generation bar[1]; the others poll the
+// generation, at most spin_limit times.
+__device__ bool grid_barrier(unsigned* bar, int* err, unsigned long long spin_limit, int phantom) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* gen = bar + 1;
     const unsigned g = *gen;
     __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1u) {
+    if (atomicAdd(bar, 1u) == gridDim.x + unsigned(phantom) - 1u) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
       unsigned long long spins = 0;
       while (*gen == g) {
-        if (++spins > kBarrierSpins) {
+        if (++spins > spin_limit) {
           atomicOr(err, 1);
           break;
         }
@@ -136,11 +136,11 @@ __global__ void __launch_bounds__(T, 65536 / (T * 128)) k_batch_fused(const __gr
   int cur = -1;
   for (int s = 0; s < A.nsteps; ++s) {
     for (int t = blockIdx.x; t < A.n_el; t += gridDim.x) el_tile<real, 0>(A, &sP, t, cur);
-    if (!grid_barrier(A.bar, A.err)) return;
+    if (!grid_barrier(A.bar, A.err, A.spin_limit, A.phantom)) return;
     for (int t = blockIdx.x; t < A.n_face; t += gridDim.x) face_tile<real>(A, &sP, t, cur);
-    if (!grid_barrier(A.bar, A.err)) return;
+    if (!grid_barrier(A.bar, A.err, A.spin_limit, A.phantom)) return;
     for (int t = blockIdx.x; t < A.n_el; t += gridDim.x) el_tile<real, 2>(A, &sP, t, cur);
-    if (!grid_barrier(A.bar, A.err)) return;
+    if (!grid_barrier(A.bar, A.err, A.spin_limit, A.phantom)) return;
   }
 }
 

@@ -27,6 +27,9 @@ struct BatchArgs {
   int n_face;
   unsigned* bar;                // [2] grid barrier: arrivals, generation (fused launch)
   int* err;                     // set when a grid barrier gave up waiting
+  unsigned long long spin_limit;  // polls (>= 64 ns each) before a barrier gives up
+  int phantom;                  // extra arrivals the barrier waits for (0; > 0 only in tests
+                                // of the timeout path: they never come)
   int nsteps;                   // steps per fused launch
 };
 

@@ -834,6 +834,8 @@ struct cr_batch {
   bool fp32 = false;
   cudaStream_t stream = nullptr;
   int threads = 256, mode = CR_BATCH_FUSED;
+  unsigned long long spin_limit = 1ull << 26;  // grid-barrier polls (>= 64 ns each): >= 4 s
+  int phantom = 0;                             // test hook: arrivals that never come
   int fused_grid = 0;
   unsigned char* dmem = nullptr;     // parameters, degrees, block counts, tiles, barrier
   size_t params_off = 0, deg_off = 0, nblk_off = 0, tel_off = 0, tface_off = 0, bar_off = 0;
@@ -910,6 +912,8 @@ cr_status batch_build(cr_batch* b) {
     A.n_face = (int)tface.size();
     A.bar = reinterpret_cast<unsigned*>(d + b->bar_off);
     A.err = reinterpret_cast<int*>(d + b->bar_off + 8);
+    A.spin_limit = b->spin_limit;
+    A.phantom = b->phantom;
   };
   fill(b->af, reinterpret_cast<const KParams<float>*>(d + b->params_off));
   fill(b->ad, reinterpret_cast<const KParams<double>*>(d + b->params_off));
@@ -1097,7 +1101,11 @@ cr_status cr_batch_sync(cr_batch* b) {
   if (!b) return bfail(nullptr, CR_E_INVALID_ARG, "NULL batch");
   CR_BCUDA(b, cudaMemcpyAsync(b->h_err, b->dmem + b->bar_off + 8, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   CR_BCUDA(b, cudaStreamSynchronize(b->stream));
-  if (*b->h_err) return bfail(b, CR_E_TIMEOUT, "cr_batch_sync: a grid barrier of the fused kernel gave up waiting");
+  if (*b->h_err) {  // clear the barrier and the flag so that the batch can run again
+    CR_BCUDA(b, cudaMemsetAsync(b->dmem + b->bar_off, 0, 16, b->stream));
+    CR_BCUDA(b, cudaStreamSynchronize(b->stream));
+    return bfail(b, CR_E_TIMEOUT, "cr_batch_sync: a grid barrier of the fused kernel gave up waiting");
+  }
   for (size_t i = 0; i < b->ctx.size(); ++i) {
     cr_ctx* c = b->ctx[i];
     cr_status st = read_ctl(c);
@@ -1166,6 +1174,13 @@ cr_status cr_batch_autotune(cr_batch* b, int trial_steps, int* threads_out, int*
   if (threads_out) *threads_out = cand_t[bi];
   if (mode_out) *mode_out = cand_m[bi];
   return st;
+}
+
+cr_status cr_batch_barrier_test(cr_batch* b, unsigned long long polls, int phantom) {
+  if (!b || phantom < 0) return bfail(b, CR_E_INVALID_ARG, "cr_batch_barrier_test: bad arguments");
+  b->spin_limit = polls ? polls : (1ull << 26);
+  b->phantom = phantom;
+  return batch_build(b);
 }
 
 const char* cr_batch_last_error(const cr_batch* b) { return b ? b->err.c_str() : g_init_error.c_str(); }

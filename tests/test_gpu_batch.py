@@ -179,3 +179,27 @@ def test_batch_rejects_unsupported_problems():
     with pytest.raises(crkfr.CrError) as ei:
         crkfr.cr_batch_init(c64 + c32)
     assert ei.value.status == -1
+
+
+def test_fused_barrier_timeout_is_reported_and_recoverable():
+    """A barrier that waits for a block that never arrives (fault injection):
+    every block gives up after its wait budget and returns, cr_batch_step
+    reports CR_E_TIMEOUT, and after the states are set again the batch steps
+    exactly like the single-problem path.  No block traps or hangs."""
+    import time
+    probs = _problems(70, shapes=[((13, 11), 4), ((7, 5), 3)])
+    ctxs = _contexts(probs, crkfr.CR_FP64)
+    b = crkfr.cr_batch_init(ctxs)
+    crkfr.cr_batch_config(b, 256, crkfr.CR_BATCH_FUSED)
+    crkfr.cr_batch_barrier_test(b, 20000, 1)
+    t0 = time.perf_counter()
+    with pytest.raises(crkfr.CrError) as ei:
+        crkfr.cr_batch_step(b, 1)
+    assert ei.value.status == -4
+    assert time.perf_counter() - t0 < 30.0
+    crkfr.cr_batch_barrier_test(b, 0, 0)
+    for (prob, u), c in zip(probs, ctxs):
+        crkfr.cr_set_state(c, u)
+    crkfr.cr_batch_step(b, 3)
+    got = [crkfr.cr_get_state(c, shape=u.shape) for (prob, u), c in zip(probs, ctxs)]
+    _same(got, _alone(probs, crkfr.CR_FP64, 3), crkfr.CR_FP64, "after timeout")

@@ -280,3 +280,22 @@ def test_tenmoment_256_one_step_full_size():
 def test_euler1d_4000_full_size():
     prob, u = wl.euler1d_riemann(nx=4000, degree=4, seed=0)
     one_step_check(prob, u)
+
+
+def test_checkpoint_resume_is_bitwise():
+    """cr_get_state / cr_set_state are a checkpoint: 3 + 3 steps through a fresh
+    context equal 6 steps in one run, bit for bit (FP64, limiters acting)."""
+    prob, u = _jumpy_2d(11, 9, 4, seed=9)
+    d = crkfr.desc_from_problem(prob)
+    a = crkfr.cr_init_mesh(d)
+    crkfr.cr_set_state(a, u)
+    crkfr.cr_step(a, 6, 1e300)
+    full = crkfr.cr_get_state(a, shape=u.shape)
+    b = crkfr.cr_init_mesh(d)
+    crkfr.cr_set_state(b, u)
+    crkfr.cr_step(b, 3, 1e300)
+    mid = crkfr.cr_get_state(b, shape=u.shape)
+    c = crkfr.cr_init_mesh(d)
+    crkfr.cr_set_state(c, mid)
+    crkfr.cr_step(c, 3, 1e300)
+    np.testing.assert_array_equal(crkfr.cr_get_state(c, shape=u.shape), full)
