@@ -356,7 +356,7 @@ def config_legs(steps, warmup):
     return out
 
 
-def ensemble_leg(steps, warmup, nprob=96, seed=0, config=None, learned=True):
+def ensemble_leg(steps, warmup, nprob=96, seed=0, config=None, learned=True, nmin=32, nmax=512):
     """Batched ensemble: nprob independent 2D Euler problems (sides uniform in
     32..512, N in {3, 4}, vortex plus planar Riemann jump), FP32 bulk with the
     learned alpha, advanced by one batch (autotuned threads per block and
@@ -364,7 +364,7 @@ def ensemble_leg(steps, warmup, nprob=96, seed=0, config=None, learned=True):
     import torch
     from paper_2502_07517_gb300 import crkfr
     t0 = time.perf_counter()
-    probs = wl.euler2d_ensemble(nprob=nprob, seed=seed)
+    probs = wl.euler2d_ensemble(nprob=nprob, seed=seed, nmin=nmin, nmax=nmax)
     gen_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
     nets = {N: train_alpha_network(N, stream.cuda_stream) for N in (3, 4)} if learned else None
@@ -413,7 +413,8 @@ def ensemble_leg(steps, warmup, nprob=96, seed=0, config=None, learned=True):
     seq_s = time.perf_counter() - t0
     a = np.concatenate([crkfr.cr_get_alpha(c, u.shape[1]) for (prob, u), c in zip(probs, ctxs)])
     names = ["128/phases", "128/fused", "256/phases", "256/fused"]
-    return {"problems": nprob, "elements": int(sum(u.shape[1] for _, u in probs)), "dofs": int(nodes),
+    return {"problems": nprob, "sides": [nmin, nmax],
+            "elements": int(sum(u.shape[1] for _, u in probs)), "dofs": int(nodes),
             "degrees": {"3": sum(p["degree"] == 3 for p, _ in probs), "4": sum(p["degree"] == 4 for p, _ in probs)},
             "steps": steps, "value": nodes * steps / (batch_ms * 1e-3), "unit": "DOF-updates/s",
             "ms_per_step": batch_ms / steps,
@@ -523,6 +524,8 @@ def run_ours(args):
     ensemble = None
     if not args.quick and not args.no_ensemble:
         ensemble = ensemble_leg(args.steps, args.warmup, seed=rank)
+        # many small meshes (sides 32..128): where one launch per problem is launch bound
+        ensemble["small_meshes"] = ensemble_leg(args.steps, args.warmup, seed=rank, nmin=32, nmax=128)
     configs = None
     if not args.quick and not args.no_configs:
         configs = config_legs(args.steps, args.warmup)
@@ -579,7 +582,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--mode", choices=("fp64", "fp32"), default="fp64")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
