@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 EQ_LINADV, EQ_EULER, EQ_TENMOMENT = 0, 1, 2
-BC_PERIODIC, BC_OUTFLOW = 0, 1
+BC_PERIODIC, BC_OUTFLOW, BC_WALL = 0, 1, 2
 LIM_BLEND, LIM_MH, LIM_FLUX, LIM_SCALING, LIM_TRACES = 1, 2, 4, 8, 16
 LIM_ALL = LIM_BLEND | LIM_MH | LIM_FLUX | LIM_SCALING | LIM_TRACES
 ALPHA_INDICATOR, ALPHA_FIXED, ALPHA_GIVEN = 0, 1, 2

@@ -54,7 +54,7 @@ static double node_weight(const ctx* c, int k) {
   return c->dim == 2 ? c->w[p] * c->w[q] : c->w[p];
 }
 
-/* neighbour of element e across face side f; -1 at an outflow boundary */
+/* neighbour of element e across face side f; -1 at an outflow or wall boundary */
 static int neighbour(const ctx* c, int e, int f) {
   int ix = e % c->nx, iy = e / c->nx;
   if (f == 0) { if (ix > 0) return e - 1; return c->d->bc_x == OR_BC_PERIODIC ? e + c->nx - 1 : -1; }
@@ -325,6 +325,22 @@ static double minmod3(double a, double b, double c) {
   return 0.0;
 }
 
+/* Solid wall (Sec. 3.3 eq. (reflect.time.avg), Euler): the ghost state is the
+ * interior state with the velocity normal to the face (direction dir)
+ * reversed; the ghost normal flux is the interior one with every component
+ * but the normal momentum reversed. */
+static int wall(const ctx* c, int dir) {
+  return (dir == 0 ? c->d->bc_x : c->d->bc_y) == OR_BC_WALL;
+}
+
+static void reflect_state(const ctx* c, const double* u, int dir, double* out) {
+  for (int v = 0; v < c->M; ++v) out[v] = (v == 1 + dir) ? -u[v] : u[v];
+}
+
+static void reflect_flux(const ctx* c, const double* f, int dir, double* out) {
+  for (int v = 0; v < c->M; ++v) out[v] = (v == 1 + dir) ? f[v] : -f[v];
+}
+
 static void line_slope(const ctx* c, const double* u_line /* [N+3][M], index p+1 */,
                        const double* X /* [N+3] positions */, int p, double beta, double* slope) {
   for (int v = 0; v < c->M; ++v) {
@@ -356,9 +372,12 @@ static void muscl_hancock_element(const ctx* c, const double* u, int e, double a
     for (int q = 0; q < c->nq; ++q) {
       for (int p = 0; p <= N; ++p)
         for (int v = 0; v < M; ++v) line[(p + 1) * M + v] = ue[node(c, p, q) * M + v];
+      /* across a boundary: the own node (outflow) or its reflection (wall) */
       if (eL >= 0) { gather(c, u, eL, nb); for (int v = 0; v < M; ++v) line[v] = nb[node(c, N, q) * M + v]; }
+      else if (wall(c, 0)) reflect_state(c, ue + node(c, 0, q) * M, 0, line);
       else for (int v = 0; v < M; ++v) line[v] = ue[node(c, 0, q) * M + v];
       if (eR >= 0) { gather(c, u, eR, nb); for (int v = 0; v < M; ++v) line[(N + 2) * M + v] = nb[node(c, 0, q) * M + v]; }
+      else if (wall(c, 0)) reflect_state(c, ue + node(c, N, q) * M, 0, line + (N + 2) * M);
       else for (int v = 0; v < M; ++v) line[(N + 2) * M + v] = ue[node(c, N, q) * M + v];
       for (int p = 0; p <= N; ++p) line_slope(c, line, X, p, beta, sx[node(c, p, q)]);
     }
@@ -368,8 +387,10 @@ static void muscl_hancock_element(const ctx* c, const double* u, int e, double a
         for (int q = 0; q <= N; ++q)
           for (int v = 0; v < M; ++v) line[(q + 1) * M + v] = ue[node(c, p, q) * M + v];
         if (eB >= 0) { gather(c, u, eB, nb); for (int v = 0; v < M; ++v) line[v] = nb[node(c, p, N) * M + v]; }
+        else if (wall(c, 1)) reflect_state(c, ue + node(c, p, 0) * M, 1, line);
         else for (int v = 0; v < M; ++v) line[v] = ue[node(c, p, 0) * M + v];
         if (eT >= 0) { gather(c, u, eT, nb); for (int v = 0; v < M; ++v) line[(N + 2) * M + v] = nb[node(c, p, 0) * M + v]; }
+        else if (wall(c, 1)) reflect_state(c, ue + node(c, p, N) * M, 1, line + (N + 2) * M);
         else for (int v = 0; v < M; ++v) line[(N + 2) * M + v] = ue[node(c, p, N) * M + v];
         for (int q = 0; q <= N; ++q) line_slope(c, line, X, q, beta, sy[node(c, p, q)]);
       }
@@ -515,10 +536,13 @@ typedef struct {
 #define WS(arr, e, l, j, v) arr[((((size_t)(e)) * NMAX + (l)) * (NMAX + 1) + (j)) * OR_MAXM + (v)]
 
 /* Numerical flux on one face node between elements eL (left/bottom) and eR
- * (right/top) in direction dir; either may be -1 at an outflow boundary.
+ * (right/top) in direction dir; either may be -1 at an outflow or wall boundary.
  *   high order: Sec. 3.1 eq. (numflux.general) with D2 (eq. (D2)) and EA (eq. (evaluate)),
  *               lambda from the u^n traces (eq. (rusanov.wave.speed));
  *   outflow boundary: F = the interior trace flux (Sec. 3.3);
+ *   wall boundary: the same D2 flux with the ghost values of eq.
+ *     (reflect.time.avg) (u^n trace, time-averaged flux and solution reflected)
+ *     and, for the low-order flux, the reflected evolved boundary state;
  *   low order: the subcell flux at the element face (eqs. (fo.at.face), (mh.at.face));
  *   blend: eq. (Fblend) with alpha_{e+1/2} = (alpha_L + alpha_R)/2 (reading);
  *   flux limiter (Sec. 4.3, Theorem 1; the algorithm is cited, reading):
@@ -544,6 +568,26 @@ static void face_flux(const ctx* c, const double* u, const work_t* W, int dir, i
     rusanov(c, &W->ustar[(((size_t)eL * c->np + kL) * 4 + hL) * M],
             &W->ustar[(((size_t)eR * c->np + kR) * 4 + hR) * M], dir, fLO);
     alpha_f = 0.5 * (W->alpha[eL] + W->alpha[eR]);
+  } else if (wall(c, dir)) {
+    /* the interior side (ei, face side fi) and its reflected ghost */
+    const int ei = eR >= 0 ? eR : eL, fi = eR >= 0 ? fR : fL;
+    const int ki = eR >= 0 ? kR : kL, hi = eR >= 0 ? hR : hL;
+    double ug[OR_MAXM], Fg[OR_MAXM], Ug[OR_MAXM], usg[OR_MAXM];
+    reflect_state(c, &W4(W->unt, ei, fi, j, 0), dir, ug);
+    reflect_flux(c, &W4(W->ea, ei, fi, j, 0), dir, Fg);
+    reflect_state(c, &W4(W->Ut, ei, fi, j, 0), dir, Ug);
+    const double* usi = &W->ustar[(((size_t)ei * c->np + ki) * 4 + hi) * M];
+    reflect_state(c, usi, dir, usg);
+    double lam = fmax(or_wave_speed(c->d, &W4(W->unt, ei, fi, j, 0), dir), or_wave_speed(c->d, ug, dir));
+    /* (left, right) = (ghost, interior) at a left/bottom wall, (interior, ghost) at a right/top wall */
+    const double* FlL = eR >= 0 ? Fg : &W4(W->ea, ei, fi, j, 0);
+    const double* FlR = eR >= 0 ? &W4(W->ea, ei, fi, j, 0) : Fg;
+    const double* UL = eR >= 0 ? Ug : &W4(W->Ut, ei, fi, j, 0);
+    const double* UR = eR >= 0 ? &W4(W->Ut, ei, fi, j, 0) : Ug;
+    for (int v = 0; v < M; ++v) FHO[v] = 0.5 * (FlL[v] + FlR[v]) - 0.5 * lam * (UR[v] - UL[v]);
+    if (eR >= 0) rusanov(c, usg, usi, dir, fLO);
+    else rusanov(c, usi, usg, dir, fLO);
+    alpha_f = W->alpha[ei];
   } else if (eR >= 0) {
     for (int v = 0; v < M; ++v) FHO[v] = W4(W->ea, eR, fR, j, v);
     or_flux(c->d, &W->ustar[(((size_t)eR * c->np + kR) * 4 + hR) * M], dir, fLO);

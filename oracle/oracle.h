@@ -36,7 +36,10 @@ extern "C" {
 #define OR_MAXM 6
 
 enum { OR_EQ_LINADV = 0, OR_EQ_EULER = 1, OR_EQ_TENMOMENT = 2 };
-enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1 };
+/* Boundary conditions of Sec. 3.3: periodic; outflow (F = F^+, the fully
+ * outflow rule); solid wall for the Euler equations (ghost values by
+ * reflecting the normal velocity, eq. (reflect.time.avg)). */
+enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1, OR_BC_WALL = 2 };
 enum {
   OR_LIM_BLEND = 1,    /* blend with the subcell scheme, Sec. 4 eq. (blended.scheme) */
   OR_LIM_MH = 2,       /* MUSCL-Hancock subcell fluxes (else first order), Sec. 4.2 */

@@ -2,7 +2,7 @@
 import oracle
 
 _EQ = {"linadv": oracle.EQ_LINADV, "euler": oracle.EQ_EULER, "tenmoment": oracle.EQ_TENMOMENT}
-_BC = {"periodic": oracle.BC_PERIODIC, "outflow": oracle.BC_OUTFLOW}
+_BC = {"periodic": oracle.BC_PERIODIC, "outflow": oracle.BC_OUTFLOW, "wall": oracle.BC_WALL}
 _LIM = {"blend": oracle.LIM_BLEND, "mh": oracle.LIM_MH, "flux": oracle.LIM_FLUX,
         "scaling": oracle.LIM_SCALING, "traces": oracle.LIM_TRACES}
 
