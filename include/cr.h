@@ -50,7 +50,10 @@ typedef enum {
 } cr_status;
 
 enum { CR_EQ_LINADV = 0, CR_EQ_EULER = 1, CR_EQ_TENMOMENT = 2 };
-enum { CR_BC_PERIODIC = 0, CR_BC_OUTFLOW = 1 };
+/* Boundary conditions of Sec. 3.3.  Outflow: the fully-outflow rule F = F^+.
+ * Wall (Euler only): ghost values by reflecting the velocity normal to the
+ * face, eq. (reflect.time.avg), then the D2 flux as at an interior face. */
+enum { CR_BC_PERIODIC = 0, CR_BC_OUTFLOW = 1, CR_BC_WALL = 2 };
 enum {
   CR_LIM_BLEND = 1,   /* blend with the subcell scheme, Sec. 4 eq. (blended.scheme) */
   CR_LIM_MH = 2,      /* MUSCL-Hancock subcell fluxes (otherwise first order), Sec. 4.2 */

@@ -71,7 +71,7 @@ struct Tab {
 // Mesh, physics and limiter switches (one struct per launch, by value).
 struct Mesh {
   int nx, ny, ne, nfx, nfy;  // elements and faces per direction (nf = n or n+1)
-  int bcx, bcy;              // 0 periodic, 1 outflow
+  int bcx, bcy;              // 0 periodic, 1 outflow, 2 wall (Euler)
   double x0, y0, dx, dy, invdx, invdy;
   int limiter;               // CR_LIM_* bits
   int alpha_mode;            // 0 indicator, 1 fixed, 2 learned (network, indicator fallback)

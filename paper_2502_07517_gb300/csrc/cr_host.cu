@@ -331,8 +331,10 @@ const char* check_desc(const cr_mesh_desc* d) {
   if (d->nx < 1 || (d->dim == 2 && d->ny < 1)) return "nx, ny must be >= 1";
   if ((double)d->nx * (d->dim == 2 ? d->ny : 1) > 2.0e8) return "too many elements";
   if (!(d->x1 > d->x0) || (d->dim == 2 && !(d->y1 > d->y0))) return "empty domain";
-  if (d->bc_x < 0 || d->bc_x > 1 || (d->dim == 2 && (d->bc_y < 0 || d->bc_y > 1)))
+  if (d->bc_x < 0 || d->bc_x > 2 || (d->dim == 2 && (d->bc_y < 0 || d->bc_y > 2)))
     return "unknown boundary condition";
+  if ((d->bc_x == CR_BC_WALL || (d->dim == 2 && d->bc_y == CR_BC_WALL)) && d->equation != CR_EQ_EULER)
+    return "wall boundaries are defined for the Euler equations";
   if (d->equation < 0 || d->equation > 2) return "unknown equation";
   if (d->equation == CR_EQ_EULER && !(d->gamma > 1.0)) return "gamma must be > 1";
   if (d->precision != CR_FP64 && d->precision != CR_FP32_BULK) return "unknown precision";

@@ -354,15 +354,19 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     if (m.limiter & kLimMH) {
       const real beta = real(2) - alpha;
       real um[M], up[M], sx[M], sy[M];
-      // x-line neighbours (the neighbour element's node across a face; own node at outflow)
+      // x-line neighbours: the neighbour element's node across a face; at a
+      // boundary the own node (outflow) or its reflection (wall, normal
+      // momentum reversed)
       const int nbL = p == 0 ? neighbour(m, ee, 0) : -1;
       const int nbR = p == N ? neighbour(m, ee, 1) : -1;
+      const bool wx = m.bcx == 2;
 #pragma unroll
       for (int v = 0; v < M; ++v) {
+        const real gx = (wx && v == 1) ? -un[v] : un[v];
         um[v] = p > 0 ? AT(s0, v, k - 1)
-                      : (nbL >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbL, N + n * q) : un[v]);
+                      : (nbL >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbL, N + n * q) : gx);
         up[v] = p < N ? AT(s0, v, k + 1)
-                      : (nbR >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbR, n * q) : un[v]);
+                      : (nbR >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbR, n * q) : gx);
         sx[v] = minmod3(beta * (un[v] - um[v]) * tb.ihm[p], (up[v] - um[v]) * tb.ihc[p],
                         beta * (up[v] - un[v]) * tb.ihp[p]);
         sy[v] = real(0);
@@ -370,12 +374,14 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
       if (DIM == 2) {
         const int nbB = q == 0 ? neighbour(m, ee, 2) : -1;
         const int nbT = q == N ? neighbour(m, ee, 3) : -1;
+        const bool wy = m.bcy == 2;
 #pragma unroll
         for (int v = 0; v < M; ++v) {
+          const real gy = (wy && v == 2) ? -un[v] : un[v];
           um[v] = q > 0 ? AT(s0, v, k - n)
-                        : (nbB >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbB, p + n * N) : un[v]);
+                        : (nbB >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbB, p + n * N) : gy);
           up[v] = q < N ? AT(s0, v, k + n)
-                        : (nbT >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbT, p) : un[v]);
+                        : (nbT >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbT, p) : gy);
           sy[v] = minmod3(beta * (un[v] - um[v]) * tb.ihm[q], (up[v] - um[v]) * tb.ihc[q],
                           beta * (up[v] - un[v]) * tb.ihp[q]);
         }
@@ -590,6 +596,40 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
       rusanov<EQ>(uL, uR, dir, fLO, P.ph);
     }
     alpha_f = 0.5 * (P.b.alpha[eL] + P.b.alpha[eR]);
+  } else if ((dir == 0 ? m.bcx : m.bcy) == 2) {
+    // solid wall, Sec. 3.3 eq. (reflect.time.avg): the ghost u^n trace and
+    // time-averaged solution are the interior ones with the normal momentum
+    // reversed, the ghost time-averaged flux the interior one with every other
+    // component reversed; then D2 as at an interior face (the reflected trace
+    // has the interior wave speed)
+    const int ei = eR >= 0 ? eR : eL;
+    const int si = eR >= 0 ? sR : sL;
+    const real lam = fld(0, si, ei);
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      const real Fi = fld(1 + M + v, si, ei), Ui = fld(1 + v, si, ei);
+      const real Fg = v == 1 + dir ? Fi : -Fi, Ug = v == 1 + dir ? -Ui : Ui;
+      const real FL = eR >= 0 ? Fg : Fi, FR = eR >= 0 ? Fi : Fg;
+      const real UL = eR >= 0 ? Ug : Ui, UR = eR >= 0 ? Ui : Ug;
+      FHO[v] = real(0.5) * (FL + FR) - real(0.5) * lam * (UR - UL);
+    }
+    if (need_lo) {
+      // Rusanov between the evolved boundary state and its reflection; the
+      // ghost flux is the interior flux reflected (one evaluation), so the mass
+      // and energy components cancel exactly, as the reflection requires
+      real us[M], fi[M], sp;
+#pragma unroll
+      for (int v = 0; v < M; ++v) us[v] = fld(1 + 2 * M + v, si, ei);
+      EQ::flux_speed(us, dir, fi, &sp, P.ph);
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        const real fg = v == 1 + dir ? fi[v] : -fi[v], ug = v == 1 + dir ? -us[v] : us[v];
+        const real fl = eR >= 0 ? fg : fi[v], fr = eR >= 0 ? fi[v] : fg;
+        const real ul = eR >= 0 ? ug : us[v], ur = eR >= 0 ? us[v] : ug;
+        fLO[v] = real(0.5) * (fl + fr) - real(0.5) * sp * (ur - ul);
+      }
+    }
+    alpha_f = P.b.alpha[ei];
   } else {
     const int ei = eR >= 0 ? eR : eL;
     const int si = eR >= 0 ? sR : sL;

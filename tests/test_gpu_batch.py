@@ -203,3 +203,12 @@ def test_fused_barrier_timeout_is_reported_and_recoverable():
     crkfr.cr_batch_step(b, 3)
     got = [crkfr.cr_get_state(c, shape=u.shape) for (prob, u), c in zip(probs, ctxs)]
     _same(got, _alone(probs, crkfr.CR_FP64, 3), crkfr.CR_FP64, "after timeout")
+
+
+def test_batch_with_walls_equals_single_problem_steps():
+    probs = [(dict(p, bc_x="wall"), u) for p, u in _problems(80, shapes=[((11, 9), 4), ((8, 6), 3)])]
+    probs += [(dict(p, bc_y="wall", bc_x="outflow"), u) for p, u in _problems(90, shapes=[((7, 9), 4)])]
+    ref = _alone(probs, crkfr.CR_FP64, 4)
+    for config in ((128, crkfr.CR_BATCH_PHASES), (256, crkfr.CR_BATCH_FUSED)):
+        got, _ = _batched(probs, crkfr.CR_FP64, 4, config)
+        _same(got, ref, crkfr.CR_FP64, "walls %s" % (config,))

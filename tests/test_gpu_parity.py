@@ -299,3 +299,45 @@ def test_checkpoint_resume_is_bitwise():
     crkfr.cr_set_state(c, mid)
     crkfr.cr_step(c, 3, 1e300)
     np.testing.assert_array_equal(crkfr.cr_get_state(c, shape=u.shape), full)
+
+
+# ------------------------------------------------------- solid walls ------
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_euler1d_walls_one_step(N):
+    from tests.test_oracle_walls import _euler1d
+    prob, u = _euler1d(31, N, seed=20 + N)
+    one_step_check(dict(prob, bc_x="wall"), u)
+
+
+@pytest.mark.parametrize("bcx,bcy", [("wall", "periodic"), ("periodic", "wall"), ("wall", "wall"),
+                                     ("wall", "outflow")])
+@pytest.mark.parametrize("N", [3, 4])
+def test_euler2d_walls_one_step(N, bcx, bcy):
+    prob, u = _jumpy_2d(12, 10, N, seed=30 + N)
+    prob = dict(prob, bc_x=bcx, bc_y=bcy)
+    one_step_check(prob, u)
+
+
+def test_euler1d_walls_trajectory():
+    """A Riemann problem between two walls: per-step parity along the oracle
+    trajectory while the waves reflect off the walls (40 steps)."""
+    from tests.test_oracle_walls import _euler1d
+    prob, u = _euler1d(60, 4, seed=3)
+    prob = dict(prob, bc_x="wall")
+    d = oracle_desc(prob)
+    ctx = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob))
+    for _ in range(40):
+        dt = oracle.dt(d, u)
+        ref, st = oracle.step(d, u, dt)
+        assert st == 0
+        crkfr.cr_set_state(ctx, u)
+        crkfr.cr_step(ctx, 1, 1e300, dt)
+        assert_parity(crkfr.cr_get_state(ctx, shape=u.shape), ref)
+        u = ref
+
+
+def test_walls_refused_for_other_equations():
+    prob, u = wl.tenmoment2d_voronoi(nx=6, ny=5, degree=3, seed=0)
+    with pytest.raises(crkfr.CrError) as ei:
+        crkfr.cr_workspace_bytes(crkfr.desc_from_problem(dict(prob, bc_x="wall")))
+    assert ei.value.status == -1
