@@ -322,8 +322,9 @@ def fp32_variants(prob, u, ctx64, steps, warmup, stream, fp64_ms):
 
 def config_legs(steps, warmup):
     """The other workloads: 1D linear advection to t = 1 (error against the
-    exact solution), 1D Euler Riemann problems (4000 elements, N = 4) and 2D
-    ten-moment with the Gaussian source (256x256, N = 3), each in FP64 (plain,
+    exact solution), 1D Euler Riemann problems (4000 elements, N = 4), 2D Euler
+    in a box closed by solid walls (256x256, N = 4) and 2D ten-moment with the
+    Gaussian source (256x256, N = 3), each in FP64 (plain,
     indicator alpha) and FP32 bulk with the learned alpha (a network trained
     for that workload on the GPU): device time per step, DOF-updates/s and the
     normalised L1 difference from the FP64 path after the same steps at the
@@ -381,6 +382,12 @@ def config_legs(steps, warmup):
     leg("euler1d_riemann_4000_N4", prob, u,
         lambda seed: wl.euler1d_riemann(nx=4000, degree=4, seed=seed),
         "1D Euler Riemann problems, 4000 elements, N=4", range(1000, 1024), (0, 50, 200, 800))
+    prob, u = wl.euler2d_vortex_riemann(nx=256, degree=4, seed=0)
+    box = lambda pr: dict(pr, bc_x="wall", bc_y="wall")
+    leg("euler2d_closed_box_walls_256x256_N4", box(prob), u,
+        lambda seed: (lambda pu: (box(pu[0]), pu[1]))(wl.euler2d_vortex_riemann(nx=96, degree=4, seed=seed)),
+        "vortex + planar Riemann jump in a box closed by walls, 96x96, N=4", range(1000, 1008),
+        (0, 10, 40))
     prob, u = wl.tenmoment2d_voronoi(nx=256, degree=3, seed=0)
     leg("tenmoment2d_voronoi_256x256_N3", prob, u,
         lambda seed: wl.tenmoment2d_voronoi(nx=128, degree=3, seed=seed),
