@@ -20,6 +20,8 @@ BC_PERIODIC, BC_OUTFLOW, BC_WALL = 0, 1, 2
 LIM_BLEND, LIM_MH, LIM_FLUX, LIM_SCALING, LIM_TRACES = 1, 2, 4, 8, 16
 LIM_ALL = LIM_BLEND | LIM_MH | LIM_FLUX | LIM_SCALING | LIM_TRACES
 ALPHA_INDICATOR, ALPHA_FIXED, ALPHA_GIVEN = 0, 1, 2
+DISS_D2, DISS_D1, DISS_DCSX = 0, 1, 2
+CENTRAL_EA, CENTRAL_AE = 0, 1
 
 
 class Desc(ctypes.Structure):
@@ -37,6 +39,7 @@ class Desc(ctypes.Structure):
         ("alpha_fixed", ctypes.c_double),
         ("cfl", ctypes.c_double), ("cfl_safety", ctypes.c_double),
         ("alpha_given", ctypes.POINTER(ctypes.c_double)),
+        ("dissipation", ctypes.c_int), ("central", ctypes.c_int),
     ]
 
 
@@ -96,13 +99,13 @@ def make_desc(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=BC_PERIOD
               bc_y=BC_PERIODIC, degree=3, equation=EQ_LINADV, gamma=1.4, adv=(1.0, 0.0),
               source=0, src_amp=0.0, src_k=0.0, src_cx=0.5, src_cy=0.5, limiter=0,
               alpha_mode=ALPHA_INDICATOR, alpha_fixed=0.0, cfl=None, cfl_safety=0.98,
-              alpha_given=None):
+              alpha_given=None, dissipation=DISS_D2, central=CENTRAL_EA):
     """Mesh/scheme description; cfl defaults to CFL(degree) from the Fourier analysis.
     alpha_given: per-element raw alpha array for alpha_mode ALPHA_GIVEN (kept alive on
     the returned object)."""
     if cfl is None:
         from .cfl import cfl_number
-        cfl = cfl_number(degree)
+        cfl = cfl_number(degree, dissipation == DISS_D1)
     d = Desc()
     d.dim, d.nx, d.ny = dim, nx, (ny if dim == 2 else 1)
     d.x0, d.x1, d.y0, d.y1 = x0, x1, y0, y1
@@ -112,6 +115,7 @@ def make_desc(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=BC_PERIOD
     d.source, d.src_amp, d.src_k, d.src_cx, d.src_cy = source, src_amp, src_k, src_cx, src_cy
     d.limiter, d.alpha_mode, d.alpha_fixed = limiter, alpha_mode, alpha_fixed
     d.cfl, d.cfl_safety = cfl, cfl_safety
+    d.dissipation, d.central = dissipation, central
     if alpha_given is not None:
         arr = np.ascontiguousarray(alpha_given, dtype=np.float64)
         d._alpha_given_keep = arr

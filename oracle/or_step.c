@@ -97,9 +97,10 @@ static void rusanov(const ctx* c, const double* uL, const double* uR, int dir, d
  *   u^(i) = u^n - dt sum_{j<i} a_ij [ Dloc f(u^(j)) - s(u^(j)) ]
  *   F = sum_i b_i f(u^(i)), G likewise in y, U = sum_i b_i u^(i), S = sum_i b_i s(u^(i))
  *   EA: F^{+-} = sum_i b_i f(u^(i)(face))
- * ea is [4][NMAX][M] (face side, face node, variable). */
+ * ea is [4][NMAX][M] (face side, face node, variable); stg (may be NULL)
+ * receives the stage traces u^(i)(face), [s][4][NMAX][M], for D-CSX. */
 static void local_crk_ea(const ctx* c, const double* ue, double dt, int ix, int iy, double* F,
-                         double* G, double* U, double* S, double* ea) {
+                         double* G, double* U, double* S, double* ea, double* stg) {
   const int M = c->M, n = c->n, nq = c->nq, np = c->np;
   static double ui[OR_MAXS][NPMAX][OR_MAXM];
   static double L[OR_MAXS][NPMAX][OR_MAXM];
@@ -161,6 +162,10 @@ static void local_crk_ea(const ctx* c, const double* ue, double dt, int ix, int 
       for (int v = 0; v < M; ++v) {
         ea[(0 * NMAX + q) * OR_MAXM + v] += c->b[i] * fL[v];
         ea[(1 * NMAX + q) * OR_MAXM + v] += c->b[i] * fR[v];
+        if (stg) {
+          stg[((i * 4 + 0) * NMAX + q) * OR_MAXM + v] = uL[v];
+          stg[((i * 4 + 1) * NMAX + q) * OR_MAXM + v] = uR[v];
+        }
       }
     }
     if (c->dim == 2)
@@ -178,6 +183,10 @@ static void local_crk_ea(const ctx* c, const double* ue, double dt, int ix, int 
         for (int v = 0; v < M; ++v) {
           ea[(2 * NMAX + p) * OR_MAXM + v] += c->b[i] * gB[v];
           ea[(3 * NMAX + p) * OR_MAXM + v] += c->b[i] * gT[v];
+          if (stg) {
+            stg[((i * 4 + 2) * NMAX + p) * OR_MAXM + v] = uB[v];
+            stg[((i * 4 + 3) * NMAX + p) * OR_MAXM + v] = uT[v];
+          }
         }
       }
   }
@@ -187,7 +196,7 @@ void or_local_crk(const or_desc* d, const double* ue, double dt, int ix, int iy,
                   double* G, double* U, double* S) {
   ctx c;
   ctx_init(&c, d);
-  local_crk_ea(&c, ue, dt, ix, iy, F, G, U, S, NULL);
+  local_crk_ea(&c, ue, dt, ix, iy, F, G, U, S, NULL, NULL);
 }
 
 /* trace of nodal data X[k][v] on face side f at face node j (Sec. 2 eq. (soln.poly)
@@ -530,10 +539,46 @@ typedef struct {
   double *alpha;          /* [ne] */
   double *fnum;           /* [ne][4][NMAX][M] numerical flux on each face side */
   double *theta;          /* [ne][4][NMAX] */
+  double *stg;            /* [ne][s][4][NMAX][M] stage traces (D-CSX) */
 } work_t;
 
 #define W4(arr, e, f, j, v) arr[((((size_t)(e)) * 4 + (f)) * NMAX + (j)) * OR_MAXM + (v)]
+#define WST(arr, e, i, f, j, v) arr[(((((size_t)(e)) * OR_MAXS + (i)) * 4 + (f)) * NMAX + (j)) * OR_MAXM + (v)]
 #define WS(arr, e, l, j, v) arr[((((size_t)(e)) * NMAX + (l)) * (NMAX + 1) + (j)) * OR_MAXM + (v)]
+
+/* Central part F^{+-} of eq. (numflux.general) on face side f of element e at
+ * face node j: EA, eq. (evaluate) (the stage fluxes at the face, averaged), or
+ * AE, eq. (extrapolate) (the trace of the time-averaged flux). */
+static const double* central_part(const ctx* c, const work_t* W, int e, int f, int j) {
+  return c->d->central == OR_CENTRAL_AE ? &W4(W->Fd, e, f, j, 0) : &W4(W->ea, e, f, j, 0);
+}
+
+/* High-order numerical flux eq. (numflux.general), F = (F^- + F^+)/2 - D, from
+ * the face data of the left (L) and right (R) sides: central parts Fc, u^n
+ * traces un, time-averaged solution traces U and stage traces st.
+ *   D2,    eq. (D2):   D = lambda/2 (U^+ - U^-),
+ *   D1,    eq. (D1):   D = lambda/2 (u^+ - u^-),
+ *          lambda = max(sigma(u^-), sigma(u^+)) from the u^n traces (eq. (rusanov.wave.speed));
+ *   D-CSX, eq. (dcsx): D = sum_i b_i lambda_i/2 (u^(i)+ - u^(i)-), lambda_i from the stage traces. */
+static void high_order_flux(const ctx* c, int dir, const double* FcL, const double* FcR,
+                            const double* unL, const double* unR, const double* UL, const double* UR,
+                            double stL[][OR_MAXM], double stR[][OR_MAXM], double* FHO) {
+  const int M = c->M;
+  if (c->d->dissipation == OR_DISS_DCSX) {
+    double Dv[OR_MAXM] = {0};
+    for (int i = 0; i < c->s; ++i) {
+      if (c->b[i] == 0.0) continue;
+      double lam = fmax(or_wave_speed(c->d, stL[i], dir), or_wave_speed(c->d, stR[i], dir));
+      for (int v = 0; v < M; ++v) Dv[v] += c->b[i] * 0.5 * lam * (stR[i][v] - stL[i][v]);
+    }
+    for (int v = 0; v < M; ++v) FHO[v] = 0.5 * (FcL[v] + FcR[v]) - Dv[v];
+    return;
+  }
+  double lam = fmax(or_wave_speed(c->d, unL, dir), or_wave_speed(c->d, unR, dir));
+  const double* jL = c->d->dissipation == OR_DISS_D1 ? unL : UL;
+  const double* jR = c->d->dissipation == OR_DISS_D1 ? unR : UR;
+  for (int v = 0; v < M; ++v) FHO[v] = 0.5 * (FcL[v] + FcR[v]) - 0.5 * lam * (jR[v] - jL[v]);
+}
 
 /* Numerical flux on one face node between elements eL (left/bottom) and eR
  * (right/top) in direction dir; either may be -1 at an outflow or wall boundary.
@@ -559,12 +604,17 @@ static void face_flux(const ctx* c, const double* u, const work_t* W, int dir, i
   const int kR = dir == 0 ? node(c, 0, j) : node(c, j, 0);
   const int hL = dir == 0 ? 1 : 3, hR = dir == 0 ? 0 : 2; /* ustar slots x+ / x- (y+ / y-) */
   double FHO[OR_MAXM], fLO[OR_MAXM], alpha_f;
+  const int S = c->s;
   if (eL >= 0 && eR >= 0) {
-    double lam = fmax(or_wave_speed(c->d, &W4(W->unt, eL, fL, j, 0), dir),
-                      or_wave_speed(c->d, &W4(W->unt, eR, fR, j, 0), dir));
-    for (int v = 0; v < M; ++v)
-      FHO[v] = 0.5 * (W4(W->ea, eL, fL, j, v) + W4(W->ea, eR, fR, j, v)) -
-               0.5 * lam * (W4(W->Ut, eR, fR, j, v) - W4(W->Ut, eL, fL, j, v));
+    double stL[OR_MAXS][OR_MAXM], stR[OR_MAXS][OR_MAXM];
+    for (int i = 0; i < S; ++i)
+      for (int v = 0; v < M; ++v) {
+        stL[i][v] = WST(W->stg, eL, i, fL, j, v);
+        stR[i][v] = WST(W->stg, eR, i, fR, j, v);
+      }
+    high_order_flux(c, dir, central_part(c, W, eL, fL, j), central_part(c, W, eR, fR, j),
+                    &W4(W->unt, eL, fL, j, 0), &W4(W->unt, eR, fR, j, 0), &W4(W->Ut, eL, fL, j, 0),
+                    &W4(W->Ut, eR, fR, j, 0), stL, stR, FHO);
     rusanov(c, &W->ustar[(((size_t)eL * c->np + kL) * 4 + hL) * M],
             &W->ustar[(((size_t)eR * c->np + kR) * 4 + hR) * M], dir, fLO);
     alpha_f = 0.5 * (W->alpha[eL] + W->alpha[eR]);
@@ -573,27 +623,35 @@ static void face_flux(const ctx* c, const double* u, const work_t* W, int dir, i
     const int ei = eR >= 0 ? eR : eL, fi = eR >= 0 ? fR : fL;
     const int ki = eR >= 0 ? kR : kL, hi = eR >= 0 ? hR : hL;
     double ug[OR_MAXM], Fg[OR_MAXM], Ug[OR_MAXM], usg[OR_MAXM];
+    double sti[OR_MAXS][OR_MAXM], stg[OR_MAXS][OR_MAXM];
+    const double* Fi = central_part(c, W, ei, fi, j);
     reflect_state(c, &W4(W->unt, ei, fi, j, 0), dir, ug);
-    reflect_flux(c, &W4(W->ea, ei, fi, j, 0), dir, Fg);
+    reflect_flux(c, Fi, dir, Fg);
     reflect_state(c, &W4(W->Ut, ei, fi, j, 0), dir, Ug);
+    for (int i = 0; i < S; ++i) {
+      for (int v = 0; v < M; ++v) sti[i][v] = WST(W->stg, ei, i, fi, j, v);
+      reflect_state(c, sti[i], dir, stg[i]);
+    }
     const double* usi = &W->ustar[(((size_t)ei * c->np + ki) * 4 + hi) * M];
     reflect_state(c, usi, dir, usg);
-    double lam = fmax(or_wave_speed(c->d, &W4(W->unt, ei, fi, j, 0), dir), or_wave_speed(c->d, ug, dir));
     /* (left, right) = (ghost, interior) at a left/bottom wall, (interior, ghost) at a right/top wall */
-    const double* FlL = eR >= 0 ? Fg : &W4(W->ea, ei, fi, j, 0);
-    const double* FlR = eR >= 0 ? &W4(W->ea, ei, fi, j, 0) : Fg;
-    const double* UL = eR >= 0 ? Ug : &W4(W->Ut, ei, fi, j, 0);
-    const double* UR = eR >= 0 ? &W4(W->Ut, ei, fi, j, 0) : Ug;
-    for (int v = 0; v < M; ++v) FHO[v] = 0.5 * (FlL[v] + FlR[v]) - 0.5 * lam * (UR[v] - UL[v]);
+    if (eR >= 0)
+      high_order_flux(c, dir, Fg, Fi, ug, &W4(W->unt, ei, fi, j, 0), Ug, &W4(W->Ut, ei, fi, j, 0),
+                      stg, sti, FHO);
+    else
+      high_order_flux(c, dir, Fi, Fg, &W4(W->unt, ei, fi, j, 0), ug, &W4(W->Ut, ei, fi, j, 0), Ug,
+                      sti, stg, FHO);
     if (eR >= 0) rusanov(c, usg, usi, dir, fLO);
     else rusanov(c, usi, usg, dir, fLO);
     alpha_f = W->alpha[ei];
   } else if (eR >= 0) {
-    for (int v = 0; v < M; ++v) FHO[v] = W4(W->ea, eR, fR, j, v);
+    const double* Fc = central_part(c, W, eR, fR, j);
+    for (int v = 0; v < M; ++v) FHO[v] = Fc[v];
     or_flux(c->d, &W->ustar[(((size_t)eR * c->np + kR) * 4 + hR) * M], dir, fLO);
     alpha_f = W->alpha[eR];
   } else {
-    for (int v = 0; v < M; ++v) FHO[v] = W4(W->ea, eL, fL, j, v);
+    const double* Fc = central_part(c, W, eL, fL, j);
+    for (int v = 0; v < M; ++v) FHO[v] = Fc[v];
     or_flux(c->d, &W->ustar[(((size_t)eL * c->np + kL) * 4 + hL) * M], dir, fLO);
     alpha_f = W->alpha[eL];
   }
@@ -671,6 +729,7 @@ int or_step(const or_desc* d, const double* u_in, double dt, double* u_out, or_d
   W.fsx = calloc(subsz, sizeof(double));
   W.fsy = calloc(subsz, sizeof(double));
   W.alpha = calloc(ne, sizeof(double));
+  W.stg = calloc((size_t)ne * OR_MAXS * 4 * NMAX * OR_MAXM, sizeof(double));
   double* alpha_raw = calloc(ne, sizeof(double));
   double ue[NPMAX * OR_MAXM], U[NPMAX * OR_MAXM], ea[4 * NMAX * OR_MAXM];
   const int nside = c.dim == 2 ? 4 : 2;
@@ -698,7 +757,7 @@ int or_step(const or_desc* d, const double* u_in, double dt, double* u_out, or_d
     int ix = e % c.nx, iy = e / c.nx;
     gather(&c, u_in, e, ue);
     local_crk_ea(&c, ue, dt, ix, iy, W.F + (size_t)e * np * M, W.G + (size_t)e * np * M, U,
-                 W.S + (size_t)e * np * M, ea);
+                 W.S + (size_t)e * np * M, ea, &WST(W.stg, e, 0, 0, 0, 0));
     for (int f = 0; f < nside; ++f) {
       int nj = f < 2 ? c.nq : n;
       for (int j = 0; j < nj; ++j) {
@@ -848,7 +907,7 @@ int or_step(const or_desc* d, const double* u_in, double dt, double* u_out, or_d
     }
   }
   free(W.F); free(W.G); free(W.S); free(W.ea); free(W.Ut); free(W.unt); free(W.Fd);
-  free(W.fnum); free(W.theta); free(W.ustar); free(W.fsx); free(W.fsy); free(W.alpha);
+  free(W.fnum); free(W.theta); free(W.ustar); free(W.fsx); free(W.fsy); free(W.alpha); free(W.stg);
   free(alpha_raw);
   return status;
 }

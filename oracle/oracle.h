@@ -48,6 +48,12 @@ enum {
   OR_LIM_TRACES = 16   /* scaling limiter also enforces admissibility at face traces */
 };
 enum { OR_ALPHA_INDICATOR = 0, OR_ALPHA_FIXED = 1, OR_ALPHA_GIVEN = 2 };
+/* D2 eq. (D2) (time-averaged solution traces), D1 eq. (D1) (u^n traces),
+ * D-CSX eq. (dcsx) (stage traces with a wave speed per stage) */
+enum { OR_DISS_D2 = 0, OR_DISS_D1 = 1, OR_DISS_DCSX = 2 };
+/* EA eq. (evaluate) (stage fluxes at the face), AE eq. (extrapolate) (trace of
+ * the time-averaged flux) */
+enum { OR_CENTRAL_EA = 0, OR_CENTRAL_AE = 1 };
 
 typedef struct {
   int dim;                 /* 1 or 2 */
@@ -66,6 +72,8 @@ typedef struct {
   double cfl;              /* CFL(N) of Sec. 5 eq. (time.step.2d) */
   double cfl_safety;       /* C_s */
   const double* alpha_given; /* [Ne] raw alpha_e (before smoothing) when alpha_mode == OR_ALPHA_GIVEN */
+  int dissipation;         /* OR_DISS_*: dissipative part of eq. (numflux.general), Sec. 3.1.1 */
+  int central;             /* OR_CENTRAL_*: central part F^{+-}, Sec. 3.1.2 */
 } or_desc;
 
 /* Optional outputs of or_step; any pointer may be NULL. */
