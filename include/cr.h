@@ -54,6 +54,16 @@ enum { CR_EQ_LINADV = 0, CR_EQ_EULER = 1, CR_EQ_TENMOMENT = 2 };
  * Wall (Euler only): ghost values by reflecting the velocity normal to the
  * face, eq. (reflect.time.avg), then the D2 flux as at an interior face. */
 enum { CR_BC_PERIODIC = 0, CR_BC_OUTFLOW = 1, CR_BC_WALL = 2 };
+/* Dissipative part D of the numerical flux eq. (numflux.general), Sec. 3.1:
+ * D2 eq. (D2) (default: jump of the time-averaged solution traces), D1 eq.
+ * (D1) (jump of the u^n traces; lower CFL numbers, computed for it), D-CSX
+ * eq. (dcsx) (stage-trace jumps, one wave speed per stage; equal to D2 for
+ * linear problems).  The wave speed of D2 and D1 comes from the u^n traces. */
+enum { CR_DISS_D2 = 0, CR_DISS_D1 = 1, CR_DISS_DCSX = 2 };
+/* Central part F^{+-}, Sec. 3.1.2: EA eq. (evaluate) (default: the stage
+ * fluxes at the face, averaged), AE eq. (extrapolate) (the trace of the
+ * time-averaged flux; equal to EA for linear problems). */
+enum { CR_CENTRAL_EA = 0, CR_CENTRAL_AE = 1 };
 enum {
   CR_LIM_BLEND = 1,   /* blend with the subcell scheme, Sec. 4 eq. (blended.scheme) */
   CR_LIM_MH = 2,      /* MUSCL-Hancock subcell fluxes (otherwise first order), Sec. 4.2 */
@@ -91,6 +101,8 @@ typedef struct {
   double cfl;            /* CFL(N) of eq. (time.step.2d); <= 0: Fourier analysis */
   double cfl_safety;     /* C_s of eq. (time.step.2d); <= 0: 0.98 */
   void* stream;          /* cudaStream_t or NULL */
+  int dissipation;       /* CR_DISS_*; 0 (D2) when zero-initialised */
+  int central;           /* CR_CENTRAL_*; 0 (EA) when zero-initialised */
 } cr_mesh_desc;
 
 /* Device workspace needed by cr_init_mesh for this descriptor.
@@ -203,6 +215,11 @@ cr_status cr_profile_steps(cr_ctx* ctx, int max_steps, double t_final, double dt
 /* CFL(N) of eq. (time.step.2d) from the library's Fourier analysis of the
  * D2 scheme for linear advection (host only, no device needed). */
 cr_status cr_cfl_number(int degree, double* cfl);
+
+/* CFL(N) for a dissipation model (CR_DISS_*): the same Fourier analysis of
+ * the linear scheme with D1's dissipation for CR_DISS_D1; D2 and D-CSX share
+ * one value.  Host only.  Errors: CR_E_INVALID_ARG. */
+cr_status cr_cfl_number_for(int degree, int dissipation, double* cfl);
 
 /* Reference-element tables the kernels use (host only): Gauss-Legendre nodes
  * xi[N+1] and weights w[N+1] on [0,1], and D[(N+1)*(N+1)], D_ij = l_j'(xi_i)

@@ -23,10 +23,13 @@ CR_LIM_BLEND, CR_LIM_MH, CR_LIM_FLUX, CR_LIM_SCALING, CR_LIM_TRACES = 1, 2, 4, 8
 CR_ALPHA_INDICATOR, CR_ALPHA_FIXED, CR_ALPHA_MLP = 0, 1, 2
 CR_FP64, CR_FP32_BULK = 0, 1
 CR_BATCH_PHASES, CR_BATCH_FUSED = 0, 1
+CR_DISS_D2, CR_DISS_D1, CR_DISS_DCSX = 0, 1, 2
+CR_CENTRAL_EA, CR_CENTRAL_AE = 0, 1
 
 # C symbols declared in include/cr.h
 SYMBOLS = ("cr_workspace_bytes", "cr_init_mesh", "cr_destroy", "cr_set_state", "cr_get_state",
            "cr_step", "cr_step_async", "cr_sync", "cr_get_alpha", "cr_get_means", "cr_next_dt",
+           "cr_cfl_number_for",
            "cr_launches_per_step", "cr_profile_steps", "cr_cfl_number", "cr_reference_tables",
            "cr_step_static", "cr_last_error", "cr_mlp_param_count", "cr_mlp_load",
            "cr_get_features", "cr_mlp_grad", "cr_mlp_train", "cr_batch_init", "cr_batch_destroy",
@@ -55,6 +58,7 @@ class cr_mesh_desc(ctypes.Structure):
         ("alpha_fixed", ctypes.c_double), ("precision", ctypes.c_int),
         ("cfl", ctypes.c_double), ("cfl_safety", ctypes.c_double),
         ("stream", ctypes.c_void_p),
+        ("dissipation", ctypes.c_int), ("central", ctypes.c_int),
     ]
 
 
@@ -86,6 +90,7 @@ def lib():
         L.cr_launches_per_step.argtypes = [V, ctypes.POINTER(I)]
         L.cr_profile_steps.argtypes = [V, I, ctypes.c_double, ctypes.c_double, D]
         L.cr_cfl_number.argtypes = [I, D]
+        L.cr_cfl_number_for.argtypes = [I, I, D]
         L.cr_reference_tables.argtypes = [I, D, D, D]
         L.cr_step_static.argtypes = [P, V, V, ctypes.c_double]
         F = ctypes.POINTER(ctypes.c_float)
@@ -128,6 +133,12 @@ def _dptr(a):
 def cr_cfl_number(degree):
     out = ctypes.c_double()
     _check(lib().cr_cfl_number(int(degree), ctypes.byref(out)))
+    return out.value
+
+
+def cr_cfl_number_for(degree, dissipation):
+    out = ctypes.c_double()
+    _check(lib().cr_cfl_number_for(int(degree), int(dissipation), ctypes.byref(out)))
     return out.value
 
 

@@ -82,6 +82,8 @@ struct Mesh {
   double T_ind, s_ind;       // indicator threshold T(N) and sharpness s
   double cflim[4];           // 1/(kappa w h) of the flux-limiter candidates on face sides
                              // 0..3 (x-left: w_0 dx, x-right: w_N dx, y-bottom, y-top)
+  int dissipation;           // 0 D2, 1 D1, 2 D-CSX (Sec. 3.1)
+  int central;               // 0 EA, 1 AE (Sec. 3.1.2)
 };
 
 enum : int { kLimBlend = 1, kLimMH = 2, kLimFlux = 4, kLimScaling = 8, kLimTraces = 16 };

@@ -183,7 +183,7 @@ double spectral_radius(const cd* G, int n) {
   return r;
 }
 
-double max_growth(const HostTables& h, double nu) {
+double max_growth(const HostTables& h, double nu, bool d1) {
   const int n = h.N + 1;
   double T[25] = {}, Dm[25] = {}, tmp[25];
   for (int i = 0; i < n; ++i) Dm[i * n + i] = 1.0;
@@ -200,9 +200,12 @@ double max_growth(const HostTables& h, double nu) {
       }
     memcpy(Dm, tmp, sizeof(tmp));
   }
-  double A0[25], A1[25];
+  // the jump term uses V = T (D2) or V = I (D1): with g_R' = l(1)/w,
+  //   A0 = D T + g_R' (l1^T V - l1^T T)/2 - g_L' (l0^T T + l0^T V)/2   (k independent)
+  //   Ap = g_R' (l0^T T - l0^T V)/2 (times exp(ik)), A1 = g_L' (l1^T T + l1^T V)/2 (exp(-ik))
+  double A0[25], A1[25], Ap[25];
   for (int i = 0; i < n; ++i) {
-    const double gL = -h.l0[i] / h.w[i];
+    const double gL = -h.l0[i] / h.w[i], gR = h.l1[i] / h.w[i];
     for (int j = 0; j < n; ++j) {
       double dt = 0.0, l0T = 0.0, l1T = 0.0;
       for (int r = 0; r < n; ++r) {
@@ -210,38 +213,40 @@ double max_growth(const HostTables& h, double nu) {
         l0T += h.l0[r] * T[r * n + j];
         l1T += h.l1[r] * T[r * n + j];
       }
-      A0[i * n + j] = dt - gL * l0T;
-      A1[i * n + j] = gL * l1T;
+      const double l0V = d1 ? h.l0[j] : l0T, l1V = d1 ? h.l1[j] : l1T;
+      A0[i * n + j] = dt + 0.5 * gR * (l1V - l1T) - 0.5 * gL * (l0T + l0V);
+      Ap[i * n + j] = 0.5 * gR * (l0T - l0V);
+      A1[i * n + j] = 0.5 * gL * (l1T + l1V);
     }
   }
   double g = 0.0;
   const int nk = 721;
   for (int ik = 0; ik < nk; ++ik) {
     const double k = 2.0 * M_PI * ik / (nk - 1);
-    const cd ph = std::exp(cd(0.0, -k));
+    const cd ph = std::exp(cd(0.0, -k)), pp = std::exp(cd(0.0, k));
     cd G[25];
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j)
-        G[i * n + j] = (i == j ? 1.0 : 0.0) - nu * (A0[i * n + j] + ph * A1[i * n + j]);
+        G[i * n + j] = (i == j ? 1.0 : 0.0) - nu * (A0[i * n + j] + ph * A1[i * n + j] + pp * Ap[i * n + j]);
     g = std::fmax(g, spectral_radius(G, n));
   }
   return g;
 }
 
-double cfl_compute(int N) {
-  static double cache[kMaxN + 1] = {0, 0, 0, 0, 0};
+double cfl_compute(int N, bool d1 = false) {
+  static double cache[2][kMaxN + 1] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
-  if (cache[N] > 0.0) return cache[N];
+  if (cache[d1][N] > 0.0) return cache[d1][N];
   HostTables h;
   build_tables(N, &h);
   double lo = 0.0, hi = 1.0;
   for (int it = 0; it < 40; ++it) {
     const double mid = 0.5 * (lo + hi);
-    if (max_growth(h, mid) <= 1.0 + 1e-4) lo = mid;
+    if (max_growth(h, mid, d1) <= 1.0 + 1e-4) lo = mid;
     else hi = mid;
   }
-  cache[N] = lo;
+  cache[d1][N] = lo;
   return lo;
 }
 
@@ -303,7 +308,10 @@ Layout layout_of(const cr_mesh_desc* d) {
   L.umean_f = take(mixed ? M * ne * sizeof(float) : 0);
   L.P = take(M * ne * np * rs);
   L.smean = take(mixed ? M * ne * sizeof(double) : 0);
-  L.slot = take((4 * M + 1) * nside * ne * nfn * rs);
+  // face-node slots: 4M+1 fields, plus the stage traces for D-CSX
+  const int nstage = d->degree == 4 ? 6 : d->degree + 1;
+  const size_t nslotf = 4 * M + 1 + (d->dissipation == CR_DISS_DCSX ? (size_t)nstage * M : 0);
+  L.slot = take(nslotf * nside * ne * nfn * rs);
   L.fx = take(M * ny * nfx * nfn * rs);
   L.fy = take(dim == 2 ? M * nfy * nx * n * rs : 0);
   L.alpha_raw = take(ne * sizeof(double));
@@ -336,6 +344,8 @@ const char* check_desc(const cr_mesh_desc* d) {
   if ((d->bc_x == CR_BC_WALL || (d->dim == 2 && d->bc_y == CR_BC_WALL)) && d->equation != CR_EQ_EULER)
     return "wall boundaries are defined for the Euler equations";
   if (d->equation < 0 || d->equation > 2) return "unknown equation";
+  if (d->dissipation < 0 || d->dissipation > 2) return "unknown dissipation model";
+  if (d->central < 0 || d->central > 1) return "unknown central flux";
   if (d->equation == CR_EQ_EULER && !(d->gamma > 1.0)) return "gamma must be > 1";
   if (d->precision != CR_FP64 && d->precision != CR_FP32_BULK) return "unknown precision";
   if (d->alpha_mode != CR_ALPHA_INDICATOR && d->alpha_mode != CR_ALPHA_FIXED &&
@@ -407,6 +417,8 @@ void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
   m.invdx = 1.0 / m.dx;
   m.invdy = d.dim == 2 ? 1.0 / m.dy : 0.0;
   m.limiter = d.limiter;
+  m.dissipation = d.dissipation;
+  m.central = d.central;
   m.alpha_mode = d.alpha_mode;
   m.alpha_fixed = d.alpha_fixed;
   m.gamma = d.gamma;
@@ -519,6 +531,12 @@ cr_status launch_steps(cr_ctx* c, int n) {
 // ===========================================================================
 extern "C" {
 
+cr_status cr_cfl_number_for(int degree, int dissipation, double* cfl) {
+  if (degree < 1 || degree > kMaxN || !cfl || dissipation < 0 || dissipation > 2) return CR_E_INVALID_ARG;
+  *cfl = cfl_compute(degree, dissipation == CR_DISS_D1);
+  return CR_OK;
+}
+
 cr_status cr_cfl_number(int degree, double* cfl) {
   if (degree < 1 || degree > kMaxN || !cfl) return CR_E_INVALID_ARG;
   *cfl = cfl_compute(degree);
@@ -585,7 +603,7 @@ cr_status cr_init_mesh(const cr_mesh_desc* desc, void* workspace, size_t workspa
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMallocHost"));
   e = ks->configure();
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaFuncSetAttribute"));
-  c->cfl = desc->cfl > 0.0 ? desc->cfl : cfl_compute(desc->degree);
+  c->cfl = desc->cfl > 0.0 ? desc->cfl : cfl_compute(desc->degree, desc->dissipation == CR_DISS_D1);
   if (!(c->d.cfl_safety > 0.0)) c->d.cfl_safety = 0.98;
   HostTables h;
   build_tables(desc->degree, &h);

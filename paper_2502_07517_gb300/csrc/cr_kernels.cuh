@@ -284,9 +284,16 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
             }
             ut[v] = acc;
           }
-          EQ::flux(ut, side >> 1, fn, ph);
+          if (m.dissipation == 2 && valid) {  // D-CSX: the stage trace, for the face kernel
 #pragma unroll
-          for (int v = 0; v < M; ++v) ea[mm][v] += bi * fn[v];
+            for (int v = 0; v < M; ++v)
+              P.b.slot[slot_index(1 + 4 * M + i * M + v, side, e, j, NSIDE, m.ne, NFN)] = ut[v];
+          }
+          if (m.central == 0) {  // EA, eq. (evaluate)
+            EQ::flux(ut, side >> 1, fn, ph);
+#pragma unroll
+            for (int v = 0; v < M; ++v) ea[mm][v] += bi * fn[v];
+          }
         }
       }
     }
@@ -318,26 +325,31 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     const int sl = k + mm * NP;
     if (valid && sl < NSLOT) {
       const int side = sl / NFN, j = sl - side * NFN;
-      real Ut[M], ut[M];
+      // slot 1..M: the trace the dissipation jumps over (U for D2, u^n for D1);
+      // slot 1+M..: the central part (EA average, or for AE the trace of the
+      // time-averaged flux F (x faces) or G (y faces), eq. (extrapolate))
+      real Ut[M], ut[M], Ft[M];
 #pragma unroll
       for (int v = 0; v < M; ++v) {
-        real a1 = real(0), a2 = real(0);
+        real a1 = real(0), a2 = real(0), a3 = real(0);
 #pragma unroll
         for (int r = 0; r < n; ++r) {
           const real l = (side & 1) ? tb.l1[r] : tb.l0[r];
           const int node = side < 2 ? r + n * j : j + n * r;
           a1 += l * AT(sA, v, node);
           a2 += l * AT(s0, v, node);
+          if (m.central == 1) a3 += l * (side < 2 ? AT(sB, v, node) : AT(sC, v, node));
         }
         Ut[v] = a1;
         ut[v] = a2;
+        Ft[v] = a3;
       }
       real* sl_out = P.b.slot;
       sl_out[slot_index(0, side, e, j, NSIDE, m.ne, NFN)] = EQ::speed(ut, side >> 1, ph);
 #pragma unroll
       for (int v = 0; v < M; ++v) {
-        sl_out[slot_index(1 + v, side, e, j, NSIDE, m.ne, NFN)] = Ut[v];
-        sl_out[slot_index(1 + M + v, side, e, j, NSIDE, m.ne, NFN)] = ea[mm][v];
+        sl_out[slot_index(1 + v, side, e, j, NSIDE, m.ne, NFN)] = m.dissipation == 1 ? ut[v] : Ut[v];
+        sl_out[slot_index(1 + M + v, side, e, j, NSIDE, m.ne, NFN)] = m.central == 1 ? Ft[v] : ea[mm][v];
       }
     }
   }
@@ -581,11 +593,36 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
   const bool blend = (m.limiter & kLimBlend) || m.alpha_mode == 1;
   const bool need_lo = blend || (m.limiter & kLimFlux);
   if (eL >= 0 && eR >= 0) {
-    const real lam = fmax(fld(0, sL, eL), fld(0, sR, eR));
+    if (m.dissipation == 2) {
+      // D-CSX, eq. (dcsx): sum_i b_i lambda_i/2 (u^(i)+ - u^(i)-), lambda_i
+      // from the stage traces of both sides
+      real Dv[M];
 #pragma unroll
-    for (int v = 0; v < M; ++v)
-      FHO[v] = real(0.5) * (fld(1 + M + v, sL, eL) + fld(1 + M + v, sR, eR)) -
-               real(0.5) * lam * (fld(1 + v, sR, eR) - fld(1 + v, sL, eL));
+      for (int v = 0; v < M; ++v) Dv[v] = real(0);
+#pragma unroll
+      for (int i = 0; i < Tableau<N>::S; ++i) {
+        if (Tableau<N>::b(i) == 0.0) continue;
+        real uL[M], uR[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          uL[v] = fld(1 + 4 * M + i * M + v, sL, eL);
+          uR[v] = fld(1 + 4 * M + i * M + v, sR, eR);
+        }
+        const real lam = fmax(EQ::speed(uL, dir, P.ph), EQ::speed(uR, dir, P.ph));
+        const real bi = real(Tableau<N>::b(i));
+#pragma unroll
+        for (int v = 0; v < M; ++v) Dv[v] += bi * real(0.5) * lam * (uR[v] - uL[v]);
+      }
+#pragma unroll
+      for (int v = 0; v < M; ++v)
+        FHO[v] = real(0.5) * (fld(1 + M + v, sL, eL) + fld(1 + M + v, sR, eR)) - Dv[v];
+    } else {  // D2 (slots 1..M hold U traces) or D1 (they hold u^n traces)
+      const real lam = fmax(fld(0, sL, eL), fld(0, sR, eR));
+#pragma unroll
+      for (int v = 0; v < M; ++v)
+        FHO[v] = real(0.5) * (fld(1 + M + v, sL, eL) + fld(1 + M + v, sR, eR)) -
+                 real(0.5) * lam * (fld(1 + v, sR, eR) - fld(1 + v, sL, eL));
+    }
     if (need_lo) {
       real uL[M], uR[M];
 #pragma unroll
@@ -604,14 +641,40 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
     // has the interior wave speed)
     const int ei = eR >= 0 ? eR : eL;
     const int si = eR >= 0 ? sR : sL;
-    const real lam = fld(0, si, ei);
+    real Dv[M];
+    if (m.dissipation == 2) {  // D-CSX with reflected ghost stage traces (same wave speed)
+#pragma unroll
+      for (int v = 0; v < M; ++v) Dv[v] = real(0);
+#pragma unroll
+      for (int i = 0; i < Tableau<N>::S; ++i) {
+        if (Tableau<N>::b(i) == 0.0) continue;
+        real ui[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) ui[v] = fld(1 + 4 * M + i * M + v, si, ei);
+        const real lam = EQ::speed(ui, dir, P.ph);
+        const real bi = real(Tableau<N>::b(i));
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          const real ug = v == 1 + dir ? -ui[v] : ui[v];
+          const real uL = eR >= 0 ? ug : ui[v], uR = eR >= 0 ? ui[v] : ug;
+          Dv[v] += bi * real(0.5) * lam * (uR - uL);
+        }
+      }
+    } else {
+      const real lam = fld(0, si, ei);
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        const real Ui = fld(1 + v, si, ei), Ug = v == 1 + dir ? -Ui : Ui;
+        const real UL = eR >= 0 ? Ug : Ui, UR = eR >= 0 ? Ui : Ug;
+        Dv[v] = real(0.5) * lam * (UR - UL);
+      }
+    }
 #pragma unroll
     for (int v = 0; v < M; ++v) {
-      const real Fi = fld(1 + M + v, si, ei), Ui = fld(1 + v, si, ei);
-      const real Fg = v == 1 + dir ? Fi : -Fi, Ug = v == 1 + dir ? -Ui : Ui;
+      const real Fi = fld(1 + M + v, si, ei);
+      const real Fg = v == 1 + dir ? Fi : -Fi;
       const real FL = eR >= 0 ? Fg : Fi, FR = eR >= 0 ? Fi : Fg;
-      const real UL = eR >= 0 ? Ug : Ui, UR = eR >= 0 ? Ui : Ug;
-      FHO[v] = real(0.5) * (FL + FR) - real(0.5) * lam * (UR - UL);
+      FHO[v] = real(0.5) * (FL + FR) - Dv[v];
     }
     if (need_lo) {
       // Rusanov between the evolved boundary state and its reflection; the

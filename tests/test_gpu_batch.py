@@ -212,3 +212,11 @@ def test_batch_with_walls_equals_single_problem_steps():
     for config in ((128, crkfr.CR_BATCH_PHASES), (256, crkfr.CR_BATCH_FUSED)):
         got, _ = _batched(probs, crkfr.CR_FP64, 4, config)
         _same(got, ref, crkfr.CR_FP64, "walls %s" % (config,))
+
+
+@pytest.mark.parametrize("diss,cen", [(1, 0), (2, 1)])
+def test_batch_with_variants_equals_single_problem_steps(diss, cen):
+    probs = _problems(100, shapes=[((11, 9), 4), ((8, 6), 3), ((5, 7), 4)])
+    ref = _alone(probs, crkfr.CR_FP64, 3, dissipation=diss, central=cen)
+    got, _ = _batched(probs, crkfr.CR_FP64, 3, (128, crkfr.CR_BATCH_FUSED), dissipation=diss, central=cen)
+    _same(got, ref, crkfr.CR_FP64, "variant %d %d" % (diss, cen))

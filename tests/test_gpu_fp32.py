@@ -104,3 +104,19 @@ def test_fp32_walls_conserve_and_match(bcx, bcy):
     t0, t1 = m0.sum(axis=1), m1.sum(axis=1)
     for v in (0, 3):
         assert abs(t1[v] - t0[v]) <= 1e-13 * abs(t0[v]), (v, t1[v] - t0[v])
+
+
+@pytest.mark.parametrize("diss,cen", [(1, 0), (2, 0), (0, 1), (2, 1)])
+def test_fp32_variants_one_step(diss, cen):
+    prob, u = wl.euler2d_vortex(nx=16, ny=14, degree=4, seed=2)
+    u = u * np.random.default_rng(2).uniform(0.5, 2.0, (1, u.shape[1], 1))
+    d = oracle_desc(prob, dissipation=diss, central=cen)
+    dt = oracle.dt(d, u)
+    ref, st = oracle.step(d, u, dt)
+    assert st == 0
+    ctx = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, precision=crkfr.CR_FP32_BULK,
+                                                     dissipation=diss, central=cen))
+    crkfr.cr_set_state(ctx, u)
+    crkfr.cr_step(ctx, 1, 1e300, dt)
+    err = l1_rel(crkfr.cr_get_state(ctx, shape=u.shape), ref)
+    assert np.all(err < L1_ONE_STEP), err

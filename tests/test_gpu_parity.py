@@ -341,3 +341,46 @@ def test_walls_refused_for_other_equations():
     with pytest.raises(crkfr.CrError) as ei:
         crkfr.cr_workspace_bytes(crkfr.desc_from_problem(dict(prob, bc_x="wall")))
     assert ei.value.status == -1
+
+
+# ------------------------------------- dissipation models and central flux ------
+VARIANTS = [(1, 0), (2, 0), (0, 1), (1, 1), (2, 1)]   # (dissipation, central): D1/D-CSX, AE
+VIDS = ["D1-EA", "DCSX-EA", "D2-AE", "D1-AE", "DCSX-AE"]
+
+
+def _variant_case(case):
+    if case == "euler1d_outflow":
+        return wl.euler1d_riemann(nx=41, degree=4, seed=4)
+    if case == "euler2d_periodic":
+        return _jumpy_2d(11, 9, 4, seed=5)
+    if case == "euler2d_walls_N3":
+        prob, u = _jumpy_2d(10, 8, 3, seed=6)
+        return dict(prob, bc_x="wall", bc_y="outflow"), u
+    if case == "tenmoment_N3":
+        return wl.tenmoment2d_voronoi(nx=9, ny=7, degree=3, seed=3)
+    return wl.linadv_random(nx=9, ny=7, dim=2, degree=3, seed=3, adv=(0.7, -1.2))
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
+@pytest.mark.parametrize("case", ["euler1d_outflow", "euler2d_periodic", "euler2d_walls_N3",
+                                  "tenmoment_N3", "linadv2d"])
+def test_variants_one_step(variant, case):
+    diss, cen = variant
+    prob, u = _variant_case(case)
+    over = dict(dissipation=diss, central=cen)
+    one_step_check(prob, u, over_oracle=over, over_gpu=over)
+
+
+def test_d1_multi_step():
+    """D1 over 12 CFL steps (its own, smaller CFL number) against 12 oracle steps."""
+    from oracle.cfl import cfl_number
+    prob, u = wl.euler2d_vortex(nx=12, ny=10, degree=4, seed=2)
+    cfl = cfl_number(4, True)
+    d = oracle_desc(prob, dissipation=1, cfl=cfl)
+    ref = u
+    for _ in range(12):
+        ref, st = oracle.step(d, ref, oracle.dt(d, ref))
+        assert st == 0
+    g, _, t, n, _ = gpu_run(prob, u, nsteps=12, dissipation=1, cfl=cfl)
+    assert n == 12
+    assert_parity(g, ref, rtol=1e-11)

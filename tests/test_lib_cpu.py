@@ -59,3 +59,11 @@ def test_invalid_descriptor_rejected(built):
     assert ei.value.status == -1
     d.degree = 3
     assert crkfr.cr_workspace_bytes(d) > 0
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_library_cfl_for_dissipation_models_matches_oracle(N):
+    from oracle.cfl import cfl_number
+    assert abs(crkfr.cr_cfl_number_for(N, crkfr.CR_DISS_D1) - cfl_number(N, True)) < 1e-6
+    assert crkfr.cr_cfl_number_for(N, crkfr.CR_DISS_DCSX) == crkfr.cr_cfl_number(N)
+    assert crkfr.cr_cfl_number_for(N, crkfr.CR_DISS_D1) < crkfr.cr_cfl_number(N)
