@@ -388,6 +388,17 @@ def config_legs(steps, warmup):
         lambda seed: (lambda pu: (box(pu[0]), pu[1]))(wl.euler2d_vortex_riemann(nx=96, degree=4, seed=seed)),
         "vortex + planar Riemann jump in a box closed by walls, 96x96, N=4", range(1000, 1008),
         (0, 10, 40))
+    # dissipation models and central fluxes of Sec. 3.1 on the 2D Euler recipe (FP64)
+    prob, u = wl.euler2d_vortex(nx=256, degree=4, seed=0)
+    var = {}
+    for name, diss, cen in (("D2-EA", 0, 0), ("D1-EA", 1, 0), ("DCSX-EA", 2, 0), ("D2-AE", 0, 1),
+                            ("DCSX-AE", 2, 1)):
+        c = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, stream=sp, dissipation=diss, central=cen))
+        crkfr.cr_set_state(c, u)
+        ms = timed_steps(c, steps, warmup, stream)
+        var[name] = {"ms_per_step": ms, "value": u.shape[1] * u.shape[2] / (ms * 1e-3)}
+        crkfr.cr_destroy(c)
+    out["euler2d_vortex_256x256_N4_dissipation_central"] = {"unit": "DOF-updates/s", "fp64": var}
     prob, u = wl.tenmoment2d_voronoi(nx=256, degree=3, seed=0)
     leg("tenmoment2d_voronoi_256x256_N3", prob, u,
         lambda seed: wl.tenmoment2d_voronoi(nx=128, degree=3, seed=seed),
