@@ -40,8 +40,8 @@ typedef enum {
   CR_OK = 0,
   CR_E_INVALID_ARG = -1,   /* a descriptor field, size or pointer is out of range */
   CR_E_INVALID_STATE = -2, /* cr_set_state: a solution point is inadmissible or not finite */
-  CR_E_INADMISSIBLE = -3,  /* cr_step: an element mean or a limited point left the
-                              admissible set, or a value is not finite */
+  CR_E_INADMISSIBLE = -3,  /* cr_step: an element mean left the admissible set,
+                              or a value is not finite */
   CR_E_TIMEOUT = -4,       /* a bounded device wait gave up */
   CR_E_CUDA = -5,          /* a CUDA runtime call failed (message in cr_last_error) */
   CR_E_NOMEM = -6,         /* device or host allocation failed */
