@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-EQ_LINADV, EQ_EULER, EQ_TENMOMENT = 0, 1, 2
+EQ_LINADV, EQ_EULER, EQ_TENMOMENT, EQ_BURGERS = 0, 1, 2, 3
 BC_PERIODIC, BC_OUTFLOW, BC_WALL = 0, 1, 2
 LIM_BLEND, LIM_MH, LIM_FLUX, LIM_SCALING, LIM_TRACES = 1, 2, 4, 8, 16
 LIM_ALL = LIM_BLEND | LIM_MH | LIM_FLUX | LIM_SCALING | LIM_TRACES

@@ -10,6 +10,7 @@ int or_nvars(const or_desc* d) {
     case OR_EQ_LINADV: return 1;
     case OR_EQ_EULER: return d->dim == 1 ? 3 : 4;
     case OR_EQ_TENMOMENT: return 6;
+    case OR_EQ_BURGERS: return 1;
   }
   return 0;
 }
@@ -38,6 +39,10 @@ static void tm_pressure(const double* u, double* p11, double* p12, double* p22) 
 void or_flux(const or_desc* d, const double* u, int dir, double* f) {
   if (d->equation == OR_EQ_LINADV) {
     f[0] = d->adv[dir] * u[0];
+    return;
+  }
+  if (d->equation == OR_EQ_BURGERS) { /* Sec. 5.1: f(u) = u^2/2 */
+    f[0] = 0.5 * u[0] * u[0];
     return;
   }
   if (d->equation == OR_EQ_EULER) {
@@ -87,13 +92,14 @@ void or_flux(const or_desc* d, const double* u, int dir, double* f) {
 }
 
 /* Spectral radius sigma of the flux Jacobian in direction dir.
- * Linear advection: |a|.  Euler: |v| + c, c = sqrt(gamma p / rho)
+ * Linear advection: |a|.  Burgers: |u|.  Euler: |v| + c, c = sqrt(gamma p / rho)
  * (Sec. 5.2 eq. (spectral.radius.1d), Sec. 5.3).  Ten-moment (not given in
  * the paper; reading): |v_dir| + sqrt(3 p_dirdir / rho), the largest
  * eigenvalue magnitude of the x-Jacobian v1 +- sqrt(3 p11/rho).
  * The square root is taken of max(., 0). */
 double or_wave_speed(const or_desc* d, const double* u, int dir) {
   if (d->equation == OR_EQ_LINADV) return fabs(d->adv[dir]);
+  if (d->equation == OR_EQ_BURGERS) return fabs(u[0]); /* f'(u) = u */
   double rho = u[0];
   if (d->equation == OR_EQ_EULER) {
     double v = u[1 + dir] / rho;
@@ -112,7 +118,7 @@ double or_wave_speed(const or_desc* d, const double* u, int dir) {
  * eigenvalue of the pressure tensor (x^T P x > 0 for all x != 0 exactly when
  * lambda_min(P) > 0; lambda_min is concave in u for rho > 0). */
 int or_num_constraints(const or_desc* d) {
-  return d->equation == OR_EQ_LINADV ? 0 : 2;
+  return (d->equation == OR_EQ_LINADV || d->equation == OR_EQ_BURGERS) ? 0 : 2;
 }
 
 double or_constraint(const or_desc* d, const double* u, int k) {

@@ -234,7 +234,7 @@ static double legendre01(int j, double xi) {
 }
 
 static double indicator_variable(const or_desc* d, const double* u) {
-  if (d->equation == OR_EQ_LINADV) return u[0];
+  if (d->equation == OR_EQ_LINADV || d->equation == OR_EQ_BURGERS) return u[0];
   if (d->equation == OR_EQ_EULER) return u[0] * or_constraint(d, u, 1);
   double rho = u[0], v1 = u[1] / rho, v2 = u[2] / rho;
   double p11 = 2.0 * u[3] - rho * v1 * v1, p22 = 2.0 * u[5] - rho * v2 * v2;

@@ -35,7 +35,8 @@ extern "C" {
 #define OR_MAXS 6
 #define OR_MAXM 6
 
-enum { OR_EQ_LINADV = 0, OR_EQ_EULER = 1, OR_EQ_TENMOMENT = 2 };
+/* Burgers: 1D only, f(u) = u^2/2 (Sec. 5.1, Burgers' equation). */
+enum { OR_EQ_LINADV = 0, OR_EQ_EULER = 1, OR_EQ_TENMOMENT = 2, OR_EQ_BURGERS = 3 };
 /* Boundary conditions of Sec. 3.3: periodic; outflow (F = F^+, the fully
  * outflow rule); solid wall for the Euler equations (ghost values by
  * reflecting the normal velocity, eq. (reflect.time.avg)). */

@@ -9,8 +9,9 @@ the same arrays.
 State layout: float64 array [M][Ne][Np], element e = ix + nx * iy, node
 k = p + (N + 1) * q with p along x.
 
-Problem dict keys: dim, nx, ny, x0, x1, y0, y1, bc_x, bc_y ("periodic" or
-"outflow"), degree, equation ("linadv", "euler", "tenmoment"), gamma, adv,
+Problem dict keys: dim, nx, ny, x0, x1, y0, y1, bc_x, bc_y ("periodic",
+"outflow" or "wall"), degree, equation ("linadv", "euler", "tenmoment",
+"burgers"), gamma, adv,
 source (None or dict amp, k, cx, cy), limiter (set of "blend", "mh", "flux",
 "scaling", "traces"), t_final, steps.
 """
@@ -71,7 +72,8 @@ def base_problem(**kw):
 
 
 def nvars(prob):
-    return {"linadv": 1, "euler": 3 if prob["dim"] == 1 else 4, "tenmoment": 6}[prob["equation"]]
+    return {"linadv": 1, "burgers": 1, "euler": 3 if prob["dim"] == 1 else 4,
+            "tenmoment": 6}[prob["equation"]]
 
 
 def euler_conservative(rho, v1, v2, p, gamma, dim):
@@ -93,6 +95,49 @@ def linadv_sine(nx=64, degree=3, t_final=1.0, a=1.0):
                         t_final=t_final)
     x, _ = node_coords(prob)
     return prob, np.sin(2.0 * np.pi * x)[None, :, :].copy()
+
+
+def burgers_sine(nx=64, degree=3, t_final=2.0, amp=0.2):
+    """1D Burgers u_t + (u^2/2)_x = 0 on [0, 2 pi] periodic, u0 = amp sin(x)
+    (Sec. 5.1): smooth until t = 1/amp = 5, no limiter."""
+    prob = base_problem(dim=1, nx=nx, degree=degree, equation="burgers", x0=0.0,
+                        x1=2.0 * math.pi, t_final=t_final)
+    prob["burgers_amp"] = amp
+    x, _ = node_coords(prob)
+    return prob, (amp * np.sin(x))[None, :, :].copy()
+
+
+def sedov1d(nx=201, degree=3, limiter=LIMITER_ALL, t_final=1e-3):
+    """1D Sedov blast (Sec. 5.2): Euler (gamma 1.4) on [-1, 1] between solid
+    walls, rho = 1, v = 0, total energy E = 3.2e6/dx in the centre element
+    (|x| <= dx/2; nx odd) and 1e-12 elsewhere."""
+    if nx % 2 == 0:
+        raise ValueError("the 1D Sedov blast wants an odd element count")
+    prob = base_problem(dim=1, nx=nx, degree=degree, equation="euler", x0=-1.0, x1=1.0,
+                        bc_x="wall", limiter=frozenset(limiter), t_final=t_final)
+    dx = 2.0 / nx
+    x, _ = node_coords(prob)
+    centre = (np.arange(nx) == nx // 2)[:, None]
+    E = np.where(np.broadcast_to(centre, x.shape), 3.2e6 / dx, 1e-12)
+    one = np.ones_like(x)
+    return prob, np.stack([one, 0.0 * one, E])
+
+
+def sedov2d_periodic(nx=64, degree=3, limiter=LIMITER_ALL, t_final=20.0):
+    """2D periodic Sedov blast (Sec. 5.3): Euler (gamma 1.4) on [-1.5, 1.5]^2
+    periodic, gas at rest, rho = rho0 + exp(-r^2/(2 s_rho^2))/(4 pi s_rho^2),
+    p = p0 + (gamma - 1) exp(-r^2/(2 s_p^2))/(4 pi s_p^2), rho0 = 1, p0 = 1e-5,
+    s_rho = 0.25, s_p = 0.15."""
+    prob = base_problem(dim=2, nx=nx, ny=nx, degree=degree, equation="euler", x0=-1.5, x1=1.5,
+                        y0=-1.5, y1=1.5, limiter=frozenset(limiter), t_final=t_final)
+    g = prob["gamma"]
+    x, y = node_coords(prob)
+    r2 = x * x + y * y
+    sr, sp = 0.25, 0.15
+    rho = 1.0 + np.exp(-r2 / (2.0 * sr * sr)) / (4.0 * math.pi * sr * sr)
+    p = 1e-5 + (g - 1.0) * np.exp(-r2 / (2.0 * sp * sp)) / (4.0 * math.pi * sp * sp)
+    zero = np.zeros_like(x)
+    return prob, euler_conservative(rho, zero, zero, p, g, 2)
 
 
 def linadv_random(nx=8, ny=1, dim=1, degree=3, seed=0, adv=(1.0, 0.0), bc="periodic"):

@@ -1,7 +1,8 @@
 """Test helper: build an oracle description from a workload problem dict."""
 import oracle
 
-_EQ = {"linadv": oracle.EQ_LINADV, "euler": oracle.EQ_EULER, "tenmoment": oracle.EQ_TENMOMENT}
+_EQ = {"linadv": oracle.EQ_LINADV, "euler": oracle.EQ_EULER, "tenmoment": oracle.EQ_TENMOMENT,
+       "burgers": oracle.EQ_BURGERS}
 _BC = {"periodic": oracle.BC_PERIODIC, "outflow": oracle.BC_OUTFLOW, "wall": oracle.BC_WALL}
 _LIM = {"blend": oracle.LIM_BLEND, "mh": oracle.LIM_MH, "flux": oracle.LIM_FLUX,
         "scaling": oracle.LIM_SCALING, "traces": oracle.LIM_TRACES}
