@@ -49,7 +49,8 @@ typedef enum {
   CR_E_TOO_LARGE = -8      /* cr_step_static: the mesh needs more scratch than its fixed array */
 } cr_status;
 
-enum { CR_EQ_LINADV = 0, CR_EQ_EULER = 1, CR_EQ_TENMOMENT = 2 };
+/* CR_EQ_BURGERS: u_t + (u^2/2)_x = 0 (Sec. 5.1), 1D, FP64 */
+enum { CR_EQ_LINADV = 0, CR_EQ_EULER = 1, CR_EQ_TENMOMENT = 2, CR_EQ_BURGERS = 3 };
 /* Boundary conditions of Sec. 3.3.  Outflow: the fully-outflow rule F = F^+.
  * Wall (Euler only): ghost values by reflecting the velocity normal to the
  * face, eq. (reflect.time.avg), then the D2 flux as at an interior face. */
@@ -87,7 +88,7 @@ typedef struct {
   int bc_x, bc_y;        /* CR_BC_*; outflow is the fully-outflow rule of Sec. 3.3 */
   int degree;            /* N, 1..4; the RK method has order N+1 (Sec. 3) */
   int equation;          /* CR_EQ_*: u_t + a.grad u = 0 (Sec. 5.1.1), Euler (Sec. 5.2,
-                            5.3), ten-moment (Sec. 5.4) */
+                            5.3), ten-moment (Sec. 5.4), Burgers (Sec. 5.1, 1D) */
   double gamma;          /* Euler adiabatic constant */
   double adv[2];         /* linear advection velocity */
   int source;            /* 0 none; 1 ten-moment source of eq. (tenmom.source) with

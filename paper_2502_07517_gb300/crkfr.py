@@ -17,7 +17,7 @@ CR_OK = 0
 STATUS = {0: "CR_OK", -1: "CR_E_INVALID_ARG", -2: "CR_E_INVALID_STATE", -3: "CR_E_INADMISSIBLE",
           -4: "CR_E_TIMEOUT", -5: "CR_E_CUDA", -6: "CR_E_NOMEM", -7: "CR_E_UNSUPPORTED",
           -8: "CR_E_TOO_LARGE"}
-CR_EQ_LINADV, CR_EQ_EULER, CR_EQ_TENMOMENT = 0, 1, 2
+CR_EQ_LINADV, CR_EQ_EULER, CR_EQ_TENMOMENT, CR_EQ_BURGERS = 0, 1, 2, 3
 CR_BC_PERIODIC, CR_BC_OUTFLOW, CR_BC_WALL = 0, 1, 2
 CR_LIM_BLEND, CR_LIM_MH, CR_LIM_FLUX, CR_LIM_SCALING, CR_LIM_TRACES = 1, 2, 4, 8, 16
 CR_ALPHA_INDICATOR, CR_ALPHA_FIXED, CR_ALPHA_MLP = 0, 1, 2
@@ -393,7 +393,8 @@ def cr_last_error(ctx=None):
 
 
 # ------------------------------------------------------ problem marshalling -
-_EQ = {"linadv": CR_EQ_LINADV, "euler": CR_EQ_EULER, "tenmoment": CR_EQ_TENMOMENT}
+_EQ = {"linadv": CR_EQ_LINADV, "euler": CR_EQ_EULER, "tenmoment": CR_EQ_TENMOMENT,
+       "burgers": CR_EQ_BURGERS}
 _BC = {"periodic": CR_BC_PERIODIC, "outflow": CR_BC_OUTFLOW, "wall": CR_BC_WALL}
 _LIM = {"blend": CR_LIM_BLEND, "mh": CR_LIM_MH, "flux": CR_LIM_FLUX, "scaling": CR_LIM_SCALING,
         "traces": CR_LIM_TRACES}

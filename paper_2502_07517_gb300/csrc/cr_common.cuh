@@ -209,6 +209,32 @@ struct EqLinAdv {  // u_t + a . grad u = 0, Sec. 5.1.1
   __device__ static real indicator_var(const real* u, const Phys<real>&) { return u[0]; }
 };
 
+struct EqBurgers {  // u_t + (u^2/2)_x = 0, Sec. 5.1 (1D); sigma = |u|
+  static constexpr int M = 1, K = 0;
+  template <typename real>
+  __device__ static void flux(const real* u, int, real* f, const Phys<real>&) {
+    f[0] = real(0.5) * u[0] * u[0];
+  }
+  template <typename real>
+  __device__ static void flux_xy(const real* u, real* f, real* g, const Phys<real>&) {
+    f[0] = real(0.5) * u[0] * u[0];
+    g[0] = real(0);
+  }
+  template <typename real>
+  __device__ static real speed(const real* u, int, const Phys<real>&) { return fabs(u[0]); }
+  template <typename real>
+  __device__ static void flux_speed(const real* u, int dir, real* f, real* s, const Phys<real>& ph) {
+    flux(u, dir, f, ph);
+    *s = speed(u, dir, ph);
+  }
+  template <typename real>
+  __device__ static real constraint(const real*, int, const Phys<real>&) { return real(1); }
+  template <typename real>
+  __device__ static bool admissible_fast(const real*, const Phys<real>&) { return true; }
+  template <typename real>
+  __device__ static real indicator_var(const real* u, const Phys<real>&) { return u[0]; }
+};
+
 // Euler, Sec. 5.2 eq. (1deuler) (DIM 1, u = rho, rho v, E) and Sec. 5.3
 // eq. (2deuler) (DIM 2, u = rho, rho v1, rho v2, E); p from eqs. (state), (2dstate);
 // sigma = |v_dir| + c, c = sqrt(gamma p / rho) (eq. (spectral.radius.1d)).

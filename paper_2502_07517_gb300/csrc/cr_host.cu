@@ -281,7 +281,7 @@ struct Layout {
 };
 
 int nvars_of(const cr_mesh_desc* d) {
-  if (d->equation == CR_EQ_LINADV) return 1;
+  if (d->equation == CR_EQ_LINADV || d->equation == CR_EQ_BURGERS) return 1;
   if (d->equation == CR_EQ_EULER) return d->dim == 1 ? 3 : 4;
   return 6;
 }
@@ -328,6 +328,7 @@ const KernelSet* lookup(const cr_mesh_desc* d) {
     return d->dim == 1 ? kernels_linadv1d(d->degree, mixed) : kernels_linadv2d(d->degree, mixed);
   if (d->equation == CR_EQ_EULER)
     return d->dim == 1 ? kernels_euler1d(d->degree, mixed) : kernels_euler2d(d->degree, mixed);
+  if (d->equation == CR_EQ_BURGERS) return d->dim == 1 ? kernels_burgers1d(d->degree, mixed) : nullptr;
   return d->dim == 1 ? kernels_tenmoment1d(d->degree, mixed)
                      : kernels_tenmoment2d(d->degree, mixed);
 }
@@ -343,7 +344,8 @@ const char* check_desc(const cr_mesh_desc* d) {
     return "unknown boundary condition";
   if ((d->bc_x == CR_BC_WALL || (d->dim == 2 && d->bc_y == CR_BC_WALL)) && d->equation != CR_EQ_EULER)
     return "wall boundaries are defined for the Euler equations";
-  if (d->equation < 0 || d->equation > 2) return "unknown equation";
+  if (d->equation < 0 || d->equation > 3) return "unknown equation";
+  if (d->equation == CR_EQ_BURGERS && d->dim != 1) return "Burgers' equation is 1D";
   if (d->dissipation < 0 || d->dissipation > 2) return "unknown dissipation model";
   if (d->central < 0 || d->central > 1) return "unknown central flux";
   if (d->equation == CR_EQ_EULER && !(d->gamma > 1.0)) return "gamma must be > 1";

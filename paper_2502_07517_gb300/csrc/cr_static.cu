@@ -128,6 +128,7 @@ extern "C" cr_status cr_step_static(const cr_mesh_desc* d, const double* u_in, d
     const int N = d->degree;
     if (d->equation == CR_EQ_LINADV) ks = d->dim == 1 ? kernels_linadv1d(N, 0) : kernels_linadv2d(N, 0);
     else if (d->equation == CR_EQ_EULER) ks = d->dim == 1 ? kernels_euler1d(N, 0) : kernels_euler2d(N, 0);
+    else if (d->equation == CR_EQ_BURGERS) ks = d->dim == 1 ? kernels_burgers1d(N, 0) : nullptr;
     else ks = d->dim == 1 ? kernels_tenmoment1d(N, 0) : kernels_tenmoment2d(N, 0);
   }
   if (!ks) return static_fail(CR_E_UNSUPPORTED, "cr_step_static: combination not built");

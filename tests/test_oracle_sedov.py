@@ -1,0 +1,68 @@
+"""Pins of the oracle on the Sedov blasts (1D between solid walls, Sec. 5.2;
+2D periodic, Sec. 5.3), against what the physics and the paper fix:
+
+* the walls pass neither mass nor energy, and a periodic box conserves every
+  variable: the sums of element means stay put to rounding;
+* the data are mirror symmetric (1D: about x = 0; 2D: in x, in y and under
+  x <-> y), and so must the computed solution be, to rounding;
+* the paper reports nonphysical solutions without the admissibility
+  corrections: without the scaling limiter the 1D blast fails within a few
+  steps, with all limiters it keeps going with admissible means.
+"""
+import numpy as np
+
+import oracle
+from paper_2502_07517_gb300 import workloads as wl
+from tests._oracle_util import oracle_desc
+
+
+def mirror_1d(g):
+    flip = g[:, ::-1, ::-1]
+    sgn = np.array([1.0, -1.0, 1.0])[:, None, None]
+    return max(np.abs(g[v] - sgn[v] * flip[v]).max() / np.abs(g[v]).max() for v in range(3))
+
+
+def test_sedov1d_conserves_and_stays_symmetric():
+    prob, u = wl.sedov1d()
+    d = oracle_desc(prob)
+    g, t, n, st = oracle.run(d, u, 60, 1.0)
+    assert st == 0 and n == 60
+    m0, m1 = oracle.element_means(d, u), oracle.element_means(d, g)
+    assert abs(m1[0].sum() - m0[0].sum()) <= 1e-15 * n * m0[0].sum()
+    assert abs(m1[2].sum() - m0[2].sum()) <= 1e-15 * n * m0[2].sum()
+    assert mirror_1d(g) <= 1e-14
+    p = 0.4 * (m1[2] - 0.5 * m1[1] ** 2 / m1[0])
+    assert m1[0].min() > 0 and p.min() > 0
+    # the blast has spread beyond the centre element
+    assert np.sum(m1[2] > 1.0) >= 3
+
+
+def test_sedov1d_needs_the_scaling_limiter():
+    for lim, fails in (({"blend", "mh"}, True), ({"blend", "mh", "flux"}, True),
+                       ({"blend", "mh", "flux", "scaling", "traces"}, False)):
+        prob, u = wl.sedov1d(limiter=lim)
+        g, t, n, st = oracle.run(oracle_desc(prob), u, 200, 1.0)
+        if fails:
+            assert st != 0 and n <= 10, (lim, n, st)
+        else:
+            assert st == 0 and n == 200
+
+
+def test_sedov2d_periodic_conserves_and_keeps_symmetry():
+    nx, N = 12, 3
+    prob, u = wl.sedov2d_periodic(nx=nx, degree=N)
+    d = oracle_desc(prob)
+    g, t, n, st = oracle.run(d, u, 30, 100.0)
+    assert st == 0 and n == 30
+    m0, m1 = oracle.element_means(d, u).sum(axis=1), oracle.element_means(d, g).sum(axis=1)
+    assert np.abs(m1 - m0).max() <= 1e-14 * n * m0[0]
+    n1 = N + 1
+    G = g.reshape(4, nx, nx, n1, n1)               # [v][iy][ix][q][p]
+    fx = G[:, :, ::-1, :, ::-1]
+    fy = G[:, ::-1, :, ::-1, :]
+    tr = G.transpose(0, 2, 1, 4, 3)[[0, 2, 1, 3]]
+    scale = np.abs(G).max(axis=(1, 2, 3, 4))
+    for v, (sx, sy) in enumerate([(1, 1), (-1, 1), (1, -1), (1, 1)]):
+        assert np.abs(G[v] - sx * fx[v]).max() <= 1e-14 * scale[v]
+        assert np.abs(G[v] - sy * fy[v]).max() <= 1e-14 * scale[v]
+        assert np.abs(G[v] - tr[v]).max() <= 1e-14 * scale[v]
