@@ -16,7 +16,8 @@ import numpy as np
 from . import build as _build
 
 EQ_LINADV, EQ_EULER, EQ_TENMOMENT, EQ_BURGERS = 0, 1, 2, 3
-BC_PERIODIC, BC_OUTFLOW, BC_WALL = 0, 1, 2
+BC_PERIODIC, BC_OUTFLOW, BC_WALL, BC_DIRICHLET, BC_INFLOW = 0, 1, 2, 3, 4
+SRC_NONE, SRC_TENMOMENT, SRC_GRAVITY = 0, 1, 2
 LIM_BLEND, LIM_MH, LIM_FLUX, LIM_SCALING, LIM_TRACES = 1, 2, 4, 8, 16
 LIM_ALL = LIM_BLEND | LIM_MH | LIM_FLUX | LIM_SCALING | LIM_TRACES
 ALPHA_INDICATOR, ALPHA_FIXED, ALPHA_GIVEN = 0, 1, 2
@@ -40,6 +41,8 @@ class Desc(ctypes.Structure):
         ("cfl", ctypes.c_double), ("cfl_safety", ctypes.c_double),
         ("alpha_given", ctypes.POINTER(ctypes.c_double)),
         ("dissipation", ctypes.c_int), ("central", ctypes.c_int),
+        ("bc_side", ctypes.c_int * 4), ("bc_state", (ctypes.c_double * 6) * 4),
+        ("gravity", ctypes.c_double * 2),
     ]
 
 
@@ -99,7 +102,8 @@ def make_desc(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=BC_PERIOD
               bc_y=BC_PERIODIC, degree=3, equation=EQ_LINADV, gamma=1.4, adv=(1.0, 0.0),
               source=0, src_amp=0.0, src_k=0.0, src_cx=0.5, src_cy=0.5, limiter=0,
               alpha_mode=ALPHA_INDICATOR, alpha_fixed=0.0, cfl=None, cfl_safety=0.98,
-              alpha_given=None, dissipation=DISS_D2, central=CENTRAL_EA):
+              alpha_given=None, dissipation=DISS_D2, central=CENTRAL_EA, bc_side=(0, 0, 0, 0),
+              bc_state=None, gravity=(0.0, 0.0)):
     """Mesh/scheme description; cfl defaults to CFL(degree) from the Fourier analysis.
     alpha_given: per-element raw alpha array for alpha_mode ALPHA_GIVEN (kept alive on
     the returned object)."""
@@ -116,6 +120,12 @@ def make_desc(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=BC_PERIOD
     d.limiter, d.alpha_mode, d.alpha_fixed = limiter, alpha_mode, alpha_fixed
     d.cfl, d.cfl_safety = cfl, cfl_safety
     d.dissipation, d.central = dissipation, central
+    for s in range(4):
+        d.bc_side[s] = bc_side[s]
+        if bc_state is not None and bc_state[s] is not None:
+            for v, x in enumerate(bc_state[s]):
+                d.bc_state[s][v] = x
+    d.gravity[0], d.gravity[1] = gravity
     if alpha_given is not None:
         arr = np.ascontiguousarray(alpha_given, dtype=np.float64)
         d._alpha_given_keep = arr

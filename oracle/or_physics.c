@@ -130,12 +130,27 @@ double or_constraint(const or_desc* d, const double* u, int k) {
   return 0.5 * (p11 + p22) - sqrt(h * h + p12 * p12);
 }
 
-/* Ten-moment source of Sec. 5.4 eq. (tenmom.source), s = s^x + s^y with
- * W = amp exp(-k |x - c|^2) (in 1D only the x part, W = amp exp(-k (x-cx)^2)). */
+/* Source terms.  Euler with gravity (Sec. 5.5): s = (0, rho g, g . (rho v)),
+ * the momentum source rho g and the work of gravity on the gas in the energy
+ * (reading: the printed energy component names the velocity across gravity;
+ * the work of a force rho g is rho v . g).  Ten-moment source of Sec. 5.4
+ * eq. (tenmom.source), s = s^x + s^y with W = amp exp(-k |x - c|^2) (in 1D
+ * only the x part, W = amp exp(-k (x-cx)^2)). */
 void or_source(const or_desc* d, const double* u, double x, double y, double* s) {
   int M = or_nvars(d);
   for (int v = 0; v < M; ++v) s[v] = 0.0;
-  if (d->source != 1 || d->equation != OR_EQ_TENMOMENT) return;
+  if (d->source == OR_SRC_GRAVITY && d->equation == OR_EQ_EULER) {
+    double gx = d->gravity[0], gy = d->dim == 2 ? d->gravity[1] : 0.0;
+    s[1] = u[0] * gx;
+    if (d->dim == 2) {
+      s[2] = u[0] * gy;
+      s[3] = u[1] * gx + u[2] * gy;
+    } else {
+      s[2] = u[1] * gx;
+    }
+    return;
+  }
+  if (d->source != OR_SRC_TENMOMENT || d->equation != OR_EQ_TENMOMENT) return;
   double rx = x - d->src_cx, ry = (d->dim == 2) ? (y - d->src_cy) : 0.0;
   double W = d->src_amp * exp(-d->src_k * (rx * rx + ry * ry));
   double dWx = -2.0 * d->src_k * rx * W;

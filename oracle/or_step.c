@@ -338,8 +338,20 @@ static double minmod3(double a, double b, double c) {
  * interior state with the velocity normal to the face (direction dir)
  * reversed; the ghost normal flux is the interior one with every component
  * but the normal momentum reversed. */
-static int wall(const ctx* c, int dir) {
-  return (dir == 0 ? c->d->bc_x : c->d->bc_y) == OR_BC_WALL;
+/* Boundary type of side s (0 x-, 1 x+, 2 y-, 3 y+). */
+static int side_bc(const ctx* c, int s) {
+  if (c->d->bc_side[s] != 0) return c->d->bc_side[s];
+  return s < 2 ? c->d->bc_x : c->d->bc_y;
+}
+
+/* Ghost node of the MUSCL-Hancock reconstruction beyond side s, from the own
+ * boundary node ub: the node itself (outflow), its reflection (wall), or the
+ * given state (Dirichlet, inflow). */
+static void ghost_node(const ctx* c, int s, const double* ub, double* out) {
+  int bc = side_bc(c, s);
+  if (bc == OR_BC_WALL) { for (int v = 0; v < c->M; ++v) out[v] = (v == 1 + s / 2) ? -ub[v] : ub[v]; }
+  else if (bc == OR_BC_DIRICHLET || bc == OR_BC_INFLOW) { for (int v = 0; v < c->M; ++v) out[v] = c->d->bc_state[s][v]; }
+  else { for (int v = 0; v < c->M; ++v) out[v] = ub[v]; }
 }
 
 static void reflect_state(const ctx* c, const double* u, int dir, double* out) {
@@ -381,13 +393,11 @@ static void muscl_hancock_element(const ctx* c, const double* u, int e, double a
     for (int q = 0; q < c->nq; ++q) {
       for (int p = 0; p <= N; ++p)
         for (int v = 0; v < M; ++v) line[(p + 1) * M + v] = ue[node(c, p, q) * M + v];
-      /* across a boundary: the own node (outflow) or its reflection (wall) */
+      /* across a boundary: the ghost node of that side */
       if (eL >= 0) { gather(c, u, eL, nb); for (int v = 0; v < M; ++v) line[v] = nb[node(c, N, q) * M + v]; }
-      else if (wall(c, 0)) reflect_state(c, ue + node(c, 0, q) * M, 0, line);
-      else for (int v = 0; v < M; ++v) line[v] = ue[node(c, 0, q) * M + v];
+      else ghost_node(c, 0, ue + node(c, 0, q) * M, line);
       if (eR >= 0) { gather(c, u, eR, nb); for (int v = 0; v < M; ++v) line[(N + 2) * M + v] = nb[node(c, 0, q) * M + v]; }
-      else if (wall(c, 0)) reflect_state(c, ue + node(c, N, q) * M, 0, line + (N + 2) * M);
-      else for (int v = 0; v < M; ++v) line[(N + 2) * M + v] = ue[node(c, N, q) * M + v];
+      else ghost_node(c, 1, ue + node(c, N, q) * M, line + (N + 2) * M);
       for (int p = 0; p <= N; ++p) line_slope(c, line, X, p, beta, sx[node(c, p, q)]);
     }
     if (c->dim == 2) {
@@ -396,11 +406,9 @@ static void muscl_hancock_element(const ctx* c, const double* u, int e, double a
         for (int q = 0; q <= N; ++q)
           for (int v = 0; v < M; ++v) line[(q + 1) * M + v] = ue[node(c, p, q) * M + v];
         if (eB >= 0) { gather(c, u, eB, nb); for (int v = 0; v < M; ++v) line[v] = nb[node(c, p, N) * M + v]; }
-        else if (wall(c, 1)) reflect_state(c, ue + node(c, p, 0) * M, 1, line);
-        else for (int v = 0; v < M; ++v) line[v] = ue[node(c, p, 0) * M + v];
+        else ghost_node(c, 2, ue + node(c, p, 0) * M, line);
         if (eT >= 0) { gather(c, u, eT, nb); for (int v = 0; v < M; ++v) line[(N + 2) * M + v] = nb[node(c, p, 0) * M + v]; }
-        else if (wall(c, 1)) reflect_state(c, ue + node(c, p, N) * M, 1, line + (N + 2) * M);
-        else for (int v = 0; v < M; ++v) line[(N + 2) * M + v] = ue[node(c, p, N) * M + v];
+        else ghost_node(c, 3, ue + node(c, p, N) * M, line + (N + 2) * M);
         for (int q = 0; q <= N; ++q) line_slope(c, line, X, q, beta, sy[node(c, p, q)]);
       }
     }
@@ -588,6 +596,11 @@ static void high_order_flux(const ctx* c, int dir, const double* FcL, const doub
  *   wall boundary: the same D2 flux with the ghost values of eq.
  *     (reflect.time.avg) (u^n trace, time-averaged flux and solution reflected)
  *     and, for the low-order flux, the reflected evolved boundary state;
+ *   Dirichlet boundary (the inflow/outflow ghost values of Sec. 3.3 for a
+ *     time-independent g): u^- = U^- = g, F^- = f(g), stage traces g, then the
+ *     scheme's own flux (the paper takes an HLLC flux there; reading) and,
+ *     for the low-order flux, Rusanov between the evolved boundary state and g;
+ *   fully inflow boundary: F = F^- = f(g) (Sec. 3.3), high and low order;
  *   low order: the subcell flux at the element face (eqs. (fo.at.face), (mh.at.face));
  *   blend: eq. (Fblend) with alpha_{e+1/2} = (alpha_L + alpha_R)/2 (reading);
  *   flux limiter (Sec. 4.3, Theorem 1; the algorithm is cited, reading):
@@ -605,6 +618,9 @@ static void face_flux(const ctx* c, const double* u, const work_t* W, int dir, i
   const int hL = dir == 0 ? 1 : 3, hR = dir == 0 ? 0 : 2; /* ustar slots x+ / x- (y+ / y-) */
   double FHO[OR_MAXM], fLO[OR_MAXM], alpha_f;
   const int S = c->s;
+  /* boundary side of this face when one neighbour is missing */
+  const int side = eR >= 0 ? (dir == 0 ? 0 : 2) : (dir == 0 ? 1 : 3);
+  const int bc = (eL >= 0 && eR >= 0) ? OR_BC_PERIODIC : side_bc(c, side);
   if (eL >= 0 && eR >= 0) {
     double stL[OR_MAXS][OR_MAXM], stR[OR_MAXS][OR_MAXM];
     for (int i = 0; i < S; ++i)
@@ -618,22 +634,30 @@ static void face_flux(const ctx* c, const double* u, const work_t* W, int dir, i
     rusanov(c, &W->ustar[(((size_t)eL * c->np + kL) * 4 + hL) * M],
             &W->ustar[(((size_t)eR * c->np + kR) * 4 + hR) * M], dir, fLO);
     alpha_f = 0.5 * (W->alpha[eL] + W->alpha[eR]);
-  } else if (wall(c, dir)) {
-    /* the interior side (ei, face side fi) and its reflected ghost */
+  } else if (bc == OR_BC_WALL || bc == OR_BC_DIRICHLET) {
+    /* the interior side (ei, face side fi) and its ghost: reflected (wall) or
+     * the given state g with F^- = f(g) (Dirichlet) */
     const int ei = eR >= 0 ? eR : eL, fi = eR >= 0 ? fR : fL;
     const int ki = eR >= 0 ? kR : kL, hi = eR >= 0 ? hR : hL;
     double ug[OR_MAXM], Fg[OR_MAXM], Ug[OR_MAXM], usg[OR_MAXM];
     double sti[OR_MAXS][OR_MAXM], stg[OR_MAXS][OR_MAXM];
     const double* Fi = central_part(c, W, ei, fi, j);
-    reflect_state(c, &W4(W->unt, ei, fi, j, 0), dir, ug);
-    reflect_flux(c, Fi, dir, Fg);
-    reflect_state(c, &W4(W->Ut, ei, fi, j, 0), dir, Ug);
-    for (int i = 0; i < S; ++i) {
-      for (int v = 0; v < M; ++v) sti[i][v] = WST(W->stg, ei, i, fi, j, v);
-      reflect_state(c, sti[i], dir, stg[i]);
-    }
     const double* usi = &W->ustar[(((size_t)ei * c->np + ki) * 4 + hi) * M];
-    reflect_state(c, usi, dir, usg);
+    for (int i = 0; i < S; ++i)
+      for (int v = 0; v < M; ++v) sti[i][v] = WST(W->stg, ei, i, fi, j, v);
+    if (bc == OR_BC_WALL) {
+      reflect_state(c, &W4(W->unt, ei, fi, j, 0), dir, ug);
+      reflect_flux(c, Fi, dir, Fg);
+      reflect_state(c, &W4(W->Ut, ei, fi, j, 0), dir, Ug);
+      for (int i = 0; i < S; ++i) reflect_state(c, sti[i], dir, stg[i]);
+      reflect_state(c, usi, dir, usg);
+    } else {
+      const double* g = c->d->bc_state[side];
+      or_flux(c->d, g, dir, Fg);
+      for (int v = 0; v < M; ++v) ug[v] = Ug[v] = usg[v] = g[v];
+      for (int i = 0; i < S; ++i)
+        for (int v = 0; v < M; ++v) stg[i][v] = g[v];
+    }
     /* (left, right) = (ghost, interior) at a left/bottom wall, (interior, ghost) at a right/top wall */
     if (eR >= 0)
       high_order_flux(c, dir, Fg, Fi, ug, &W4(W->unt, ei, fi, j, 0), Ug, &W4(W->Ut, ei, fi, j, 0),
@@ -644,6 +668,11 @@ static void face_flux(const ctx* c, const double* u, const work_t* W, int dir, i
     if (eR >= 0) rusanov(c, usg, usi, dir, fLO);
     else rusanov(c, usi, usg, dir, fLO);
     alpha_f = W->alpha[ei];
+  } else if (bc == OR_BC_INFLOW) {
+    /* fully inflow (Sec. 3.3): F = F^- = f(g) for both fluxes */
+    or_flux(c->d, c->d->bc_state[side], dir, FHO);
+    for (int v = 0; v < M; ++v) fLO[v] = FHO[v];
+    alpha_f = W->alpha[eR >= 0 ? eR : eL];
   } else if (eR >= 0) {
     const double* Fc = central_part(c, W, eR, fR, j);
     for (int v = 0; v < M; ++v) FHO[v] = Fc[v];

@@ -39,8 +39,12 @@ extern "C" {
 enum { OR_EQ_LINADV = 0, OR_EQ_EULER = 1, OR_EQ_TENMOMENT = 2, OR_EQ_BURGERS = 3 };
 /* Boundary conditions of Sec. 3.3: periodic; outflow (F = F^+, the fully
  * outflow rule); solid wall for the Euler equations (ghost values by
- * reflecting the normal velocity, eq. (reflect.time.avg)). */
-enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1, OR_BC_WALL = 2 };
+ * reflecting the normal velocity, eq. (reflect.time.avg)); a given ghost
+ * state g (inflow/outflow: ghost values u^- = U^- = g, F^- = f(g), then the
+ * scheme's own numerical flux); fully inflow (F = F^- = f(g)). */
+enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1, OR_BC_WALL = 2, OR_BC_DIRICHLET = 3, OR_BC_INFLOW = 4 };
+/* Source terms: ten-moment Gaussian potential (Sec. 5.4), Euler gravity (Sec. 5.5). */
+enum { OR_SRC_NONE = 0, OR_SRC_TENMOMENT = 1, OR_SRC_GRAVITY = 2 };
 enum {
   OR_LIM_BLEND = 1,    /* blend with the subcell scheme, Sec. 4 eq. (blended.scheme) */
   OR_LIM_MH = 2,       /* MUSCL-Hancock subcell fluxes (else first order), Sec. 4.2 */
@@ -65,7 +69,7 @@ typedef struct {
   int equation;            /* OR_EQ_* */
   double gamma;            /* Euler */
   double adv[2];           /* linear advection velocity */
-  int source;              /* 0 none, 1 ten-moment Gaussian W */
+  int source;              /* OR_SRC_* */
   double src_amp, src_k, src_cx, src_cy;
   int limiter;             /* OR_LIM_* bits */
   int alpha_mode;          /* OR_ALPHA_* */
@@ -75,6 +79,9 @@ typedef struct {
   const double* alpha_given; /* [Ne] raw alpha_e (before smoothing) when alpha_mode == OR_ALPHA_GIVEN */
   int dissipation;         /* OR_DISS_*: dissipative part of eq. (numflux.general), Sec. 3.1.1 */
   int central;             /* OR_CENTRAL_*: central part F^{+-}, Sec. 3.1.2 */
+  int bc_side[4];          /* per side (x-, x+, y-, y+): 0 = bc_x / bc_y, else OR_BC_* (not periodic) */
+  double bc_state[4][OR_MAXM]; /* ghost state g of each side (conservative), OR_BC_DIRICHLET / OR_BC_INFLOW */
+  double gravity[2];       /* acceleration (g_x, g_y) of OR_SRC_GRAVITY */
 } or_desc;
 
 /* Optional outputs of or_step; any pointer may be NULL. */

@@ -12,8 +12,11 @@ k = p + (N + 1) * q with p along x.
 Problem dict keys: dim, nx, ny, x0, x1, y0, y1, bc_x, bc_y ("periodic",
 "outflow" or "wall"), degree, equation ("linadv", "euler", "tenmoment",
 "burgers"), gamma, adv,
-source (None or dict amp, k, cx, cy), limiter (set of "blend", "mh", "flux",
-"scaling", "traces"), t_final, steps.
+source (None, dict amp, k, cx, cy for the ten-moment potential, or dict
+gravity=(gx, gy) for Euler), limiter (set of "blend", "mh", "flux",
+"scaling", "traces"), t_final, steps; optional bc_side (dict side -> bc name,
+sides "x-", "x+", "y-", "y+", overriding bc_x / bc_y) and bc_state (dict side
+-> conservative ghost state) for "dirichlet" and "inflow" sides.
 """
 import math
 
@@ -276,6 +279,29 @@ def tenmoment2d_voronoi(nx=256, ny=None, degree=3, seed=0, ncells=16, limiter=LI
     u = tenmoment_conservative(rep(rho_c), rep(v_c[:, 0]), rep(v_c[:, 1]), rep(p11), rep(p12),
                                rep(p22))
     return prob, u
+
+
+def rayleigh_taylor(nx=64, ny=256, degree=3, limiter=LIMITER_ALL, t_final=2.5):
+    """Rayleigh-Taylor instability (Sec. 5.5): Euler (gamma 5/3) with gravity
+    g = (0, 1) (pointing to +y) on [0, 0.25] x [0, 1]; walls in x; given ghost
+    states at the bottom (rho, v1, v2, p) = (2, 0, 0, 1) and top (1, 0, 0, 2.5);
+    (rho, v1, v2, p) = (2, 0, -0.025 c cos(8 pi x), 2y + 1) for y <= 0.5 and
+    (1, 0, -0.025 c cos(8 pi x), y + 1.5) above, c = sqrt(gamma p / rho)."""
+    g = 5.0 / 3.0
+    prob = base_problem(dim=2, nx=nx, ny=ny, degree=degree, equation="euler", gamma=g, x0=0.0,
+                        x1=0.25, y0=0.0, y1=1.0, bc_x="wall", bc_y="dirichlet",
+                        limiter=frozenset(limiter), t_final=t_final, source=dict(gravity=(0.0, 1.0)))
+    bottom = euler_conservative(np.array(2.0), np.array(0.0), np.array(0.0), np.array(1.0), g, 2)
+    top = euler_conservative(np.array(1.0), np.array(0.0), np.array(0.0), np.array(2.5), g, 2)
+    prob["bc_state"] = {"y-": [float(x) for x in bottom], "y+": [float(x) for x in top]}
+    x, y = node_coords(prob)
+    _, yc = element_centres(prob)
+    low = np.broadcast_to((yc <= 0.5)[:, None], x.shape)
+    rho = np.where(low, 2.0, 1.0)
+    p = np.where(low, 2.0 * y + 1.0, y + 1.5)
+    c = np.sqrt(g * p / rho)
+    v2 = -0.025 * c * np.cos(8.0 * math.pi * x)
+    return prob, euler_conservative(rho, np.zeros_like(x), v2, p, g, 2)
 
 
 def uniform_state(prob, prim):
