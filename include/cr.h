@@ -53,8 +53,16 @@ typedef enum {
 enum { CR_EQ_LINADV = 0, CR_EQ_EULER = 1, CR_EQ_TENMOMENT = 2, CR_EQ_BURGERS = 3 };
 /* Boundary conditions of Sec. 3.3.  Outflow: the fully-outflow rule F = F^+.
  * Wall (Euler only): ghost values by reflecting the velocity normal to the
- * face, eq. (reflect.time.avg), then the D2 flux as at an interior face. */
-enum { CR_BC_PERIODIC = 0, CR_BC_OUTFLOW = 1, CR_BC_WALL = 2 };
+ * face, eq. (reflect.time.avg), then the D2 flux as at an interior face.
+ * Dirichlet: the inflow/outflow ghost values for a time-independent boundary
+ * state g (u^- = U^- = g, F^- = f(g)), then the scheme's own numerical flux
+ * (the paper takes an HLLC flux there; Rusanov-type D2 here).  Inflow: the
+ * fully-inflow rule F = F^- = f(g).  g is bc_state of the side. */
+enum { CR_BC_PERIODIC = 0, CR_BC_OUTFLOW = 1, CR_BC_WALL = 2, CR_BC_DIRICHLET = 3, CR_BC_INFLOW = 4 };
+/* Source terms (field source): none; the ten-moment potential of eq.
+ * (tenmom.source) with W = src_amp exp(-src_k |x - (src_cx, src_cy)|^2);
+ * Euler gravity of Sec. 5.5, s = (0, rho g, rho v . g) with g = gravity. */
+enum { CR_SRC_NONE = 0, CR_SRC_TENMOMENT = 1, CR_SRC_GRAVITY = 2 };
 /* Dissipative part D of the numerical flux eq. (numflux.general), Sec. 3.1:
  * D2 eq. (D2) (default: jump of the time-averaged solution traces), D1 eq.
  * (D1) (jump of the u^n traces; lower CFL numbers, computed for it), D-CSX
@@ -85,14 +93,13 @@ typedef struct {
   int dim;               /* 1 or 2 */
   int nx, ny;            /* elements per direction, >= 1 (ny ignored in 1D) */
   double x0, x1, y0, y1; /* domain [x0,x1] x [y0,y1] */
-  int bc_x, bc_y;        /* CR_BC_*; outflow is the fully-outflow rule of Sec. 3.3 */
+  int bc_x, bc_y;        /* CR_BC_* of both sides of each direction (see bc_side) */
   int degree;            /* N, 1..4; the RK method has order N+1 (Sec. 3) */
   int equation;          /* CR_EQ_*: u_t + a.grad u = 0 (Sec. 5.1.1), Euler (Sec. 5.2,
                             5.3), ten-moment (Sec. 5.4), Burgers (Sec. 5.1, 1D) */
   double gamma;          /* Euler adiabatic constant */
   double adv[2];         /* linear advection velocity */
-  int source;            /* 0 none; 1 ten-moment source of eq. (tenmom.source) with
-                            W = src_amp exp(-src_k |x - (src_cx, src_cy)|^2) */
+  int source;            /* CR_SRC_*: none, ten-moment potential, Euler gravity */
   double src_amp, src_k, src_cx, src_cy;
   int limiter;           /* CR_LIM_* bits */
   int alpha_mode;        /* CR_ALPHA_*: smoothness indicator, or alpha_e = alpha_fixed */
@@ -104,6 +111,12 @@ typedef struct {
   void* stream;          /* cudaStream_t or NULL */
   int dissipation;       /* CR_DISS_*; 0 (D2) when zero-initialised */
   int central;           /* CR_CENTRAL_*; 0 (EA) when zero-initialised */
+  int bc_side[4];        /* per side x-, x+, y-, y+: 0 = as bc_x / bc_y, else a CR_BC_*
+                            code other than periodic for that side alone (a periodic
+                            direction takes no override) */
+  double bc_state[4][6]; /* conservative ghost state g of each Dirichlet / inflow side
+                            (first M entries; admissible for Euler and ten-moment) */
+  double gravity[2];     /* (g_x, g_y) of CR_SRC_GRAVITY (Euler) */
 } cr_mesh_desc;
 
 /* Device workspace needed by cr_init_mesh for this descriptor.

@@ -18,7 +18,8 @@ STATUS = {0: "CR_OK", -1: "CR_E_INVALID_ARG", -2: "CR_E_INVALID_STATE", -3: "CR_
           -4: "CR_E_TIMEOUT", -5: "CR_E_CUDA", -6: "CR_E_NOMEM", -7: "CR_E_UNSUPPORTED",
           -8: "CR_E_TOO_LARGE"}
 CR_EQ_LINADV, CR_EQ_EULER, CR_EQ_TENMOMENT, CR_EQ_BURGERS = 0, 1, 2, 3
-CR_BC_PERIODIC, CR_BC_OUTFLOW, CR_BC_WALL = 0, 1, 2
+CR_BC_PERIODIC, CR_BC_OUTFLOW, CR_BC_WALL, CR_BC_DIRICHLET, CR_BC_INFLOW = 0, 1, 2, 3, 4
+CR_SRC_NONE, CR_SRC_TENMOMENT, CR_SRC_GRAVITY = 0, 1, 2
 CR_LIM_BLEND, CR_LIM_MH, CR_LIM_FLUX, CR_LIM_SCALING, CR_LIM_TRACES = 1, 2, 4, 8, 16
 CR_ALPHA_INDICATOR, CR_ALPHA_FIXED, CR_ALPHA_MLP = 0, 1, 2
 CR_FP64, CR_FP32_BULK = 0, 1
@@ -59,6 +60,8 @@ class cr_mesh_desc(ctypes.Structure):
         ("cfl", ctypes.c_double), ("cfl_safety", ctypes.c_double),
         ("stream", ctypes.c_void_p),
         ("dissipation", ctypes.c_int), ("central", ctypes.c_int),
+        ("bc_side", ctypes.c_int * 4), ("bc_state", (ctypes.c_double * 6) * 4),
+        ("gravity", ctypes.c_double * 2),
     ]
 
 
@@ -395,7 +398,9 @@ def cr_last_error(ctx=None):
 # ------------------------------------------------------ problem marshalling -
 _EQ = {"linadv": CR_EQ_LINADV, "euler": CR_EQ_EULER, "tenmoment": CR_EQ_TENMOMENT,
        "burgers": CR_EQ_BURGERS}
-_BC = {"periodic": CR_BC_PERIODIC, "outflow": CR_BC_OUTFLOW, "wall": CR_BC_WALL}
+_BC = {"periodic": CR_BC_PERIODIC, "outflow": CR_BC_OUTFLOW, "wall": CR_BC_WALL,
+       "dirichlet": CR_BC_DIRICHLET, "inflow": CR_BC_INFLOW}
+_SIDES = ("x-", "x+", "y-", "y+")
 _LIM = {"blend": CR_LIM_BLEND, "mh": CR_LIM_MH, "flux": CR_LIM_FLUX, "scaling": CR_LIM_SCALING,
         "traces": CR_LIM_TRACES}
 
@@ -409,8 +414,17 @@ def desc_from_problem(prob, precision=CR_FP64, alpha_fixed=None, stream=None, **
     d.degree, d.equation, d.gamma = prob["degree"], _EQ[prob["equation"]], prob["gamma"]
     d.adv[0], d.adv[1] = prob["adv"]
     src = prob.get("source")
-    if src:
-        d.source, d.src_amp, d.src_k, d.src_cx, d.src_cy = 1, src["amp"], src["k"], src["cx"], src["cy"]
+    if src and "gravity" in src:
+        d.source = CR_SRC_GRAVITY
+        d.gravity[0], d.gravity[1] = src["gravity"]
+    elif src:
+        d.source, d.src_amp, d.src_k, d.src_cx, d.src_cy = (CR_SRC_TENMOMENT, src["amp"], src["k"],
+                                                             src["cx"], src["cy"])
+    sides, states = prob.get("bc_side") or {}, prob.get("bc_state") or {}
+    for i, s in enumerate(_SIDES):
+        d.bc_side[i] = _BC[sides[s]] if s in sides else 0
+        for v, x in enumerate(states.get(s) or ()):
+            d.bc_state[i][v] = x
     lim = 0
     for name in prob["limiter"]:
         lim |= _LIM[name]

@@ -71,7 +71,7 @@ struct Tab {
 // Mesh, physics and limiter switches (one struct per launch, by value).
 struct Mesh {
   int nx, ny, ne, nfx, nfy;  // elements and faces per direction (nf = n or n+1)
-  int bcx, bcy;              // 0 periodic, 1 outflow, 2 wall (Euler)
+  int bcx, bcy;              // 0 periodic, else not periodic (the side types are in bcs)
   double x0, y0, dx, dy, invdx, invdy;
   int limiter;               // CR_LIM_* bits
   int alpha_mode;            // 0 indicator, 1 fixed, 2 learned (network, indicator fallback)
@@ -84,7 +84,12 @@ struct Mesh {
                              // 0..3 (x-left: w_0 dx, x-right: w_N dx, y-bottom, y-top)
   int dissipation;           // 0 D2, 1 D1, 2 D-CSX (Sec. 3.1)
   int central;               // 0 EA, 1 AE (Sec. 3.1.2)
+  int bcs[4];                // boundary type of sides x-, x+, y-, y+ (CR_BC_* codes)
+  double bcg[4][6];          // ghost state g of Dirichlet / inflow sides
+  double grav[2];            // gravity (g_x, g_y), source 2
 };
+
+enum : int { kBcPeriodic = 0, kBcOutflow = 1, kBcWall = 2, kBcDirichlet = 3, kBcInflow = 4 };
 
 enum : int { kLimBlend = 1, kLimMH = 2, kLimFlux = 4, kLimScaling = 8, kLimTraces = 16 };
 
@@ -413,10 +418,26 @@ __device__ __forceinline__ void source_grad(const Mesh& m, real rx, real ry, rea
   *dWy = DIM == 2 ? real(-2) * kk * ry * W : real(0);
 }
 
-// s = s^x + s^y of eq. (tenmom.source), linear in u for fixed grad W.
+template <class EQ> struct IsEuler { static constexpr bool value = false; };
+template <int DIM> struct IsEuler<EqEuler<DIM>> { static constexpr bool value = true; };
+
+// Source at one point.  Ten-moment: s = s^x + s^y of eq. (tenmom.source),
+// linear in u for fixed grad W = (dWx, dWy).  Euler with gravity (Sec. 5.5):
+// (dWx, dWy) holds g and s = (0, rho g, rho v . g) (the energy term is the
+// work of the force rho g).
 template <class EQ, typename real>
 __device__ __forceinline__ void source_eval(const real* u, real dWx, real dWy, real* s) {
-  if constexpr (EQ::M == 6) {
+  if constexpr (IsEuler<EQ>::value) {
+    s[0] = real(0);
+    if constexpr (EQ::M == 3) {
+      s[1] = u[0] * dWx;
+      s[2] = u[1] * dWx;
+    } else {
+      s[1] = u[0] * dWx;
+      s[2] = u[0] * dWy;
+      s[3] = u[1] * dWx + u[2] * dWy;
+    }
+  } else if constexpr (EQ::M == 6) {
     s[0] = real(0);
     s[1] = real(-0.5) * u[0] * dWx;
     s[2] = real(-0.5) * u[0] * dWy;

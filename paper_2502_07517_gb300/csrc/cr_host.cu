@@ -333,6 +333,33 @@ const KernelSet* lookup(const cr_mesh_desc* d) {
                      : kernels_tenmoment2d(d->degree, mixed);
 }
 
+// Boundary type of side s (0 x-, 1 x+, 2 y-, 3 y+): the per-side override or
+// the direction's type.
+int side_bc(const cr_mesh_desc* d, int s) {
+  if (d->bc_side[s] != 0) return d->bc_side[s];
+  return s < 2 ? d->bc_x : d->bc_y;
+}
+
+// A Dirichlet / inflow ghost state must be finite and, for Euler and
+// ten-moment, admissible (rho > 0 and p > 0, or a positive-definite pressure
+// tensor).
+const char* check_ghost_state(const cr_mesh_desc* d, const double* g) {
+  const int M = nvars_of(d);
+  for (int v = 0; v < M; ++v)
+    if (!std::isfinite(g[v])) return "a boundary state is not finite";
+  if (d->equation == CR_EQ_EULER) {
+    const double kin = d->dim == 1 ? 0.5 * g[1] * g[1] : 0.5 * (g[1] * g[1] + g[2] * g[2]);
+    if (!(g[0] > 0.0) || !((d->gamma - 1.0) * (g[M - 1] - kin / g[0]) > 0.0))
+      return "a boundary state is not admissible (rho > 0, p > 0)";
+  } else if (d->equation == CR_EQ_TENMOMENT) {
+    const double p11 = 2.0 * g[3] - g[1] * g[1] / g[0], p22 = 2.0 * g[5] - g[2] * g[2] / g[0];
+    const double p12 = 2.0 * g[4] - g[1] * g[2] / g[0];
+    if (!(g[0] > 0.0) || !(p11 > 0.0) || !(p11 * p22 - p12 * p12 > 0.0))
+      return "a boundary state is not admissible (rho > 0, positive-definite pressure tensor)";
+  }
+  return nullptr;
+}
+
 const char* check_desc(const cr_mesh_desc* d) {
   if (!d) return "descriptor is NULL";
   if (d->dim != 1 && d->dim != 2) return "dim must be 1 or 2";
@@ -340,10 +367,21 @@ const char* check_desc(const cr_mesh_desc* d) {
   if (d->nx < 1 || (d->dim == 2 && d->ny < 1)) return "nx, ny must be >= 1";
   if ((double)d->nx * (d->dim == 2 ? d->ny : 1) > 2.0e8) return "too many elements";
   if (!(d->x1 > d->x0) || (d->dim == 2 && !(d->y1 > d->y0))) return "empty domain";
-  if (d->bc_x < 0 || d->bc_x > 2 || (d->dim == 2 && (d->bc_y < 0 || d->bc_y > 2)))
+  if (d->bc_x < 0 || d->bc_x > 4 || (d->dim == 2 && (d->bc_y < 0 || d->bc_y > 4)))
     return "unknown boundary condition";
-  if ((d->bc_x == CR_BC_WALL || (d->dim == 2 && d->bc_y == CR_BC_WALL)) && d->equation != CR_EQ_EULER)
-    return "wall boundaries are defined for the Euler equations";
+  for (int s = 0; s < (d->dim == 2 ? 4 : 2); ++s) {
+    const int dirbc = s < 2 ? d->bc_x : d->bc_y;
+    if (d->bc_side[s] < 0 || d->bc_side[s] > 4) return "unknown per-side boundary condition";
+    if (d->bc_side[s] != 0 && dirbc == CR_BC_PERIODIC)
+      return "a periodic direction takes no per-side boundary condition";
+    const int bc = side_bc(d, s);
+    if (bc == CR_BC_WALL && d->equation != CR_EQ_EULER)
+      return "wall boundaries are defined for the Euler equations";
+    if (bc == CR_BC_DIRICHLET || bc == CR_BC_INFLOW) {
+      const char* why = check_ghost_state(d, d->bc_state[s]);
+      if (why) return why;
+    }
+  }
   if (d->equation < 0 || d->equation > 3) return "unknown equation";
   if (d->equation == CR_EQ_BURGERS && d->dim != 1) return "Burgers' equation is 1D";
   if (d->dissipation < 0 || d->dissipation > 2) return "unknown dissipation model";
@@ -355,13 +393,32 @@ const char* check_desc(const cr_mesh_desc* d) {
     return "unknown alpha mode";
   if (d->alpha_mode == CR_ALPHA_FIXED && !(d->alpha_fixed >= 0.0 && d->alpha_fixed <= 1.0))
     return "alpha_fixed must be in [0,1]";
-  if (d->source != 0 && !(d->source == 1 && d->equation == CR_EQ_TENMOMENT))
+  if (d->source < 0 || d->source > 2) return "unknown source";
+  if (d->source == CR_SRC_TENMOMENT && d->equation != CR_EQ_TENMOMENT)
     return "source 1 needs the ten-moment equations";
+  if (d->source == CR_SRC_GRAVITY &&
+      (d->equation != CR_EQ_EULER || !std::isfinite(d->gravity[0]) || !std::isfinite(d->gravity[1])))
+    return "source 2 (gravity) needs the Euler equations and a finite gravity vector";
   if (d->limiter < 0 || d->limiter > 31) return "unknown limiter bits";
   return nullptr;
 }
 
 }  // namespace
+
+namespace crk {
+
+// Per-side boundary types, ghost states and gravity of the kernels' Mesh.
+void fill_mesh_extras(const cr_mesh_desc* d, Mesh* m) {
+  const int M = nvars_of(d);
+  for (int s = 0; s < 4; ++s) {
+    m->bcs[s] = (d->dim == 2 || s < 2) ? side_bc(d, s) : CR_BC_PERIODIC;
+    for (int v = 0; v < 6; ++v) m->bcg[s][v] = v < M ? d->bc_state[s][v] : 0.0;
+  }
+  m->grav[0] = d->source == CR_SRC_GRAVITY ? d->gravity[0] : 0.0;
+  m->grav[1] = d->source == CR_SRC_GRAVITY && d->dim == 2 ? d->gravity[1] : 0.0;
+}
+
+}  // namespace crk
 
 struct cr_ctx {
   cr_mesh_desc d;
@@ -431,6 +488,7 @@ void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
   m.src_k = d.src_k;
   m.src_cx = d.src_cx;
   m.src_cy = d.src_cy;
+  fill_mesh_extras(&d, &m);
   // indicator constants (Hennemann et al. form): T(N) = 0.5 10^(-1.8 (N+1)^(1/4)),
   // s = ln((1 - 1e-4)/1e-4)
   m.T_ind = 0.5 * std::pow(10.0, -1.8 * std::pow(d.degree + 1.0, 0.25));

@@ -196,10 +196,13 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   const bool need_lo = blend || (m.limiter & kLimFlux);
   const real a = blend ? alpha : real(0);
 
-  // source: grad W at this node (time independent)
-  const bool has_src = (EQ::M == 6) && m.source == 1;
+  // source: grad W at this node (ten-moment; time independent) or gravity (Euler)
+  const bool has_src = (EQ::M == 6 && m.source == 1) || (IsEuler<EQ>::value && m.source == 2);
   real dWx = real(0), dWy = real(0);
-  if (has_src) {
+  if (IsEuler<EQ>::value && has_src) {
+    dWx = real(m.grav[0]);
+    dWy = real(DIM == 2 ? m.grav[1] : 0.0);
+  } else if (has_src) {
     const double x = m.x0 + (ix + double(tb.xi[p])) * m.dx;
     const double y = DIM == 2 ? m.y0 + (iy + double(tb.xi[q])) * m.dy : 0.0;
     source_grad<DIM, real>(m, real(x - m.src_cx), real(DIM == 2 ? y - m.src_cy : 0.0), &dWx, &dWy);
@@ -367,14 +370,17 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
       const real beta = real(2) - alpha;
       real um[M], up[M], sx[M], sy[M];
       // x-line neighbours: the neighbour element's node across a face; at a
-      // boundary the own node (outflow) or its reflection (wall, normal
-      // momentum reversed)
+      // boundary the ghost node of that side: the own node (outflow), its
+      // reflection (wall, normal momentum reversed) or the given state
+      // (Dirichlet, inflow)
       const int nbL = p == 0 ? neighbour(m, ee, 0) : -1;
       const int nbR = p == N ? neighbour(m, ee, 1) : -1;
-      const bool wx = m.bcx == 2;
+      const int sgx = p == 0 ? 0 : 1;
+      const int bgx = m.bcs[sgx];
 #pragma unroll
       for (int v = 0; v < M; ++v) {
-        const real gx = (wx && v == 1) ? -un[v] : un[v];
+        const real gx = bgx == kBcWall ? (v == 1 ? -un[v] : un[v])
+                        : (bgx == kBcDirichlet || bgx == kBcInflow) ? real(m.bcg[sgx][v]) : un[v];
         um[v] = p > 0 ? AT(s0, v, k - 1)
                       : (nbL >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbL, N + n * q) : gx);
         up[v] = p < N ? AT(s0, v, k + 1)
@@ -386,10 +392,12 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
       if (DIM == 2) {
         const int nbB = q == 0 ? neighbour(m, ee, 2) : -1;
         const int nbT = q == N ? neighbour(m, ee, 3) : -1;
-        const bool wy = m.bcy == 2;
+        const int sgy = q == 0 ? 2 : 3;
+        const int bgy = m.bcs[sgy];
 #pragma unroll
         for (int v = 0; v < M; ++v) {
-          const real gy = (wy && v == 2) ? -un[v] : un[v];
+          const real gy = bgy == kBcWall ? (v == 2 ? -un[v] : un[v])
+                          : (bgy == kBcDirichlet || bgy == kBcInflow) ? real(m.bcg[sgy][v]) : un[v];
           um[v] = q > 0 ? AT(s0, v, k - n)
                         : (nbB >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbB, p + n * N) : gy);
           up[v] = q < N ? AT(s0, v, k + n)
@@ -633,76 +641,98 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
       rusanov<EQ>(uL, uR, dir, fLO, P.ph);
     }
     alpha_f = 0.5 * (P.b.alpha[eL] + P.b.alpha[eR]);
-  } else if ((dir == 0 ? m.bcx : m.bcy) == 2) {
-    // solid wall, Sec. 3.3 eq. (reflect.time.avg): the ghost u^n trace and
-    // time-averaged solution are the interior ones with the normal momentum
-    // reversed, the ghost time-averaged flux the interior one with every other
-    // component reversed; then D2 as at an interior face (the reflected trace
-    // has the interior wave speed)
+  } else {
+    // boundary face: the interior side (ei, slot side si) and the type of this side
     const int ei = eR >= 0 ? eR : eL;
     const int si = eR >= 0 ? sR : sL;
-    real Dv[M];
-    if (m.dissipation == 2) {  // D-CSX with reflected ghost stage traces (same wave speed)
+    const int side = eR >= 0 ? (dir == 0 ? 0 : 2) : (dir == 0 ? 1 : 3);
+    const int bc = m.bcs[side];
+    real gs[M];  // given ghost state (Dirichlet, inflow)
 #pragma unroll
-      for (int v = 0; v < M; ++v) Dv[v] = real(0);
+    for (int v = 0; v < M; ++v) gs[v] = real(m.bcg[side][v]);
+    if (bc == kBcWall || bc == kBcDirichlet) {
+      // ghost values: wall, Sec. 3.3 eq. (reflect.time.avg): the interior u^n
+      // trace and time-averaged solution with the normal momentum reversed, the
+      // interior time-averaged flux with every other component reversed (the
+      // reflection has the interior wave speed); Dirichlet: u^- = U^- = g,
+      // F^- = f(g).  Then the scheme's flux as at an interior face.
+      const bool wall = bc == kBcWall;
+      real fg[M], sg = real(0);
+      if (!wall) EQ::flux_speed(gs, dir, fg, &sg, P.ph);
+      real Dv[M];
+      if (m.dissipation == 2) {  // D-CSX with ghost stage traces
 #pragma unroll
-      for (int i = 0; i < Tableau<N>::S; ++i) {
-        if (Tableau<N>::b(i) == 0.0) continue;
-        real ui[M];
+        for (int v = 0; v < M; ++v) Dv[v] = real(0);
 #pragma unroll
-        for (int v = 0; v < M; ++v) ui[v] = fld(1 + 4 * M + i * M + v, si, ei);
-        const real lam = EQ::speed(ui, dir, P.ph);
-        const real bi = real(Tableau<N>::b(i));
+        for (int i = 0; i < Tableau<N>::S; ++i) {
+          if (Tableau<N>::b(i) == 0.0) continue;
+          real ui[M];
+#pragma unroll
+          for (int v = 0; v < M; ++v) ui[v] = fld(1 + 4 * M + i * M + v, si, ei);
+          const real lam = wall ? EQ::speed(ui, dir, P.ph) : fmax(EQ::speed(ui, dir, P.ph), sg);
+          const real bi = real(Tableau<N>::b(i));
+#pragma unroll
+          for (int v = 0; v < M; ++v) {
+            const real ug = wall ? (v == 1 + dir ? -ui[v] : ui[v]) : gs[v];
+            const real uL = eR >= 0 ? ug : ui[v], uR = eR >= 0 ? ui[v] : ug;
+            Dv[v] += bi * real(0.5) * lam * (uR - uL);
+          }
+        }
+      } else {
+        const real lam = wall ? fld(0, si, ei) : fmax(fld(0, si, ei), sg);
 #pragma unroll
         for (int v = 0; v < M; ++v) {
-          const real ug = v == 1 + dir ? -ui[v] : ui[v];
-          const real uL = eR >= 0 ? ug : ui[v], uR = eR >= 0 ? ui[v] : ug;
-          Dv[v] += bi * real(0.5) * lam * (uR - uL);
+          const real Ui = fld(1 + v, si, ei);
+          const real Ug = wall ? (v == 1 + dir ? -Ui : Ui) : gs[v];
+          const real UL = eR >= 0 ? Ug : Ui, UR = eR >= 0 ? Ui : Ug;
+          Dv[v] = real(0.5) * lam * (UR - UL);
         }
       }
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        const real Fi = fld(1 + M + v, si, ei);
+        const real Fg = wall ? (v == 1 + dir ? Fi : -Fi) : fg[v];
+        const real FL = eR >= 0 ? Fg : Fi, FR = eR >= 0 ? Fi : Fg;
+        FHO[v] = real(0.5) * (FL + FR) - Dv[v];
+      }
+      if (need_lo) {
+        real us[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) us[v] = fld(1 + 2 * M + v, si, ei);
+        if (wall) {
+          // Rusanov between the evolved boundary state and its reflection; the
+          // ghost flux is the interior flux reflected (one evaluation), so the
+          // mass and energy components cancel exactly, as the reflection requires
+          real fi[M], sp;
+          EQ::flux_speed(us, dir, fi, &sp, P.ph);
+#pragma unroll
+          for (int v = 0; v < M; ++v) {
+            const real fgv = v == 1 + dir ? fi[v] : -fi[v], ug = v == 1 + dir ? -us[v] : us[v];
+            const real fl = eR >= 0 ? fgv : fi[v], fr = eR >= 0 ? fi[v] : fgv;
+            const real ul = eR >= 0 ? ug : us[v], ur = eR >= 0 ? us[v] : ug;
+            fLO[v] = real(0.5) * (fl + fr) - real(0.5) * sp * (ur - ul);
+          }
+        } else if (eR >= 0) {
+          rusanov<EQ>(gs, us, dir, fLO, P.ph);
+        } else {
+          rusanov<EQ>(us, gs, dir, fLO, P.ph);
+        }
+      }
+    } else if (bc == kBcInflow) {
+      // fully inflow, Sec. 3.3: F = F^- = f(g), high and low order
+      EQ::flux(gs, dir, FHO, P.ph);
+#pragma unroll
+      for (int v = 0; v < M; ++v) fLO[v] = FHO[v];
     } else {
-      const real lam = fld(0, si, ei);
+      // fully outflow, Sec. 3.3: F = F^+ (the interior trace flux)
 #pragma unroll
-      for (int v = 0; v < M; ++v) {
-        const real Ui = fld(1 + v, si, ei), Ug = v == 1 + dir ? -Ui : Ui;
-        const real UL = eR >= 0 ? Ug : Ui, UR = eR >= 0 ? Ui : Ug;
-        Dv[v] = real(0.5) * lam * (UR - UL);
+      for (int v = 0; v < M; ++v) FHO[v] = fld(1 + M + v, si, ei);
+      if (need_lo) {
+        real us[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) us[v] = fld(1 + 2 * M + v, si, ei);
+        EQ::flux(us, dir, fLO, P.ph);
       }
-    }
-#pragma unroll
-    for (int v = 0; v < M; ++v) {
-      const real Fi = fld(1 + M + v, si, ei);
-      const real Fg = v == 1 + dir ? Fi : -Fi;
-      const real FL = eR >= 0 ? Fg : Fi, FR = eR >= 0 ? Fi : Fg;
-      FHO[v] = real(0.5) * (FL + FR) - Dv[v];
-    }
-    if (need_lo) {
-      // Rusanov between the evolved boundary state and its reflection; the
-      // ghost flux is the interior flux reflected (one evaluation), so the mass
-      // and energy components cancel exactly, as the reflection requires
-      real us[M], fi[M], sp;
-#pragma unroll
-      for (int v = 0; v < M; ++v) us[v] = fld(1 + 2 * M + v, si, ei);
-      EQ::flux_speed(us, dir, fi, &sp, P.ph);
-#pragma unroll
-      for (int v = 0; v < M; ++v) {
-        const real fg = v == 1 + dir ? fi[v] : -fi[v], ug = v == 1 + dir ? -us[v] : us[v];
-        const real fl = eR >= 0 ? fg : fi[v], fr = eR >= 0 ? fi[v] : fg;
-        const real ul = eR >= 0 ? ug : us[v], ur = eR >= 0 ? us[v] : ug;
-        fLO[v] = real(0.5) * (fl + fr) - real(0.5) * sp * (ur - ul);
-      }
-    }
-    alpha_f = P.b.alpha[ei];
-  } else {
-    const int ei = eR >= 0 ? eR : eL;
-    const int si = eR >= 0 ? sR : sL;
-#pragma unroll
-    for (int v = 0; v < M; ++v) FHO[v] = fld(1 + M + v, si, ei);
-    if (need_lo) {
-      real us[M];
-#pragma unroll
-      for (int v = 0; v < M; ++v) us[v] = fld(1 + 2 * M + v, si, ei);
-      EQ::flux(us, dir, fLO, P.ph);
     }
     alpha_f = P.b.alpha[ei];
   }

@@ -20,6 +20,12 @@
 #include "../../include/cr.h"
 #include "cr_launch.cuh"
 
+namespace crk {
+// Per-side boundary types, ghost states and gravity of the kernels' Mesh
+// (defined with the context code).
+void fill_mesh_extras(const cr_mesh_desc* d, Mesh* m);
+}  // namespace crk
+
 using namespace crk;
 
 namespace {
@@ -208,6 +214,7 @@ extern "C" cr_status cr_step_static(const cr_mesh_desc* d, const double* u_in, d
   m.src_k = d->src_k;
   m.src_cx = d->src_cx;
   m.src_cy = d->src_cy;
+  fill_mesh_extras(d, &m);
   m.T_ind = 0.5 * std::pow(10.0, -1.8 * std::pow(d->degree + 1.0, 0.25));
   m.s_ind = std::log((1.0 - 1e-4) / 1e-4);
   P.ph.gamma = d->gamma;

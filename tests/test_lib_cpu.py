@@ -67,3 +67,49 @@ def test_library_cfl_for_dissipation_models_matches_oracle(N):
     assert abs(crkfr.cr_cfl_number_for(N, crkfr.CR_DISS_D1) - cfl_number(N, True)) < 1e-6
     assert crkfr.cr_cfl_number_for(N, crkfr.CR_DISS_DCSX) == crkfr.cr_cfl_number(N)
     assert crkfr.cr_cfl_number_for(N, crkfr.CR_DISS_D1) < crkfr.cr_cfl_number(N)
+
+
+def _rejected(d):
+    with pytest.raises(crkfr.CrError) as ei:
+        crkfr.cr_workspace_bytes(d)
+    return ei.value.status == -1
+
+
+def test_boundary_and_source_descriptors_checked(built):
+    """Host checks of the per-side boundaries, ghost states and sources (no
+    device work): what is accepted and what is refused."""
+    from paper_2502_07517_gb300 import workloads as wl
+    prob, _ = wl.rayleigh_taylor(nx=8, ny=32)
+    d = crkfr.desc_from_problem(prob)
+    assert crkfr.cr_workspace_bytes(d) > 0
+    d.bc_state[2][3] = 0.0                       # bottom ghost state: E = 0, p < 0
+    assert _rejected(d)
+    d = crkfr.desc_from_problem(prob)
+    d.bc_state[3][0] = float("nan")
+    assert _rejected(d)
+    d = crkfr.desc_from_problem(prob)
+    d.bc_side[0] = 5                             # unknown code
+    assert _rejected(d)
+    d = crkfr.desc_from_problem(prob)
+    d.gravity[1] = float("inf")
+    assert _rejected(d)
+    d = crkfr.desc_from_problem(prob)
+    d.bc_side[1] = crkfr.CR_BC_INFLOW            # x+ becomes inflow of the zero state
+    assert _rejected(d)
+    d.bc_state[1][0], d.bc_state[1][3] = 1.0, 2.0
+    assert crkfr.cr_workspace_bytes(d) > 0
+    # a periodic direction takes no per-side override
+    pv, _ = wl.euler2d_vortex(nx=8, degree=3)
+    d = crkfr.desc_from_problem(pv)
+    d.bc_side[2] = crkfr.CR_BC_OUTFLOW
+    assert _rejected(d)
+    # gravity is an Euler source; walls stay Euler only, also per side
+    pl, _ = wl.linadv_random(nx=8, degree=3, bc="outflow")
+    d = crkfr.desc_from_problem(pl)
+    d.source, d.gravity[0] = crkfr.CR_SRC_GRAVITY, 1.0
+    assert _rejected(d)
+    d = crkfr.desc_from_problem(pl)
+    d.bc_side[1] = crkfr.CR_BC_WALL
+    assert _rejected(d)
+    d.bc_side[1] = crkfr.CR_BC_DIRICHLET          # a scalar ghost state needs only finiteness
+    assert crkfr.cr_workspace_bytes(d) > 0
