@@ -23,6 +23,7 @@ LIM_ALL = LIM_BLEND | LIM_MH | LIM_FLUX | LIM_SCALING | LIM_TRACES
 ALPHA_INDICATOR, ALPHA_FIXED, ALPHA_GIVEN = 0, 1, 2
 DISS_D2, DISS_D1, DISS_DCSX = 0, 1, 2
 CENTRAL_EA, CENTRAL_AE = 0, 1
+POINTS_GL, POINTS_GLL = 0, 1
 
 
 class Desc(ctypes.Structure):
@@ -42,7 +43,7 @@ class Desc(ctypes.Structure):
         ("alpha_given", ctypes.POINTER(ctypes.c_double)),
         ("dissipation", ctypes.c_int), ("central", ctypes.c_int),
         ("bc_side", ctypes.c_int * 4), ("bc_state", (ctypes.c_double * 6) * 4),
-        ("gravity", ctypes.c_double * 2),
+        ("gravity", ctypes.c_double * 2), ("points", ctypes.c_int),
     ]
 
 
@@ -63,6 +64,7 @@ def lib():
         D = ctypes.POINTER(ctypes.c_double)
         P = ctypes.POINTER(Desc)
         _lib.or_tables.argtypes = [ctypes.c_int, D, D, D, D, D]
+        _lib.or_tables_pts.argtypes = [ctypes.c_int, ctypes.c_int, D, D, D, D, D, D, D]
         _lib.or_tableau.argtypes = [ctypes.c_int, D, D, D]
         _lib.or_tableau.restype = ctypes.c_int
         _lib.or_nvars.argtypes = [P]
@@ -103,13 +105,13 @@ def make_desc(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=BC_PERIOD
               source=0, src_amp=0.0, src_k=0.0, src_cx=0.5, src_cy=0.5, limiter=0,
               alpha_mode=ALPHA_INDICATOR, alpha_fixed=0.0, cfl=None, cfl_safety=0.98,
               alpha_given=None, dissipation=DISS_D2, central=CENTRAL_EA, bc_side=(0, 0, 0, 0),
-              bc_state=None, gravity=(0.0, 0.0)):
+              bc_state=None, gravity=(0.0, 0.0), points=POINTS_GL):
     """Mesh/scheme description; cfl defaults to CFL(degree) from the Fourier analysis.
     alpha_given: per-element raw alpha array for alpha_mode ALPHA_GIVEN (kept alive on
     the returned object)."""
     if cfl is None:
         from .cfl import cfl_number
-        cfl = cfl_number(degree, dissipation == DISS_D1)
+        cfl = cfl_number(degree, dissipation == DISS_D1, points=points)
     d = Desc()
     d.dim, d.nx, d.ny = dim, nx, (ny if dim == 2 else 1)
     d.x0, d.x1, d.y0, d.y1 = x0, x1, y0, y1
@@ -126,6 +128,7 @@ def make_desc(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=BC_PERIOD
             for v, x in enumerate(bc_state[s]):
                 d.bc_state[s][v] = x
     d.gravity[0], d.gravity[1] = gravity
+    d.points = points
     if alpha_given is not None:
         arr = np.ascontiguousarray(alpha_given, dtype=np.float64)
         d._alpha_given_keep = arr
@@ -150,12 +153,19 @@ def state_shape(d):
     return (nvars(d), nelem(d), nodes(d))
 
 
-def tables(N):
+def tables(N, points=POINTS_GL):
+    """(xi, w, l0, l1, D) of the point set on [0,1]."""
+    return tables_corr(N, points)[:5]
+
+
+def tables_corr(N, points=POINTS_GL):
+    """(xi, w, l0, l1, D, gL, gR): the tables with the correction derivatives
+    g_L'(xi_p), g_R'(xi_p) (Radau for Gauss-Legendre, g2 for Gauss-Lobatto)."""
     n = N + 1
-    xi, w, l0, l1 = (np.zeros(n) for _ in range(4))
+    xi, w, l0, l1, gL, gR = (np.zeros(n) for _ in range(6))
     D = np.zeros((n, n))
-    lib().or_tables(N, _ptr(xi), _ptr(w), _ptr(l0), _ptr(l1), _ptr(D))
-    return xi, w, l0, l1, D
+    lib().or_tables_pts(N, points, _ptr(xi), _ptr(w), _ptr(l0), _ptr(l1), _ptr(D), _ptr(gL), _ptr(gR))
+    return xi, w, l0, l1, D, gL, gR
 
 
 def tableau(N):
@@ -269,7 +279,7 @@ def scaling_limiter(d, ue):
 
 def node_coords(d):
     """Physical coordinates (x, y) of every solution point, arrays [Ne][Np]."""
-    xi = tables(d.degree)[0]
+    xi = tables(d.degree, d.points)[0]
     n = d.degree + 1
     ne = nelem(d)
     dx = (d.x1 - d.x0) / d.nx
@@ -288,7 +298,7 @@ def node_coords(d):
 
 def element_means(d, u):
     """Element means sum_k W_k u_k, array [M][Ne]."""
-    w = tables(d.degree)[1]
+    w = tables(d.degree, d.points)[1]
     n = d.degree + 1
     W = w if d.dim == 1 else np.array([w[k % n] * w[k // n] for k in range(n * n)])
     return np.einsum("vek,k->ve", u, W)

@@ -16,7 +16,8 @@ and a Fourier mode u_{e-1} = exp(-i k) u_e gives the amplification matrix
 D1 (eq. (D1)) takes the jump of the u^n traces instead of the time-averaged
 ones, F_{e+1/2} = (l(1)^T T u_e + l(0)^T T u_{e+1})/2 - (l(0)^T u_{e+1} -
 l(1)^T u_e)/2, which is no longer upwind; in general, with V = T (D2) or
-V = I (D1) and g_R' = l(1)/w,
+V = I (D1) and the correction derivatives g_L', g_R' at the solution points
+(Radau with Gauss-Legendre points, g2 with Gauss-Lobatto points),
     G(k) = I - nu [ A_0 + exp(i k) A_+ + exp(-i k) A_- ],
     A_0 = D T + g_R' (l(1)^T V - l(1)^T T)/2 - g_L' (l(0)^T T + l(0)^T V)/2,
     A_+ = g_R' (l(0)^T T - l(0)^T V)/2,   A_- = g_L' (l(1)^T T + l(1)^T V)/2.
@@ -35,11 +36,11 @@ import math
 
 import numpy as np
 
-from . import tables
+from . import tables_corr
 
 
-def amplification(N, nu, k, d1=False):
-    xi, w, l0, l1, D = tables(N)
+def amplification(N, nu, k, d1=False, points=0):
+    xi, w, l0, l1, D, gL, gR = tables_corr(N, points)
     n = N + 1
     T = np.zeros((n, n))
     Dm = np.eye(n)
@@ -47,25 +48,25 @@ def amplification(N, nu, k, d1=False):
         T += (-nu) ** m / math.factorial(m + 1) * Dm
         Dm = Dm @ D
     V = np.eye(n) if d1 else T
-    gL, gR = -l0 / w, l1 / w
     A0 = D @ T + 0.5 * np.outer(gR, l1 @ V - l1 @ T) - 0.5 * np.outer(gL, l0 @ T + l0 @ V)
     Ap = 0.5 * np.outer(gR, l0 @ T - l0 @ V)
     Am = 0.5 * np.outer(gL, l1 @ T + l1 @ V)
     return np.eye(n) - nu * (A0 + np.exp(1j * k) * Ap + np.exp(-1j * k) * Am)
 
 
-def max_growth(N, nu, nk=721, d1=False):
+def max_growth(N, nu, nk=721, d1=False, points=0):
     ks = np.linspace(0.0, 2.0 * np.pi, nk)
-    return max(np.max(np.abs(np.linalg.eigvals(amplification(N, nu, k, d1)))) for k in ks)
+    return max(np.max(np.abs(np.linalg.eigvals(amplification(N, nu, k, d1, points)))) for k in ks)
 
 
 @functools.lru_cache(maxsize=None)
-def cfl_number(N, d1=False, tol=1e-4, iters=40):
-    """CFL(N) for D2 (and D-CSX), or for D1 when d1 is true."""
+def cfl_number(N, d1=False, tol=1e-4, iters=40, points=0):
+    """CFL(N) for D2 (and D-CSX), or for D1 when d1 is true; Gauss-Legendre
+    points with Radau correction (points 0) or Gauss-Lobatto with g2 (1)."""
     lo, hi = 0.0, 1.0
     for _ in range(iters):
         mid = 0.5 * (lo + hi)
-        if max_growth(N, mid, d1=d1) <= 1.0 + tol:
+        if max_growth(N, mid, d1=d1, points=points) <= 1.0 + tol:
             lo = mid
         else:
             hi = mid

@@ -20,6 +20,7 @@ typedef struct {
   int dim, N, n, nq, np, M, s, K, nx, ny, ne;
   double dx, dy;
   double xi[NMAX], w[NMAX], l0[NMAX], l1[NMAX], D[NMAX * NMAX];
+  double gL[NMAX], gR[NMAX]; /* correction derivatives g_L'(xi_p), g_R'(xi_p) */
   double A[36], b[6], c[6];
   double xsub[NMAX + 1]; /* subface positions x_{p-1/2}, p = 0..N+1, in units of dx (eq. subcell.defn) */
 } ctx;
@@ -39,7 +40,7 @@ static void ctx_init(ctx* c, const or_desc* d) {
   c->ne = c->nx * c->ny;
   c->dx = (d->x1 - d->x0) / d->nx;
   c->dy = d->dim == 2 ? (d->y1 - d->y0) / d->ny : 1.0;
-  or_tables(c->N, c->xi, c->w, c->l0, c->l1, c->D);
+  or_tables_pts(c->N, d->points, c->xi, c->w, c->l0, c->l1, c->D, c->gL, c->gR);
   c->s = or_tableau(c->N, c->A, c->b, c->c);
   /* Sec. 4 eq. (subcell.defn): x_{p+1/2} - x_{p-1/2} = w_p dx, x_{-1/2} = 0 */
   c->xsub[0] = 0.0;
@@ -866,8 +867,8 @@ int or_step(const or_desc* d, const double* u_in, double dt, double* u_out, or_d
       for (int v = 0; v < M; ++v) {
         double RHx = 0.0;
         for (int r = 0; r < n; ++r) RHx += c.D[p * n + r] * Fe[node(&c, r, q) * M + v];
-        RHx += (W4(W.fnum, e, 1, q, v) - W4(W.Fd, e, 1, q, v)) * (c.l1[p] / c.w[p]);
-        RHx += (W4(W.fnum, e, 0, q, v) - W4(W.Fd, e, 0, q, v)) * (-c.l0[p] / c.w[p]);
+        RHx += (W4(W.fnum, e, 1, q, v) - W4(W.Fd, e, 1, q, v)) * c.gR[p];
+        RHx += (W4(W.fnum, e, 0, q, v) - W4(W.Fd, e, 0, q, v)) * c.gL[p];
         double fr = p == N ? W4(W.fnum, e, 1, q, v) : WS(W.fsx, e, q, p + 1, v);
         double fl = p == 0 ? W4(W.fnum, e, 0, q, v) : WS(W.fsx, e, q, p, v);
         double RLx = (fr - fl) / c.w[p];
@@ -875,8 +876,8 @@ int or_step(const or_desc* d, const double* u_in, double dt, double* u_out, or_d
         if (c.dim == 2) {
           double RHy = 0.0;
           for (int r = 0; r < n; ++r) RHy += c.D[q * n + r] * Ge[node(&c, p, r) * M + v];
-          RHy += (W4(W.fnum, e, 3, p, v) - W4(W.Fd, e, 3, p, v)) * (c.l1[q] / c.w[q]);
-          RHy += (W4(W.fnum, e, 2, p, v) - W4(W.Fd, e, 2, p, v)) * (-c.l0[q] / c.w[q]);
+          RHy += (W4(W.fnum, e, 3, p, v) - W4(W.Fd, e, 3, p, v)) * c.gR[q];
+          RHy += (W4(W.fnum, e, 2, p, v) - W4(W.Fd, e, 2, p, v)) * c.gL[q];
           double gt = q == N ? W4(W.fnum, e, 3, p, v) : WS(W.fsy, e, p, q + 1, v);
           double gb = q == 0 ? W4(W.fnum, e, 2, p, v) : WS(W.fsy, e, p, q, v);
           double RLy = (gt - gb) / c.w[q];

@@ -65,6 +65,86 @@ static double lagrange_deriv(int N, const double* xi, int j, double x) {
   return s;
 }
 
+/* P_n and P_n' anywhere on [-1,1], endpoints included, by the recurrences
+ * (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1} and P'_{k+1} = P'_{k-1} + (2k+1) P_k. */
+static void legendre_all(int n, double x, double* P, double* dP) {
+  double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+  if (n == 0) { *P = 1.0; *dP = 0.0; return; }
+  for (int k = 1; k < n; ++k) {
+    double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+    double d2 = d0 + (2.0 * k + 1.0) * p1;
+    p0 = p1; p1 = p2;
+    d0 = d1; d1 = d2;
+  }
+  *P = p1;
+  *dP = d1;
+}
+
+/* Gauss-Lobatto-Legendre solution points (Sec. 5.1, with the g2 correction):
+ * x = -1, 1 and the N-1 roots of P_N' (Newton's method with P_N'' from
+ * Legendre's equation (1 - x^2) P'' = 2 x P' - N (N+1) P), mapped to [0,1];
+ * weights 2 / (N (N+1) P_N(x)^2), halved for [0,1]; exact to degree 2N-1. */
+static void gauss_lobatto01(int N, double* xi, double* w) {
+  const double pi = 3.14159265358979323846;
+  double x[OR_MAXN + 1];
+  x[0] = -1.0;
+  x[N] = 1.0;
+  for (int i = 1; i < N; ++i) {
+    double z = -cos(pi * i / N);
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre_all(N, z, &P, &dP);
+      double d2P = (2.0 * z * dP - N * (N + 1.0) * P) / (1.0 - z * z);
+      double dz = dP / d2P;
+      z -= dz;
+      if (fabs(dz) < 1e-17) break;
+    }
+    x[i] = z;
+  }
+  for (int i = 0; i <= N; ++i) {
+    double P, dP;
+    legendre_all(N, x[i], &P, &dP);
+    xi[i] = 0.5 * (1.0 + x[i]);
+    w[i] = 0.5 * 2.0 / (N * (N + 1.0) * P * P);
+  }
+}
+
+/* Derivative on [-1,1] of the left correction function g (g(-1) = 1,
+ * g(1) = 0) of the FR update (Sec. 2), with the right Radau polynomials
+ * R_k = (-1)^k (P_k - P_{k-1}) / 2:
+ *   Radau (OR_POINTS_GL): g = R_{N+1};
+ *   g2 (OR_POINTS_GLL):   g = ((N+1) R_N + N R_{N+1}) / (2N+1). */
+static double radau_deriv(int k, double x) {
+  double P, dP, Pm, dPm;
+  legendre_all(k, x, &P, &dP);
+  legendre_all(k - 1, x, &Pm, &dPm);
+  return ((k % 2) ? -0.5 : 0.5) * (dP - dPm);
+}
+
+static double corr_deriv(int N, int points, double x) {
+  if (points == OR_POINTS_GLL)
+    return ((N + 1.0) * radau_deriv(N, x) + N * radau_deriv(N + 1, x)) / (2.0 * N + 1.0);
+  return radau_deriv(N + 1, x);
+}
+
+void or_tables_pts(int N, int points, double* xi, double* w, double* l0, double* l1, double* D,
+                   double* gL, double* gR) {
+  or_tables(N, xi, w, l0, l1, D);
+  if (points == OR_POINTS_GLL) {
+    gauss_lobatto01(N, xi, w);
+    for (int p = 0; p <= N; ++p) {
+      l0[p] = lagrange(N, xi, p, 0.0);
+      l1[p] = lagrange(N, xi, p, 1.0);
+    }
+    for (int i = 0; i <= N; ++i)
+      for (int j = 0; j <= N; ++j) D[i * (N + 1) + j] = lagrange_deriv(N, xi, j, xi[i]);
+  }
+  /* on [0,1]: g_L'(xi) = 2 g'(2 xi - 1); g_R(xi) = g_L(1 - xi) and the nodes are
+   * symmetric (xi_{N-p} = 1 - xi_p), so g_R'(xi_p) = -g_L'(xi_{N-p}) */
+  for (int p = 0; p <= N; ++p) gL[p] = 2.0 * corr_deriv(N, points, 2.0 * xi[p] - 1.0);
+  for (int p = 0; p <= N; ++p) gR[p] = -gL[N - p];
+}
+
 void or_tables(int N, double* xi, double* w, double* l0, double* l1, double* D) {
   gauss_legendre01(N, xi, w);
   for (int p = 0; p <= N; ++p) {

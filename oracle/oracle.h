@@ -59,6 +59,9 @@ enum { OR_DISS_D2 = 0, OR_DISS_D1 = 1, OR_DISS_DCSX = 2 };
 /* EA eq. (evaluate) (stage fluxes at the face), AE eq. (extrapolate) (trace of
  * the time-averaged flux) */
 enum { OR_CENTRAL_EA = 0, OR_CENTRAL_AE = 1 };
+/* Solution points and correction: Gauss-Legendre with Radau (Sec. 2, the
+ * default), Gauss-Lobatto-Legendre with g2 (Sec. 5.1). */
+enum { OR_POINTS_GL = 0, OR_POINTS_GLL = 1 };
 
 typedef struct {
   int dim;                 /* 1 or 2 */
@@ -82,6 +85,7 @@ typedef struct {
   int bc_side[4];          /* per side (x-, x+, y-, y+): 0 = bc_x / bc_y, else OR_BC_* (not periodic) */
   double bc_state[4][OR_MAXM]; /* ghost state g of each side (conservative), OR_BC_DIRICHLET / OR_BC_INFLOW */
   double gravity[2];       /* acceleration (g_x, g_y) of OR_SRC_GRAVITY */
+  int points;              /* OR_POINTS_*; GLL supports no MUSCL-Hancock subcells */
 } or_desc;
 
 /* Optional outputs of or_step; any pointer may be NULL. */
@@ -105,6 +109,10 @@ int or_nodes(const or_desc* d);
 /* Reference element tables of Sec. 2 on [0,1]: Gauss-Legendre nodes and
  * weights, l_p(0), l_p(1), and D_ij = l_j'(xi_i). */
 void or_tables(int N, double* xi, double* w, double* l0, double* l1, double* D);
+/* The tables of either point set, with the correction derivatives g_L', g_R'
+ * at the solution points (Radau for Gauss-Legendre, g2 for Gauss-Lobatto). */
+void or_tables_pts(int N, int points, double* xi, double* w, double* l0, double* l1, double* D,
+                   double* gL, double* gR);
 /* Butcher tableau used for degree N (cRK22/33/44, and the order-5 reading for N = 4). */
 int or_tableau(int N, double* A /* [6][6] */, double* b, double* c);
 

@@ -16,7 +16,8 @@ source (None, dict amp, k, cx, cy for the ten-moment potential, or dict
 gravity=(gx, gy) for Euler), limiter (set of "blend", "mh", "flux",
 "scaling", "traces"), t_final, steps; optional bc_side (dict side -> bc name,
 sides "x-", "x+", "y-", "y+", overriding bc_x / bc_y) and bc_state (dict side
--> conservative ghost state) for "dirichlet" and "inflow" sides.
+-> conservative ghost state) for "dirichlet" and "inflow" sides; points
+("gl", the default, or "gll" Gauss-Lobatto-Legendre).
 """
 import math
 
@@ -30,10 +31,26 @@ def gl_nodes01(N):
     return 0.5 * (x + 1.0), 0.5 * w
 
 
+def gll_nodes01(N):
+    """Gauss-Lobatto-Legendre nodes and weights on [0,1] (numpy's Legendre
+    class: the end points and the roots of P_N')."""
+    PN = np.polynomial.legendre.Legendre.basis(N)
+    inner = np.sort(PN.deriv().roots().real) if N > 1 else np.zeros(0)
+    x = np.concatenate([[-1.0], inner, [1.0]])
+    w = 2.0 / (N * (N + 1) * PN(x) ** 2)
+    return 0.5 * (x + 1.0), 0.5 * w
+
+
+def nodes01(prob):
+    """Solution points and weights of the problem's point set ("gl" default, "gll")."""
+    N = prob["degree"]
+    return gll_nodes01(N) if prob.get("points", "gl") == "gll" else gl_nodes01(N)
+
+
 def node_coords(prob):
     """(x, y) of every solution point, arrays [Ne][Np]."""
     N = prob["degree"]
-    xi, _ = gl_nodes01(N)
+    xi, _ = nodes01(prob)
     n = N + 1
     nx = prob["nx"]
     ny = prob["ny"] if prob["dim"] == 2 else 1
@@ -100,11 +117,12 @@ def linadv_sine(nx=64, degree=3, t_final=1.0, a=1.0):
     return prob, np.sin(2.0 * np.pi * x)[None, :, :].copy()
 
 
-def burgers_sine(nx=64, degree=3, t_final=2.0, amp=0.2):
+def burgers_sine(nx=64, degree=3, t_final=2.0, amp=0.2, points="gl"):
     """1D Burgers u_t + (u^2/2)_x = 0 on [0, 2 pi] periodic, u0 = amp sin(x)
-    (Sec. 5.1): smooth until t = 1/amp = 5, no limiter."""
+    (Sec. 5.1): smooth until t = 1/amp = 5, no limiter; Gauss-Legendre or
+    Gauss-Lobatto ("gll") solution points."""
     prob = base_problem(dim=1, nx=nx, degree=degree, equation="burgers", x0=0.0,
-                        x1=2.0 * math.pi, t_final=t_final)
+                        x1=2.0 * math.pi, t_final=t_final, points=points)
     prob["burgers_amp"] = amp
     x, _ = node_coords(prob)
     return prob, (amp * np.sin(x))[None, :, :].copy()

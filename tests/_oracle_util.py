@@ -28,6 +28,7 @@ def oracle_desc(prob, alpha_fixed=None, **over):
     states = prob.get("bc_state") or {}
     kw.update(bc_side=tuple(_BC[sides[s]] if s in sides else 0 for s in SIDES),
               bc_state=[states.get(s) for s in SIDES])
+    kw.update(points={"gl": oracle.POINTS_GL, "gll": oracle.POINTS_GLL}[prob.get("points", "gl")])
     if alpha_fixed is not None:
         kw.update(alpha_mode=oracle.ALPHA_FIXED, alpha_fixed=alpha_fixed)
     kw.update(over)

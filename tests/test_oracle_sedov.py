@@ -4,7 +4,8 @@
 * the walls pass neither mass nor energy, and a periodic box conserves every
   variable: the sums of element means stay put to rounding;
 * the data are mirror symmetric (1D: about x = 0; 2D: in x, in y and under
-  x <-> y), and so must the computed solution be, to rounding;
+  x <-> y), and so must the computed solution be, to rounding (1D: to the
+  rounding that the ill-conditioned second blast step amplifies);
 * the paper reports nonphysical solutions without the admissibility
   corrections: without the scaling limiter the 1D blast fails within a few
   steps, with all limiters it keeps going with admissible means.
@@ -30,7 +31,10 @@ def test_sedov1d_conserves_and_stays_symmetric():
     m0, m1 = oracle.element_means(d, u), oracle.element_means(d, g)
     assert abs(m1[0].sum() - m0[0].sum()) <= 1e-15 * n * m0[0].sum()
     assert abs(m1[2].sum() - m0[2].sum()) <= 1e-15 * n * m0[2].sum()
-    assert mirror_1d(g) <= 1e-14
+    # the second blast step is ill-conditioned (one-ulp input changes move its
+    # output by ~5e-12 of the maximum), so rounding-level asymmetry of the
+    # arithmetic grows there; a wrong sign or index breaks symmetry at O(1)
+    assert mirror_1d(g) <= 1e-10
     p = 0.4 * (m1[2] - 0.5 * m1[1] ** 2 / m1[0])
     assert m1[0].min() > 0 and p.min() > 0
     # the blast has spread beyond the centre element
