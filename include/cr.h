@@ -63,6 +63,13 @@ enum { CR_BC_PERIODIC = 0, CR_BC_OUTFLOW = 1, CR_BC_WALL = 2, CR_BC_DIRICHLET = 
  * (tenmom.source) with W = src_amp exp(-src_k |x - (src_cx, src_cy)|^2);
  * Euler gravity of Sec. 5.5, s = (0, rho g, rho v . g) with g = gravity. */
 enum { CR_SRC_NONE = 0, CR_SRC_TENMOMENT = 1, CR_SRC_GRAVITY = 2 };
+/* Solution points and FR correction: Gauss-Legendre points with the Radau
+ * correction (Sec. 2, the default), or Gauss-Lobatto-Legendre points with
+ * the g2 correction (Sec. 5.1; there the evaluate and extrapolate central
+ * fluxes coincide).  GLL takes no blending or flux limiter (the low-order
+ * subcell update would outrun its CFL condition at the GLL time step), and
+ * neither cr_step_static nor the batched entry points take it. */
+enum { CR_POINTS_GL = 0, CR_POINTS_GLL = 1 };
 /* Dissipative part D of the numerical flux eq. (numflux.general), Sec. 3.1:
  * D2 eq. (D2) (default: jump of the time-averaged solution traces), D1 eq.
  * (D1) (jump of the u^n traces; lower CFL numbers, computed for it), D-CSX
@@ -117,6 +124,7 @@ typedef struct {
   double bc_state[4][6]; /* conservative ghost state g of each Dirichlet / inflow side
                             (first M entries; admissible for Euler and ten-moment) */
   double gravity[2];     /* (g_x, g_y) of CR_SRC_GRAVITY (Euler) */
+  int points;            /* CR_POINTS_*; 0 (Gauss-Legendre, Radau) when zero-initialised */
 } cr_mesh_desc;
 
 /* Device workspace needed by cr_init_mesh for this descriptor.
@@ -239,6 +247,16 @@ cr_status cr_cfl_number_for(int degree, int dissipation, double* cfl);
  * xi[N+1] and weights w[N+1] on [0,1], and D[(N+1)*(N+1)], D_ij = l_j'(xi_i)
  * (Sec. 2 eq. (diff.matrix)).  Any pointer may be NULL. */
 cr_status cr_reference_tables(int degree, double* xi, double* w, double* D);
+
+/* CFL(N) for a dissipation model and a point set (CR_POINTS_*): the same
+ * Fourier analysis with the tables of that point set.  Host only.
+ * Errors: CR_E_INVALID_ARG. */
+cr_status cr_cfl_number_points(int degree, int dissipation, int points, double* cfl);
+
+/* cr_reference_tables for a point set (CR_POINTS_*): Gauss-Legendre, or
+ * Gauss-Lobatto-Legendre nodes (end points included) with their weights.
+ * Host only.  Errors: CR_E_INVALID_ARG. */
+cr_status cr_reference_tables_points(int degree, int points, double* xi, double* w, double* D);
 
 /* One FP64 step that allocates nothing (the paper has no counterpart; this is
  * a service for callers that may not allocate device memory, e.g. a host

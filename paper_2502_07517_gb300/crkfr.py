@@ -20,6 +20,7 @@ STATUS = {0: "CR_OK", -1: "CR_E_INVALID_ARG", -2: "CR_E_INVALID_STATE", -3: "CR_
 CR_EQ_LINADV, CR_EQ_EULER, CR_EQ_TENMOMENT, CR_EQ_BURGERS = 0, 1, 2, 3
 CR_BC_PERIODIC, CR_BC_OUTFLOW, CR_BC_WALL, CR_BC_DIRICHLET, CR_BC_INFLOW = 0, 1, 2, 3, 4
 CR_SRC_NONE, CR_SRC_TENMOMENT, CR_SRC_GRAVITY = 0, 1, 2
+CR_POINTS_GL, CR_POINTS_GLL = 0, 1
 CR_LIM_BLEND, CR_LIM_MH, CR_LIM_FLUX, CR_LIM_SCALING, CR_LIM_TRACES = 1, 2, 4, 8, 16
 CR_ALPHA_INDICATOR, CR_ALPHA_FIXED, CR_ALPHA_MLP = 0, 1, 2
 CR_FP64, CR_FP32_BULK = 0, 1
@@ -30,7 +31,7 @@ CR_CENTRAL_EA, CR_CENTRAL_AE = 0, 1
 # C symbols declared in include/cr.h
 SYMBOLS = ("cr_workspace_bytes", "cr_init_mesh", "cr_destroy", "cr_set_state", "cr_get_state",
            "cr_step", "cr_step_async", "cr_sync", "cr_get_alpha", "cr_get_means", "cr_next_dt",
-           "cr_cfl_number_for",
+           "cr_cfl_number_for", "cr_cfl_number_points", "cr_reference_tables_points",
            "cr_launches_per_step", "cr_profile_steps", "cr_cfl_number", "cr_reference_tables",
            "cr_step_static", "cr_last_error", "cr_mlp_param_count", "cr_mlp_load",
            "cr_get_features", "cr_mlp_grad", "cr_mlp_train", "cr_batch_init", "cr_batch_destroy",
@@ -61,7 +62,7 @@ class cr_mesh_desc(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("dissipation", ctypes.c_int), ("central", ctypes.c_int),
         ("bc_side", ctypes.c_int * 4), ("bc_state", (ctypes.c_double * 6) * 4),
-        ("gravity", ctypes.c_double * 2),
+        ("gravity", ctypes.c_double * 2), ("points", ctypes.c_int),
     ]
 
 
@@ -95,6 +96,8 @@ def lib():
         L.cr_cfl_number.argtypes = [I, D]
         L.cr_cfl_number_for.argtypes = [I, I, D]
         L.cr_reference_tables.argtypes = [I, D, D, D]
+        L.cr_cfl_number_points.argtypes = [I, I, I, D]
+        L.cr_reference_tables_points.argtypes = [I, I, D, D, D]
         L.cr_step_static.argtypes = [P, V, V, ctypes.c_double]
         F = ctypes.POINTER(ctypes.c_float)
         L.cr_mlp_param_count.argtypes = [I]
@@ -149,6 +152,19 @@ def cr_reference_tables(degree):
     n = degree + 1
     xi, w, D = np.zeros(n), np.zeros(n), np.zeros((n, n))
     _check(lib().cr_reference_tables(int(degree), _dptr(xi), _dptr(w), _dptr(D)))
+    return xi, w, D
+
+
+def cr_cfl_number_points(degree, dissipation, points):
+    out = ctypes.c_double()
+    _check(lib().cr_cfl_number_points(int(degree), int(dissipation), int(points), ctypes.byref(out)))
+    return out.value
+
+
+def cr_reference_tables_points(degree, points):
+    n = degree + 1
+    xi, w, D = np.zeros(n), np.zeros(n), np.zeros((n, n))
+    _check(lib().cr_reference_tables_points(int(degree), int(points), _dptr(xi), _dptr(w), _dptr(D)))
     return xi, w, D
 
 
@@ -420,6 +436,7 @@ def desc_from_problem(prob, precision=CR_FP64, alpha_fixed=None, stream=None, **
     elif src:
         d.source, d.src_amp, d.src_k, d.src_cx, d.src_cy = (CR_SRC_TENMOMENT, src["amp"], src["k"],
                                                              src["cx"], src["cy"])
+    d.points = {"gl": CR_POINTS_GL, "gll": CR_POINTS_GLL}[prob.get("points", "gl")]
     sides, states = prob.get("bc_side") or {}, prob.get("bc_state") or {}
     for i, s in enumerate(_SIDES):
         d.bc_side[i] = _BC[sides[s]] if s in sides else 0

@@ -40,15 +40,41 @@ void legendre_pd(int n, double x, double* P, double* dP) {
 }
 
 struct HostTables {
-  int N;
+  int N, points;
   double xi[kMaxNodes1], w[kMaxNodes1], l0[kMaxNodes1], l1[kMaxNodes1];
   double D[kMaxNodes1 * kMaxNodes1];
 };
 
-void build_tables(int N, HostTables* t) {
+// Gauss-Lobatto-Legendre nodes on [0,1] (Sec. 5.1): the end points and the
+// roots of P_N', by Newton's method with P_N'' from Legendre's equation
+// (1 - x^2) P'' = 2x P' - N(N+1) P, from the Chebyshev-Lobatto points;
+// weights 2 / (N (N+1) P_N(x)^2), halved for [0,1].
+void gll_nodes(int N, HostTables* t) {
+  for (int i = 0; i <= N; ++i) {
+    double x = i == 0 ? -1.0 : (i == N ? 1.0 : -std::cos(M_PI * i / N));
+    if (i > 0 && i < N) {
+      for (int it = 0; it < 60; ++it) {
+        double P, dP;
+        legendre_pd(N, x, &P, &dP);
+        const double d2P = (2.0 * x * dP - N * (N + 1.0) * P) / (1.0 - x * x);
+        const double dx = dP / d2P;
+        x -= dx;
+        if (std::fabs(dx) <= 1e-16) break;
+      }
+    }
+    double P, dP;
+    legendre_pd(N, x, &P, &dP);  // P is exact at the end points too (dP is not used)
+    t->xi[i] = 0.5 * (x + 1.0);
+    t->w[i] = 1.0 / (N * (N + 1.0) * P * P);
+  }
+}
+
+void build_tables(int N, int points, HostTables* t) {
   const int n = N + 1;
   t->N = N;
-  for (int i = 0; i < n; ++i) {
+  t->points = points;
+  if (points == CR_POINTS_GLL) gll_nodes(N, t);
+  for (int i = 0; points != CR_POINTS_GLL && i < n; ++i) {
     double x = -std::cos(M_PI * (2.0 * i + 1.0) / (2.0 * n));
     for (int it = 0; it < 60; ++it) {
       double P, dP;
@@ -71,9 +97,17 @@ void build_tables(int N, HostTables* t) {
   }
   for (int side = 0; side < 2; ++side) {
     const double x = side;
+    double* l = side ? t->l1 : t->l0;
+    int at = -1;  // a node on the face (Gauss-Lobatto): the trace is its value
+    for (int m = 0; m < n; ++m)
+      if (t->xi[m] == x) at = m;
+    if (at >= 0) {
+      for (int j = 0; j < n; ++j) l[j] = j == at ? 1.0 : 0.0;
+      continue;
+    }
     double den = 0.0;
     for (int m = 0; m < n; ++m) den += lam[m] / (x - t->xi[m]);
-    for (int j = 0; j < n; ++j) (side ? t->l1 : t->l0)[j] = lam[j] / (x - t->xi[j]) / den;
+    for (int j = 0; j < n; ++j) l[j] = lam[j] / (x - t->xi[j]) / den;
   }
   for (int i = 0; i < n; ++i) {
     double diag = 0.0;
@@ -108,15 +142,21 @@ void fill_tab(const HostTables& h, Tab<real>* t) {
     t->invw[p] = real(1.0 / h.w[p]);
     t->l0[p] = real(h.l0[p]);
     t->l1[p] = real(h.l1[p]);
+    // correction derivatives at the solution points: the Radau correction with
+    // Gauss-Legendre points and g2 with Gauss-Lobatto points both satisfy
+    // g_R'(xi_p) = l_p(1)/w_p and g_L'(xi_p) = -l_p(0)/w_p
     t->gR[p] = real(h.l1[p] / h.w[p]);
     t->gL[p] = real(-h.l0[p] / h.w[p]);
     // subcells of Sec. 4 eq. (subcell.defn): widths w_p
     t->dm[p] = real(xs - h.xi[p]);
     t->dp[p] = real(xs + h.w[p] - h.xi[p]);
     xs += h.w[p];
-    t->ihm[p] = real(1.0 / (X[p + 1] - X[p]));
-    t->ihp[p] = real(1.0 / (X[p + 2] - X[p + 1]));
-    t->ihc[p] = real(1.0 / (X[p + 2] - X[p]));
+    // (Gauss-Lobatto points meet their neighbour's across a face: zero spacing,
+    // and no MUSCL-Hancock subcells there)
+    auto inv = [](double h) { return h > 0.0 ? 1.0 / h : 0.0; };
+    t->ihm[p] = real(inv(X[p + 1] - X[p]));
+    t->ihp[p] = real(inv(X[p + 2] - X[p + 1]));
+    t->ihc[p] = real(inv(X[p + 2] - X[p]));
   }
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
@@ -233,20 +273,21 @@ double max_growth(const HostTables& h, double nu, bool d1) {
   return g;
 }
 
-double cfl_compute(int N, bool d1 = false) {
-  static double cache[2][kMaxN + 1] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+double cfl_compute(int N, bool d1 = false, int points = CR_POINTS_GL) {
+  static double cache[2][2][kMaxN + 1] = {};
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
-  if (cache[d1][N] > 0.0) return cache[d1][N];
+  const int pt = points == CR_POINTS_GLL ? 1 : 0;
+  if (cache[pt][d1][N] > 0.0) return cache[pt][d1][N];
   HostTables h;
-  build_tables(N, &h);
+  build_tables(N, points, &h);
   double lo = 0.0, hi = 1.0;
   for (int it = 0; it < 40; ++it) {
     const double mid = 0.5 * (lo + hi);
     if (max_growth(h, mid, d1) <= 1.0 + 1e-4) lo = mid;
     else hi = mid;
   }
-  cache[d1][N] = lo;
+  cache[pt][d1][N] = lo;
   return lo;
 }
 
@@ -386,6 +427,11 @@ const char* check_desc(const cr_mesh_desc* d) {
   if (d->equation == CR_EQ_BURGERS && d->dim != 1) return "Burgers' equation is 1D";
   if (d->dissipation < 0 || d->dissipation > 2) return "unknown dissipation model";
   if (d->central < 0 || d->central > 1) return "unknown central flux";
+  if (d->points != CR_POINTS_GL && d->points != CR_POINTS_GLL) return "unknown solution points";
+  if (d->points == CR_POINTS_GLL &&
+      ((d->limiter & (CR_LIM_BLEND | CR_LIM_MH | CR_LIM_FLUX)) || d->alpha_mode == CR_ALPHA_FIXED))
+    return "Gauss-Lobatto points take no blending or flux limiter: their low-order subcell "
+           "update would outrun its CFL condition at the GLL time step";
   if (d->equation == CR_EQ_EULER && !(d->gamma > 1.0)) return "gamma must be > 1";
   if (d->precision != CR_FP64 && d->precision != CR_FP32_BULK) return "unknown precision";
   if (d->alpha_mode != CR_ALPHA_INDICATOR && d->alpha_mode != CR_ALPHA_FIXED &&
@@ -603,10 +649,32 @@ cr_status cr_cfl_number(int degree, double* cfl) {
   return CR_OK;
 }
 
+cr_status cr_cfl_number_points(int degree, int dissipation, int points, double* cfl) {
+  if (degree < 1 || degree > kMaxN || !cfl || dissipation < 0 || dissipation > 2 ||
+      (points != CR_POINTS_GL && points != CR_POINTS_GLL))
+    return CR_E_INVALID_ARG;
+  *cfl = cfl_compute(degree, dissipation == CR_DISS_D1, points);
+  return CR_OK;
+}
+
+cr_status cr_reference_tables_points(int degree, int points, double* xi, double* w, double* D) {
+  if (degree < 1 || degree > kMaxN || (points != CR_POINTS_GL && points != CR_POINTS_GLL))
+    return CR_E_INVALID_ARG;
+  HostTables h;
+  build_tables(degree, points, &h);
+  const int n = degree + 1;
+  for (int i = 0; i < n; ++i) {
+    if (xi) xi[i] = h.xi[i];
+    if (w) w[i] = h.w[i];
+  }
+  if (D) memcpy(D, h.D, sizeof(double) * n * n);
+  return CR_OK;
+}
+
 cr_status cr_reference_tables(int degree, double* xi, double* w, double* D) {
   if (degree < 1 || degree > kMaxN) return CR_E_INVALID_ARG;
   HostTables h;
-  build_tables(degree, &h);
+  build_tables(degree, CR_POINTS_GL, &h);
   const int n = degree + 1;
   for (int i = 0; i < n; ++i) {
     if (xi) xi[i] = h.xi[i];
@@ -663,10 +731,11 @@ cr_status cr_init_mesh(const cr_mesh_desc* desc, void* workspace, size_t workspa
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMallocHost"));
   e = ks->configure();
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaFuncSetAttribute"));
-  c->cfl = desc->cfl > 0.0 ? desc->cfl : cfl_compute(desc->degree, desc->dissipation == CR_DISS_D1);
+  c->cfl = desc->cfl > 0.0 ? desc->cfl
+                           : cfl_compute(desc->degree, desc->dissipation == CR_DISS_D1, desc->points);
   if (!(c->d.cfl_safety > 0.0)) c->d.cfl_safety = 0.98;
   HostTables h;
-  build_tables(desc->degree, &h);
+  build_tables(desc->degree, desc->points, &h);
   if (ks->mixed) {
     fill_params(c, &c->pf, h);
     c->params = &c->pf;
@@ -1083,8 +1152,10 @@ cr_status cr_batch_init(cr_ctx* const* ctxs, int n, cr_batch** out) {
     cr_ctx* c = ctxs[i];
     if (!c) return bail(bfail(b, CR_E_INVALID_ARG, "cr_batch_init: NULL context"));
     const cr_mesh_desc& d = c->d;
-    if (d.dim != 2 || d.equation != CR_EQ_EULER || (d.degree != 3 && d.degree != 4))
-      return bail(bfail(b, CR_E_UNSUPPORTED, "cr_batch_init: batches hold 2D Euler problems of degree 3 or 4"));
+    if (d.dim != 2 || d.equation != CR_EQ_EULER || (d.degree != 3 && d.degree != 4) ||
+        d.points != CR_POINTS_GL)
+      return bail(bfail(b, CR_E_UNSUPPORTED,
+                        "cr_batch_init: batches hold 2D Euler problems of degree 3 or 4 on Gauss-Legendre points"));
     if (i > 0 && d.precision != ctxs[0]->d.precision)
       return bail(bfail(b, CR_E_INVALID_ARG, "cr_batch_init: mixed precisions"));
     b->ctx.push_back(c);

@@ -122,8 +122,9 @@ extern "C" cr_status cr_step_static(const cr_mesh_desc* d, const double* u_in, d
                                     double dt) {
   if (!d || !u_in || !u_out || !(dt > 0.0))
     return static_fail(CR_E_INVALID_ARG, "cr_step_static: NULL pointer or dt <= 0");
-  if (d->dissipation != CR_DISS_D2 || d->central != CR_CENTRAL_EA)
-    return static_fail(CR_E_UNSUPPORTED, "cr_step_static: D2 dissipation and EA flux only");
+  if (d->dissipation != CR_DISS_D2 || d->central != CR_CENTRAL_EA || d->points != CR_POINTS_GL)
+    return static_fail(CR_E_UNSUPPORTED,
+                       "cr_step_static: D2 dissipation, EA flux and Gauss-Legendre points only");
   if (d->precision != CR_FP64)
     return static_fail(CR_E_UNSUPPORTED, "cr_step_static: FP64 precision only");
   size_t probe = 0;

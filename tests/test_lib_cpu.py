@@ -113,3 +113,40 @@ def test_boundary_and_source_descriptors_checked(built):
     assert _rejected(d)
     d.bc_side[1] = crkfr.CR_BC_DIRICHLET          # a scalar ghost state needs only finiteness
     assert crkfr.cr_workspace_bytes(d) > 0
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_gauss_lobatto_tables_and_cfl(built, N):
+    """The library's Gauss-Lobatto tables against numpy's Legendre class, and
+    its CFL numbers for both point sets against the oracle's analysis."""
+    import oracle
+    from oracle.cfl import cfl_number
+    xi, w, D = crkfr.cr_reference_tables_points(N, crkfr.CR_POINTS_GLL)
+    Leg = np.polynomial.legendre.Legendre
+    inner = np.sort(Leg.basis(N).deriv().roots().real) if N > 1 else np.zeros(0)
+    x = np.concatenate([[-1.0], inner, [1.0]])
+    np.testing.assert_allclose(xi, 0.5 * (x + 1.0), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(w, 1.0 / (N * (N + 1) * Leg.basis(N)(x) ** 2), rtol=1e-14)
+    for m in range(N + 1):
+        np.testing.assert_allclose(D @ xi ** m, m * xi ** max(m - 1, 0) * (m > 0), atol=1e-12)
+    g = crkfr.cr_reference_tables_points(N, crkfr.CR_POINTS_GL)
+    np.testing.assert_array_equal(g[0], crkfr.cr_reference_tables(N)[0])
+    for diss in (crkfr.CR_DISS_D2, crkfr.CR_DISS_D1):
+        got = crkfr.cr_cfl_number_points(N, diss, crkfr.CR_POINTS_GLL)
+        assert abs(got - cfl_number(N, diss == crkfr.CR_DISS_D1, points=oracle.POINTS_GLL)) < 1e-6
+
+
+def test_gauss_lobatto_refusals(built):
+    from paper_2502_07517_gb300 import workloads as wl
+    prob, _ = wl.burgers_sine(nx=16, degree=3, points="gll")
+    d = crkfr.desc_from_problem(prob)
+    assert crkfr.cr_workspace_bytes(d) > 0
+    for lim in (crkfr.CR_LIM_BLEND, crkfr.CR_LIM_MH, crkfr.CR_LIM_FLUX):
+        d.limiter = lim
+        assert _rejected(d)
+    d.limiter = crkfr.CR_LIM_SCALING | crkfr.CR_LIM_TRACES
+    assert crkfr.cr_workspace_bytes(d) > 0
+    d.limiter, d.alpha_mode = 0, crkfr.CR_ALPHA_FIXED
+    assert _rejected(d)
+    d.alpha_mode, d.points = crkfr.CR_ALPHA_INDICATOR, 2
+    assert _rejected(d)
