@@ -210,11 +210,11 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
 
   // ---------------- local cRK stages -----------------------------------
   real Lst[S > 1 ? S - 1 : 1][M];
-  real Fa[M], Ga[M], Ua[M], Sa[M];
+  real Fa[M], Ga[M], Ua[M];
   real ea[SPT][M];
 #pragma unroll
   for (int v = 0; v < M; ++v) {
-    Fa[v] = Ga[v] = Ua[v] = Sa[v] = real(0);
+    Fa[v] = Ga[v] = Ua[v] = real(0);
 #pragma unroll
     for (int mm = 0; mm < SPT; ++mm) ea[mm][v] = real(0);
   }
@@ -231,14 +231,9 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
         if (TB::a(i, j) != 0.0) acc -= (dt * real(TB::a(i, j))) * Lst[j][v];
       ui[v] = acc;
     }
-    real f[M], g[M], s[M];
+    real f[M], g[M];
     if (DIM == 2) EQ::flux_xy(ui, f, g, ph);
     else EQ::flux(ui, 0, f, ph);
-    if (has_src) source_eval<EQ>(ui, dWx, dWy, s);
-    else {
-#pragma unroll
-      for (int v = 0; v < M; ++v) s[v] = real(0);
-    }
     if (TB::b(i) != 0.0) {
       const real bi = real(TB::b(i));
 #pragma unroll
@@ -246,7 +241,6 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
         Fa[v] += bi * f[v];
         if (DIM == 2) Ga[v] += bi * g[v];
         Ua[v] += bi * ui[v];
-        Sa[v] += bi * s[v];
       }
     }
 #pragma unroll
@@ -266,7 +260,15 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
 #pragma unroll
           for (int r = 0; r < n; ++r) hy += tb.D[q * n + r] * AT(sC, v, p + n * r);
         }
-        Lst[i < S - 1 ? i : 0][v] = invdx * hx + (DIM == 2 ? invdy * hy : real(0)) - s[v];
+        Lst[i < S - 1 ? i : 0][v] = invdx * hx + (DIM == 2 ? invdy * hy : real(0));
+      }
+      if (has_src) {  // the stage's source, from its node value still in shared memory
+        real us[M], s[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) us[v] = AT(sA, v, k);
+        source_eval<EQ>(us, dWx, dWy, s);
+#pragma unroll
+        for (int v = 0; v < M; ++v) Lst[i < S - 1 ? i : 0][v] -= s[v];
       }
     }
     if (TB::b(i) != 0.0) {
@@ -323,6 +325,24 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     }
     HO[v] = invdx * hx + (DIM == 2 ? invdy * hy : real(0));
   }
+  // time-averaged source S = sum_i b_i s(u^(i)) (App. B eq. (crkfr.source)):
+  // both sources are linear in u (the ten-moment one for fixed grad W), so it
+  // equals s(U) of the time-averaged solution.  HO becomes the high-order part
+  // of the update, u^n - dt (1 - a) HO + dt S (the low-order part follows).
+  real Sa[M];
+#pragma unroll
+  for (int v = 0; v < M; ++v) Sa[v] = real(0);
+  if (has_src) {
+    real us[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) us[v] = AT(sA, v, k);
+    source_eval<EQ>(us, dWx, dWy, Sa);
+  }
+#pragma unroll
+  for (int v = 0; v < M; ++v) {
+    HO[v] = un[v] - dt * ((real(1) - a) * HO[v]);
+    if (has_src) HO[v] += dt * Sa[v];
+  }
 #pragma unroll
   for (int mm = 0; mm < SPT; ++mm) {
     const int sl = k + mm * NP;
@@ -354,6 +374,20 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
         sl_out[slot_index(1 + v, side, e, j, NSIDE, m.ne, NFN)] = m.dissipation == 1 ? ut[v] : Ut[v];
         sl_out[slot_index(1 + M + v, side, e, j, NSIDE, m.ne, NFN)] = m.central == 1 ? Ft[v] : ea[mm][v];
       }
+    }
+  }
+  if constexpr (MIXED) {
+    // source contribution to the FP64 element mean, sum_k W_k S_k (tree sum)
+    __syncthreads();
+    if (has_src) {
+      const real W = DIM == 2 ? tb.w[p] * tb.w[q] : tb.w[p];
+#pragma unroll
+      for (int v = 0; v < M; ++v) AT(sA, v, k) = W * Sa[v];
+      elem_tree<NP, M>(sA, epb, el, k, OpSum());
+      for (int v = k; valid && v < M; v += NP)
+        P.b.smean[(size_t)v * m.ne + e] = double(sA[v * stride + el * NP]);
+    } else {
+      for (int v = k; valid && v < M; v += NP) P.b.smean[(size_t)v * m.ne + e] = 0.0;
     }
   }
   __syncthreads();
@@ -520,22 +554,8 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   if (valid) {
 #pragma unroll
     for (int v = 0; v < M; ++v) {
-      const real val = un[v] - dt * ((real(1) - a) * HO[v] + a * LO[v]) + dt * Sa[v];
+      const real val = HO[v] - dt * (a * LO[v]);
       P.b.P[((size_t)v * m.ne + e) * NP + k] = val;
-    }
-  }
-  if constexpr (MIXED) {
-    // source contribution to the FP64 element mean, sum_k W_k S_k (tree sum)
-    if (has_src) {
-      const real W = DIM == 2 ? tb.w[p] * tb.w[q] : tb.w[p];
-      __syncthreads();
-#pragma unroll
-      for (int v = 0; v < M; ++v) AT(sA, v, k) = W * Sa[v];
-      elem_tree<NP, M>(sA, epb, el, k, OpSum());
-      for (int v = k; valid && v < M; v += NP)
-        P.b.smean[(size_t)v * m.ne + e] = double(sA[v * stride + el * NP]);
-    } else {
-      for (int v = k; valid && v < M; v += NP) P.b.smean[(size_t)v * m.ne + e] = 0.0;
     }
   }
 #undef AT
