@@ -403,6 +403,80 @@ def config_legs(steps, warmup):
     leg("tenmoment2d_voronoi_256x256_N3", prob, u,
         lambda seed: wl.tenmoment2d_voronoi(nx=128, degree=3, seed=seed),
         "ten-moment Voronoi states with source, 128x128, N=3", range(1000, 1020), (0, 5, 20))
+    out.update(widened_legs(steps, warmup, stream))
+    return out
+
+
+def widened_legs(steps, warmup, stream):
+    """Workloads of the further rows: the Rayleigh-Taylor instability (walls,
+    given-state boundaries, gravity; 64x256, N = 3), the periodic 2D Sedov
+    blast (64x64, N = 3) and the 1D Sedov blast between walls (201, N = 3),
+    per step in FP64 and FP32 bulk (indicator alpha, normalised L1 from FP64
+    after the same steps at the same dt); Gauss-Lobatto points (scaling
+    limiter only) against Gauss-Legendre points on the 2D Euler recipe
+    (256x256, N = 4, FP64); and Burgers (Sec. 5.1, 128 elements, N = 3, to
+    t = 2) with the EA and AE fluxes on both point sets: whole-run time and
+    L2 error against the exact solution."""
+    import torch
+    from paper_2502_07517_gb300 import crkfr
+    sp = stream.cuda_stream
+    out = {}
+
+    def per_step(prob, u, precision=crkfr.CR_FP64, dt=None, **over):
+        c = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, precision=precision, stream=sp, **over))
+        crkfr.cr_set_state(c, u)
+        ms = timed_steps(c, steps, warmup, stream)
+        crkfr.cr_set_state(c, u)
+        dt0 = crkfr.cr_next_dt(c) if dt is None else dt
+        crkfr.cr_step(c, steps, 1e300, dt0)
+        g = crkfr.cr_get_state(c, shape=u.shape)
+        crkfr.cr_destroy(c)
+        return ms, g, dt0
+
+    for name, (prob, u) in (("rayleigh_taylor_64x256_N3", wl.rayleigh_taylor()),
+                            ("sedov2d_periodic_64x64_N3", wl.sedov2d_periodic()),
+                            ("sedov1d_walls_201_N3", wl.sedov1d())):
+        nodes = u.shape[1] * u.shape[2]
+        ms64, ref, dt0 = per_step(prob, u)
+        ms32, g, _ = per_step(prob, u, crkfr.CR_FP32_BULK, dt=dt0)
+        out[name] = {"dofs": nodes, "steps": steps, "unit": "DOF-updates/s",
+                     "fp64": {"ms_per_step": ms64, "value": nodes / (ms64 * 1e-3)},
+                     "fp32_indicator": {"ms_per_step": ms32, "value": nodes / (ms32 * 1e-3),
+                                        "speedup_vs_fp64": ms64 / ms32, "l1_rel_vs_fp64": l1_rel(g, ref)}}
+    prob, u = wl.euler2d_vortex(nx=256, degree=4, seed=0, limiter=("scaling", "traces"))
+    pts = {}
+    for label in ("gl", "gll"):
+        pr = dict(prob, points=label)
+        x, y = wl.node_coords(pr)
+        rho, v1, v2, p = wl.isentropic_vortex(x, y, pr["gamma"])
+        uu = wl.euler_conservative(rho, v1, v2, p, pr["gamma"], 2)
+        ms, _, dt0 = per_step(pr, uu)
+        pts[label] = {"ms_per_step": ms, "value": uu.shape[1] * uu.shape[2] / (ms * 1e-3), "dt": dt0}
+    out["euler2d_vortex_256x256_N4_points"] = {
+        "unit": "DOF-updates/s", "limiters": "scaling", "fp64": pts,
+        "note": "the Gauss-Lobatto scheme takes a larger step (CFL 0.104 against 0.070)"}
+    burg = {}
+    for label in ("gl", "gll"):
+        for cname, cen in (("EA", crkfr.CR_CENTRAL_EA), ("AE", crkfr.CR_CENTRAL_AE)):
+            prob, u = wl.burgers_sine(nx=128, degree=3, points=label)
+            c = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, stream=sp, central=cen))
+            crkfr.cr_set_state(c, u)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            t, n = crkfr.cr_step(c, 10 ** 6, 2.0)
+            wall = time.perf_counter() - t0
+            g = crkfr.cr_get_state(c, shape=u.shape)
+            crkfr.cr_destroy(c)
+            x, _ = wl.node_coords(prob)
+            _, w = wl.nodes01(prob)
+            ex = 0.2 * np.sin(x)
+            for _ in range(100):
+                ex = ex - (ex - 0.2 * np.sin(x - 2.0 * ex)) / (1.0 + 0.4 * np.cos(x - 2.0 * ex))
+            err = float(np.sqrt(((g[0] - ex) ** 2 * w * 2 * np.pi / 128).sum()))
+            burg["%s-%s" % (label, cname)] = {"steps": n, "wall_s": wall, "l2_error_vs_exact": err,
+                                             "value": u.size * n / wall}
+    out["burgers1d_sine_128_N3_t2"] = {"unit": "DOF-updates/s", "fp64": burg,
+                                       "note": "512 DOF: launch-bound whole runs incl. the host loop"}
     return out
 
 
@@ -657,6 +731,8 @@ def main():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the legs of the other workloads (1D linear advection, 1D Euler, ten-moment)")
     ap.add_argument("--configs-only", action="store_true", help="run only those legs and print them")
+    ap.add_argument("--widened-only", action="store_true",
+                    help="run only the legs of the further rows (boundaries, sources, points, Burgers)")
     ap.add_argument("--ens-problems", type=int, default=96, help="problems in the ensemble leg")
     ap.add_argument("--ens-config", default=None,
                     help="fixed batch configuration threads/mode (128|256 / phases|fused) instead of autotuning")
@@ -675,6 +751,12 @@ def main():
         lib_build.build()
         torch.cuda.set_device(0)
         print(json.dumps(config_legs(args.steps, args.warmup)))
+    elif args.widened_only:
+        import torch
+        from paper_2502_07517_gb300 import build as lib_build
+        lib_build.build()
+        torch.cuda.set_device(0)
+        print(json.dumps(widened_legs(args.steps, args.warmup, torch.cuda.Stream())))
     elif args.ensemble_only:
         import torch
         from paper_2502_07517_gb300 import build as lib_build
