@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-EQ_LINADV, EQ_EULER, EQ_TENMOMENT, EQ_BURGERS = 0, 1, 2, 3
+EQ_LINADV, EQ_EULER, EQ_TENMOMENT, EQ_BURGERS, EQ_VARADV = 0, 1, 2, 3, 4
 BC_PERIODIC, BC_OUTFLOW, BC_WALL, BC_DIRICHLET, BC_INFLOW = 0, 1, 2, 3, 4
 SRC_NONE, SRC_TENMOMENT, SRC_GRAVITY = 0, 1, 2
 LIM_BLEND, LIM_MH, LIM_FLUX, LIM_SCALING, LIM_TRACES = 1, 2, 4, 8, 16
@@ -44,6 +44,9 @@ class Desc(ctypes.Structure):
         ("dissipation", ctypes.c_int), ("central", ctypes.c_int),
         ("bc_side", ctypes.c_int * 4), ("bc_state", (ctypes.c_double * 6) * 4),
         ("gravity", ctypes.c_double * 2), ("points", ctypes.c_int),
+        ("adv_poly", ctypes.c_double * 4), ("bc_time_terms", ctypes.c_int),
+        ("bc_time_span", ctypes.c_double * 2), ("bc_time_coef", (ctypes.c_double * 16) * 4),
+        ("time", ctypes.c_double),
     ]
 
 
@@ -72,6 +75,9 @@ def lib():
         _lib.or_flux.argtypes = [P, D, ctypes.c_int, D]
         _lib.or_wave_speed.argtypes = [P, D, ctypes.c_int]
         _lib.or_wave_speed.restype = ctypes.c_double
+        _lib.or_flux_x.argtypes = [P, D, ctypes.c_double, ctypes.c_int, D]
+        _lib.or_wave_speed_x.argtypes = [P, D, ctypes.c_double, ctypes.c_int]
+        _lib.or_wave_speed_x.restype = ctypes.c_double
         _lib.or_num_constraints.argtypes = [P]
         _lib.or_constraint.argtypes = [P, D, ctypes.c_int]
         _lib.or_constraint.restype = ctypes.c_double
@@ -105,7 +111,8 @@ def make_desc(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=BC_PERIOD
               source=0, src_amp=0.0, src_k=0.0, src_cx=0.5, src_cy=0.5, limiter=0,
               alpha_mode=ALPHA_INDICATOR, alpha_fixed=0.0, cfl=None, cfl_safety=0.98,
               alpha_given=None, dissipation=DISS_D2, central=CENTRAL_EA, bc_side=(0, 0, 0, 0),
-              bc_state=None, gravity=(0.0, 0.0), points=POINTS_GL):
+              bc_state=None, gravity=(0.0, 0.0), points=POINTS_GL, adv_poly=(0.0, 0.0, 0.0, 0.0),
+              bc_time=None):
     """Mesh/scheme description; cfl defaults to CFL(degree) from the Fourier analysis.
     alpha_given: per-element raw alpha array for alpha_mode ALPHA_GIVEN (kept alive on
     the returned object)."""
@@ -129,6 +136,15 @@ def make_desc(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=BC_PERIOD
                 d.bc_state[s][v] = x
     d.gravity[0], d.gravity[1] = gravity
     d.points = points
+    for k in range(4):
+        d.adv_poly[k] = adv_poly[k]
+    if bc_time is not None:                  # (span, {side index: Chebyshev coefficients})
+        span, coefs = bc_time
+        d.bc_time_span[0], d.bc_time_span[1] = span
+        d.bc_time_terms = max(len(c) for c in coefs.values())
+        for s, c in coefs.items():
+            for k, a in enumerate(c):
+                d.bc_time_coef[s][k] = a
     if alpha_given is not None:
         arr = np.ascontiguousarray(alpha_given, dtype=np.float64)
         d._alpha_given_keep = arr
@@ -188,6 +204,19 @@ def wave_speed(d, u, direction):
     return lib().or_wave_speed(ctypes.byref(d), _ptr(u), direction)
 
 
+def flux_x(d, u, x, direction):
+    """Flux at position x (variable advection depends on it)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    f = np.zeros(nvars(d))
+    lib().or_flux_x(ctypes.byref(d), _ptr(u), float(x), direction, _ptr(f))
+    return f
+
+
+def wave_speed_x(d, u, x, direction):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return lib().or_wave_speed_x(ctypes.byref(d), _ptr(u), float(x), direction)
+
+
 def constraint(d, u, k):
     u = np.ascontiguousarray(u, dtype=np.float64)
     return lib().or_constraint(ctypes.byref(d), _ptr(u), k)
@@ -235,8 +264,11 @@ def dt(d, u):
     return lib().or_dt(ctypes.byref(d), _ptr(u))
 
 
-def step(d, u, dt_, want_diag=False):
-    """One step; returns (u_new, status) or (u_new, status, diag dict)."""
+def step(d, u, dt_, want_diag=False, time=None):
+    """One step from time t^n = time (default: d.time); returns (u_new, status)
+    or (u_new, status, diag dict)."""
+    if time is not None:
+        d.time = time
     u = np.ascontiguousarray(u, dtype=np.float64)
     out = np.empty_like(u)
     M, ne, npn = state_shape(d)

@@ -11,6 +11,7 @@ int or_nvars(const or_desc* d) {
     case OR_EQ_EULER: return d->dim == 1 ? 3 : 4;
     case OR_EQ_TENMOMENT: return 6;
     case OR_EQ_BURGERS: return 1;
+    case OR_EQ_VARADV: return 1;
   }
   return 0;
 }
@@ -34,6 +35,24 @@ static void tm_pressure(const double* u, double* p11, double* p12, double* p22) 
   *p11 = 2.0 * u[3] - rho * v1 * v1;
   *p12 = 2.0 * u[4] - rho * v1 * v2;
   *p22 = 2.0 * u[5] - rho * v2 * v2;
+}
+
+/* a(x) of the variable advection equation, by Horner's rule. */
+static double varadv_a(const or_desc* d, double x) {
+  return ((d->adv_poly[3] * x + d->adv_poly[2]) * x + d->adv_poly[1]) * x + d->adv_poly[0];
+}
+
+void or_flux_x(const or_desc* d, const double* u, double x, int dir, double* f) {
+  if (d->equation == OR_EQ_VARADV) { /* Sec. 5.1: f(x, u) = a(x) u */
+    f[0] = varadv_a(d, x) * u[0];
+    return;
+  }
+  or_flux(d, u, dir, f);
+}
+
+double or_wave_speed_x(const or_desc* d, const double* u, double x, int dir) {
+  if (d->equation == OR_EQ_VARADV) return fabs(varadv_a(d, x));
+  return or_wave_speed(d, u, dir);
 }
 
 void or_flux(const or_desc* d, const double* u, int dir, double* f) {
@@ -118,7 +137,7 @@ double or_wave_speed(const or_desc* d, const double* u, int dir) {
  * eigenvalue of the pressure tensor (x^T P x > 0 for all x != 0 exactly when
  * lambda_min(P) > 0; lambda_min is concave in u for rho > 0). */
 int or_num_constraints(const or_desc* d) {
-  return (d->equation == OR_EQ_LINADV || d->equation == OR_EQ_BURGERS) ? 0 : 2;
+  return (d->equation == OR_EQ_LINADV || d->equation == OR_EQ_BURGERS || d->equation == OR_EQ_VARADV) ? 0 : 2;
 }
 
 double or_constraint(const or_desc* d, const double* u, int k) {

@@ -82,12 +82,13 @@ static int admissible(const ctx* c, const double* u) {
   return 1;
 }
 
-/* Rusanov flux of Sec. 2 eq. (num.flux.fr) with eq. (rusanov.wave.speed). */
-static void rusanov(const ctx* c, const double* uL, const double* uR, int dir, double* out) {
+/* Rusanov flux of Sec. 2 eq. (num.flux.fr) with eq. (rusanov.wave.speed), at
+ * position x along the face normal (used by variable advection only). */
+static void rusanov(const ctx* c, const double* uL, const double* uR, int dir, double x, double* out) {
   double fL[OR_MAXM], fR[OR_MAXM];
-  or_flux(c->d, uL, dir, fL);
-  or_flux(c->d, uR, dir, fR);
-  double lam = fmax(or_wave_speed(c->d, uL, dir), or_wave_speed(c->d, uR, dir));
+  or_flux_x(c->d, uL, x, dir, fL);
+  or_flux_x(c->d, uR, x, dir, fR);
+  double lam = fmax(or_wave_speed_x(c->d, uL, x, dir), or_wave_speed_x(c->d, uR, x, dir));
   for (int v = 0; v < c->M; ++v) out[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lam * (uR[v] - uL[v]);
 }
 
@@ -124,7 +125,7 @@ static void local_crk_ea(const ctx* c, const double* ue, double dt, int ix, int 
       int p = k % n, q = k / n;
       double x = c->d->x0 + (ix + c->xi[p]) * c->dx;
       double y = c->dim == 2 ? c->d->y0 + (iy + c->xi[q]) * c->dy : 0.0;
-      or_flux(c->d, ui[i][k], 0, f[k]);
+      or_flux_x(c->d, ui[i][k], x, 0, f[k]);
       if (c->dim == 2) or_flux(c->d, ui[i][k], 1, g[k]);
       or_source(c->d, ui[i][k], x, y, src[k]);
     }
@@ -158,8 +159,8 @@ static void local_crk_ea(const ctx* c, const double* ue, double dt, int ix, int 
           uR[v] += c->l1[p] * ui[i][node(c, p, q)][v];
         }
       }
-      or_flux(c->d, uL, 0, fL);
-      or_flux(c->d, uR, 0, fR);
+      or_flux_x(c->d, uL, c->d->x0 + ix * c->dx, 0, fL);
+      or_flux_x(c->d, uR, c->d->x0 + (ix + 1) * c->dx, 0, fR);
       for (int v = 0; v < M; ++v) {
         ea[(0 * NMAX + q) * OR_MAXM + v] += c->b[i] * fL[v];
         ea[(1 * NMAX + q) * OR_MAXM + v] += c->b[i] * fR[v];
@@ -235,7 +236,7 @@ static double legendre01(int j, double xi) {
 }
 
 static double indicator_variable(const or_desc* d, const double* u) {
-  if (d->equation == OR_EQ_LINADV || d->equation == OR_EQ_BURGERS) return u[0];
+  if (d->equation == OR_EQ_LINADV || d->equation == OR_EQ_BURGERS || d->equation == OR_EQ_VARADV) return u[0];
   if (d->equation == OR_EQ_EULER) return u[0] * or_constraint(d, u, 1);
   double rho = u[0], v1 = u[1] / rho, v2 = u[2] / rho;
   double p11 = 2.0 * u[3] - rho * v1 * v1, p22 = 2.0 * u[5] - rho * v2 * v2;
@@ -345,14 +346,59 @@ static int side_bc(const ctx* c, int s) {
   return s < 2 ? c->d->bc_x : c->d->bc_y;
 }
 
+/* Given ghost state g of side s at time t: bc_state, or for a scalar equation
+ * with bc_time_terms > 0 the Chebyshev series sum_k a_k T_k(tau) (Clenshaw's
+ * recurrence), tau = 2 (t - t0)/(t1 - t0) - 1 clamped to [-1, 1]. */
+static void ghost_at(const ctx* c, int s, double t, double* g) {
+  const or_desc* d = c->d;
+  if (d->bc_time_terms <= 0 || c->M != 1) {
+    for (int v = 0; v < c->M; ++v) g[v] = d->bc_state[s][v];
+    return;
+  }
+  double tau = 2.0 * (t - d->bc_time_span[0]) / (d->bc_time_span[1] - d->bc_time_span[0]) - 1.0;
+  tau = fmin(1.0, fmax(-1.0, tau));
+  double b1 = 0.0, b2 = 0.0;
+  for (int k = d->bc_time_terms - 1; k >= 1; --k) {
+    double b0 = 2.0 * tau * b1 - b2 + d->bc_time_coef[s][k];
+    b2 = b1;
+    b1 = b0;
+  }
+  g[0] = tau * b1 - b2 + d->bc_time_coef[s][0];
+}
+
 /* Ghost node of the MUSCL-Hancock reconstruction beyond side s, from the own
  * boundary node ub: the node itself (outflow), its reflection (wall), or the
- * given state (Dirichlet, inflow). */
+ * given state at t^n (Dirichlet, inflow). */
 static void ghost_node(const ctx* c, int s, const double* ub, double* out) {
   int bc = side_bc(c, s);
   if (bc == OR_BC_WALL) { for (int v = 0; v < c->M; ++v) out[v] = (v == 1 + s / 2) ? -ub[v] : ub[v]; }
-  else if (bc == OR_BC_DIRICHLET || bc == OR_BC_INFLOW) { for (int v = 0; v < c->M; ++v) out[v] = c->d->bc_state[s][v]; }
+  else if (bc == OR_BC_DIRICHLET || bc == OR_BC_INFLOW) ghost_at(c, s, c->d->time, out);
   else { for (int v = 0; v < c->M; ++v) out[v] = ub[v]; }
+}
+
+/* Time-dependent ghost values of a Dirichlet / inflow side (Sec. 3.3):
+ * g at the stage times t^n + c_i dt, U^- = sum_i b_i g_i and F^- =
+ * sum_i b_i f(x, g_i); for a time-independent g they are g and f(g). */
+static void ghost_averages(const ctx* c, int s, double dt, double x, int dir, double gst[][OR_MAXM],
+                           double* Ug, double* Fg) {
+  const int M = c->M;
+  if (c->d->bc_time_terms <= 0 || M != 1) {
+    for (int i = 0; i < c->s; ++i)
+      for (int v = 0; v < M; ++v) gst[i][v] = c->d->bc_state[s][v];
+    for (int v = 0; v < M; ++v) Ug[v] = c->d->bc_state[s][v];
+    or_flux_x(c->d, c->d->bc_state[s], x, dir, Fg);
+    return;
+  }
+  for (int v = 0; v < M; ++v) Ug[v] = Fg[v] = 0.0;
+  for (int i = 0; i < c->s; ++i) {
+    double f[OR_MAXM];
+    ghost_at(c, s, c->d->time + c->c[i] * dt, gst[i]);
+    or_flux_x(c->d, gst[i], x, dir, f);
+    for (int v = 0; v < M; ++v) {
+      Ug[v] += c->b[i] * gst[i][v];
+      Fg[v] += c->b[i] * f[v];
+    }
+  }
 }
 
 static void reflect_state(const ctx* c, const double* u, int dir, double* out) {
@@ -376,6 +422,7 @@ static void line_slope(const ctx* c, const double* u_line /* [N+3][M], index p+1
 static void muscl_hancock_element(const ctx* c, const double* u, int e, double alpha, double dt,
                                   int use_mh, double* ustar) {
   const int M = c->M, n = c->n, N = c->N;
+  const double xe = c->d->x0 + (e % c->nx) * c->dx; /* left face of the element */
   double ue[NPMAX * OR_MAXM];
   gather(c, u, e, ue);
   double sx[NPMAX][OR_MAXM], sy[NPMAX][OR_MAXM];
@@ -429,8 +476,8 @@ static void muscl_hancock_element(const ctx* c, const double* u, int e, double a
         face[3][v] = uk[v] + ax * sy[k][v] * (c->xsub[q + 1] - c->xi[q]);
       }
       double fm[OR_MAXM], fp[OR_MAXM], gm[OR_MAXM], gp[OR_MAXM], delta[OR_MAXM];
-      or_flux(c->d, face[0], 0, fm);
-      or_flux(c->d, face[1], 0, fp);
+      or_flux_x(c->d, face[0], xe + c->xsub[p] * c->dx, 0, fm);
+      or_flux_x(c->d, face[1], xe + c->xsub[p + 1] * c->dx, 0, fp);
       if (c->dim == 2) {
         or_flux(c->d, face[2], 1, gm);
         or_flux(c->d, face[3], 1, gp);
@@ -528,8 +575,17 @@ double or_max_rate(const or_desc* d, const double* u) {
     double ubar[OR_MAXM] = {0};
     for (int k = 0; k < c.np; ++k)
       for (int v = 0; v < c.M; ++v) ubar[v] += node_weight(&c, k) * ue[k * c.M + v];
-    double r = or_wave_speed(d, ubar, 0) / c.dx;
-    if (c.dim == 2) r += or_wave_speed(d, ubar, 1) / c.dy;
+    double r;
+    if (c.dim == 2) {
+      r = or_wave_speed(d, ubar, 0) / c.dx + or_wave_speed(d, ubar, 1) / c.dy;
+    } else {
+      /* sigma of the mean at the element's faces and solution points (they
+       * differ only for variable advection; reading) */
+      double xe = d->x0 + (e % c.nx) * c.dx, s = fmax(or_wave_speed_x(d, ubar, xe, 0),
+                                                       or_wave_speed_x(d, ubar, xe + c.dx, 0));
+      for (int p = 0; p < c.n; ++p) s = fmax(s, or_wave_speed_x(d, ubar, xe + c.xi[p] * c.dx, 0));
+      r = s / c.dx;
+    }
     rmax = fmax(rmax, r);
   }
   return rmax;
@@ -569,7 +625,7 @@ static const double* central_part(const ctx* c, const work_t* W, int e, int f, i
  *   D1,    eq. (D1):   D = lambda/2 (u^+ - u^-),
  *          lambda = max(sigma(u^-), sigma(u^+)) from the u^n traces (eq. (rusanov.wave.speed));
  *   D-CSX, eq. (dcsx): D = sum_i b_i lambda_i/2 (u^(i)+ - u^(i)-), lambda_i from the stage traces. */
-static void high_order_flux(const ctx* c, int dir, const double* FcL, const double* FcR,
+static void high_order_flux(const ctx* c, int dir, double x, const double* FcL, const double* FcR,
                             const double* unL, const double* unR, const double* UL, const double* UR,
                             double stL[][OR_MAXM], double stR[][OR_MAXM], double* FHO) {
   const int M = c->M;
@@ -577,13 +633,13 @@ static void high_order_flux(const ctx* c, int dir, const double* FcL, const doub
     double Dv[OR_MAXM] = {0};
     for (int i = 0; i < c->s; ++i) {
       if (c->b[i] == 0.0) continue;
-      double lam = fmax(or_wave_speed(c->d, stL[i], dir), or_wave_speed(c->d, stR[i], dir));
+      double lam = fmax(or_wave_speed_x(c->d, stL[i], x, dir), or_wave_speed_x(c->d, stR[i], x, dir));
       for (int v = 0; v < M; ++v) Dv[v] += c->b[i] * 0.5 * lam * (stR[i][v] - stL[i][v]);
     }
     for (int v = 0; v < M; ++v) FHO[v] = 0.5 * (FcL[v] + FcR[v]) - Dv[v];
     return;
   }
-  double lam = fmax(or_wave_speed(c->d, unL, dir), or_wave_speed(c->d, unR, dir));
+  double lam = fmax(or_wave_speed_x(c->d, unL, x, dir), or_wave_speed_x(c->d, unR, x, dir));
   const double* jL = c->d->dissipation == OR_DISS_D1 ? unL : UL;
   const double* jR = c->d->dissipation == OR_DISS_D1 ? unR : UR;
   for (int v = 0; v < M; ++v) FHO[v] = 0.5 * (FcL[v] + FcR[v]) - 0.5 * lam * (jR[v] - jL[v]);
@@ -622,6 +678,9 @@ static void face_flux(const ctx* c, const double* u, const work_t* W, int dir, i
   /* boundary side of this face when one neighbour is missing */
   const int side = eR >= 0 ? (dir == 0 ? 0 : 2) : (dir == 0 ? 1 : 3);
   const int bc = (eL >= 0 && eR >= 0) ? OR_BC_PERIODIC : side_bc(c, side);
+  /* position of the face along x (variable advection) */
+  const double xf = dir == 1 ? 0.0
+                    : c->d->x0 + (eR >= 0 ? (eR % c->nx) : (eL % c->nx) + 1) * c->dx;
   if (eL >= 0 && eR >= 0) {
     double stL[OR_MAXS][OR_MAXM], stR[OR_MAXS][OR_MAXM];
     for (int i = 0; i < S; ++i)
@@ -629,11 +688,11 @@ static void face_flux(const ctx* c, const double* u, const work_t* W, int dir, i
         stL[i][v] = WST(W->stg, eL, i, fL, j, v);
         stR[i][v] = WST(W->stg, eR, i, fR, j, v);
       }
-    high_order_flux(c, dir, central_part(c, W, eL, fL, j), central_part(c, W, eR, fR, j),
+    high_order_flux(c, dir, xf, central_part(c, W, eL, fL, j), central_part(c, W, eR, fR, j),
                     &W4(W->unt, eL, fL, j, 0), &W4(W->unt, eR, fR, j, 0), &W4(W->Ut, eL, fL, j, 0),
                     &W4(W->Ut, eR, fR, j, 0), stL, stR, FHO);
     rusanov(c, &W->ustar[(((size_t)eL * c->np + kL) * 4 + hL) * M],
-            &W->ustar[(((size_t)eR * c->np + kR) * 4 + hR) * M], dir, fLO);
+            &W->ustar[(((size_t)eR * c->np + kR) * 4 + hR) * M], dir, xf, fLO);
     alpha_f = 0.5 * (W->alpha[eL] + W->alpha[eR]);
   } else if (bc == OR_BC_WALL || bc == OR_BC_DIRICHLET) {
     /* the interior side (ei, face side fi) and its ghost: reflected (wall) or
@@ -653,36 +712,35 @@ static void face_flux(const ctx* c, const double* u, const work_t* W, int dir, i
       for (int i = 0; i < S; ++i) reflect_state(c, sti[i], dir, stg[i]);
       reflect_state(c, usi, dir, usg);
     } else {
-      const double* g = c->d->bc_state[side];
-      or_flux(c->d, g, dir, Fg);
-      for (int v = 0; v < M; ++v) ug[v] = Ug[v] = usg[v] = g[v];
-      for (int i = 0; i < S; ++i)
-        for (int v = 0; v < M; ++v) stg[i][v] = g[v];
+      ghost_at(c, side, c->d->time, ug);
+      for (int v = 0; v < M; ++v) usg[v] = ug[v];
+      ghost_averages(c, side, dt, xf, dir, stg, Ug, Fg);
     }
     /* (left, right) = (ghost, interior) at a left/bottom wall, (interior, ghost) at a right/top wall */
     if (eR >= 0)
-      high_order_flux(c, dir, Fg, Fi, ug, &W4(W->unt, ei, fi, j, 0), Ug, &W4(W->Ut, ei, fi, j, 0),
+      high_order_flux(c, dir, xf, Fg, Fi, ug, &W4(W->unt, ei, fi, j, 0), Ug, &W4(W->Ut, ei, fi, j, 0),
                       stg, sti, FHO);
     else
-      high_order_flux(c, dir, Fi, Fg, &W4(W->unt, ei, fi, j, 0), ug, &W4(W->Ut, ei, fi, j, 0), Ug,
+      high_order_flux(c, dir, xf, Fi, Fg, &W4(W->unt, ei, fi, j, 0), ug, &W4(W->Ut, ei, fi, j, 0), Ug,
                       sti, stg, FHO);
-    if (eR >= 0) rusanov(c, usg, usi, dir, fLO);
-    else rusanov(c, usi, usg, dir, fLO);
+    if (eR >= 0) rusanov(c, usg, usi, dir, xf, fLO);
+    else rusanov(c, usi, usg, dir, xf, fLO);
     alpha_f = W->alpha[ei];
   } else if (bc == OR_BC_INFLOW) {
-    /* fully inflow (Sec. 3.3): F = F^- = f(g) for both fluxes */
-    or_flux(c->d, c->d->bc_state[side], dir, FHO);
+    /* fully inflow (Sec. 3.3): F = F^- (f(g) for a time-independent g) for both fluxes */
+    double gst[OR_MAXS][OR_MAXM], Ug[OR_MAXM];
+    ghost_averages(c, side, dt, xf, dir, gst, Ug, FHO);
     for (int v = 0; v < M; ++v) fLO[v] = FHO[v];
     alpha_f = W->alpha[eR >= 0 ? eR : eL];
   } else if (eR >= 0) {
     const double* Fc = central_part(c, W, eR, fR, j);
     for (int v = 0; v < M; ++v) FHO[v] = Fc[v];
-    or_flux(c->d, &W->ustar[(((size_t)eR * c->np + kR) * 4 + hR) * M], dir, fLO);
+    or_flux_x(c->d, &W->ustar[(((size_t)eR * c->np + kR) * 4 + hR) * M], xf, dir, fLO);
     alpha_f = W->alpha[eR];
   } else {
     const double* Fc = central_part(c, W, eL, fL, j);
     for (int v = 0; v < M; ++v) FHO[v] = Fc[v];
-    or_flux(c->d, &W->ustar[(((size_t)eL * c->np + kL) * 4 + hL) * M], dir, fLO);
+    or_flux_x(c->d, &W->ustar[(((size_t)eL * c->np + kL) * 4 + hL) * M], xf, dir, fLO);
     alpha_f = W->alpha[eL];
   }
   double F[OR_MAXM];
@@ -810,15 +868,16 @@ int or_step(const or_desc* d, const double* u_in, double dt, double* u_out, or_d
     muscl_hancock_element(&c, u_in, e, W.alpha[e], dt, (d->limiter & OR_LIM_MH) != 0,
                           W.ustar + (size_t)e * np * 4 * M);
     const double* us = W.ustar + (size_t)e * np * 4 * M;
+    const double xe = d->x0 + (e % c.nx) * c.dx;
     for (int q = 0; q < c.nq; ++q)
       for (int p = 1; p <= N; ++p) /* subface p-1/2 between nodes p-1 and p */
         rusanov(&c, &us[(node(&c, p - 1, q) * 4 + 1) * M], &us[(node(&c, p, q) * 4 + 0) * M], 0,
-                &WS(W.fsx, e, q, p, 0));
+                xe + c.xsub[p] * c.dx, &WS(W.fsx, e, q, p, 0));
     if (c.dim == 2)
       for (int p = 0; p <= N; ++p)
         for (int q = 1; q <= N; ++q)
           rusanov(&c, &us[(node(&c, p, q - 1) * 4 + 3) * M], &us[(node(&c, p, q) * 4 + 2) * M], 1,
-                  &WS(W.fsy, e, p, q, 0));
+                  0.0, &WS(W.fsy, e, p, q, 0));
   }
 
   /* 4. one numerical flux per face node; each face is visited from the element on
@@ -953,12 +1012,14 @@ int or_run(const or_desc* d, double* u, int max_steps, double t_final, double* t
   double* tmp = malloc(nvals * sizeof(double));
   double t = 0.0;
   int steps = 0, status = 0;
+  or_desc dl = *d; /* its time field follows t^n */
   while (steps < max_steps && t < t_final) {
     double dt = or_dt(d, u);
     double remaining = t_final - t;
     int last = dt >= remaining;
     if (last) dt = remaining;
-    status = or_step(d, u, dt, tmp, NULL);
+    dl.time = t;
+    status = or_step(&dl, u, dt, tmp, NULL);
     memcpy(u, tmp, nvals * sizeof(double));
     t = last ? t_final : t + dt;
     ++steps;

@@ -35,8 +35,10 @@ extern "C" {
 #define OR_MAXS 6
 #define OR_MAXM 6
 
-/* Burgers: 1D only, f(u) = u^2/2 (Sec. 5.1, Burgers' equation). */
-enum { OR_EQ_LINADV = 0, OR_EQ_EULER = 1, OR_EQ_TENMOMENT = 2, OR_EQ_BURGERS = 3 };
+/* Burgers: 1D only, f(u) = u^2/2 (Sec. 5.1, Burgers' equation).  Variable
+ * advection: 1D only, f(x, u) = a(x) u with a(x) = sum_k adv_poly[k] x^k
+ * (Sec. 5.1, variable advection equation). */
+enum { OR_EQ_LINADV = 0, OR_EQ_EULER = 1, OR_EQ_TENMOMENT = 2, OR_EQ_BURGERS = 3, OR_EQ_VARADV = 4 };
 /* Boundary conditions of Sec. 3.3: periodic; outflow (F = F^+, the fully
  * outflow rule); solid wall for the Euler equations (ghost values by
  * reflecting the normal velocity, eq. (reflect.time.avg)); a given ghost
@@ -86,6 +88,14 @@ typedef struct {
   double bc_state[4][OR_MAXM]; /* ghost state g of each side (conservative), OR_BC_DIRICHLET / OR_BC_INFLOW */
   double gravity[2];       /* acceleration (g_x, g_y) of OR_SRC_GRAVITY */
   int points;              /* OR_POINTS_*; GLL supports no MUSCL-Hancock subcells */
+  double adv_poly[4];      /* a(x) of OR_EQ_VARADV */
+  /* time-dependent ghost states of Dirichlet / inflow sides (scalar equations):
+   * when bc_time_terms > 0, g(t) = sum_{k < terms} bc_time_coef[side][k] T_k(tau),
+   * tau = 2 (t - t0) / (t1 - t0) - 1 clamped to [-1, 1], (t0, t1) = bc_time_span */
+  int bc_time_terms;
+  double bc_time_span[2];
+  double bc_time_coef[4][16];
+  double time;             /* t^n of or_step (or_run advances it in its own copy) */
 } or_desc;
 
 /* Optional outputs of or_step; any pointer may be NULL. */
@@ -118,6 +128,10 @@ int or_tableau(int N, double* A /* [6][6] */, double* b, double* c);
 
 /* Physics, exposed for the tests. dir 0 = x, 1 = y. */
 void or_flux(const or_desc* d, const double* u, int dir, double* f);
+/* The flux and wave speed at position x (variable advection depends on it;
+ * the other equations ignore it). */
+void or_flux_x(const or_desc* d, const double* u, double x, int dir, double* f);
+double or_wave_speed_x(const or_desc* d, const double* u, double x, int dir);
 double or_wave_speed(const or_desc* d, const double* u, int dir);
 int or_num_constraints(const or_desc* d);
 double or_constraint(const or_desc* d, const double* u, int k);

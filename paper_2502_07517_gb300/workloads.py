@@ -92,7 +92,7 @@ def base_problem(**kw):
 
 
 def nvars(prob):
-    return {"linadv": 1, "burgers": 1, "euler": 3 if prob["dim"] == 1 else 4,
+    return {"linadv": 1, "burgers": 1, "varadv": 1, "euler": 3 if prob["dim"] == 1 else 4,
             "tenmoment": 6}[prob["equation"]]
 
 
@@ -126,6 +126,28 @@ def burgers_sine(nx=64, degree=3, t_final=2.0, amp=0.2, points="gl"):
     prob["burgers_amp"] = amp
     x, _ = node_coords(prob)
     return prob, (amp * np.sin(x))[None, :, :].copy()
+
+
+def varadv_exact(x, t):
+    """Exact solution of u_t + (x^2 u)_x = 0 with u0 = cos(pi x / 2), by the
+    characteristics x0 = x / (1 + t x): u = u0(x0) / (1 + t x)^2 (Sec. 5.1)."""
+    s = 1.0 + t * x
+    return np.cos(0.5 * math.pi * x / s) / (s * s)
+
+
+def varadv_x2(nx=32, degree=3, t_final=1.0, terms=16):
+    """Variable advection u_t + (a(x) u)_x = 0, a(x) = x^2, on [0.1, 1]
+    (Sec. 5.1): u0 = cos(pi x / 2); inflow on the left with the exact solution
+    as boundary data (a Chebyshev fit in t on [0, t_final] of u(0.1, t), numpy's
+    chebinterpolate), outflow on the right; no limiter."""
+    prob = base_problem(dim=1, nx=nx, degree=degree, equation="varadv", x0=0.1, x1=1.0,
+                        bc_x="outflow", t_final=t_final, adv_poly=(0.0, 0.0, 1.0, 0.0))
+    prob["bc_side"] = {"x-": "inflow"}
+    tt = lambda tau: 0.5 * (tau + 1.0) * t_final
+    coef = np.polynomial.chebyshev.chebinterpolate(lambda tau: varadv_exact(0.1, tt(tau)), terms - 1)
+    prob["bc_time"] = {"span": (0.0, t_final), "coef": {"x-": [float(c) for c in coef]}}
+    x, _ = node_coords(prob)
+    return prob, np.cos(0.5 * math.pi * x)[None, :, :].copy()
 
 
 def sedov1d(nx=201, degree=3, limiter=LIMITER_ALL, t_final=1e-3):

@@ -2,7 +2,7 @@
 import oracle
 
 _EQ = {"linadv": oracle.EQ_LINADV, "euler": oracle.EQ_EULER, "tenmoment": oracle.EQ_TENMOMENT,
-       "burgers": oracle.EQ_BURGERS}
+       "burgers": oracle.EQ_BURGERS, "varadv": oracle.EQ_VARADV}
 _BC = {"periodic": oracle.BC_PERIODIC, "outflow": oracle.BC_OUTFLOW, "wall": oracle.BC_WALL,
        "dirichlet": oracle.BC_DIRICHLET, "inflow": oracle.BC_INFLOW}
 SIDES = ("x-", "x+", "y-", "y+")
@@ -29,6 +29,11 @@ def oracle_desc(prob, alpha_fixed=None, **over):
     kw.update(bc_side=tuple(_BC[sides[s]] if s in sides else 0 for s in SIDES),
               bc_state=[states.get(s) for s in SIDES])
     kw.update(points={"gl": oracle.POINTS_GL, "gll": oracle.POINTS_GLL}[prob.get("points", "gl")])
+    if "adv_poly" in prob:
+        kw.update(adv_poly=tuple(prob["adv_poly"]))
+    bt = prob.get("bc_time")
+    if bt:
+        kw.update(bc_time=(tuple(bt["span"]), {SIDES.index(s): c for s, c in bt["coef"].items()}))
     if alpha_fixed is not None:
         kw.update(alpha_mode=oracle.ALPHA_FIXED, alpha_fixed=alpha_fixed)
     kw.update(over)
