@@ -49,8 +49,10 @@ typedef enum {
   CR_E_TOO_LARGE = -8      /* cr_step_static: the mesh needs more scratch than its fixed array */
 } cr_status;
 
-/* CR_EQ_BURGERS: u_t + (u^2/2)_x = 0 (Sec. 5.1), 1D, FP64 */
-enum { CR_EQ_LINADV = 0, CR_EQ_EULER = 1, CR_EQ_TENMOMENT = 2, CR_EQ_BURGERS = 3 };
+/* CR_EQ_BURGERS: u_t + (u^2/2)_x = 0 (Sec. 5.1), 1D, FP64.  CR_EQ_VARADV:
+ * u_t + (a(x) u)_x = 0 with a(x) = sum_k adv_poly[k] x^k (Sec. 5.1, variable
+ * advection), 1D, FP64; the flux is evaluated at each point's position. */
+enum { CR_EQ_LINADV = 0, CR_EQ_EULER = 1, CR_EQ_TENMOMENT = 2, CR_EQ_BURGERS = 3, CR_EQ_VARADV = 4 };
 /* Boundary conditions of Sec. 3.3.  Outflow: the fully-outflow rule F = F^+.
  * Wall (Euler only): ghost values by reflecting the velocity normal to the
  * face, eq. (reflect.time.avg), then the D2 flux as at an interior face.
@@ -125,6 +127,14 @@ typedef struct {
                             (first M entries; admissible for Euler and ten-moment) */
   double gravity[2];     /* (g_x, g_y) of CR_SRC_GRAVITY (Euler) */
   int points;            /* CR_POINTS_*; 0 (Gauss-Legendre, Radau) when zero-initialised */
+  double adv_poly[4];    /* a(x) of CR_EQ_VARADV */
+  int bc_time_terms;     /* 0..16; > 0 (scalar equations): the ghost states of Dirichlet and
+                            inflow sides follow g(t) = sum_{k < terms} bc_time_coef[side][k]
+                            T_k(tau), T_k the Chebyshev polynomials, tau = 2 (t - t0) / (t1 - t0)
+                            - 1 clamped to [-1, 1], (t0, t1) = bc_time_span; the boundary
+                            averages take g at the stage times (Sec. 3.3) */
+  double bc_time_span[2];
+  double bc_time_coef[4][16];
 } cr_mesh_desc;
 
 /* Device workspace needed by cr_init_mesh for this descriptor.

@@ -17,7 +17,7 @@ CR_OK = 0
 STATUS = {0: "CR_OK", -1: "CR_E_INVALID_ARG", -2: "CR_E_INVALID_STATE", -3: "CR_E_INADMISSIBLE",
           -4: "CR_E_TIMEOUT", -5: "CR_E_CUDA", -6: "CR_E_NOMEM", -7: "CR_E_UNSUPPORTED",
           -8: "CR_E_TOO_LARGE"}
-CR_EQ_LINADV, CR_EQ_EULER, CR_EQ_TENMOMENT, CR_EQ_BURGERS = 0, 1, 2, 3
+CR_EQ_LINADV, CR_EQ_EULER, CR_EQ_TENMOMENT, CR_EQ_BURGERS, CR_EQ_VARADV = 0, 1, 2, 3, 4
 CR_BC_PERIODIC, CR_BC_OUTFLOW, CR_BC_WALL, CR_BC_DIRICHLET, CR_BC_INFLOW = 0, 1, 2, 3, 4
 CR_SRC_NONE, CR_SRC_TENMOMENT, CR_SRC_GRAVITY = 0, 1, 2
 CR_POINTS_GL, CR_POINTS_GLL = 0, 1
@@ -63,6 +63,8 @@ class cr_mesh_desc(ctypes.Structure):
         ("dissipation", ctypes.c_int), ("central", ctypes.c_int),
         ("bc_side", ctypes.c_int * 4), ("bc_state", (ctypes.c_double * 6) * 4),
         ("gravity", ctypes.c_double * 2), ("points", ctypes.c_int),
+        ("adv_poly", ctypes.c_double * 4), ("bc_time_terms", ctypes.c_int),
+        ("bc_time_span", ctypes.c_double * 2), ("bc_time_coef", (ctypes.c_double * 16) * 4),
     ]
 
 
@@ -413,7 +415,7 @@ def cr_last_error(ctx=None):
 
 # ------------------------------------------------------ problem marshalling -
 _EQ = {"linadv": CR_EQ_LINADV, "euler": CR_EQ_EULER, "tenmoment": CR_EQ_TENMOMENT,
-       "burgers": CR_EQ_BURGERS}
+       "burgers": CR_EQ_BURGERS, "varadv": CR_EQ_VARADV}
 _BC = {"periodic": CR_BC_PERIODIC, "outflow": CR_BC_OUTFLOW, "wall": CR_BC_WALL,
        "dirichlet": CR_BC_DIRICHLET, "inflow": CR_BC_INFLOW}
 _SIDES = ("x-", "x+", "y-", "y+")
@@ -437,6 +439,15 @@ def desc_from_problem(prob, precision=CR_FP64, alpha_fixed=None, stream=None, **
         d.source, d.src_amp, d.src_k, d.src_cx, d.src_cy = (CR_SRC_TENMOMENT, src["amp"], src["k"],
                                                              src["cx"], src["cy"])
     d.points = {"gl": CR_POINTS_GL, "gll": CR_POINTS_GLL}[prob.get("points", "gl")]
+    for k, a in enumerate(prob.get("adv_poly") or ()):
+        d.adv_poly[k] = a
+    bt = prob.get("bc_time")
+    if bt:
+        d.bc_time_span[0], d.bc_time_span[1] = bt["span"]
+        d.bc_time_terms = max(len(c) for c in bt["coef"].values())
+        for s, c in bt["coef"].items():
+            for k, a in enumerate(c):
+                d.bc_time_coef[_SIDES.index(s)][k] = a
     sides, states = prob.get("bc_side") or {}, prob.get("bc_state") or {}
     for i, s in enumerate(_SIDES):
         d.bc_side[i] = _BC[sides[s]] if s in sides else 0

@@ -64,6 +64,7 @@ struct Tab {
   real Dt[kMaxNodes1 * kMaxNodes1];        // D - g_R' l(1)^T - g_L' l(0)^T (FR volume part)
   real gR[kMaxNodes1], gL[kMaxNodes1];     // g_R'(xi_p) = l_p(1)/w_p, g_L'(xi_p) = -l_p(0)/w_p
   real dm[kMaxNodes1], dp[kMaxNodes1];     // subcell faces relative to the node: x_{p-+1/2} - xi_p
+  real xs[kMaxNodes1 + 1];                 // subcell faces x_{p-1/2} (cumulative weights)
   real ihm[kMaxNodes1], ihp[kMaxNodes1], ihc[kMaxNodes1];  // inverse node spacings incl. halo nodes
   real V[kMaxNodes1 * kMaxNodes1];         // V[j*n+p] = (2j+1) w_p L_j(2 xi_p - 1) (Legendre modes)
 };
@@ -87,6 +88,9 @@ struct Mesh {
   int bcs[4];                // boundary type of sides x-, x+, y-, y+ (CR_BC_* codes)
   double bcg[4][6];          // ghost state g of Dirichlet / inflow sides
   double grav[2];            // gravity (g_x, g_y), source 2
+  int bcnt;                  // > 0: Dirichlet / inflow ghost states are Chebyshev series in t
+  double bct0, bct1;         // their time interval
+  double bcc[4][16];         // their coefficients per side (scalar equations)
 };
 
 enum : int { kBcPeriodic = 0, kBcOutflow = 1, kBcWall = 2, kBcDirichlet = 3, kBcInflow = 4 };
@@ -118,6 +122,7 @@ template <typename real>
 struct Phys {
   real gamma, gm1, ax, ay;
   real invdx, invdy;  // 1/dx, 1/dy of the mesh
+  real a0, a1, a2, a3;  // a(x) = a0 + a1 x + a2 x^2 + a3 x^3 of variable advection
 };
 
 template <typename real>
@@ -136,6 +141,13 @@ struct KParams {
 // paper prints no fifth-order scheme for N=4; the six-stage fifth-order method
 // of Butcher with c = (0, 1/4, 1/4, 1/2, 3/4, 1) is used.
 template <int N> struct Tableau;
+// c_i = sum_j a_ij (summed in j order)
+template <int N>
+__host__ __device__ constexpr double tableau_c(int i) {
+  double r = 0.0;
+  for (int j = 0; j < Tableau<N>::S; ++j) r += Tableau<N>::a(i, j);
+  return r;
+}
 template <> struct Tableau<1> {
   static constexpr int S = 2;
   __host__ __device__ static constexpr double a(int i, int j) { return (i == 1 && j == 0) ? 0.5 : 0.0; }
@@ -213,6 +225,87 @@ struct EqLinAdv {  // u_t + a . grad u = 0, Sec. 5.1.1
   template <typename real>
   __device__ static real indicator_var(const real* u, const Phys<real>&) { return u[0]; }
 };
+
+// Variable advection, Sec. 5.1: f(x, u) = a(x) u with a cubic a(x) (1D).
+// The flux depends on the position: the kernels call it through flux_at /
+// speed_at with the coordinate of the point; the position-free forms below
+// (a at x = 0) exist only so that the shared templates compile.
+struct EqVarAdv {
+  static constexpr int M = 1, K = 0;
+  template <typename real>
+  __device__ static real coef(real x, const Phys<real>& ph) {
+    return ((ph.a3 * x + ph.a2) * x + ph.a1) * x + ph.a0;
+  }
+  template <typename real>
+  __device__ static void flux(const real* u, int, real* f, const Phys<real>& ph) { f[0] = ph.a0 * u[0]; }
+  template <typename real>
+  __device__ static void flux_xy(const real* u, real* f, real* g, const Phys<real>& ph) {
+    f[0] = ph.a0 * u[0];
+    g[0] = real(0);
+  }
+  template <typename real>
+  __device__ static real speed(const real*, int, const Phys<real>& ph) { return fabs(ph.a0); }
+  template <typename real>
+  __device__ static void flux_speed(const real* u, int dir, real* f, real* s, const Phys<real>& ph) {
+    flux(u, dir, f, ph);
+    *s = speed(u, dir, ph);
+  }
+  template <typename real>
+  __device__ static real constraint(const real*, int, const Phys<real>&) { return real(1); }
+  template <typename real>
+  __device__ static bool admissible_fast(const real*, const Phys<real>&) { return true; }
+  template <typename real>
+  __device__ static real indicator_var(const real* u, const Phys<real>&) { return u[0]; }
+};
+
+template <class EQ> struct IsVarAdv { static constexpr bool value = false; };
+template <> struct IsVarAdv<EqVarAdv> { static constexpr bool value = true; };
+
+// Flux, wave speed and both at position x along the face normal: variable
+// advection evaluates a(x); every other equation ignores x.
+template <class EQ, typename real>
+__device__ __forceinline__ void flux_at(const real* u, int dir, real* f, const Phys<real>& ph, real x) {
+  if constexpr (IsVarAdv<EQ>::value) f[0] = EqVarAdv::coef(x, ph) * u[0];
+  else EQ::flux(u, dir, f, ph);
+}
+template <class EQ, typename real>
+__device__ __forceinline__ real speed_at(const real* u, int dir, const Phys<real>& ph, real x) {
+  if constexpr (IsVarAdv<EQ>::value) return fabs(EqVarAdv::coef(x, ph));
+  else return EQ::speed(u, dir, ph);
+}
+template <class EQ, typename real>
+__device__ __forceinline__ void flux_speed_at(const real* u, int dir, real* f, real* s,
+                                              const Phys<real>& ph, real x) {
+  if constexpr (IsVarAdv<EQ>::value) {
+    const real a = EqVarAdv::coef(x, ph);
+    f[0] = a * u[0];
+    *s = fabs(a);
+  } else {
+    EQ::flux_speed(u, dir, f, s, ph);
+  }
+}
+
+// Given ghost state of side s at time t (Dirichlet / inflow): the constant
+// bcg, or for a scalar equation with bcnt > 0 the Chebyshev series
+// sum_k bcc[s][k] T_k(tau), tau = 2 (t - t0)/(t1 - t0) - 1 clamped to [-1, 1],
+// by Clenshaw's recurrence.
+template <int M, typename real>
+__device__ __forceinline__ void ghost_at(const Mesh& m, int s, double t, real* g) {
+  if (M != 1 || m.bcnt <= 0) {
+#pragma unroll
+    for (int v = 0; v < M; ++v) g[v] = real(m.bcg[s][v]);
+    return;
+  }
+  double tau = 2.0 * (t - m.bct0) / (m.bct1 - m.bct0) - 1.0;
+  tau = fmin(1.0, fmax(-1.0, tau));
+  double b1 = 0.0, b2 = 0.0;
+  for (int k = m.bcnt - 1; k >= 1; --k) {
+    const double b0 = 2.0 * tau * b1 - b2 + m.bcc[s][k];
+    b2 = b1;
+    b1 = b0;
+  }
+  g[0] = real(tau * b1 - b2 + m.bcc[s][0]);
+}
 
 struct EqBurgers {  // u_t + (u^2/2)_x = 0, Sec. 5.1 (1D); sigma = |u|
   static constexpr int M = 1, K = 0;

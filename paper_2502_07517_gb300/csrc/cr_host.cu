@@ -148,6 +148,7 @@ void fill_tab(const HostTables& h, Tab<real>* t) {
     t->gR[p] = real(h.l1[p] / h.w[p]);
     t->gL[p] = real(-h.l0[p] / h.w[p]);
     // subcells of Sec. 4 eq. (subcell.defn): widths w_p
+    t->xs[p] = real(xs);
     t->dm[p] = real(xs - h.xi[p]);
     t->dp[p] = real(xs + h.w[p] - h.xi[p]);
     xs += h.w[p];
@@ -158,6 +159,7 @@ void fill_tab(const HostTables& h, Tab<real>* t) {
     t->ihp[p] = real(inv(X[p + 2] - X[p + 1]));
     t->ihc[p] = real(inv(X[p + 2] - X[p]));
   }
+  t->xs[n] = real(xs);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
       t->D[i * n + j] = real(h.D[i * n + j]);
@@ -322,7 +324,7 @@ struct Layout {
 };
 
 int nvars_of(const cr_mesh_desc* d) {
-  if (d->equation == CR_EQ_LINADV || d->equation == CR_EQ_BURGERS) return 1;
+  if (d->equation == CR_EQ_LINADV || d->equation == CR_EQ_BURGERS || d->equation == CR_EQ_VARADV) return 1;
   if (d->equation == CR_EQ_EULER) return d->dim == 1 ? 3 : 4;
   return 6;
 }
@@ -370,6 +372,7 @@ const KernelSet* lookup(const cr_mesh_desc* d) {
   if (d->equation == CR_EQ_EULER)
     return d->dim == 1 ? kernels_euler1d(d->degree, mixed) : kernels_euler2d(d->degree, mixed);
   if (d->equation == CR_EQ_BURGERS) return d->dim == 1 ? kernels_burgers1d(d->degree, mixed) : nullptr;
+  if (d->equation == CR_EQ_VARADV) return d->dim == 1 ? kernels_varadv1d(d->degree, mixed) : nullptr;
   return d->dim == 1 ? kernels_tenmoment1d(d->degree, mixed)
                      : kernels_tenmoment2d(d->degree, mixed);
 }
@@ -423,8 +426,21 @@ const char* check_desc(const cr_mesh_desc* d) {
       if (why) return why;
     }
   }
-  if (d->equation < 0 || d->equation > 3) return "unknown equation";
+  if (d->equation < 0 || d->equation > 4) return "unknown equation";
   if (d->equation == CR_EQ_BURGERS && d->dim != 1) return "Burgers' equation is 1D";
+  if (d->equation == CR_EQ_VARADV && d->dim != 1) return "variable advection is 1D";
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(d->adv_poly[k])) return "adv_poly is not finite";
+  if (d->bc_time_terms < 0 || d->bc_time_terms > 16) return "bc_time_terms must be in 0..16";
+  if (d->bc_time_terms > 0) {
+    if (nvars_of(d) != 1) return "time-dependent boundary states are for scalar equations";
+    if (!std::isfinite(d->bc_time_span[0]) || !(d->bc_time_span[1] > d->bc_time_span[0]) ||
+        !std::isfinite(d->bc_time_span[1]))
+      return "bc_time_span must be a finite interval t0 < t1";
+    for (int s = 0; s < 4; ++s)
+      for (int k = 0; k < d->bc_time_terms; ++k)
+        if (!std::isfinite(d->bc_time_coef[s][k])) return "a boundary-state coefficient is not finite";
+  }
   if (d->dissipation < 0 || d->dissipation > 2) return "unknown dissipation model";
   if (d->central < 0 || d->central > 1) return "unknown central flux";
   if (d->points != CR_POINTS_GL && d->points != CR_POINTS_GLL) return "unknown solution points";
@@ -462,6 +478,11 @@ void fill_mesh_extras(const cr_mesh_desc* d, Mesh* m) {
   }
   m->grav[0] = d->source == CR_SRC_GRAVITY ? d->gravity[0] : 0.0;
   m->grav[1] = d->source == CR_SRC_GRAVITY && d->dim == 2 ? d->gravity[1] : 0.0;
+  m->bcnt = d->bc_time_terms;
+  m->bct0 = d->bc_time_span[0];
+  m->bct1 = d->bc_time_span[1];
+  for (int s = 0; s < 4; ++s)
+    for (int k = 0; k < 16; ++k) m->bcc[s][k] = k < d->bc_time_terms ? d->bc_time_coef[s][k] : 0.0;
 }
 
 }  // namespace crk
@@ -551,6 +572,10 @@ void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
   P->ph.gm1 = real(d.gamma - 1.0);
   P->ph.ax = real(d.adv[0]);
   P->ph.ay = real(d.adv[1]);
+  P->ph.a0 = real(d.adv_poly[0]);
+  P->ph.a1 = real(d.adv_poly[1]);
+  P->ph.a2 = real(d.adv_poly[2]);
+  P->ph.a3 = real(d.adv_poly[3]);
   P->ph.invdx = real(m.invdx);
   P->ph.invdy = real(m.invdy);
   P->phd.invdx = m.invdx;
@@ -559,6 +584,10 @@ void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
   P->phd.gm1 = d.gamma - 1.0;
   P->phd.ax = d.adv[0];
   P->phd.ay = d.adv[1];
+  P->phd.a0 = d.adv_poly[0];
+  P->phd.a1 = d.adv_poly[1];
+  P->phd.a2 = d.adv_poly[2];
+  P->phd.a3 = d.adv_poly[3];
   fill_tab(h, &P->tb);
   fill_tab(h, &P->td);
   Bufs<real>& b = P->b;

@@ -60,13 +60,14 @@ __device__ __forceinline__ bool admissible(const real* u, const Phys<real>& ph) 
   return ok;
 }
 
-// Rusanov flux, Sec. 2 eqs. (num.flux.fr), (rusanov.wave.speed).
+// Rusanov flux, Sec. 2 eqs. (num.flux.fr), (rusanov.wave.speed), at position x
+// along the normal (variable advection only).
 template <class EQ, typename real>
 __device__ __forceinline__ void rusanov(const real* uL, const real* uR, int dir, real* out,
-                                        const Phys<real>& ph) {
+                                        const Phys<real>& ph, real x = real(0)) {
   real fL[EQ::M], fR[EQ::M], sL, sR;
-  EQ::flux_speed(uL, dir, fL, &sL, ph);
-  EQ::flux_speed(uR, dir, fR, &sR, ph);
+  flux_speed_at<EQ>(uL, dir, fL, &sL, ph, x);
+  flux_speed_at<EQ>(uR, dir, fR, &sR, ph, x);
   const real lam = fmax(sL, sR);
 #pragma unroll
   for (int v = 0; v < EQ::M; ++v)
@@ -152,6 +153,11 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   const double dtd = P.b.ctl->dt_step;
   if (!(dtd > 0.0)) return;
   const real dt = sizeof(real) == 4 ? real(P.b.ctl->dt_step_f) : real(dtd);
+  // positions along x, for a flux that depends on them (variable advection):
+  // the element's left face, and the node
+  constexpr bool XDEP = IsVarAdv<EQ>::value;
+  const real xe = XDEP ? real(m.x0 + ix * m.dx) : real(0);
+  const real xnode = XDEP ? real(m.x0 + (ix + double(tb.xi[p])) * m.dx) : real(0);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sh = reinterpret_cast<real*>(smem_raw);
@@ -233,7 +239,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     }
     real f[M], g[M];
     if (DIM == 2) EQ::flux_xy(ui, f, g, ph);
-    else EQ::flux(ui, 0, f, ph);
+    else flux_at<EQ>(ui, 0, f, ph, xnode);
     if (TB::b(i) != 0.0) {
       const real bi = real(TB::b(i));
 #pragma unroll
@@ -295,7 +301,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
               P.b.slot[slot_index(1 + 4 * M + i * M + v, side, e, j, NSIDE, m.ne, NFN)] = ut[v];
           }
           if (m.central == 0) {  // EA, eq. (evaluate)
-            EQ::flux(ut, side >> 1, fn, ph);
+            flux_at<EQ>(ut, side >> 1, fn, ph, XDEP ? real(m.x0 + (ix + side) * m.dx) : real(0));
 #pragma unroll
             for (int v = 0; v < M; ++v) ea[mm][v] += bi * fn[v];
           }
@@ -368,7 +374,8 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
         Ft[v] = a3;
       }
       real* sl_out = P.b.slot;
-      sl_out[slot_index(0, side, e, j, NSIDE, m.ne, NFN)] = EQ::speed(ut, side >> 1, ph);
+      sl_out[slot_index(0, side, e, j, NSIDE, m.ne, NFN)] =
+          speed_at<EQ>(ut, side >> 1, ph, XDEP ? real(m.x0 + (ix + side) * m.dx) : real(0));
 #pragma unroll
       for (int v = 0; v < M; ++v) {
         sl_out[slot_index(1 + v, side, e, j, NSIDE, m.ne, NFN)] = m.dissipation == 1 ? ut[v] : Ut[v];
@@ -411,10 +418,13 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
       const int nbR = p == N ? neighbour(m, ee, 1) : -1;
       const int sgx = p == 0 ? 0 : 1;
       const int bgx = m.bcs[sgx];
+      real gvx[M];  // the given state at t^n (Dirichlet, inflow)
+#pragma unroll
+      for (int v = 0; v < M; ++v) gvx[v] = un[v];
+      if (bgx == kBcDirichlet || bgx == kBcInflow) ghost_at<M>(m, sgx, P.b.ctl->t, gvx);
 #pragma unroll
       for (int v = 0; v < M; ++v) {
-        const real gx = bgx == kBcWall ? (v == 1 ? -un[v] : un[v])
-                        : (bgx == kBcDirichlet || bgx == kBcInflow) ? real(m.bcg[sgx][v]) : un[v];
+        const real gx = bgx == kBcWall ? (v == 1 ? -un[v] : un[v]) : gvx[v];
         um[v] = p > 0 ? AT(s0, v, k - 1)
                       : (nbL >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbL, N + n * q) : gx);
         up[v] = p < N ? AT(s0, v, k + 1)
@@ -428,10 +438,13 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
         const int nbT = q == N ? neighbour(m, ee, 3) : -1;
         const int sgy = q == 0 ? 2 : 3;
         const int bgy = m.bcs[sgy];
+        real gvy[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) gvy[v] = un[v];
+        if (bgy == kBcDirichlet || bgy == kBcInflow) ghost_at<M>(m, sgy, P.b.ctl->t, gvy);
 #pragma unroll
         for (int v = 0; v < M; ++v) {
-          const real gy = bgy == kBcWall ? (v == 2 ? -un[v] : un[v])
-                          : (bgy == kBcDirichlet || bgy == kBcInflow) ? real(m.bcg[sgy][v]) : un[v];
+          const real gy = bgy == kBcWall ? (v == 2 ? -un[v] : un[v]) : gvy[v];
           um[v] = q > 0 ? AT(s0, v, k - n)
                         : (nbB >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbB, p + n * N) : gy);
           up[v] = q < N ? AT(s0, v, k + n)
@@ -448,8 +461,8 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
         fym[v] = un[v] + sy[v] * tb.dm[q];
         fyp[v] = un[v] + sy[v] * tb.dp[q];
       }
-      EQ::flux(fxm, 0, Fm, ph);
-      EQ::flux(fxp, 0, Fp, ph);
+      flux_at<EQ>(fxm, 0, Fm, ph, XDEP ? real(m.x0 + (ix + double(tb.xs[p])) * m.dx) : real(0));
+      flux_at<EQ>(fxp, 0, Fp, ph, XDEP ? real(m.x0 + (ix + double(tb.xs[p + 1])) * m.dx) : real(0));
       if (DIM == 2) {
         EQ::flux(fym, 1, Gm, ph);
         EQ::flux(fyp, 1, Gp, ph);
@@ -498,7 +511,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
         uL[v] = AT(sB, v, k);
         uR[v] = AT(sA, v, k + 1);
       }
-      rusanov<EQ>(uL, uR, 0, fr, ph);
+      rusanov<EQ>(uL, uR, 0, fr, ph, XDEP ? real(m.x0 + (ix + double(tb.xs[p + 1])) * m.dx) : real(0));
 #pragma unroll
       for (int v = 0; v < M; ++v) AT(sB, v, k) = fr[v];
     }
@@ -589,13 +602,14 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
   const int nY = DIM == 2 ? m.nfy * m.nx * n : 0;
   const int idx = blk * blockDim.x + threadIdx.x;
   if (idx >= nX + nY) return;
-  int dir, j, eL, eR;
+  int dir, j, eL, eR, fx_i = 0;
   size_t out_idx, vstride;
   real* out;
   if (idx < nX) {
     dir = 0;
     j = idx % NFN;
     const int r = idx / NFN, i = r % m.nfx, iy = r / m.nfx;
+    fx_i = i;
     eR = i < m.nx ? i + m.nx * iy : -1;
     eL = i > 0 ? i - 1 + m.nx * iy : (m.bcx == 0 ? m.nx - 1 + m.nx * iy : -1);
     out = P.b.fx;
@@ -613,6 +627,9 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
     vstride = (size_t)nY;
   }
   const int sL = dir == 0 ? 1 : 3, sR = dir == 0 ? 0 : 2;
+  // the face's position along x, for a flux that depends on it (variable advection)
+  constexpr bool XDEP = IsVarAdv<EQ>::value;
+  const real xf = XDEP && dir == 0 ? real(m.x0 + fx_i * m.dx) : real(0);
   const real* sl = P.b.slot;
   auto fld = [&](int f, int side, int e) { return sl[slot_index(f, side, e, j, NSIDE, m.ne, NFN)]; };
 
@@ -636,7 +653,7 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
           uL[v] = fld(1 + 4 * M + i * M + v, sL, eL);
           uR[v] = fld(1 + 4 * M + i * M + v, sR, eR);
         }
-        const real lam = fmax(EQ::speed(uL, dir, P.ph), EQ::speed(uR, dir, P.ph));
+        const real lam = fmax(speed_at<EQ>(uL, dir, P.ph, xf), speed_at<EQ>(uR, dir, P.ph, xf));
         const real bi = real(Tableau<N>::b(i));
 #pragma unroll
         for (int v = 0; v < M; ++v) Dv[v] += bi * real(0.5) * lam * (uR[v] - uL[v]);
@@ -658,7 +675,7 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
         uL[v] = fld(1 + 2 * M + v, sL, eL);
         uR[v] = fld(1 + 2 * M + v, sR, eR);
       }
-      rusanov<EQ>(uL, uR, dir, fLO, P.ph);
+      rusanov<EQ>(uL, uR, dir, fLO, P.ph, xf);
     }
     alpha_f = 0.5 * (P.b.alpha[eL] + P.b.alpha[eR]);
   } else {
@@ -667,18 +684,43 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
     const int si = eR >= 0 ? sR : sL;
     const int side = eR >= 0 ? (dir == 0 ? 0 : 2) : (dir == 0 ? 1 : 3);
     const int bc = m.bcs[side];
-    real gs[M];  // given ghost state (Dirichlet, inflow)
+    const bool given = bc == kBcDirichlet || bc == kBcInflow;
+    // given ghost state at t^n, and at the stage times with the averages
+    // U^- = sum_i b_i g_i, F^- = sum_i b_i f(g_i) (Sec. 3.3; g and f(g) when g
+    // does not depend on time)
+    const bool tdep = given && M == 1 && m.bcnt > 0;
+    real gs[M], Ug[M], Fg[M], sg = real(0);
 #pragma unroll
-    for (int v = 0; v < M; ++v) gs[v] = real(m.bcg[side][v]);
+    for (int v = 0; v < M; ++v) gs[v] = Ug[v] = Fg[v] = real(0);
+    if (given) {
+      ghost_at<M>(m, side, P.b.ctl->t, gs);
+      flux_speed_at<EQ>(gs, dir, Fg, &sg, P.ph, xf);
+#pragma unroll
+      for (int v = 0; v < M; ++v) Ug[v] = gs[v];
+      if (tdep) {
+#pragma unroll
+        for (int v = 0; v < M; ++v) Ug[v] = Fg[v] = real(0);
+#pragma unroll
+        for (int i = 0; i < Tableau<N>::S; ++i) {
+          real gi[M], fi[M];
+          ghost_at<M>(m, side, P.b.ctl->t + tableau_c<N>(i) * dtd, gi);
+          flux_at<EQ>(gi, dir, fi, P.ph, xf);
+          const real bi = real(Tableau<N>::b(i));
+#pragma unroll
+          for (int v = 0; v < M; ++v) {
+            Ug[v] += bi * gi[v];
+            Fg[v] += bi * fi[v];
+          }
+        }
+      }
+    }
     if (bc == kBcWall || bc == kBcDirichlet) {
       // ghost values: wall, Sec. 3.3 eq. (reflect.time.avg): the interior u^n
       // trace and time-averaged solution with the normal momentum reversed, the
       // interior time-averaged flux with every other component reversed (the
-      // reflection has the interior wave speed); Dirichlet: u^- = U^- = g,
-      // F^- = f(g).  Then the scheme's flux as at an interior face.
+      // reflection has the interior wave speed); Dirichlet: u^- = g(t^n),
+      // U^- and F^- as above.  Then the scheme's flux as at an interior face.
       const bool wall = bc == kBcWall;
-      real fg[M], sg = real(0);
-      if (!wall) EQ::flux_speed(gs, dir, fg, &sg, P.ph);
       real Dv[M];
       if (m.dissipation == 2) {  // D-CSX with ghost stage traces
 #pragma unroll
@@ -686,14 +728,18 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
 #pragma unroll
         for (int i = 0; i < Tableau<N>::S; ++i) {
           if (Tableau<N>::b(i) == 0.0) continue;
-          real ui[M];
+          real ui[M], gi[M];
 #pragma unroll
           for (int v = 0; v < M; ++v) ui[v] = fld(1 + 4 * M + i * M + v, si, ei);
-          const real lam = wall ? EQ::speed(ui, dir, P.ph) : fmax(EQ::speed(ui, dir, P.ph), sg);
+#pragma unroll
+          for (int v = 0; v < M; ++v) gi[v] = gs[v];
+          if (tdep) ghost_at<M>(m, side, P.b.ctl->t + tableau_c<N>(i) * dtd, gi);
+          const real lam = wall ? speed_at<EQ>(ui, dir, P.ph, xf)
+                                : fmax(speed_at<EQ>(ui, dir, P.ph, xf), speed_at<EQ>(gi, dir, P.ph, xf));
           const real bi = real(Tableau<N>::b(i));
 #pragma unroll
           for (int v = 0; v < M; ++v) {
-            const real ug = wall ? (v == 1 + dir ? -ui[v] : ui[v]) : gs[v];
+            const real ug = wall ? (v == 1 + dir ? -ui[v] : ui[v]) : gi[v];
             const real uL = eR >= 0 ? ug : ui[v], uR = eR >= 0 ? ui[v] : ug;
             Dv[v] += bi * real(0.5) * lam * (uR - uL);
           }
@@ -703,16 +749,17 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
 #pragma unroll
         for (int v = 0; v < M; ++v) {
           const real Ui = fld(1 + v, si, ei);
-          const real Ug = wall ? (v == 1 + dir ? -Ui : Ui) : gs[v];
-          const real UL = eR >= 0 ? Ug : Ui, UR = eR >= 0 ? Ui : Ug;
+          // the jump is of U (D2) or of u^n (D1): the ghost U^- or g(t^n)
+          const real Ug_v = wall ? (v == 1 + dir ? -Ui : Ui) : (m.dissipation == 1 ? gs[v] : Ug[v]);
+          const real UL = eR >= 0 ? Ug_v : Ui, UR = eR >= 0 ? Ui : Ug_v;
           Dv[v] = real(0.5) * lam * (UR - UL);
         }
       }
 #pragma unroll
       for (int v = 0; v < M; ++v) {
         const real Fi = fld(1 + M + v, si, ei);
-        const real Fg = wall ? (v == 1 + dir ? Fi : -Fi) : fg[v];
-        const real FL = eR >= 0 ? Fg : Fi, FR = eR >= 0 ? Fi : Fg;
+        const real Fgv = wall ? (v == 1 + dir ? Fi : -Fi) : Fg[v];
+        const real FL = eR >= 0 ? Fgv : Fi, FR = eR >= 0 ? Fi : Fgv;
         FHO[v] = real(0.5) * (FL + FR) - Dv[v];
       }
       if (need_lo) {
@@ -733,16 +780,16 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
             fLO[v] = real(0.5) * (fl + fr) - real(0.5) * sp * (ur - ul);
           }
         } else if (eR >= 0) {
-          rusanov<EQ>(gs, us, dir, fLO, P.ph);
+          rusanov<EQ>(gs, us, dir, fLO, P.ph, xf);
         } else {
-          rusanov<EQ>(us, gs, dir, fLO, P.ph);
+          rusanov<EQ>(us, gs, dir, fLO, P.ph, xf);
         }
       }
     } else if (bc == kBcInflow) {
-      // fully inflow, Sec. 3.3: F = F^- = f(g), high and low order
-      EQ::flux(gs, dir, FHO, P.ph);
+      // fully inflow, Sec. 3.3: F = F^- (f(g) for a time-independent g), high
+      // and low order
 #pragma unroll
-      for (int v = 0; v < M; ++v) fLO[v] = FHO[v];
+      for (int v = 0; v < M; ++v) FHO[v] = fLO[v] = Fg[v];
     } else {
       // fully outflow, Sec. 3.3: F = F^+ (the interior trace flux)
 #pragma unroll
@@ -751,7 +798,7 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
         real us[M];
 #pragma unroll
         for (int v = 0; v < M; ++v) us[v] = fld(1 + 2 * M + v, si, ei);
-        EQ::flux(us, dir, fLO, P.ph);
+        flux_at<EQ>(us, dir, fLO, P.ph, xf);
       }
     }
     alpha_f = P.b.alpha[ei];
@@ -1021,14 +1068,25 @@ __device__ __forceinline__ void finish_block(TimeCtl* ctl, double block_rate, in
 }
 
 // CFL rate sigma_x(u_bar)/dx + sigma_y(u_bar)/dy of each element, block max,
-// then finish_block.  Thread k = 0 of each element evaluates x, k = 1 y.
+// then finish_block.  Thread k = 0 of each element evaluates x, k = 1 y.  A
+// flux that depends on the position (variable advection, 1D) takes the
+// largest sigma over the element's faces and solution points (ix: the
+// element's index along x, xi: the nodes).
 template <int DIM, int NP, class EQ, typename T>
 __device__ __forceinline__ void rate_and_finish(const Mesh& m, const Phys<T>& ph, const T* ubar,
                                                 T* rbuf, int epb, int el, int k, bool valid,
                                                 TimeCtl* ctl, int advance, double dtd, int last,
-                                                int nblk) {
+                                                int nblk, int ix, const T* xi) {
   if (k < DIM) {
-    const T r = EQ::speed(ubar, k, ph) * T(k == 0 ? m.invdx : m.invdy);
+    T s;
+    if constexpr (IsVarAdv<EQ>::value) {
+      const double xe = m.x0 + ix * m.dx;
+      s = fmax(speed_at<EQ>(ubar, 0, ph, T(xe)), speed_at<EQ>(ubar, 0, ph, T(xe + m.dx)));
+      for (int pp = 0; pp < NP; ++pp) s = fmax(s, speed_at<EQ>(ubar, 0, ph, T(xe + double(xi[pp]) * m.dx)));
+    } else {
+      s = EQ::speed(ubar, k, ph);
+    }
+    const T r = s * T(k == 0 ? m.invdx : m.invdy);
     rbuf[el * 2 + k] = valid ? r : T(0);
   }
   __syncthreads();
@@ -1399,10 +1457,10 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
   __syncthreads();
   if constexpr (MIXED) {
     rate_and_finish<DIM, NP, EQ, float>(m, P.ph, ubr, reinterpret_cast<float*>(sEl), epb, el, k,
-                                        valid, P.b.ctl, 1, dtd, last_step, nblk);
+                                        valid, P.b.ctl, 1, dtd, last_step, nblk, ix, tb.xi);
   } else {
     rate_and_finish<DIM, NP, EQ, double>(m, P.phd, ubar, sEl, epb, el, k, valid, P.b.ctl, 1, dtd,
-                                         last_step, nblk);
+                                         last_step, nblk, ix, td.xi);
   }
 #undef ATU
 #undef RED
@@ -1469,7 +1527,7 @@ __global__ void k_prologue(const __grid_constant__ KParams<real> P) {
   }
   __syncthreads();
   rate_and_finish<DIM, NP, EQ, double>(m, P.phd, ubar, sEl, epb, el, k, valid, P.b.ctl, 0, 0.0, 0,
-                                       gridDim.x);
+                                       gridDim.x, ee % m.nx, P.td.xi);
 }
 
 // FP32_BULK state conversion: FP64 nodal values <-> FP64 mean + FP32 fluctuation.

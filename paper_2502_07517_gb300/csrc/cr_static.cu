@@ -93,6 +93,7 @@ void static_tables(int N, Tab<double>* t) {
     t->l1[p] = l1[p];
     t->gR[p] = l1[p] / w[p];
     t->gL[p] = -l0[p] / w[p];
+    t->xs[p] = xs;
     t->dm[p] = xs - xi[p];
     t->dp[p] = xs + w[p] - xi[p];
     xs += w[p];
@@ -100,6 +101,7 @@ void static_tables(int N, Tab<double>* t) {
     t->ihp[p] = 1.0 / (X[p + 2] - X[p + 1]);
     t->ihc[p] = 1.0 / (X[p + 2] - X[p]);
   }
+  t->xs[n] = xs;
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
       t->D[i * n + j] = D[i * n + j];
@@ -122,6 +124,8 @@ extern "C" cr_status cr_step_static(const cr_mesh_desc* d, const double* u_in, d
                                     double dt) {
   if (!d || !u_in || !u_out || !(dt > 0.0))
     return static_fail(CR_E_INVALID_ARG, "cr_step_static: NULL pointer or dt <= 0");
+  if (d->bc_time_terms > 0)
+    return static_fail(CR_E_UNSUPPORTED, "cr_step_static: time-independent boundary states only");
   if (d->dissipation != CR_DISS_D2 || d->central != CR_CENTRAL_EA || d->points != CR_POINTS_GL)
     return static_fail(CR_E_UNSUPPORTED,
                        "cr_step_static: D2 dissipation, EA flux and Gauss-Legendre points only");
@@ -136,6 +140,7 @@ extern "C" cr_status cr_step_static(const cr_mesh_desc* d, const double* u_in, d
     if (d->equation == CR_EQ_LINADV) ks = d->dim == 1 ? kernels_linadv1d(N, 0) : kernels_linadv2d(N, 0);
     else if (d->equation == CR_EQ_EULER) ks = d->dim == 1 ? kernels_euler1d(N, 0) : kernels_euler2d(N, 0);
     else if (d->equation == CR_EQ_BURGERS) ks = d->dim == 1 ? kernels_burgers1d(N, 0) : nullptr;
+    else if (d->equation == CR_EQ_VARADV) ks = d->dim == 1 ? kernels_varadv1d(N, 0) : nullptr;
     else ks = d->dim == 1 ? kernels_tenmoment1d(N, 0) : kernels_tenmoment2d(N, 0);
   }
   if (!ks) return static_fail(CR_E_UNSUPPORTED, "cr_step_static: combination not built");
@@ -222,6 +227,10 @@ extern "C" cr_status cr_step_static(const cr_mesh_desc* d, const double* u_in, d
   P.ph.gm1 = d->gamma - 1.0;
   P.ph.ax = d->adv[0];
   P.ph.ay = d->adv[1];
+  P.ph.a0 = d->adv_poly[0];
+  P.ph.a1 = d->adv_poly[1];
+  P.ph.a2 = d->adv_poly[2];
+  P.ph.a3 = d->adv_poly[3];
   P.ph.invdx = m.invdx;
   P.ph.invdy = m.invdy;
   P.phd = P.ph;

@@ -150,3 +150,26 @@ def test_gauss_lobatto_refusals(built):
     assert _rejected(d)
     d.alpha_mode, d.points = crkfr.CR_ALPHA_INDICATOR, 2
     assert _rejected(d)
+
+
+def test_time_dependent_boundary_descriptors(built):
+    from paper_2502_07517_gb300 import workloads as wl
+    prob, _ = wl.varadv_x2(nx=8, degree=3)
+    d = crkfr.desc_from_problem(prob)
+    assert d.bc_time_terms == 16 and crkfr.cr_workspace_bytes(d) > 0
+    d.bc_time_span[1] = d.bc_time_span[0]
+    assert _rejected(d)
+    d = crkfr.desc_from_problem(prob)
+    d.bc_time_coef[0][3] = float("inf")
+    assert _rejected(d)
+    d = crkfr.desc_from_problem(prob)
+    d.bc_time_terms = 17
+    assert _rejected(d)
+    d = crkfr.desc_from_problem(prob)
+    d.adv_poly[2] = float("nan")
+    assert _rejected(d)
+    # time-dependent states are for scalar equations
+    pe, _ = wl.euler1d_riemann(nx=8, degree=3)
+    d = crkfr.desc_from_problem(pe)
+    d.bc_time_terms, d.bc_time_span[1] = 4, 1.0
+    assert _rejected(d)
