@@ -414,9 +414,10 @@ def widened_legs(steps, warmup, stream):
     per step in FP64 and FP32 bulk (indicator alpha, normalised L1 from FP64
     after the same steps at the same dt); Gauss-Lobatto points (scaling
     limiter only) against Gauss-Legendre points on the 2D Euler recipe
-    (256x256, N = 4, FP64); and Burgers (Sec. 5.1, 128 elements, N = 3, to
-    t = 2) with the EA and AE fluxes on both point sets: whole-run time and
-    L2 error against the exact solution."""
+    (256x256, N = 4, FP64); Burgers (Sec. 5.1, 128 elements, N = 3, to
+    t = 2) with the EA and AE fluxes on both point sets, and variable
+    advection (a = x^2, 128 elements, N = 3, to t = 1) with EA and AE: whole-run
+    time and L2 error against the exact solution."""
     import torch
     from paper_2502_07517_gb300 import crkfr
     sp = stream.cuda_stream
@@ -477,6 +478,23 @@ def widened_legs(steps, warmup, stream):
                                              "value": u.size * n / wall}
     out["burgers1d_sine_128_N3_t2"] = {"unit": "DOF-updates/s", "fp64": burg,
                                        "note": "512 DOF: launch-bound whole runs incl. the host loop"}
+    var = {}
+    for cname, cen in (("EA", crkfr.CR_CENTRAL_EA), ("AE", crkfr.CR_CENTRAL_AE)):
+        prob, u = wl.varadv_x2(nx=128, degree=3)
+        c = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, stream=sp, central=cen))
+        crkfr.cr_set_state(c, u)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t, n = crkfr.cr_step(c, 10 ** 6, 1.0)
+        wall = time.perf_counter() - t0
+        g = crkfr.cr_get_state(c, shape=u.shape)
+        crkfr.cr_destroy(c)
+        x, _ = wl.node_coords(prob)
+        _, w = wl.nodes01(prob)
+        err = float(np.sqrt(((g[0] - wl.varadv_exact(x, 1.0)) ** 2 * w * 0.9 / 128).sum()))
+        var[cname] = {"steps": n, "wall_s": wall, "l2_error_vs_exact": err, "value": u.size * n / wall}
+    out["varadv1d_x2_128_N3_t1"] = {"unit": "DOF-updates/s", "fp64": var,
+                                    "note": "a(x) = x^2, exact inflow; 512 DOF: launch-bound whole runs"}
     return out
 
 
