@@ -300,8 +300,8 @@ const char* cr_last_error(const cr_ctx* ctx);
  * with its own dt) for every problem of a set of contexts, in one launch per
  * phase or in one persistent launch, so many small meshes fill the GPU.  A
  * batched step computes exactly what cr_step computes on each context.
- * Supported: 2D Euler, degree 3 or 4 (mixed in one batch), all contexts in the
- * same precision.  The contexts keep their state and remain usable with
+ * Supported: 2D Euler without a source on Gauss-Legendre points, degree 3 or 4
+ * (mixed in one batch), all contexts in the same precision.  The contexts keep their state and remain usable with
  * cr_set_state / cr_get_state / cr_get_alpha / cr_mlp_load. */
 typedef struct cr_batch cr_batch;
 enum {

@@ -511,8 +511,16 @@ __device__ __forceinline__ void source_grad(const Mesh& m, real rx, real ry, rea
   *dWy = DIM == 2 ? real(-2) * kk * ry * W : real(0);
 }
 
+// Euler with the gravity source of Sec. 5.5: the same equations as a type of
+// its own, so that kernels for problems without a source carry no source code
+// (a runtime switch cost the FP32 element kernel 4%).
+template <int DIM> struct EqEulerG : EqEuler<DIM> {};
+
 template <class EQ> struct IsEuler { static constexpr bool value = false; };
 template <int DIM> struct IsEuler<EqEuler<DIM>> { static constexpr bool value = true; };
+template <int DIM> struct IsEuler<EqEulerG<DIM>> { static constexpr bool value = true; };
+template <class EQ> struct HasGravity { static constexpr bool value = false; };
+template <int DIM> struct HasGravity<EqEulerG<DIM>> { static constexpr bool value = true; };
 
 // Source at one point.  Ten-moment: s = s^x + s^y of eq. (tenmom.source),
 // linear in u for fixed grad W = (dWx, dWy).  Euler with gravity (Sec. 5.5):

@@ -369,6 +369,8 @@ const KernelSet* lookup(const cr_mesh_desc* d) {
   const int mixed = d->precision == CR_FP32_BULK;
   if (d->equation == CR_EQ_LINADV)
     return d->dim == 1 ? kernels_linadv1d(d->degree, mixed) : kernels_linadv2d(d->degree, mixed);
+  if (d->equation == CR_EQ_EULER && d->source == CR_SRC_GRAVITY)
+    return d->dim == 1 ? kernels_euler1d_grav(d->degree, mixed) : kernels_euler2d_grav(d->degree, mixed);
   if (d->equation == CR_EQ_EULER)
     return d->dim == 1 ? kernels_euler1d(d->degree, mixed) : kernels_euler2d(d->degree, mixed);
   if (d->equation == CR_EQ_BURGERS) return d->dim == 1 ? kernels_burgers1d(d->degree, mixed) : nullptr;
@@ -1182,9 +1184,9 @@ cr_status cr_batch_init(cr_ctx* const* ctxs, int n, cr_batch** out) {
     if (!c) return bail(bfail(b, CR_E_INVALID_ARG, "cr_batch_init: NULL context"));
     const cr_mesh_desc& d = c->d;
     if (d.dim != 2 || d.equation != CR_EQ_EULER || (d.degree != 3 && d.degree != 4) ||
-        d.points != CR_POINTS_GL)
+        d.points != CR_POINTS_GL || d.source != CR_SRC_NONE)
       return bail(bfail(b, CR_E_UNSUPPORTED,
-                        "cr_batch_init: batches hold 2D Euler problems of degree 3 or 4 on Gauss-Legendre points"));
+                        "cr_batch_init: batches hold 2D Euler problems of degree 3 or 4 on Gauss-Legendre points, without a source"));
     if (i > 0 && d.precision != ctxs[0]->d.precision)
       return bail(bfail(b, CR_E_INVALID_ARG, "cr_batch_init: mixed precisions"));
     b->ctx.push_back(c);

@@ -203,9 +203,9 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   const real a = blend ? alpha : real(0);
 
   // source: grad W at this node (ten-moment; time independent) or gravity (Euler)
-  const bool has_src = (EQ::M == 6 && m.source == 1) || (IsEuler<EQ>::value && m.source == 2);
+  const bool has_src = (EQ::M == 6 && m.source == 1) || (HasGravity<EQ>::value && m.source == 2);
   real dWx = real(0), dWy = real(0);
-  if (IsEuler<EQ>::value && has_src) {
+  if (HasGravity<EQ>::value && has_src) {
     dWx = real(m.grav[0]);
     dWy = real(DIM == 2 ? m.grav[1] : 0.0);
   } else if (has_src) {
@@ -384,9 +384,10 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     }
   }
   if constexpr (MIXED) {
-    // source contribution to the FP64 element mean, sum_k W_k S_k (tree sum)
-    __syncthreads();
+    // source contribution to the FP64 element mean, sum_k W_k S_k (tree sum;
+    // has_src is the same for the whole block)
     if (has_src) {
+      __syncthreads();
       const real W = DIM == 2 ? tb.w[p] * tb.w[q] : tb.w[p];
 #pragma unroll
       for (int v = 0; v < M; ++v) AT(sA, v, k) = W * Sa[v];

@@ -136,5 +136,7 @@ const KernelSet* kernels_tenmoment1d(int N, int mixed);
 const KernelSet* kernels_tenmoment2d(int N, int mixed);
 const KernelSet* kernels_burgers1d(int N, int mixed);
 const KernelSet* kernels_varadv1d(int N, int mixed);
+const KernelSet* kernels_euler1d_grav(int N, int mixed);
+const KernelSet* kernels_euler2d_grav(int N, int mixed);
 
 }  // namespace crk

@@ -138,6 +138,8 @@ extern "C" cr_status cr_step_static(const cr_mesh_desc* d, const double* u_in, d
   {
     const int N = d->degree;
     if (d->equation == CR_EQ_LINADV) ks = d->dim == 1 ? kernels_linadv1d(N, 0) : kernels_linadv2d(N, 0);
+    else if (d->equation == CR_EQ_EULER && d->source == CR_SRC_GRAVITY)
+      ks = d->dim == 1 ? kernels_euler1d_grav(N, 0) : kernels_euler2d_grav(N, 0);
     else if (d->equation == CR_EQ_EULER) ks = d->dim == 1 ? kernels_euler1d(N, 0) : kernels_euler2d(N, 0);
     else if (d->equation == CR_EQ_BURGERS) ks = d->dim == 1 ? kernels_burgers1d(N, 0) : nullptr;
     else if (d->equation == CR_EQ_VARADV) ks = d->dim == 1 ? kernels_varadv1d(N, 0) : nullptr;

@@ -158,11 +158,17 @@ def test_fp32_ghost_states_one_step():
     assert np.all(l1_rel(g, ref) < L1_ONE_STEP), l1_rel(g, ref)
 
 
-def test_batch_with_ghost_states_and_gravity_equals_single_steps():
-    from tests.test_gpu_batch import _alone, _batched, _same
-    probs = [_mixed_2d(4, 7), _mixed_2d(3, 8), wl.rayleigh_taylor(nx=8, ny=32, degree=3),
-             wl.rayleigh_taylor(nx=12, ny=20, degree=4)]
+def test_batch_with_ghost_states_equals_single_steps():
+    """Batches take ghost-state sides; gravity problems run alone (the batched
+    kernels carry no source code)."""
+    from tests.test_gpu_batch import _alone, _batched, _contexts, _same
+    rt = lambda nx, ny, N: (lambda pu: (dict(pu[0], source=None), pu[1]))(
+        wl.rayleigh_taylor(nx=nx, ny=ny, degree=N))
+    probs = [_mixed_2d(4, 7), _mixed_2d(3, 8), rt(8, 32, 3), rt(12, 20, 4)]
     ref = _alone(probs, crkfr.CR_FP64, 3)
     for config in ((128, crkfr.CR_BATCH_PHASES), (256, crkfr.CR_BATCH_FUSED)):
         got, _ = _batched(probs, crkfr.CR_FP64, 3, config)
         _same(got, ref, crkfr.CR_FP64, "ghost states %s" % (config,))
+    ctxs = _contexts([wl.rayleigh_taylor(nx=8, ny=32, degree=3)], crkfr.CR_FP64)
+    with pytest.raises(crkfr.CrError):
+        crkfr.cr_batch_init(ctxs)
