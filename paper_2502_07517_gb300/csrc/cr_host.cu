@@ -799,9 +799,8 @@ void cr_destroy(cr_ctx* c) {
 cr_status cr_set_state(cr_ctx* c, const double* u, int on_device) {
   if (!c || !u) return fail(c, CR_E_INVALID_ARG, "NULL argument");
   const size_t nvals = (size_t)c->ks->nvars * c->d.nx * (c->d.dim == 2 ? c->d.ny : 1) * c->ks->nodes;
-  if (!on_device)
-    for (size_t i = 0; i < nvals; ++i)
-      if (!std::isfinite(u[i])) return fail(c, CR_E_INVALID_STATE, "state holds a non-finite value");
+  // (non-finite and inadmissible values are found by the prologue kernel, on
+  // the device, for host and device input alike)
   k_reset_ctl<<<1, 1, 0, c->stream>>>(c->d_ctl, c->d.cfl_safety * c->cfl);
   CR_CUDA(c, cudaGetLastError());
   const double* src = u;

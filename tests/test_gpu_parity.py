@@ -219,6 +219,16 @@ def test_invalid_state_rejected():
     with pytest.raises(crkfr.CrError):
         crkfr.cr_set_state(ctx, bad)
     crkfr.cr_set_state(ctx, u)  # the context stays usable
+    # an equation without admissibility constraints still refuses non-finite input
+    prob, u = wl.linadv_random(nx=9, degree=2, seed=1)
+    for value in (np.nan, np.inf):
+        ctx = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob))
+        bad = u.copy()
+        bad[0, 4, 1] = value
+        with pytest.raises(crkfr.CrError) as ei:
+            crkfr.cr_set_state(ctx, bad)
+        assert ei.value.status == -2
+        crkfr.cr_set_state(ctx, u)
 
 
 def test_inadmissible_step_reported_like_the_oracle():
