@@ -46,7 +46,7 @@ class Desc(ctypes.Structure):
         ("gravity", ctypes.c_double * 2), ("points", ctypes.c_int),
         ("adv_poly", ctypes.c_double * 4), ("bc_time_terms", ctypes.c_int),
         ("bc_time_span", ctypes.c_double * 2), ("bc_time_coef", (ctypes.c_double * 16) * 4),
-        ("time", ctypes.c_double),
+        ("time", ctypes.c_double), ("bc_flux", ctypes.c_int),
     ]
 
 
@@ -112,7 +112,7 @@ def make_desc(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=BC_PERIOD
               alpha_mode=ALPHA_INDICATOR, alpha_fixed=0.0, cfl=None, cfl_safety=0.98,
               alpha_given=None, dissipation=DISS_D2, central=CENTRAL_EA, bc_side=(0, 0, 0, 0),
               bc_state=None, gravity=(0.0, 0.0), points=POINTS_GL, adv_poly=(0.0, 0.0, 0.0, 0.0),
-              bc_time=None):
+              bc_time=None, bc_flux=0):
     """Mesh/scheme description; cfl defaults to CFL(degree) from the Fourier analysis.
     alpha_given: per-element raw alpha array for alpha_mode ALPHA_GIVEN (kept alive on
     the returned object)."""
@@ -136,6 +136,7 @@ def make_desc(dim=1, nx=16, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc_x=BC_PERIOD
                 d.bc_state[s][v] = x
     d.gravity[0], d.gravity[1] = gravity
     d.points = points
+    d.bc_flux = bc_flux
     for k in range(4):
         d.adv_poly[k] = adv_poly[k]
     if bc_time is not None:                  # (span, {side index: Chebyshev coefficients})

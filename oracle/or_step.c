@@ -82,6 +82,39 @@ static int admissible(const ctx* c, const double* u) {
   return 1;
 }
 
+/* HLLC flux of the Euler equations (the upwind flux Sec. 3.3 names for
+ * boundaries that mix inflow and outflow), normal direction dir, from states
+ * UL, UR and fluxes FL, FR given separately (the time averages at a boundary
+ * face; f(U) for the low-order flux).  Wave speeds S_L = min(v_L - c_L,
+ * v_R - c_R), S_R = max(v_L + c_L, v_R + c_R); contact speed
+ *   S* = (p_R - p_L + rho_L v_L (S_L - v_L) - rho_R v_R (S_R - v_R))
+ *        / (rho_L (S_L - v_L) - rho_R (S_R - v_R));
+ * star states U*_K = rho_K (S_K - v_K)/(S_K - S*) (1, S* in the normal
+ * momentum, the tangential velocity, E_K/rho_K + (S* - v_K)(S* + p_K/(rho_K (S_K - v_K))));
+ * F = F_L, F_L + S_L (U*_L - U_L), F_R + S_R (U*_R - U_R) or F_R by the signs
+ * of S_L, S*, S_R (the classical three-wave solver of gas dynamics). */
+static void hllc(const ctx* c, int dir, const double* UL, const double* UR, const double* FL,
+                 const double* FR, double* out) {
+  const int M = c->M, mn = 1 + dir, E = M - 1;
+  const double g = c->d->gamma;
+  double rl = UL[0], rr = UR[0], vl = UL[mn] / rl, vr = UR[mn] / rr;
+  double pl = or_constraint(c->d, UL, 1), pr = or_constraint(c->d, UR, 1);
+  double cl = sqrt(fmax(g * pl / rl, 0.0)), cr = sqrt(fmax(g * pr / rr, 0.0));
+  double sl = fmin(vl - cl, vr - cr), sr = fmax(vl + cl, vr + cr);
+  if (sl >= 0.0) { for (int v = 0; v < M; ++v) out[v] = FL[v]; return; }
+  if (sr <= 0.0) { for (int v = 0; v < M; ++v) out[v] = FR[v]; return; }
+  double ss = (pr - pl + rl * vl * (sl - vl) - rr * vr * (sr - vr)) / (rl * (sl - vl) - rr * (sr - vr));
+  const double* U = ss >= 0.0 ? UL : UR;
+  const double* F = ss >= 0.0 ? FL : FR;
+  double r = ss >= 0.0 ? rl : rr, vn = ss >= 0.0 ? vl : vr, p = ss >= 0.0 ? pl : pr, sk = ss >= 0.0 ? sl : sr;
+  double fac = r * (sk - vn) / (sk - ss), us[OR_MAXM];
+  for (int v = 0; v < M; ++v) us[v] = fac * U[v] / r; /* tangential momentum: rho* v_t */
+  us[0] = fac;
+  us[mn] = fac * ss;
+  us[E] = fac * (U[E] / r + (ss - vn) * (ss + p / (r * (sk - vn))));
+  for (int v = 0; v < M; ++v) out[v] = F[v] + sk * (us[v] - U[v]);
+}
+
 /* Rusanov flux of Sec. 2 eq. (num.flux.fr) with eq. (rusanov.wave.speed), at
  * position x along the face normal (used by variable advection only). */
 static void rusanov(const ctx* c, const double* uL, const double* uR, int dir, double x, double* out) {
@@ -717,6 +750,17 @@ static void face_flux(const ctx* c, const double* u, const work_t* W, int dir, i
       ghost_averages(c, side, dt, xf, dir, stg, Ug, Fg);
     }
     /* (left, right) = (ghost, interior) at a left/bottom wall, (interior, ghost) at a right/top wall */
+    if (bc == OR_BC_DIRICHLET && c->d->bc_flux == 1) {
+      /* HLLC on the time-averaged ghost values (high order) and on the evolved
+       * boundary state against g (low order) */
+      double fi_lo[OR_MAXM], fg_lo[OR_MAXM];
+      const double* Ui = &W4(W->Ut, ei, fi, j, 0);
+      or_flux(c->d, usi, dir, fi_lo);
+      or_flux(c->d, usg, dir, fg_lo);
+      if (eR >= 0) { hllc(c, dir, Ug, Ui, Fg, Fi, FHO); hllc(c, dir, usg, usi, fg_lo, fi_lo, fLO); }
+      else { hllc(c, dir, Ui, Ug, Fi, Fg, FHO); hllc(c, dir, usi, usg, fi_lo, fg_lo, fLO); }
+      alpha_f = W->alpha[ei];
+    } else {
     if (eR >= 0)
       high_order_flux(c, dir, xf, Fg, Fi, ug, &W4(W->unt, ei, fi, j, 0), Ug, &W4(W->Ut, ei, fi, j, 0),
                       stg, sti, FHO);
@@ -726,6 +770,7 @@ static void face_flux(const ctx* c, const double* u, const work_t* W, int dir, i
     if (eR >= 0) rusanov(c, usg, usi, dir, xf, fLO);
     else rusanov(c, usi, usg, dir, xf, fLO);
     alpha_f = W->alpha[ei];
+    }
   } else if (bc == OR_BC_INFLOW) {
     /* fully inflow (Sec. 3.3): F = F^- (f(g) for a time-independent g) for both fluxes */
     double gst[OR_MAXS][OR_MAXM], Ug[OR_MAXM];

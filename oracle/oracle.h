@@ -96,6 +96,7 @@ typedef struct {
   double bc_time_span[2];
   double bc_time_coef[4][16];
   double time;             /* t^n of or_step (or_run advances it in its own copy) */
+  int bc_flux;             /* flux at Dirichlet sides: 0 the scheme's own, 1 HLLC (Euler) */
 } or_desc;
 
 /* Optional outputs of or_step; any pointer may be NULL. */

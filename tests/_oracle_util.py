@@ -29,6 +29,8 @@ def oracle_desc(prob, alpha_fixed=None, **over):
     kw.update(bc_side=tuple(_BC[sides[s]] if s in sides else 0 for s in SIDES),
               bc_state=[states.get(s) for s in SIDES])
     kw.update(points={"gl": oracle.POINTS_GL, "gll": oracle.POINTS_GLL}[prob.get("points", "gl")])
+    if prob.get("bc_flux") == "hllc":
+        kw.update(bc_flux=1)
     if "adv_poly" in prob:
         kw.update(adv_poly=tuple(prob["adv_poly"]))
     bt = prob.get("bc_time")
