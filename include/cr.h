@@ -135,6 +135,9 @@ typedef struct {
                             averages take g at the stage times (Sec. 3.3) */
   double bc_time_span[2];
   double bc_time_coef[4][16];
+  int bc_flux;           /* flux at Dirichlet sides: 0 the scheme's own (Rusanov-type D2), 1 the
+                            HLLC flux of Sec. 3.3 on the time-averaged ghost values (Euler; not
+                            with D1) */
 } cr_mesh_desc;
 
 /* Device workspace needed by cr_init_mesh for this descriptor.

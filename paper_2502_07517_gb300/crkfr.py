@@ -65,6 +65,7 @@ class cr_mesh_desc(ctypes.Structure):
         ("gravity", ctypes.c_double * 2), ("points", ctypes.c_int),
         ("adv_poly", ctypes.c_double * 4), ("bc_time_terms", ctypes.c_int),
         ("bc_time_span", ctypes.c_double * 2), ("bc_time_coef", (ctypes.c_double * 16) * 4),
+        ("bc_flux", ctypes.c_int),
     ]
 
 
@@ -441,6 +442,7 @@ def desc_from_problem(prob, precision=CR_FP64, alpha_fixed=None, stream=None, **
     d.points = {"gl": CR_POINTS_GL, "gll": CR_POINTS_GLL}[prob.get("points", "gl")]
     for k, a in enumerate(prob.get("adv_poly") or ()):
         d.adv_poly[k] = a
+    d.bc_flux = 1 if prob.get("bc_flux") == "hllc" else 0
     bt = prob.get("bc_time")
     if bt:
         d.bc_time_span[0], d.bc_time_span[1] = bt["span"]

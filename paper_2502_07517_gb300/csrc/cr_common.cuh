@@ -88,6 +88,7 @@ struct Mesh {
   int bcs[4];                // boundary type of sides x-, x+, y-, y+ (CR_BC_* codes)
   double bcg[4][6];          // ghost state g of Dirichlet / inflow sides
   double grav[2];            // gravity (g_x, g_y), source 2
+  int bcflux;                // flux at Dirichlet sides: 0 the scheme's own, 1 HLLC (Euler)
   int bcnt;                  // > 0: Dirichlet / inflow ghost states are Chebyshev series in t
   double bct0, bct1;         // their time interval
   double bcc[4][16];         // their coefficients per side (scalar equations)

@@ -434,6 +434,10 @@ const char* check_desc(const cr_mesh_desc* d) {
   for (int k = 0; k < 4; ++k)
     if (!std::isfinite(d->adv_poly[k])) return "adv_poly is not finite";
   if (d->bc_time_terms < 0 || d->bc_time_terms > 16) return "bc_time_terms must be in 0..16";
+  if (d->bc_flux < 0 || d->bc_flux > 1) return "unknown boundary flux";
+  if (d->bc_flux == 1 && d->equation != CR_EQ_EULER) return "the HLLC boundary flux is for the Euler equations";
+  if (d->bc_flux == 1 && d->dissipation == CR_DISS_D1)
+    return "the HLLC boundary flux takes the time-averaged solution traces, which D1 does not keep";
   if (d->bc_time_terms > 0) {
     if (nvars_of(d) != 1) return "time-dependent boundary states are for scalar equations";
     if (!std::isfinite(d->bc_time_span[0]) || !(d->bc_time_span[1] > d->bc_time_span[0]) ||
@@ -480,6 +484,7 @@ void fill_mesh_extras(const cr_mesh_desc* d, Mesh* m) {
   }
   m->grav[0] = d->source == CR_SRC_GRAVITY ? d->gravity[0] : 0.0;
   m->grav[1] = d->source == CR_SRC_GRAVITY && d->dim == 2 ? d->gravity[1] : 0.0;
+  m->bcflux = d->bc_flux;
   m->bcnt = d->bc_time_terms;
   m->bct0 = d->bc_time_span[0];
   m->bct1 = d->bc_time_span[1];

@@ -74,6 +74,46 @@ __device__ __forceinline__ void rusanov(const real* uL, const real* uR, int dir,
     out[v] = real(0.5) * (fL[v] + fR[v]) - real(0.5) * lam * (uR[v] - uL[v]);
 }
 
+// HLLC flux of the Euler equations (the upwind flux for boundaries that mix
+// inflow and outflow, Sec. 3.3), normal direction dir, from states UL, UR and
+// fluxes FL, FR given separately (time averages at a boundary face).  Davis
+// wave speeds S_L = min(v_L - c_L, v_R - c_R), S_R = max(v_L + c_L, v_R + c_R),
+// contact speed S* and star states of the classical three-wave solver.
+template <class EQ, typename real>
+__device__ __forceinline__ void hllc(int dir, const real* UL, const real* UR, const real* FL,
+                                     const real* FR, real* out, const Phys<real>& ph) {
+  constexpr int M = EQ::M;
+  const int mn = 1 + dir, E = M - 1;
+  const real rl = UL[0], rr = UR[0], vl = UL[mn] / rl, vr = UR[mn] / rr;
+  const real pl = EQ::constraint(UL, 1, ph), pr = EQ::constraint(UR, 1, ph);
+  const real cl = sqrt_pos(ph.gamma * pl / rl), cr = sqrt_pos(ph.gamma * pr / rr);
+  const real sl = fmin(vl - cl, vr - cr), sr = fmax(vl + cl, vr + cr);
+  if (sl >= real(0)) {
+#pragma unroll
+    for (int v = 0; v < M; ++v) out[v] = FL[v];
+    return;
+  }
+  if (sr <= real(0)) {
+#pragma unroll
+    for (int v = 0; v < M; ++v) out[v] = FR[v];
+    return;
+  }
+  const real ss = (pr - pl + rl * vl * (sl - vl) - rr * vr * (sr - vr)) / (rl * (sl - vl) - rr * (sr - vr));
+  const bool left = ss >= real(0);
+  const real* U = left ? UL : UR;
+  const real* F = left ? FL : FR;
+  const real r = left ? rl : rr, vn = left ? vl : vr, p = left ? pl : pr, sk = left ? sl : sr;
+  const real fac = r * (sk - vn) / (sk - ss);
+  real us[M];
+#pragma unroll
+  for (int v = 0; v < M; ++v) us[v] = fac * U[v] / r;
+  us[0] = fac;
+  us[mn] = fac * ss;
+  us[E] = fac * (U[E] / r + (ss - vn) * (ss + p / (r * (sk - vn))));
+#pragma unroll
+  for (int v = 0; v < M; ++v) out[v] = F[v] + sk * (us[v] - U[v]);
+}
+
 // Load variable v of node k of element e from the state (mean + fluctuation
 // in FP32_BULK mode).
 template <typename real, bool MIXED>
@@ -715,7 +755,27 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
         }
       }
     }
-    if (bc == kBcWall || bc == kBcDirichlet) {
+    if (IsEuler<EQ>::value && bc == kBcDirichlet && m.bcflux == 1) {
+      // HLLC on the time-averaged ghost values (slots 1..M hold U: D1 is refused
+      // with HLLC) and, for the low-order flux, on the evolved boundary state
+      // against g(t^n)
+      real Ui[M], Fi[M], us[M], fu[M], fg0[M];
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        Ui[v] = fld(1 + v, si, ei);
+        Fi[v] = fld(1 + M + v, si, ei);
+      }
+      if (eR >= 0) hllc<EQ>(dir, Ug, Ui, Fg, Fi, FHO, P.ph);
+      else hllc<EQ>(dir, Ui, Ug, Fi, Fg, FHO, P.ph);
+      if (need_lo) {
+#pragma unroll
+        for (int v = 0; v < M; ++v) us[v] = fld(1 + 2 * M + v, si, ei);
+        EQ::flux(us, dir, fu, P.ph);
+        EQ::flux(gs, dir, fg0, P.ph);
+        if (eR >= 0) hllc<EQ>(dir, gs, us, fg0, fu, fLO, P.ph);
+        else hllc<EQ>(dir, us, gs, fu, fg0, fLO, P.ph);
+      }
+    } else if (bc == kBcWall || bc == kBcDirichlet) {
       // ghost values: wall, Sec. 3.3 eq. (reflect.time.avg): the interior u^n
       // trace and time-averaged solution with the normal momentum reversed, the
       // interior time-averaged flux with every other component reversed (the

@@ -324,7 +324,8 @@ def tenmoment2d_voronoi(nx=256, ny=None, degree=3, seed=0, ncells=16, limiter=LI
 def rayleigh_taylor(nx=64, ny=256, degree=3, limiter=LIMITER_ALL, t_final=2.5):
     """Rayleigh-Taylor instability (Sec. 5.5): Euler (gamma 5/3) with gravity
     g = (0, 1) (pointing to +y) on [0, 0.25] x [0, 1]; walls in x; given ghost
-    states at the bottom (rho, v1, v2, p) = (2, 0, 0, 1) and top (1, 0, 0, 2.5);
+    states with the HLLC flux at the bottom (rho, v1, v2, p) = (2, 0, 0, 1) and
+    top (1, 0, 0, 2.5);
     (rho, v1, v2, p) = (2, 0, -0.025 c cos(8 pi x), 2y + 1) for y <= 0.5 and
     (1, 0, -0.025 c cos(8 pi x), y + 1.5) above, c = sqrt(gamma p / rho)."""
     g = 5.0 / 3.0
@@ -334,6 +335,7 @@ def rayleigh_taylor(nx=64, ny=256, degree=3, limiter=LIMITER_ALL, t_final=2.5):
     bottom = euler_conservative(np.array(2.0), np.array(0.0), np.array(0.0), np.array(1.0), g, 2)
     top = euler_conservative(np.array(1.0), np.array(0.0), np.array(0.0), np.array(2.5), g, 2)
     prob["bc_state"] = {"y-": [float(x) for x in bottom], "y+": [float(x) for x in top]}
+    prob["bc_flux"] = "hllc"
     x, y = node_coords(prob)
     _, yc = element_centres(prob)
     low = np.broadcast_to((yc <= 0.5)[:, None], x.shape)

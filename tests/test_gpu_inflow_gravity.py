@@ -69,6 +69,29 @@ def test_linear_advection_and_tenmoment_ghost_states(N):
                         bc_state={"x-": gs, "x+": gs}), u)
 
 
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_hllc_sides_one_step(N):
+    prob, u = _mixed_2d(N, 4)
+    prob = dict(prob, bc_flux="hllc",
+                bc_side={"x-": "dirichlet", "x+": "outflow", "y-": "dirichlet", "y+": "dirichlet"},
+                bc_state={"x-": _cons(1.2, 2.5, 0.3, 1.1), "y-": _cons(0.8, -0.4, 0.6, 2.0),
+                          "y+": _cons(2.0, 0.1, -0.9, 4.0)})
+    one_step_check(prob, u)
+    prob1, u1 = wl.euler1d_riemann(nx=31, degree=N, seed=N + 3)
+    g = [1.1, 1.1 * 0.3, 2.0 / 0.4 + 0.5 * 1.1 * 0.09]
+    one_step_check(dict(prob1, bc_x="dirichlet", bc_flux="hllc", bc_state={"x-": g, "x+": g}), u1)
+
+
+def test_hllc_contact_at_rest_on_the_gpu():
+    prob = wl.base_problem(dim=1, nx=10, degree=3, equation="euler", limiter=wl.LIMITER_ALL,
+                           bc_x="dirichlet", bc_flux="hllc")
+    u = wl.uniform_state(prob, (1.0, 0.0, 1.0))
+    g = [3.0, 0.0, 1.0 / 0.4]
+    prob["bc_state"] = {"x-": g, "x+": g}
+    out, _, t, n, _ = gpu_run(prob, u, dt_fixed=1e-3)
+    np.testing.assert_allclose(out, u, rtol=0, atol=1e-15)
+
+
 @pytest.mark.parametrize("diss,cen", [(1, 0), (2, 0), (0, 1), (2, 1)])
 def test_variants_with_ghost_states(diss, cen):
     prob, u = _mixed_2d(3, 5)
