@@ -157,12 +157,17 @@ void cr_destroy(cr_ctx* ctx);
 
 /* Copy the state u[M][Ne][Np] (FP64) in, reset time to 0, and compute the
  * first time step (eq. (time.step.2d)) and the indicator.  Synchronises.
- * Errors: CR_E_INVALID_STATE when a solution point is not finite or (for
- * equations with an admissible set, Sec. 2 eq. (uad.form)) not admissible. */
+ * on_device == 0: u is host memory that the GPU reads directly (pinned memory,
+ * or any host memory on a system where the GPU shares the CPU's address
+ * translation, as on GB300); on_device == 1: a device pointer.  The input is
+ * checked on the device.  Errors: CR_E_INVALID_STATE when a solution point is
+ * not finite or (for equations with an admissible set, Sec. 2 eq. (uad.form))
+ * not admissible. */
 cr_status cr_set_state(cr_ctx* ctx, const double* u, int on_device);
 
 /* Copy the current state out as u[M][Ne][Np] (FP64); synchronises when
- * on_device == 0.  In CR_FP32_BULK mode values are mean + FP32 fluctuation. */
+ * on_device == 0 (host memory as for cr_set_state).  In CR_FP32_BULK mode
+ * values are mean + FP32 fluctuation. */
 cr_status cr_get_state(cr_ctx* ctx, double* u, int on_device);
 
 /* Advance up to max_steps cRKFR steps (Sec. 3 eq. (crkfr.avg), blended by
