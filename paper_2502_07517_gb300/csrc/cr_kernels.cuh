@@ -1075,19 +1075,25 @@ __device__ T indicator_alpha(const Mesh& m, const Tab<T>& tb, T* E, T* Tm, T* re
   red[(3 * epb + el) * NP + k] = mx == N - 1 ? e2 : T(0);
   elem_tree<NP, 4>(red, epb, el, k, OpSum());
   const T tot = red[(0 * epb + el) * NP];
-  T al = T(0);
-  if (k == 0) {
-    const T top = red[(1 * epb + el) * NP];
-    const T low = red[(2 * epb + el) * NP], top1 = red[(3 * epb + el) * NP];
-    const T r1 = tot > T(0) ? top / tot : T(0);
+  // the energy ratios and the logistic of every element of the block, side by
+  // side in its first epb threads (one warp) rather than in thread 0 of each
+  // element (one warp per element for this scalar work); the element's first
+  // slot of Tm (free once the sums are done) carries the result back
+  if (threadIdx.x < epb) {
+    const int e2 = threadIdx.x;
+    const T tot2 = red[(0 * epb + e2) * NP], top = red[(1 * epb + e2) * NP];
+    const T low = red[(2 * epb + e2) * NP], top1 = red[(3 * epb + e2) * NP];
+    const T r1 = tot2 > T(0) ? top / tot2 : T(0);
     const T r2 = (N >= 2 && low > T(0)) ? top1 / low : T(0);
     const T Ev = fmax(r1, r2);
     const T Tt = T(m.T_ind);
-    al = T(1) / (T(1) + exp(-T(m.s_ind) / Tt * (Ev - Tt)));
-    if (al < T(1e-3)) al = T(0);
-    if (al > T(1) - T(1e-3)) al = T(1);
-    al = fmin(al, T(1));
+    T a2 = T(1) / (T(1) + exp(-T(m.s_ind) / Tt * (Ev - Tt)));
+    if (a2 < T(1e-3)) a2 = T(0);
+    if (a2 > T(1) - T(1e-3)) a2 = T(1);
+    Tm[e2 * NP] = fmin(a2, T(1));
   }
+  __syncthreads();
+  T al = Tm[el * NP];
   if (m.alpha_mode == 2 || feat) {
     const float ek = tot > T(0) ? float(e2 / tot) : 0.0f;
     const float x = log10f(ek + 1e-10f) * 0.1f + 1.0f;
@@ -1102,8 +1108,8 @@ __device__ T indicator_alpha(const Mesh& m, const Tab<T>& tb, T* E, T* Tm, T* re
       }
     }
   }
-  __syncthreads();  // red is reused by the caller
-  return al;  // valid on k == 0
+  __syncthreads();  // red and Tm are reused by the caller
+  return al;  // valid on k == 0 (on every thread of the element without a network)
 }
 
 // finish the step: block max of the CFL rate, last block publishes the rate,
