@@ -1293,33 +1293,39 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
 #pragma unroll
     for (int v = 0; v < M; ++v) ubar[v] = RED0(v);
   }
-  // per-element limiter scalars: sEl[el*16 + 0..3] = mean_ok, eps1, eps2, P2(u_bar).
-  // FP32_BULK: when the FP32 copy of the mean is clearly admissible the FP64
-  // values are known without FP64 work (eps = 1e-12); otherwise FP64.
-  if (k == 0) {
+  // per-element limiter scalars: sEl[el*16 + 0..3] = mean_ok, eps1, eps2, P2(u_bar),
+  // for the block's elements side by side in its first epb threads (one warp)
+  // from the means in shared memory.  FP32_BULK: when the FP32 copy of the mean
+  // is clearly admissible the FP64 values are known without FP64 work (eps =
+  // 1e-12); otherwise FP64.
+  if (threadIdx.x < epb) {
+    const int e2 = threadIdx.x;
+    double ub2[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) ub2[v] = MIXED ? sEl[e2 * 16 + 4 + v] : sRed[(v * epb + e2) * NP];
     bool done = false;
     if constexpr (MIXED) {
       if (EQ::K > 0) {
         real ub[M];
 #pragma unroll
-        for (int v = 0; v < M; ++v) ub[v] = sElr[el * ES + ER + 1 + v];
+        for (int v = 0; v < M; ++v) ub[v] = sElr[e2 * ES + ER + 1 + v];
         const real scale = EQ::M == 6 ? fabs(ub[3]) + fabs(ub[5]) : fabs(ub[M - 1]);
         const real P2f = EQ::constraint(ub, 1, P.ph);
         if (ub[0] > real(1e-9) && P2f > real(1e-5) * scale + real(1e-9)) {
-          sEl[el * 16 + 0] = 1.0;
-          sEl[el * 16 + 1] = 1e-12;
-          sEl[el * 16 + 2] = 1e-12;
-          sEl[el * 16 + 3] = double(P2f);
+          sEl[e2 * 16 + 0] = 1.0;
+          sEl[e2 * 16 + 1] = 1e-12;
+          sEl[e2 * 16 + 2] = 1e-12;
+          sEl[e2 * 16 + 3] = double(P2f);
           done = true;
         }
       }
     }
     if (!done) {
-      const double P2 = EQ::K > 0 ? EQ::constraint(ubar, 1, P.phd) : 0.0;
-      sEl[el * 16 + 0] = admissible<EQ>(ubar, P.phd) ? 1.0 : 0.0;
-      sEl[el * 16 + 1] = EQ::K > 0 ? fmin(1e-12, ubar[0]) : 0.0;
-      sEl[el * 16 + 2] = EQ::K > 0 ? fmin(1e-12, P2) : 0.0;
-      sEl[el * 16 + 3] = P2;
+      const double P2 = EQ::K > 0 ? EQ::constraint(ub2, 1, P.phd) : 0.0;
+      sEl[e2 * 16 + 0] = admissible<EQ>(ub2, P.phd) ? 1.0 : 0.0;
+      sEl[e2 * 16 + 1] = EQ::K > 0 ? fmin(1e-12, ub2[0]) : 0.0;
+      sEl[e2 * 16 + 2] = EQ::K > 0 ? fmin(1e-12, P2) : 0.0;
+      sEl[e2 * 16 + 3] = P2;
     }
   }
   __syncthreads();
