@@ -1135,26 +1135,34 @@ __device__ __forceinline__ void finish_block(TimeCtl* ctl, double block_rate, in
 }
 
 // CFL rate sigma_x(u_bar)/dx + sigma_y(u_bar)/dy of each element, block max,
-// then finish_block.  Thread k = 0 of each element evaluates x, k = 1 y.  A
-// flux that depends on the position (variable advection, 1D) takes the
-// largest sigma over the element's faces and solution points (ix: the
-// element's index along x, xi: the nodes).
+// then finish_block.  The block's elements are evaluated side by side by its
+// first DIM * epb threads (one per element and direction) from the means in
+// shared memory (means[e * mstride + v]; the elements of the block start at
+// e_first, epr of them are whole).  A flux that depends on the position
+// (variable advection, 1D) takes the largest sigma over the element's faces
+// and solution points (xi: the nodes).  rbuf must not overlap means.
 template <int DIM, int NP, class EQ, typename T>
-__device__ __forceinline__ void rate_and_finish(const Mesh& m, const Phys<T>& ph, const T* ubar,
-                                                T* rbuf, int epb, int el, int k, bool valid,
+__device__ __forceinline__ void rate_and_finish(const Mesh& m, const Phys<T>& ph, const T* means,
+                                                int mstride, T* rbuf, int epb, int epr, int e_first,
                                                 TimeCtl* ctl, int advance, double dtd, int last,
-                                                int nblk, int ix, const T* xi) {
-  if (k < DIM) {
+                                                int nblk, const T* xi) {
+  if (threadIdx.x < DIM * epb) {
+    const int e2 = threadIdx.x / DIM, kk = threadIdx.x - e2 * DIM;
+    const int eg = e_first + e2;
+    const bool ok = e2 < epr && eg < m.ne;
+    T ub[EQ::M];
+#pragma unroll
+    for (int v = 0; v < EQ::M; ++v) ub[v] = means[e2 * mstride + v];
     T s;
     if constexpr (IsVarAdv<EQ>::value) {
-      const double xe = m.x0 + ix * m.dx;
-      s = fmax(speed_at<EQ>(ubar, 0, ph, T(xe)), speed_at<EQ>(ubar, 0, ph, T(xe + m.dx)));
-      for (int pp = 0; pp < NP; ++pp) s = fmax(s, speed_at<EQ>(ubar, 0, ph, T(xe + double(xi[pp]) * m.dx)));
+      const double xe = m.x0 + ((ok ? eg : 0) % m.nx) * m.dx;
+      s = fmax(speed_at<EQ>(ub, 0, ph, T(xe)), speed_at<EQ>(ub, 0, ph, T(xe + m.dx)));
+      for (int pp = 0; pp < NP; ++pp) s = fmax(s, speed_at<EQ>(ub, 0, ph, T(xe + double(xi[pp]) * m.dx)));
     } else {
-      s = EQ::speed(ubar, k, ph);
+      s = EQ::speed(ub, kk, ph);
     }
-    const T r = s * T(k == 0 ? m.invdx : m.invdy);
-    rbuf[el * 2 + k] = valid ? r : T(0);
+    const T r = s * T(kk == 0 ? m.invdx : m.invdy);
+    rbuf[e2 * 2 + kk] = ok ? r : T(0);
   }
   __syncthreads();
   double brate = 0.0;
@@ -1292,6 +1300,7 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
     elem_tree<NP, M>(sRed, epb, el, k, OpSum());
 #pragma unroll
     for (int v = 0; v < M; ++v) ubar[v] = RED0(v);
+    for (int v = k; v < M; v += NP) sEl[el * 16 + 4 + v] = RED0(v);  // for the CFL rate
   }
   // per-element limiter scalars: sEl[el*16 + 0..3] = mean_ok, eps1, eps2, P2(u_bar),
   // for the block's elements side by side in its first epb threads (one warp)
@@ -1529,11 +1538,11 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
   }
   __syncthreads();
   if constexpr (MIXED) {
-    rate_and_finish<DIM, NP, EQ, float>(m, P.ph, ubr, reinterpret_cast<float*>(sEl), epb, el, k,
-                                        valid, P.b.ctl, 1, dtd, last_step, nblk, ix, tb.xi);
+    rate_and_finish<DIM, NP, EQ, float>(m, P.ph, sElr + ER + 1, ES, reinterpret_cast<float*>(sRed),
+                                        epb, epr, blk * epr, P.b.ctl, 1, dtd, last_step, nblk, tb.xi);
   } else {
-    rate_and_finish<DIM, NP, EQ, double>(m, P.phd, ubar, sEl, epb, el, k, valid, P.b.ctl, 1, dtd,
-                                         last_step, nblk, ix, td.xi);
+    rate_and_finish<DIM, NP, EQ, double>(m, P.phd, sEl + 4, 16, sRed, epb, epr, blk * epr, P.b.ctl, 1,
+                                         dtd, last_step, nblk, td.xi);
   }
 #undef ATU
 #undef RED
@@ -1589,6 +1598,7 @@ __global__ void k_prologue(const __grid_constant__ KParams<real> P) {
   double ubar[M];
 #pragma unroll
   for (int v = 0; v < M; ++v) ubar[v] = sRed[(v * epb + el) * NP];
+  for (int v = k; v < M; v += NP) sEl[el * 16 + 4 + v] = ubar[v];  // for the CFL rate
   __syncthreads();
   if (((m.limiter & kLimBlend) && (m.alpha_mode == 0 || m.alpha_mode == 2)) || P.b.feat) {
     sU[el * NP + k] = EQ::indicator_var(u, P.phd);
@@ -1599,8 +1609,8 @@ __global__ void k_prologue(const __grid_constant__ KParams<real> P) {
     if (valid && k == 0) P.b.alpha_raw[e] = al;
   }
   __syncthreads();
-  rate_and_finish<DIM, NP, EQ, double>(m, P.phd, ubar, sEl, epb, el, k, valid, P.b.ctl, 0, 0.0, 0,
-                                       gridDim.x, ee % m.nx, P.td.xi);
+  rate_and_finish<DIM, NP, EQ, double>(m, P.phd, sEl + 4, 16, sRed, epb, epr, blockIdx.x * epr, P.b.ctl,
+                                       0, 0.0, 0, gridDim.x, P.td.xi);
 }
 
 // FP32_BULK state conversion: FP64 nodal values <-> FP64 mean + FP32 fluctuation.
