@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/cr.h"
 #include "cr_batch.cuh"
 #include "cr_launch.cuh"
@@ -515,6 +517,13 @@ struct cr_ctx {
 
 namespace {
 
+// NVTX range for the duration of a scope (visible to ncu --nvtx and other
+// CUDA tools; a few nanoseconds when no tool listens).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+
 cr_status fail(cr_ctx* c, cr_status st, const std::string& msg) {
   if (c) c->err = msg;
   else g_init_error = msg;
@@ -802,6 +811,7 @@ void cr_destroy(cr_ctx* c) {
 }
 
 cr_status cr_set_state(cr_ctx* c, const double* u, int on_device) {
+  Range range("cr_set_state");
   if (!c || !u) return fail(c, CR_E_INVALID_ARG, "NULL argument");
   const size_t nvals = (size_t)c->ks->nvars * c->d.nx * (c->d.dim == 2 ? c->d.ny : 1) * c->ks->nodes;
   // (non-finite and inadmissible values are found by the prologue kernel, on
@@ -825,6 +835,7 @@ cr_status cr_set_state(cr_ctx* c, const double* u, int on_device) {
 }
 
 cr_status cr_get_state(cr_ctx* c, double* u, int on_device) {
+  Range range("cr_get_state");
   if (!c || !u) return fail(c, CR_E_INVALID_ARG, "NULL argument");
   const size_t nvals = (size_t)c->ks->nvars * c->d.nx * (c->d.dim == 2 ? c->d.ny : 1) * c->ks->nodes;
   if (c->ks->mixed && !on_device) {
@@ -839,6 +850,7 @@ cr_status cr_get_state(cr_ctx* c, double* u, int on_device) {
 }
 
 cr_status cr_step_async(cr_ctx* c, int max_steps, double t_final, double dt_fixed) {
+  Range range("cr_step_async");
   if (!c) return fail(c, CR_E_INVALID_ARG, "NULL context");
   if (max_steps < 0 || !(t_final == t_final)) return fail(c, CR_E_INVALID_ARG, "bad max_steps or t_final");
   if (!c->graphs_tried) {
@@ -861,6 +873,7 @@ cr_status cr_profile_steps(cr_ctx* c, int max_steps, double t_final, double dt_f
   cr_status st = CR_OK;
   for (int s = 0; s < max_steps && st == CR_OK; ++s) {
     for (int i = 0; i < nk; ++i) {
+      Range range(c->ks->names[i]);
       CR_CUDA(c, cudaEventRecord(ev[i], c->stream));
       CR_CUDA(c, c->ks->launch[i](c->params, c->stream));
     }
@@ -1269,6 +1282,7 @@ cr_status cr_batch_config(cr_batch* b, int threads, int mode) {
 }
 
 cr_status cr_batch_step_async(cr_batch* b, int nsteps, double t_final) {
+  Range range("cr_batch_step_async");
   if (!b) return bfail(nullptr, CR_E_INVALID_ARG, "NULL batch");
   if (nsteps < 0 || !(t_final == t_final)) return bfail(b, CR_E_INVALID_ARG, "bad nsteps or t_final");
   size_t k = 0;
