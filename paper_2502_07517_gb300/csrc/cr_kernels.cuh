@@ -162,6 +162,23 @@ struct OpMin {
   __device__ T operator()(T a, T b) const { return fmin(a, b); }
 };
 
+// Face-node slot gs of a block, the slots numbered across the block so that
+// the threads left without one form whole idle warps (FP64 pipe time and
+// issue slots are charged per warp instruction): element el of the block
+// (gs / NSLOT), its side and node j along that face.
+struct FaceSlot {
+  int el, side, j;
+};
+template <int NSLOT, int NFN>
+__device__ __forceinline__ FaceSlot face_slot(int gs) {
+  FaceSlot f;
+  f.el = gs / NSLOT;
+  const int sl = gs - f.el * NSLOT;
+  f.side = sl / NFN;
+  f.j = sl - f.side * NFN;
+  return f;
+}
+
 // ===========================================================================
 // Body of k_local for block blk of a problem (the standalone kernel and the
 // batched kernels of cr_batch.cu call it).  Threads past the block's last whole
@@ -209,6 +226,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   real* sC = sB + arr;
   real* sD = sC + arr;
 #define AT(base, v, node) base[(v) * stride + el * NP + (node)]
+#define ATE(base, v, elx, node) base[(v) * stride + (elx) * NP + (node)]
 
   real un[M];
 #pragma unroll
@@ -321,9 +339,9 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
       const real bi = real(TB::b(i));
 #pragma unroll
       for (int mm = 0; mm < SPT; ++mm) {
-        const int sl = k + mm * NP;
-        if (sl < NSLOT) {
-          const int side = sl / NFN, j = sl - side * NFN;
+        const FaceSlot fs = face_slot<NSLOT, NFN>(tid + mm * blockDim.x);
+        if (fs.el < epr) {
+          const int side = fs.side, j = fs.j;
           real ut[M], fn[M];
 #pragma unroll
           for (int v = 0; v < M; ++v) {
@@ -331,17 +349,19 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
 #pragma unroll
             for (int r = 0; r < n; ++r) {
               const real l = (side & 1) ? tb.l1[r] : tb.l0[r];
-              acc += l * AT(sA, v, side < 2 ? r + n * j : j + n * r);
+              acc += l * ATE(sA, v, fs.el, side < 2 ? r + n * j : j + n * r);
             }
             ut[v] = acc;
           }
-          if (m.dissipation == 2 && valid) {  // D-CSX: the stage trace, for the face kernel
+          const int eg = blk * epr + fs.el;
+          if (m.dissipation == 2 && eg < m.ne) {  // D-CSX: the stage trace, for the face kernel
 #pragma unroll
             for (int v = 0; v < M; ++v)
-              P.b.slot[slot_index(1 + 4 * M + i * M + v, side, e, j, NSIDE, m.ne, NFN)] = ut[v];
+              P.b.slot[slot_index(1 + 4 * M + i * M + v, side, eg, j, NSIDE, m.ne, NFN)] = ut[v];
           }
           if (m.central == 0) {  // EA, eq. (evaluate)
-            flux_at<EQ>(ut, side >> 1, fn, ph, XDEP ? real(m.x0 + (ix + side) * m.dx) : real(0));
+            flux_at<EQ>(ut, side >> 1, fn, ph,
+                        XDEP ? real(m.x0 + (min(eg, m.ne - 1) % m.nx + side) * m.dx) : real(0));
 #pragma unroll
             for (int v = 0; v < M; ++v) ea[mm][v] += bi * fn[v];
           }
@@ -391,9 +411,10 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   }
 #pragma unroll
   for (int mm = 0; mm < SPT; ++mm) {
-    const int sl = k + mm * NP;
-    if (valid && sl < NSLOT) {
-      const int side = sl / NFN, j = sl - side * NFN;
+    const FaceSlot fs = face_slot<NSLOT, NFN>(tid + mm * blockDim.x);
+    const int eg = blk * epr + fs.el;
+    if (fs.el < epr && eg < m.ne) {
+      const int side = fs.side, j = fs.j;
       // slot 1..M: the trace the dissipation jumps over (U for D2, u^n for D1);
       // slot 1+M..: the central part (EA average, or for AE the trace of the
       // time-averaged flux F (x faces) or G (y faces), eq. (extrapolate))
@@ -405,21 +426,22 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
         for (int r = 0; r < n; ++r) {
           const real l = (side & 1) ? tb.l1[r] : tb.l0[r];
           const int node = side < 2 ? r + n * j : j + n * r;
-          a1 += l * AT(sA, v, node);
-          a2 += l * AT(s0, v, node);
-          if (m.central == 1) a3 += l * (side < 2 ? AT(sB, v, node) : AT(sC, v, node));
+          a1 += l * ATE(sA, v, fs.el, node);
+          a2 += l * ATE(s0, v, fs.el, node);
+          if (m.central == 1) a3 += l * (side < 2 ? ATE(sB, v, fs.el, node) : ATE(sC, v, fs.el, node));
         }
         Ut[v] = a1;
         ut[v] = a2;
         Ft[v] = a3;
       }
       real* sl_out = P.b.slot;
-      sl_out[slot_index(0, side, e, j, NSIDE, m.ne, NFN)] =
-          speed_at<EQ>(ut, side >> 1, ph, XDEP ? real(m.x0 + (ix + side) * m.dx) : real(0));
+      sl_out[slot_index(0, side, eg, j, NSIDE, m.ne, NFN)] =
+          speed_at<EQ>(ut, side >> 1, ph, XDEP ? real(m.x0 + (eg % m.nx + side) * m.dx) : real(0));
 #pragma unroll
       for (int v = 0; v < M; ++v) {
-        sl_out[slot_index(1 + v, side, e, j, NSIDE, m.ne, NFN)] = m.dissipation == 1 ? ut[v] : Ut[v];
-        sl_out[slot_index(1 + M + v, side, e, j, NSIDE, m.ne, NFN)] = m.central == 1 ? Ft[v] : ea[mm][v];
+        sl_out[slot_index(1 + v, side, eg, j, NSIDE, m.ne, NFN)] = m.dissipation == 1 ? ut[v] : Ut[v];
+        sl_out[slot_index(1 + M + v, side, eg, j, NSIDE, m.ne, NFN)] =
+            m.central == 1 ? Ft[v] : ea[mm][v];
       }
     }
   }
@@ -543,29 +565,35 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
       }
     }
     __syncthreads();
-    // subcell fluxes: thread (p,q) owns the subface to its right (x) and top (y);
-    // its own x+ (y+) state is read only by itself, so it is overwritten in place
-    if (p < N) {
+    // subcell fluxes, numbered across the block (element r / NSF of the block:
+    // its N * NFN x-subfaces, then in 2D its n * N y-subfaces) so that the
+    // threads left without one form whole idle warps.  The flux of the
+    // subface right of (above) node (p2, q2) reads that node's x+ (y+) state,
+    // which no other flux reads, and overwrites it in place.
+    constexpr int NSX = N * NFN, NSF = DIM == 2 ? 2 * N * n : N;
+    for (int gs = tid; gs < epr * NSF; gs += blockDim.x) {
+      const int el2 = gs / NSF, r = gs - el2 * NSF;
+      const bool isx = r < NSX;
+      const int rr = isx ? r : r - NSX;
+      const int p2 = isx ? rr % N : rr % n, q2 = isx ? rr / N : rr / n;
+      const int node = p2 + n * q2;
+      real* sL = isx ? sB : sD;
+      const real* sR = isx ? sA : sC;
+      const int nodeR = node + (isx ? 1 : n);
       real uL[M], uR[M], fr[M];
 #pragma unroll
       for (int v = 0; v < M; ++v) {
-        uL[v] = AT(sB, v, k);
-        uR[v] = AT(sA, v, k + 1);
+        uL[v] = ATE(sL, v, el2, node);
+        uR[v] = ATE(sR, v, el2, nodeR);
       }
-      rusanov<EQ>(uL, uR, 0, fr, ph, XDEP ? real(m.x0 + (ix + double(tb.xs[p + 1])) * m.dx) : real(0));
-#pragma unroll
-      for (int v = 0; v < M; ++v) AT(sB, v, k) = fr[v];
-    }
-    if (DIM == 2 && q < N) {
-      real uL[M], uR[M], fr[M];
-#pragma unroll
-      for (int v = 0; v < M; ++v) {
-        uL[v] = AT(sD, v, k);
-        uR[v] = AT(sC, v, k + n);
+      real xf = real(0);
+      if constexpr (XDEP) {
+        const int e2 = min(blk * epr + el2, m.ne - 1);
+        xf = real(m.x0 + (e2 % m.nx + double(tb.xs[p2 + 1])) * m.dx);
       }
-      rusanov<EQ>(uL, uR, 1, fr, ph);
+      rusanov<EQ>(uL, uR, isx ? 0 : 1, fr, ph, xf);
 #pragma unroll
-      for (int v = 0; v < M; ++v) AT(sD, v, k) = fr[v];
+      for (int v = 0; v < M; ++v) ATE(sL, v, el2, node) = fr[v];
     }
     __syncthreads();
     // low-order residual of the interior subfaces (eq. (low.order.update))
@@ -582,9 +610,10 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     // candidate base of the flux limiter, u_b -+ c f_adj
 #pragma unroll
     for (int mm = 0; mm < SPT; ++mm) {
-      const int sl = k + mm * NP;
-      if (valid && sl < NSLOT) {
-        const int side = sl / NFN, j = sl - side * NFN;
+      const FaceSlot fs = face_slot<NSLOT, NFN>(tid + mm * blockDim.x);
+      const int eg = blk * epr + fs.el;
+      if (fs.el < epr && eg < m.ne) {
+        const int side = fs.side, j = fs.j;
         int nb_node, adj_node;
         const real* ust;
         const real* adj;
@@ -595,10 +624,10 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
         const real c = dt * real(m.cflim[side]) * ((side & 1) ? real(1) : real(-1));
 #pragma unroll
         for (int v = 0; v < M; ++v) {
-          P.b.slot[slot_index(1 + 2 * M + v, side, e, j, NSIDE, m.ne, NFN)] =
-              ust[v * stride + el * NP + nb_node];
-          P.b.slot[slot_index(1 + 3 * M + v, side, e, j, NSIDE, m.ne, NFN)] =
-              AT(s0, v, nb_node) + c * adj[v * stride + el * NP + adj_node];
+          P.b.slot[slot_index(1 + 2 * M + v, side, eg, j, NSIDE, m.ne, NFN)] =
+              ATE(ust, v, fs.el, nb_node);
+          P.b.slot[slot_index(1 + 3 * M + v, side, eg, j, NSIDE, m.ne, NFN)] =
+              ATE(s0, v, fs.el, nb_node) + c * ATE(adj, v, fs.el, adj_node);
         }
       }
     }
@@ -613,6 +642,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     }
   }
 #undef AT
+#undef ATE
 }
 
 // Resident blocks per SM the step kernels ask for (measured on GB300,
