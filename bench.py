@@ -65,9 +65,9 @@ def flop_model(dim, N, eq, source=False):
     loc = nnza * M * 2                                # stage values
     loc += S * (dim * fl + (src if source else 0))    # fluxes and source at the points
     loc += nnzb * (dim + 2) * M * 2                   # F, (G), U, S accumulation
-    loc += (S - 1) * M * (dim * 2 * n + dim + 1)      # D contractions of the stage fluxes
+    loc += (S - 1) * M * dim * 2 * n                  # D contractions (1/dx, 1/dy in the tables)
     loc += nnzb * nslot * (M * 2 * n + fl + 2 * M)    # EA traces and fluxes
-    loc += M * (dim * 2 * n + dim)                    # high-order volume part
+    loc += M * dim * 2 * n                            # high-order volume part (likewise)
     loc += nslot * (2 * M * 2 * n + sp)               # U and u^n traces, wave speed
     loc += dim * M * 9 + 2 * dim * M * 2 + 2 * dim * fl + dim * M * 5 + 2 * dim * M  # MUSCL-Hancock
     loc += 4 * dim * c2                               # admissibility of face/evolved states

@@ -60,8 +60,6 @@ template <typename real>
 struct Tab {
   real xi[kMaxNodes1], w[kMaxNodes1], invw[kMaxNodes1];
   real l0[kMaxNodes1], l1[kMaxNodes1];     // l_p(0), l_p(1)
-  real D[kMaxNodes1 * kMaxNodes1];         // D[i*n+j] = l_j'(xi_i), Sec. 2 eq. (diff.matrix)
-  real Dt[kMaxNodes1 * kMaxNodes1];        // D - g_R' l(1)^T - g_L' l(0)^T (FR volume part)
   real gR[kMaxNodes1], gL[kMaxNodes1];     // g_R'(xi_p) = l_p(1)/w_p, g_L'(xi_p) = -l_p(0)/w_p
   real dm[kMaxNodes1], dp[kMaxNodes1];     // subcell faces relative to the node: x_{p-+1/2} - xi_p
   real xs[kMaxNodes1 + 1];                 // subcell faces x_{p-1/2} (cumulative weights)
@@ -126,15 +124,47 @@ struct Phys {
   real a0, a1, a2, a3;  // a(x) = a0 + a1 x + a2 x^2 + a3 x^3 of variable advection
 };
 
+// Differentiation matrix D[i*n+j] = l_j'(xi_i) (Sec. 2 eq. (diff.matrix)) and
+// FR volume matrix Dt = D - g_R' l(1)^T - g_L' l(0)^T (the trace terms of eq.
+// (crkfr.avg) folded in), scaled by the inverse element widths so that a stage
+// residual (and the FR volume part) over both directions is one FMA chain:
+// Dx = D / dx, Dy = D / dy, Dtx = Dt / dx, Dty = Dt / dy.  Per problem (a
+// batch shares Tab between problems of different widths).
+template <typename real>
+struct DiffScaled {
+  real Dx[kMaxNodes1 * kMaxNodes1], Dy[kMaxNodes1 * kMaxNodes1];
+  real Dtx[kMaxNodes1 * kMaxNodes1], Dty[kMaxNodes1 * kMaxNodes1];
+};
+
 template <typename real>
 struct KParams {
   Mesh m;
-  Phys<real> ph;     // constants in the bulk type
-  Phys<double> phd;  // FP64 constants (limiters, means)
-  Tab<real> tb;      // tables in the bulk type
-  Tab<double> td;    // FP64 tables (limiters, means)
+  Phys<real> ph;        // constants in the bulk type
+  Phys<double> phd;     // FP64 constants (limiters, means)
+  Tab<real> tb;         // tables in the bulk type
+  Tab<double> td;       // FP64 tables (limiters, means)
+  DiffScaled<real> ds;  // scaled differentiation matrices in the bulk type
   Bufs<real> b;
 };
+
+// Host: fill ds from D and Dt of degree N (FP64, row-major n x n; each
+// product rounded once), with w, l(0), l(1) of the nodes giving Dt.
+template <typename real>
+inline void fill_scaled(const double* D, const double* w, const double* l0, const double* l1, int N,
+                        double invdx, double invdy, DiffScaled<real>* ds) {
+  const int n = N + 1;
+  for (int i = 0; i < kMaxNodes1 * kMaxNodes1; ++i)
+    ds->Dx[i] = ds->Dy[i] = ds->Dtx[i] = ds->Dty[i] = real(0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double d = D[i * n + j];
+      const double dt = d - (l1[i] / w[i]) * l1[j] + (l0[i] / w[i]) * l0[j];
+      ds->Dx[i * n + j] = real(d * invdx);
+      ds->Dy[i * n + j] = real(d * invdy);
+      ds->Dtx[i * n + j] = real(dt * invdx);
+      ds->Dty[i * n + j] = real(dt * invdy);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Butcher tableaux (Sec. 2 eq. (butcher)); degree N uses order N+1 (Sec. 3).

@@ -164,11 +164,6 @@ void fill_tab(const HostTables& h, Tab<real>* t) {
   t->xs[n] = real(xs);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
-      t->D[i * n + j] = real(h.D[i * n + j]);
-      // FR update of eq. (crkfr.avg) with the trace terms F^delta(0), F^delta(1)
-      // folded into the volume matrix
-      t->Dt[i * n + j] = real(h.D[i * n + j] - (h.l1[i] / h.w[i]) * h.l1[j] +
-                              (h.l0[i] / h.w[i]) * h.l0[j]);
       t->V[i * n + j] = real((2.0 * i + 1.0) * h.w[j] * legendre01(i, h.xi[j]));
     }
 }
@@ -606,6 +601,7 @@ void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
   P->phd.a3 = d.adv_poly[3];
   fill_tab(h, &P->tb);
   fill_tab(h, &P->td);
+  fill_scaled(h.D, h.w, h.l0, h.l1, d.degree, m.invdx, m.invdy, &P->ds);
   Bufs<real>& b = P->b;
   unsigned char* w = c->ws;
   b.ctl = reinterpret_cast<TimeCtl*>(w + c->L.ctl);

@@ -283,6 +283,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     for (int mm = 0; mm < SPT; ++mm) ea[mm][v] = real(0);
   }
   const real invdx = ph.invdx, invdy = ph.invdy;
+  const DiffScaled<real>& ds = P.ds;
 
 #pragma unroll
   for (int i = 0; i < S; ++i) {
@@ -317,14 +318,14 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     if (i < S - 1) {
 #pragma unroll
       for (int v = 0; v < M; ++v) {
-        real hx = real(0), hy = real(0);
+        real h = real(0);  // (D f)/dx + (D g)/dy as one chain
 #pragma unroll
-        for (int r = 0; r < n; ++r) hx += tb.D[p * n + r] * AT(sB, v, r + n * q);
+        for (int r = 0; r < n; ++r) h += ds.Dx[p * n + r] * AT(sB, v, r + n * q);
         if (DIM == 2) {
 #pragma unroll
-          for (int r = 0; r < n; ++r) hy += tb.D[q * n + r] * AT(sC, v, p + n * r);
+          for (int r = 0; r < n; ++r) h += ds.Dy[q * n + r] * AT(sC, v, p + n * r);
         }
-        Lst[i < S - 1 ? i : 0][v] = invdx * hx + (DIM == 2 ? invdy * hy : real(0));
+        Lst[i < S - 1 ? i : 0][v] = h;
       }
       if (has_src) {  // the stage's source, from its node value still in shared memory
         real us[M], s[M];
@@ -382,14 +383,14 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   real HO[M];
 #pragma unroll
   for (int v = 0; v < M; ++v) {
-    real hx = real(0), hy = real(0);
+    real h = real(0);
 #pragma unroll
-    for (int r = 0; r < n; ++r) hx += tb.Dt[p * n + r] * AT(sB, v, r + n * q);
+    for (int r = 0; r < n; ++r) h += ds.Dtx[p * n + r] * AT(sB, v, r + n * q);
     if (DIM == 2) {
 #pragma unroll
-      for (int r = 0; r < n; ++r) hy += tb.Dt[q * n + r] * AT(sC, v, p + n * r);
+      for (int r = 0; r < n; ++r) h += ds.Dty[q * n + r] * AT(sC, v, p + n * r);
     }
-    HO[v] = invdx * hx + (DIM == 2 ? invdy * hy : real(0));
+    HO[v] = h;
   }
   // time-averaged source S = sum_i b_i s(u^(i)) (App. B eq. (crkfr.source)):
   // both sources are linear in u (the ten-moment one for fixed grad W), so it

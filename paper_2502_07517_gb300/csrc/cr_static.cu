@@ -62,10 +62,11 @@ __global__ void k_static_reset(TimeCtl* c, double dt) {
 }
 
 // Reference tables of degree N from the public host routine, plus the derived
-// per-kernel tables (same definitions as the context path).
-void static_tables(int N, Tab<double>* t) {
+// per-kernel tables (same definitions as the context path); D receives the
+// differentiation matrix (n x n).
+void static_tables(int N, Tab<double>* t, double* D) {
   const int n = N + 1;
-  double xi[kMaxNodes1], w[kMaxNodes1], D[kMaxNodes1 * kMaxNodes1];
+  double xi[kMaxNodes1], w[kMaxNodes1];
   cr_reference_tables(N, xi, w, D);
   double lam[kMaxNodes1], l0[kMaxNodes1], l1[kMaxNodes1];
   for (int j = 0; j < n; ++j) {
@@ -104,8 +105,6 @@ void static_tables(int N, Tab<double>* t) {
   t->xs[n] = xs;
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
-      t->D[i * n + j] = D[i * n + j];
-      t->Dt[i * n + j] = D[i * n + j] - (l1[i] / w[i]) * l1[j] + (l0[i] / w[i]) * l0[j];
       double pm = 1.0, pc = 2.0 * xi[j] - 1.0, x = pc;  // Legendre L_i(2 xi_j - 1)
       double Li = (i == 0) ? 1.0 : x;
       for (int k = 2; k <= i; ++k) {
@@ -236,8 +235,10 @@ extern "C" cr_status cr_step_static(const cr_mesh_desc* d, const double* u_in, d
   P.ph.invdx = m.invdx;
   P.ph.invdy = m.invdy;
   P.phd = P.ph;
-  static_tables(d->degree, &P.tb);
+  double Dref[kMaxNodes1 * kMaxNodes1];
+  static_tables(d->degree, &P.tb, Dref);
   P.td = P.tb;
+  fill_scaled(Dref, P.td.w, P.td.l0, P.td.l1, d->degree, m.invdx, m.invdy, &P.ds);
   {
     const double kappa = dim == 2 ? 0.5 : 1.0;
     m.cflim[0] = 1.0 / (kappa * P.td.w[0] * m.dx);
