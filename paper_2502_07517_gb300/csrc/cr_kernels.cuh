@@ -405,9 +405,10 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     for (int v = 0; v < M; ++v) us[v] = AT(sA, v, k);
     source_eval<EQ>(us, dWx, dWy, Sa);
   }
+  const real dho = dt * (real(1) - a);  // per-thread constants, one rounding each
 #pragma unroll
   for (int v = 0; v < M; ++v) {
-    HO[v] = un[v] - dt * ((real(1) - a) * HO[v]);
+    HO[v] = un[v] - dho * HO[v];
     if (has_src) HO[v] += dt * Sa[v];
   }
 #pragma unroll
@@ -473,6 +474,9 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     for (int v = 0; v < M; ++v) xm[v] = xp[v] = ym[v] = yp[v] = un[v];
     if (m.limiter & kLimMH) {
       const real beta = real(2) - alpha;
+      // one-sided slopes scaled by beta (per-thread constants)
+      const real bmx = beta * tb.ihm[p], bpx = beta * tb.ihp[p];
+      const real bmy = DIM == 2 ? beta * tb.ihm[q] : real(0), bpy = DIM == 2 ? beta * tb.ihp[q] : real(0);
       real um[M], up[M], sx[M], sy[M];
       // x-line neighbours: the neighbour element's node across a face; at a
       // boundary the ghost node of that side: the own node (outflow), its
@@ -493,8 +497,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
                       : (nbL >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbL, N + n * q) : gx);
         up[v] = p < N ? AT(s0, v, k + 1)
                       : (nbR >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbR, n * q) : gx);
-        sx[v] = minmod3(beta * (un[v] - um[v]) * tb.ihm[p], (up[v] - um[v]) * tb.ihc[p],
-                        beta * (up[v] - un[v]) * tb.ihp[p]);
+        sx[v] = minmod3((un[v] - um[v]) * bmx, (up[v] - um[v]) * tb.ihc[p], (up[v] - un[v]) * bpx);
         sy[v] = real(0);
       }
       if (DIM == 2) {
@@ -513,8 +516,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
                         : (nbB >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbB, p + n * N) : gy);
           up[v] = q < N ? AT(s0, v, k + n)
                         : (nbT >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbT, p) : gy);
-          sy[v] = minmod3(beta * (un[v] - um[v]) * tb.ihm[q], (up[v] - um[v]) * tb.ihc[q],
-                          beta * (up[v] - un[v]) * tb.ihp[q]);
+          sy[v] = minmod3((un[v] - um[v]) * bmy, (up[v] - um[v]) * tb.ihc[q], (up[v] - un[v]) * bpy);
         }
       }
       real fxm[M], fxp[M], fym[M], fyp[M], Fm[M], Fp[M], Gm[M], Gp[M];
@@ -532,10 +534,12 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
         EQ::flux(fyp, 1, Gp, ph);
       }
       real ex[M], exm[M], exp_[M], eym[M], eyp[M];
+      const real hx = real(0.5) * dt * (tb.invw[p] * invdx);
+      const real hy = DIM == 2 ? real(0.5) * dt * (tb.invw[q] * invdy) : real(0);
 #pragma unroll
       for (int v = 0; v < M; ++v) {
-        ex[v] = real(0.5) * dt * (Fp[v] - Fm[v]) * tb.invw[p] * invdx;
-        if (DIM == 2) ex[v] += real(0.5) * dt * (Gp[v] - Gm[v]) * tb.invw[q] * invdy;
+        ex[v] = (Fp[v] - Fm[v]) * hx;
+        if (DIM == 2) ex[v] += (Gp[v] - Gm[v]) * hy;
         exm[v] = fxm[v] - ex[v];
         exp_[v] = fxp[v] - ex[v];
         eym[v] = fym[v] - ex[v];
@@ -598,13 +602,14 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     }
     __syncthreads();
     // low-order residual of the interior subfaces (eq. (low.order.update))
+    const real wx = tb.invw[p] * invdx, wy = DIM == 2 ? tb.invw[q] * invdy : real(0);
 #pragma unroll
     for (int v = 0; v < M; ++v) {
       real rx = (p < N ? AT(sB, v, k) : real(0)) - (p > 0 ? AT(sB, v, k - 1) : real(0));
-      LO[v] = rx * tb.invw[p] * invdx;
+      LO[v] = rx * wx;
       if (DIM == 2) {
         real ry = (q < N ? AT(sD, v, k) : real(0)) - (q > 0 ? AT(sD, v, k - n) : real(0));
-        LO[v] += ry * tb.invw[q] * invdy;
+        LO[v] += ry * wy;
       }
     }
     // face-node data for the face kernel: evolved boundary state u* and the
@@ -636,9 +641,10 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
 
   // ---------------- partial update --------------------------------------
   if (valid) {
+    const real dlo = dt * a;
 #pragma unroll
     for (int v = 0; v < M; ++v) {
-      const real val = HO[v] - dt * (a * LO[v]);
+      const real val = HO[v] - dlo * LO[v];
       P.b.P[((size_t)v * m.ne + e) * NP + k] = val;
     }
   }
@@ -1263,21 +1269,23 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
   const int iyT = DIM == 2 ? (m.bcy == 0 ? (iy + 1) % m.ny : iy + 1) : 0;
   const size_t nXf = (size_t)m.ny * m.nfx * NFN;
   const size_t nYf = DIM == 2 ? (size_t)m.nfy * m.nx * n : 0;
-  const real cRx = (one - a) * tb.gR[p] + (p == N ? a * tb.invw[N] : real(0));
-  const real cLx = (one - a) * tb.gL[p] - (p == 0 ? a * tb.invw[0] : real(0));
-  const real cRy = DIM == 2 ? (one - a) * tb.gR[q] + (q == N ? a * tb.invw[N] : real(0)) : real(0);
-  const real cLy = DIM == 2 ? (one - a) * tb.gL[q] - (q == 0 ? a * tb.invw[0] : real(0)) : real(0);
+  // correction weights of the face fluxes, dt/dx and dt/dy folded in
+  const real sx = dt * invdx, sy = DIM == 2 ? dt * invdy : real(0);
+  const real cRx = sx * ((one - a) * tb.gR[p] + (p == N ? a * tb.invw[N] : real(0)));
+  const real cLx = sx * ((one - a) * tb.gL[p] - (p == 0 ? a * tb.invw[0] : real(0)));
+  const real cRy = DIM == 2 ? sy * ((one - a) * tb.gR[q] + (q == N ? a * tb.invw[N] : real(0))) : real(0);
+  const real cLy = DIM == 2 ? sy * ((one - a) * tb.gL[q] - (q == 0 ? a * tb.invw[0] : real(0))) : real(0);
   const real W = DIM == 2 ? tb.w[p] * tb.w[q] : tb.w[p];
   real val[M];
 #pragma unroll
   for (int v = 0; v < M; ++v) {
     const real FxL = P.b.fx[v * nXf + ((size_t)iy * m.nfx + ix) * NFN + q];
     const real FxR = P.b.fx[v * nXf + ((size_t)iy * m.nfx + ixR) * NFN + q];
-    real x = P.b.P[((size_t)v * m.ne + ee) * NP + k] - dt * invdx * (FxR * cRx + FxL * cLx);
+    real x = P.b.P[((size_t)v * m.ne + ee) * NP + k] - FxR * cRx - FxL * cLx;
     if (DIM == 2) {
       const real GB = P.b.fy[v * nYf + ((size_t)iy * m.nx + ix) * n + p];
       const real GT = P.b.fy[v * nYf + ((size_t)iyT * m.nx + ix) * n + p];
-      x -= dt * invdy * (GT * cRy + GB * cLy);
+      x = x - GT * cRy - GB * cLy;
     }
     val[v] = x;
   }
