@@ -38,8 +38,8 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 # DRAM bytes (read + write) per element of the dominant kernel, from one ncu
 # capture of the current kernel (profiles/k_local_euler2d_384x384_N4_fp64.md:
-# 592.0 MB at 147,456 elements; the traffic scales with the element count).
-NCU_TRAFFIC_PER_ELEMENT = {("fp64", "k_local"): 592.00e6 / 147456}
+# 593.3 MB at 147,456 elements; the traffic scales with the element count).
+NCU_TRAFFIC_PER_ELEMENT = {("fp64", "k_local"): 593.33e6 / 147456}
 PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
