@@ -130,25 +130,21 @@ __device__ __forceinline__ size_t slot_index(int f, int side, int e, int j, int 
   return (((size_t)f * nside + side) * ne + e) * nfn + j;
 }
 
-// Per-element reductions over the element's threads (shared memory trees).
-// Tree reduction of W quantities per element; buf[(w * epb + el) * NP + k];
-// the result lands in buf[(w * epb + el) * NP].  Called by every thread.
+// Per-element reductions of W quantities per element over the element's
+// threads: buf[(w * epb + el) * NP + k] holds node k's value, and the result
+// lands in buf[(w * epb + el) * NP].  Called by every thread.  One thread per
+// (quantity, element) folds the NP values in node order: the W * epb folds sit
+// in the block's first warps, where a tree would make every warp issue each of
+// its levels with a few lanes active and wait at a barrier per level.
 template <int NP, int W, typename T, class Op>
 __device__ __forceinline__ void elem_tree(T* buf, int epb, int el, int k, Op op) {
-  int s = NP;
+  __syncthreads();
+  for (int t = threadIdx.x; t < W * epb; t += blockDim.x) {
+    T* b = buf + t * NP;  // t = w * epb + element
+    T acc = b[0];
 #pragma unroll
-  for (int lev = 0; lev < 6; ++lev) {
-    if (s <= 1) break;
-    const int h = (s + 1) >> 1;
-    __syncthreads();
-    if (k < s - h) {
-#pragma unroll
-      for (int w = 0; w < W; ++w) {
-        T* b = buf + (w * epb + el) * NP;
-        b[k] = op(b[k], b[k + h]);
-      }
-    }
-    s = h;
+    for (int i = 1; i < NP; ++i) acc = op(acc, b[i]);
+    b[0] = acc;
   }
   __syncthreads();
 }
