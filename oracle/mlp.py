@@ -100,7 +100,8 @@ def grad(params, X, t):
 
 
 def alpha_from_output(y):
-    """Clip of the indicator applied to the network output (reading R6/C-14)."""
+    """Clip of the indicator applied to the network output: below 1e-3 -> 0,
+    above 1 - 1e-3 -> 1."""
     y = np.asarray(y, dtype=np.float64).copy()
     y[y < 1e-3] = 0.0
     y[y > 1.0 - 1e-3] = 1.0

@@ -137,7 +137,7 @@ __device__ __forceinline__ size_t slot_index(int f, int side, int e, int j, int 
 // in the block's first warps, where a tree would make every warp issue each of
 // its levels with a few lanes active and wait at a barrier per level.
 template <int NP, int W, typename T, class Op>
-__device__ __forceinline__ void elem_tree(T* buf, int epb, int el, int k, Op op) {
+__device__ __forceinline__ void elem_reduce(T* buf, int epb, int el, int k, Op op) {
   __syncthreads();
   for (int t = threadIdx.x; t < W * epb; t += blockDim.x) {
     T* b = buf + t * NP;  // t = w * epb + element
@@ -444,14 +444,14 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     }
   }
   if constexpr (MIXED) {
-    // source contribution to the FP64 element mean, sum_k W_k S_k (tree sum;
-    // has_src is the same for the whole block)
+    // source contribution to the FP64 element mean, sum_k W_k S_k (per-element
+    // sum; has_src is the same for the whole block)
     if (has_src) {
       __syncthreads();
       const real W = DIM == 2 ? tb.w[p] * tb.w[q] : tb.w[p];
 #pragma unroll
       for (int v = 0; v < M; ++v) AT(sA, v, k) = W * Sa[v];
-      elem_tree<NP, M>(sA, epb, el, k, OpSum());
+      elem_reduce<NP, M>(sA, epb, el, k, OpSum());
       for (int v = k; valid && v < M; v += NP)
         P.b.smean[(size_t)v * m.ne + e] = double(sA[v * stride + el * NP]);
     } else {
@@ -1009,11 +1009,12 @@ __global__ void k_face(const __grid_constant__ KParams<real> P) {
 
 // ===========================================================================
 // Element-level helpers for k_update / k_prologue (one thread per node, EPB
-// elements per block).  Per-element reductions are trees over the element's
-// threads in shared memory, so that no loop runs on a single lane (a warp
+// elements per block).  Per-element scalar work runs side by side in the
+// block's first threads rather than on one lane per element (a warp
 // instruction costs the FP64 pipe the same with 1 or 32 active lanes).
 
-// Smoothness indicator of one element (Hennemann form, see R6 of the readings):
+// Smoothness indicator of one element (the Hennemann et al. form, with T(N) and s
+// of Mesh::T_ind, Mesh::s_ind):
 // eps at the nodes in E[el*NP + k] -> Legendre modes -> energy fractions ->
 // logistic alpha, returned on thread k = 0 of the element.  T is the
 // arithmetic type (double in FP64 mode, float in FP32_BULK mode).
@@ -1106,7 +1107,7 @@ __device__ T indicator_alpha(const Mesh& m, const Tab<T>& tb, T* E, T* Tm, T* re
   red[(1 * epb + el) * NP + k] = mx == N ? e2 : T(0);
   red[(2 * epb + el) * NP + k] = mx <= N - 1 ? e2 : T(0);
   red[(3 * epb + el) * NP + k] = mx == N - 1 ? e2 : T(0);
-  elem_tree<NP, 4>(red, epb, el, k, OpSum());
+  elem_reduce<NP, 4>(red, epb, el, k, OpSum());
   const T tot = red[(0 * epb + el) * NP];
   // the energy ratios and the logistic of every element of the block, side by
   // side in its first epb threads (one warp) rather than in thread 0 of each
@@ -1288,7 +1289,7 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
   real m32[M];
   double ubar[M];
   if constexpr (MIXED) {
-    // FP32 mean of the nodal update (re-centring), tree sum
+    // FP32 mean of the nodal update (re-centring), per-element sum
     real* fRed = reinterpret_cast<real*>(sRed);
 #pragma unroll
     for (int v = 0; v < M; ++v) fRed[(v * epb + el) * NP + k] = W * val[v];
@@ -1314,7 +1315,7 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
       }
       fI[el * NSIDE * M + t] = acc;
     }
-    elem_tree<NP, M>(fRed, epb, el, k, OpSum());
+    elem_reduce<NP, M>(fRed, epb, el, k, OpSum());
     // conservative FP64 mean update of eq. (upmean), one thread per variable
     for (int v = k; v < M; v += NP) {
       const real* I = fI + el * NSIDE * M;
@@ -1332,7 +1333,7 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
   } else {
 #pragma unroll
     for (int v = 0; v < M; ++v) RED(v) = double(W) * double(val[v]);
-    elem_tree<NP, M>(sRed, epb, el, k, OpSum());
+    elem_reduce<NP, M>(sRed, epb, el, k, OpSum());
 #pragma unroll
     for (int v = 0; v < M; ++v) ubar[v] = RED0(v);
     for (int v = k; v < M; v += NP) sEl[el * 16 + 4 + v] = RED0(v);  // for the CFL rate
@@ -1451,7 +1452,7 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
       int np2 = 1;
       __syncthreads();
       RED(0) = need ? 0.0 : 1.0;
-      elem_tree<NP, 1>(sRed, epb, el, k, OpMin());
+      elem_reduce<NP, 1>(sRed, epb, el, k, OpMin());
       const bool elem_need = RED0(0) == 0.0;
       __syncthreads();
 #pragma unroll
@@ -1485,7 +1486,7 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
       double rmin = pts[0][0];
       for (int t = 1; t < np2; ++t) rmin = fmin(rmin, pts[t][0]);
       RED(0) = rmin;
-      elem_tree<NP, 1>(sRed, epb, el, k, OpMin());
+      elem_reduce<NP, 1>(sRed, epb, el, k, OpMin());
       rmin = RED0(0);
       __syncthreads();
       if (mean_ok && rmin < eps1) {
@@ -1507,7 +1508,7 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
           tmin = fmin(tmin, lo);
         }
       RED(0) = tmin;
-      elem_tree<NP, 1>(sRed, epb, el, k, OpMin());
+      elem_reduce<NP, 1>(sRed, epb, el, k, OpMin());
       const double th2 = RED0(0);
       __syncthreads();
       if (th2 < 1.0)
@@ -1629,7 +1630,7 @@ __global__ void k_prologue(const __grid_constant__ KParams<real> P) {
     atomicOr(&P.b.ctl->status, bad);
     atomicMin(&P.b.ctl->bad_elem, e);
   }
-  elem_tree<NP, M>(sRed, epb, el, k, OpSum());
+  elem_reduce<NP, M>(sRed, epb, el, k, OpSum());
   double ubar[M];
 #pragma unroll
   for (int v = 0; v < M; ++v) ubar[v] = sRed[(v * epb + el) * NP];
