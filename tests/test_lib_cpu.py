@@ -173,3 +173,17 @@ def test_time_dependent_boundary_descriptors(built):
     d = crkfr.desc_from_problem(pe)
     d.bc_time_terms, d.bc_time_span[1] = 4, 1.0
     assert _rejected(d)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the compiled library every entry point raises: there is no
+    fallback that computes anything elsewhere."""
+    monkeypatch.setattr(crkfr, "_lib", None)
+    monkeypatch.setattr(crkfr, "LIB_PATH", str(tmp_path / "libcrkfr.so"))
+    with pytest.raises(RuntimeError, match="libcrkfr.so is missing"):
+        crkfr.lib()
+    with pytest.raises(RuntimeError, match="libcrkfr.so is missing"):
+        crkfr.cr_cfl_number(3)
+    prob, _ = wl.euler2d_vortex(nx=4, ny=4, degree=3)
+    with pytest.raises(RuntimeError, match="libcrkfr.so is missing"):
+        crkfr.cr_init_mesh(crkfr.desc_from_problem(prob))
