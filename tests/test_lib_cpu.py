@@ -9,6 +9,7 @@ import pytest
 
 from paper_2502_07517_gb300 import build as lib_build
 from paper_2502_07517_gb300 import crkfr
+from paper_2502_07517_gb300 import workloads as wl
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
