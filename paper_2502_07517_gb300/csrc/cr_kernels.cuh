@@ -206,10 +206,8 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   const double dtd = P.b.ctl->dt_step;
   if (!(dtd > 0.0)) return;
   const real dt = sizeof(real) == 4 ? real(P.b.ctl->dt_step_f) : real(dtd);
-  // positions along x, for a flux that depends on them (variable advection):
-  // the element's left face, and the node
+  // position of the node along x, for a flux that depends on it (variable advection)
   constexpr bool XDEP = IsVarAdv<EQ>::value;
-  const real xe = XDEP ? real(m.x0 + ix * m.dx) : real(0);
   const real xnode = XDEP ? real(m.x0 + (ix + double(tb.xi[p])) * m.dx) : real(0);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
