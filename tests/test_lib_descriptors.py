@@ -1,7 +1,7 @@
 """Property test of the library's descriptor checks (host only, no device
 work): seeded random descriptors, each field usually valid and sometimes not,
 are either accepted (positive workspace size) or refused with
-CR_E_INVALID_ARG, never anything else, and the verdict equals the documented
+CR_E_INVALID_ARG, never anything else, and the decision equals the documented
 rules restated here: walls and HLLC only for Euler, HLLC not with D1,
 Gauss-Lobatto points without the blending and flux limiters, Burgers and
 variable advection 1D, gravity only for Euler, time-dependent ghost states
@@ -147,7 +147,7 @@ def _expected_ok(f):
     return 0 <= f["limiter"] <= 31
 
 
-def test_descriptor_verdicts():
+def test_descriptor_decisions():
     r = random.Random(20250207)
     accepted = refused = 0
     for i in range(4000):
@@ -162,5 +162,5 @@ def test_descriptor_verdicts():
         assert ok == _expected_ok(f), (i, f, ok)
         accepted += ok
         refused += not ok
-    # both verdicts are exercised in quantity
+    # both decisions are exercised in quantity
     assert accepted > 400 and refused > 400, (accepted, refused)
