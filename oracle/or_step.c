@@ -276,26 +276,34 @@ static double indicator_variable(const or_desc* d, const double* u) {
   return rho * 0.5 * (p11 + p22);
 }
 
-void or_modal_energies(const or_desc* d, const double* ue, double* e) {
-  ctx c;
-  ctx_init(&c, d);
-  const int n = c.n;
-  double eps[NPMAX], m[NPMAX], tot = 0.0;
-  for (int k = 0; k < c.np; ++k) eps[k] = indicator_variable(d, ue + k * c.M);
-  for (int k = 0; k < c.np; ++k) {
+/* Legendre modes of the indicator variable of one element, m[i + n j] for the
+ * x-mode i and the y-mode j (j = 0 in 1D): the indicator's own modes, which
+ * both the indicator and the learned alpha's inputs are built from. */
+static void indicator_modes(const ctx* c, const or_desc* d, const double* ue, double* m) {
+  const int n = c->n;
+  double eps[NPMAX];
+  for (int k = 0; k < c->np; ++k) eps[k] = indicator_variable(d, ue + k * c->M);
+  for (int k = 0; k < c->np; ++k) {
     int i = k % n, j = k / n;
     double acc = 0.0;
-    if (c.dim == 1) {
-      for (int p = 0; p < n; ++p) acc += c.w[p] * eps[p] * legendre01(i, c.xi[p]);
+    if (c->dim == 1) {
+      for (int p = 0; p < n; ++p) acc += c->w[p] * eps[p] * legendre01(i, c->xi[p]);
       m[k] = (2.0 * i + 1.0) * acc;
     } else {
       for (int p = 0; p < n; ++p)
         for (int q = 0; q < n; ++q)
-          acc += c.w[p] * c.w[q] * eps[node(&c, p, q)] * legendre01(i, c.xi[p]) * legendre01(j, c.xi[q]);
+          acc += c->w[p] * c->w[q] * eps[node(c, p, q)] * legendre01(i, c->xi[p]) * legendre01(j, c->xi[q]);
       m[k] = (2.0 * i + 1.0) * (2.0 * j + 1.0) * acc;
     }
-    tot += m[k] * m[k];
   }
+}
+
+void or_modal_energies(const or_desc* d, const double* ue, double* e) {
+  ctx c;
+  ctx_init(&c, d);
+  double m[NPMAX], tot = 0.0;
+  indicator_modes(&c, d, ue, m);
+  for (int k = 0; k < c.np; ++k) tot += m[k] * m[k];
   for (int k = 0; k < c.np; ++k) e[k] = tot > 0.0 ? m[k] * m[k] / tot : 0.0;
 }
 
@@ -303,16 +311,10 @@ double or_indicator(const or_desc* d, const double* ue) {
   ctx c;
   ctx_init(&c, d);
   const int n = c.n, N = c.N;
-  double eps[NPMAX];
-  for (int k = 0; k < c.np; ++k) eps[k] = indicator_variable(d, ue + k * c.M);
+  double m[NPMAX];
+  indicator_modes(&c, d, ue, m);
   double E;
   if (c.dim == 1) {
-    double m[NMAX];
-    for (int j = 0; j < n; ++j) {
-      double acc = 0.0;
-      for (int p = 0; p < n; ++p) acc += c.w[p] * eps[p] * legendre01(j, c.xi[p]);
-      m[j] = (2.0 * j + 1.0) * acc;
-    }
     double tot = 0.0, tot1 = 0.0;
     for (int j = 0; j <= N; ++j) tot += m[j] * m[j];
     for (int j = 0; j <= N - 1; ++j) tot1 += m[j] * m[j];
@@ -320,20 +322,10 @@ double or_indicator(const or_desc* d, const double* ue) {
     double r2 = (N >= 2 && tot1 > 0.0) ? m[N - 1] * m[N - 1] / tot1 : 0.0;
     E = fmax(r1, r2);
   } else {
-    double m[NMAX][NMAX];
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        double acc = 0.0;
-        for (int p = 0; p < n; ++p)
-          for (int q = 0; q < n; ++q)
-            acc += c.w[p] * c.w[q] * eps[node(&c, p, q)] * legendre01(i, c.xi[p]) *
-                   legendre01(j, c.xi[q]);
-        m[i][j] = (2.0 * i + 1.0) * (2.0 * j + 1.0) * acc;
-      }
     double tot = 0.0, top = 0.0, low = 0.0, top1 = 0.0;
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) {
-        double e2 = m[i][j] * m[i][j];
+        double e2 = m[i + n * j] * m[i + n * j];
         int mx = i > j ? i : j;
         tot += e2;
         if (mx == N) top += e2;

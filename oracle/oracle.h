@@ -16,10 +16,13 @@
  * Pins (tests/test_oracle_pins.py, tests/test_oracle_mlp.py): closed forms,
  * exact solutions, invariants and brute force for every step of the scheme.
  * The smoothness indicator (or_indicator) follows a method the paper cites
- * without printing it; its constants are readings.  It is pinned only by
- * special cases (constant and linear data give 0, a jump gives 1) and its
- * modal energies (or_modal_energies) by pure Legendre modes: beyond these,
- * parity unpinned.
+ * without printing it (Sec. 4); its constants are readings of the cited
+ * method.  It is pinned (tests/test_oracle_indicator.py) by elements made of
+ * chosen Legendre modes, whose energy ratio is known in closed form and set to
+ * the threshold and 5% either side of it, through the top ratio, the
+ * next-to-top ratio or both, in 1D and 2D for N = 2, 3, 4; and by special
+ * cases (constant and linear data give 0, a jump gives 1).  or_indicator and
+ * or_modal_energies compute their modes with the same routine.
  *
  * Layout of a state vector: u[(v * Ne + e) * Np + k], variable v, element
  * e = ix + nx * iy, node k = p + (N + 1) * q (p along x, q along y).
