@@ -295,10 +295,12 @@ cr_status cr_reference_tables_points(int degree, int points, double* xi, double*
  * the start of each call), so calls whose work overlaps on the GPU race.
  * Errors: CR_E_INVALID_ARG (bad desc, NULL pointer, dt <= 0),
  * CR_E_UNSUPPORTED, CR_E_TOO_LARGE, CR_E_INVALID_STATE (inadmissible input),
- * CR_E_INADMISSIBLE, CR_E_CUDA. */
+ * CR_E_INADMISSIBLE, CR_E_CUDA; cr_last_error(NULL) returns the failure's
+ * message. */
 cr_status cr_step_static(const cr_mesh_desc* desc, const double* u_in, double* u_out, double dt);
 
-/* Last error message of ctx (or of the last failed cr_init_mesh when ctx is NULL). */
+/* Last error message of ctx (or, when ctx is NULL, of the last failed call
+ * without a context: cr_init_mesh, cr_workspace_bytes or cr_step_static). */
 const char* cr_last_error(const cr_ctx* ctx);
 
 /* ---------------------------------------------------------------------------

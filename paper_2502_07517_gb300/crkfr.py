@@ -288,12 +288,34 @@ def cr_profile_steps(ctx, max_steps, t_final, dt_fixed=0.0):
     return ms
 
 
+def _state_numel(desc):
+    """M * Ne * Np of a description."""
+    M = {CR_EQ_LINADV: 1, CR_EQ_BURGERS: 1, CR_EQ_VARADV: 1, CR_EQ_TENMOMENT: 6}.get(
+        desc.equation, 3 if desc.dim == 1 else 4)
+    ne = desc.nx * (desc.ny if desc.dim == 2 else 1)
+    return M * ne * (desc.degree + 1) ** desc.dim
+
+
 def cr_step_static(desc, u_in, u_out, dt):
     """One FP64 step with the library's fixed scratch array (no allocation);
-    u_in, u_out are torch float64 CUDA tensors [M][Ne][Np]."""
-    st = lib().cr_step_static(ctypes.byref(desc), u_in.data_ptr(), u_out.data_ptr(), float(dt))
+    u_in, u_out are contiguous torch float64 tensors [M][Ne][Np] on the
+    current CUDA device, the same tensor or disjoint ones.  Anything else is
+    refused with CR_E_INVALID_ARG before the library sees the pointers."""
+    import torch
+    want = _state_numel(desc)
+    for name, t in (("u_in", u_in), ("u_out", u_out)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.is_contiguous() and t.numel() == want
+                and t.device.index == torch.cuda.current_device()):
+            raise CrError(-1, "cr_step_static: %s must be a contiguous float64 tensor of %d values "
+                              "on the current CUDA device" % (name, want))
+    a0, b0 = u_in.data_ptr(), u_out.data_ptr()
+    nbytes = want * 8
+    if a0 != b0 and a0 < b0 + nbytes and b0 < a0 + nbytes:
+        raise CrError(-1, "cr_step_static: u_in and u_out overlap without being the same tensor")
+    st = lib().cr_step_static(ctypes.byref(desc), a0, b0, float(dt))
     if st != CR_OK:
-        raise CrError(st, "cr_step_static")
+        raise CrError(st, lib().cr_last_error(None).decode())
 
 
 def cr_mlp_param_count(nin):

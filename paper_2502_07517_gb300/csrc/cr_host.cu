@@ -535,9 +535,10 @@ cr_status cuda_fail(cr_ctx* c, cudaError_t e, const char* where) {
     if (_e != cudaSuccess) return cuda_fail((c), _e, #call); \
   } while (0)
 
+// Mesh, physics and table parameters of the kernels for a description
+// (everything but the buffers).
 template <typename real>
-void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
-  const cr_mesh_desc& d = c->d;
+void fill_desc_params(const cr_mesh_desc& d, KParams<real>* P, const HostTables& h) {
   Mesh& m = P->m;
   memset(&m, 0, sizeof(m));
   m.nx = d.nx;
@@ -602,6 +603,11 @@ void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
   fill_tab(h, &P->tb);
   fill_tab(h, &P->td);
   fill_scaled(h.D, h.w, h.l0, h.l1, d.degree, m.invdx, m.invdy, &P->ds);
+}
+
+template <typename real>
+void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
+  fill_desc_params(c->d, P, h);
   Bufs<real>& b = P->b;
   unsigned char* w = c->ws;
   b.ctl = reinterpret_cast<TimeCtl*>(w + c->L.ctl);
@@ -674,6 +680,22 @@ cr_status launch_steps(cr_ctx* c, int n) {
 }
 
 }  // namespace
+
+namespace crk {
+
+// The kernel parameters of a description as a context sets them, in FP64,
+// without the buffers (cr_step_static points those at its own scratch).
+void fill_static_params(const cr_mesh_desc* d, KParams<double>* P) {
+  HostTables h;
+  build_tables(d->degree, d->points, &h);
+  fill_desc_params(*d, P, h);
+}
+
+// The message cr_last_error(NULL) returns, for the entry points without a
+// context.
+void record_global_error(const std::string& msg) { g_init_error = msg; }
+
+}  // namespace crk
 
 // ===========================================================================
 extern "C" {

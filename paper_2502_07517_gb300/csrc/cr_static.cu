@@ -21,9 +21,11 @@
 #include "cr_launch.cuh"
 
 namespace crk {
-// Per-side boundary types, ghost states and gravity of the kernels' Mesh
-// (defined with the context code).
-void fill_mesh_extras(const cr_mesh_desc* d, Mesh* m);
+// Defined with the context code: the kernel parameters of a description
+// without the buffers (the same routine a context uses), and the message
+// cr_last_error(NULL) returns.
+void fill_static_params(const cr_mesh_desc* d, KParams<double>* P);
+void record_global_error(const std::string& msg);
 }  // namespace crk
 
 using namespace crk;
@@ -42,8 +44,11 @@ unsigned char* g_static_ptr[kMaxDevices] = {};
 
 size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// The status code is the whole report; the message documents the cause here.
-cr_status static_fail(cr_status st, const std::string&) { return st; }
+// The status code, with its message kept for cr_last_error(NULL).
+cr_status static_fail(cr_status st, const std::string& msg) {
+  record_global_error(msg);
+  return st;
+}
 
 __global__ void k_static_reset(TimeCtl* c, double dt) {
   c->t = 0.0;
@@ -59,62 +64,6 @@ __global__ void k_static_reset(TimeCtl* c, double dt) {
   c->dt_step = 0.0;
   c->dt_step_f = 0.0f;
   c->last_step = 0;
-}
-
-// Reference tables of degree N from the public host routine, plus the derived
-// per-kernel tables (same definitions as the context path); D receives the
-// differentiation matrix (n x n).
-void static_tables(int N, Tab<double>* t, double* D) {
-  const int n = N + 1;
-  double xi[kMaxNodes1], w[kMaxNodes1];
-  cr_reference_tables(N, xi, w, D);
-  double lam[kMaxNodes1], l0[kMaxNodes1], l1[kMaxNodes1];
-  for (int j = 0; j < n; ++j) {
-    double prod = 1.0;
-    for (int m = 0; m < n; ++m)
-      if (m != j) prod *= xi[j] - xi[m];
-    lam[j] = 1.0 / prod;
-  }
-  for (int side = 0; side < 2; ++side) {
-    double den = 0.0;
-    for (int m = 0; m < n; ++m) den += lam[m] / (side - xi[m]);
-    for (int j = 0; j < n; ++j) (side ? l1 : l0)[j] = lam[j] / (side - xi[j]) / den;
-  }
-  memset(t, 0, sizeof(*t));
-  double X[kMaxNodes1 + 2];
-  X[0] = xi[N] - 1.0;
-  for (int p = 0; p < n; ++p) X[p + 1] = xi[p];
-  X[n + 1] = 1.0 + xi[0];
-  double xs = 0.0;
-  for (int p = 0; p < n; ++p) {
-    t->xi[p] = xi[p];
-    t->w[p] = w[p];
-    t->invw[p] = 1.0 / w[p];
-    t->l0[p] = l0[p];
-    t->l1[p] = l1[p];
-    t->gR[p] = l1[p] / w[p];
-    t->gL[p] = -l0[p] / w[p];
-    t->xs[p] = xs;
-    t->dm[p] = xs - xi[p];
-    t->dp[p] = xs + w[p] - xi[p];
-    xs += w[p];
-    t->ihm[p] = 1.0 / (X[p + 1] - X[p]);
-    t->ihp[p] = 1.0 / (X[p + 2] - X[p + 1]);
-    t->ihc[p] = 1.0 / (X[p + 2] - X[p]);
-  }
-  t->xs[n] = xs;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      double pm = 1.0, pc = 2.0 * xi[j] - 1.0, x = pc;  // Legendre L_i(2 xi_j - 1)
-      double Li = (i == 0) ? 1.0 : x;
-      for (int k = 2; k <= i; ++k) {
-        const double pn = ((2 * k - 1) * x * pc - (k - 1) * pm) / k;
-        pm = pc;
-        pc = pn;
-        Li = pc;
-      }
-      t->V[i * n + j] = (2.0 * i + 1.0) * w[j] * Li;
-    }
 }
 
 }  // namespace
@@ -196,56 +145,7 @@ extern "C" cr_status cr_step_static(const cr_mesh_desc* d, const double* u_in, d
 
   KParams<double> P;
   memset(&P, 0, sizeof(P));
-  Mesh& m = P.m;
-  m.nx = (int)nx;
-  m.ny = (int)ny;
-  m.ne = (int)ne;
-  m.nfx = (int)nfx;
-  m.nfy = (int)nfy;
-  m.bcx = d->bc_x;
-  m.bcy = dim == 2 ? d->bc_y : 0;
-  m.x0 = d->x0;
-  m.y0 = dim == 2 ? d->y0 : 0.0;
-  m.dx = (d->x1 - d->x0) / d->nx;
-  m.dy = dim == 2 ? (d->y1 - d->y0) / d->ny : 1.0;
-  m.invdx = 1.0 / m.dx;
-  m.invdy = dim == 2 ? 1.0 / m.dy : 0.0;
-  m.limiter = d->limiter;
-  m.alpha_mode = d->alpha_mode;
-  m.alpha_fixed = d->alpha_fixed;
-  m.gamma = d->gamma;
-  m.ax = d->adv[0];
-  m.ay = d->adv[1];
-  m.source = d->source;
-  m.src_amp = d->src_amp;
-  m.src_k = d->src_k;
-  m.src_cx = d->src_cx;
-  m.src_cy = d->src_cy;
-  fill_mesh_extras(d, &m);
-  m.T_ind = 0.5 * std::pow(10.0, -1.8 * std::pow(d->degree + 1.0, 0.25));
-  m.s_ind = std::log((1.0 - 1e-4) / 1e-4);
-  P.ph.gamma = d->gamma;
-  P.ph.gm1 = d->gamma - 1.0;
-  P.ph.ax = d->adv[0];
-  P.ph.ay = d->adv[1];
-  P.ph.a0 = d->adv_poly[0];
-  P.ph.a1 = d->adv_poly[1];
-  P.ph.a2 = d->adv_poly[2];
-  P.ph.a3 = d->adv_poly[3];
-  P.ph.invdx = m.invdx;
-  P.ph.invdy = m.invdy;
-  P.phd = P.ph;
-  double Dref[kMaxNodes1 * kMaxNodes1];
-  static_tables(d->degree, &P.tb, Dref);
-  P.td = P.tb;
-  fill_scaled(Dref, P.td.w, P.td.l0, P.td.l1, d->degree, m.invdx, m.invdy, &P.ds);
-  {
-    const double kappa = dim == 2 ? 0.5 : 1.0;
-    m.cflim[0] = 1.0 / (kappa * P.td.w[0] * m.dx);
-    m.cflim[1] = 1.0 / (kappa * P.td.w[d->degree] * m.dx);
-    m.cflim[2] = 1.0 / (kappa * P.td.w[0] * m.dy);
-    m.cflim[3] = 1.0 / (kappa * P.td.w[d->degree] * m.dy);
-  }
+  fill_static_params(d, &P);
   P.b.ctl = reinterpret_cast<TimeCtl*>(base + o_ctl);
   P.b.u = u_out;
   P.b.umean = nullptr;

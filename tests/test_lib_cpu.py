@@ -62,6 +62,26 @@ def test_invalid_descriptor_rejected(built):
     assert crkfr.cr_workspace_bytes(d) > 0
 
 
+def test_static_step_wrapper_refuses_bad_tensors(built):
+    """The cr_step_static binding hands the library no pointer it cannot use:
+    host tensors, a wrong dtype or size, or a non-contiguous layout are refused
+    with CR_E_INVALID_ARG before the library is called."""
+    import torch
+    prob, u = wl.euler2d_vortex(nx=4, ny=3, degree=3, seed=0)
+    d = crkfr.desc_from_problem(prob)
+    good = torch.from_numpy(u)
+    bad = [good, good.float(), good[:, :, :-1], good.transpose(1, 2), np.asarray(u)]
+    for t in bad:
+        with pytest.raises(crkfr.CrError) as ei:
+            crkfr.cr_step_static(d, t, t, 1e-3)
+        assert ei.value.status == -1
+    assert crkfr._state_numel(d) == u.size
+    prob1, u1 = wl.euler1d_riemann(nx=7, degree=4, seed=0)
+    assert crkfr._state_numel(crkfr.desc_from_problem(prob1)) == u1.size
+    prob2, u2 = wl.tenmoment2d_voronoi(nx=5, ny=4, degree=2, seed=0)
+    assert crkfr._state_numel(crkfr.desc_from_problem(prob2)) == u2.size
+
+
 @pytest.mark.parametrize("N", [1, 2, 3, 4])
 def test_library_cfl_for_dissipation_models_matches_oracle(N):
     from oracle.cfl import cfl_number
