@@ -287,6 +287,67 @@ def l1_rel(g, ref):
             for v in range(ref.shape[0])]
 
 
+def phys_flux(prob, u, direction):
+    """Physical flux of the conserved state u [M][Ne][Np] (Euler, ten-moment):
+    only used to scale differences, never on the step's path."""
+    rho = u[0]
+    if prob["equation"] == "euler":
+        g1 = prob["gamma"] - 1.0
+        if prob["dim"] == 1:
+            v = u[1] / rho
+            p = g1 * (u[2] - 0.5 * u[1] * v)
+            return np.stack([u[1], u[1] * v + p, (u[2] + p) * v])
+        v1, v2 = u[1] / rho, u[2] / rho
+        p = g1 * (u[3] - 0.5 * (u[1] * v1 + u[2] * v2))
+        vn = v1 if direction == 0 else v2
+        return np.stack([u[1 + direction], u[1] * vn + (p if direction == 0 else 0.0),
+                         u[2] * vn + (p if direction == 1 else 0.0), (u[3] + p) * vn])
+    v1, v2 = u[1] / rho, u[2] / rho
+    p11, p12, p22 = 2 * u[3] - u[1] * v1, 2 * u[4] - u[1] * v2, 2 * u[5] - u[2] * v2
+    if direction == 0:
+        return np.stack([u[1], p11 + u[1] * v1, p12 + u[1] * v2, (u[3] + p11) * v1,
+                         u[4] * v1 + 0.5 * (p11 * v2 + p12 * v1), u[5] * v1 + p12 * v2])
+    return np.stack([u[2], p12 + u[1] * v2, p22 + u[2] * v2, u[3] * v2 + p12 * v1,
+                     u[4] * v2 + 0.5 * (p12 * v2 + p22 * v1), (u[5] + p22) * v2])
+
+
+def l1_flux_scaled(prob, g, ref, steps, dt):
+    """Per variable: mean |g - ref| over the points divided by the larger of
+    the variable's mean magnitude and its flux increment over the run,
+    steps dt (max|f_v|/dx + max|g_v|/dy).  A variable that starts at zero and
+    moves only through O(1) fluxes (a transverse momentum) is then measured
+    against the size of what moves it, as the parity tests do."""
+    dx = (prob["x1"] - prob["x0"]) / prob["nx"]
+    inc = np.abs(phys_flux(prob, ref, 0)).max(axis=(1, 2)) / dx
+    if prob["dim"] == 2:
+        inc = inc + np.abs(phys_flux(prob, ref, 1)).max(axis=(1, 2)) / ((prob["y1"] - prob["y0"]) / prob["ny"])
+    inc = inc * steps * dt
+    return [float(np.abs(g[v] - ref[v]).mean() / max(np.abs(ref[v]).mean(), inc[v], 1e-300))
+            for v in range(ref.shape[0])]
+
+
+def alpha_agreement(prob, state, params, stream):
+    """Raw blending coefficients of the network and of the indicator on the
+    same state (FP64 contexts): the fraction of elements where they differ by
+    more than 0.1, the largest difference, and the fraction of elements where
+    the indicator is active (alpha > 0)."""
+    from paper_2502_07517_gb300 import crkfr
+    ne, npn = state.shape[1], state.shape[2]
+    out = {}
+    for name, mode in (("indicator", crkfr.CR_ALPHA_INDICATOR), ("network", crkfr.CR_ALPHA_MLP)):
+        c = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, alpha_mode=mode, stream=stream))
+        if mode == crkfr.CR_ALPHA_MLP:
+            crkfr.cr_mlp_load(c, params)
+        crkfr.cr_set_state(c, state)
+        out[name] = crkfr.cr_get_features(c, ne, npn)[1]
+        crkfr.cr_destroy(c)
+    d = np.abs(out["network"] - out["indicator"])
+    return {"elements": int(ne), "frac_disagree_gt_0.1": float((d > 0.1).mean()),
+            "max_abs_diff": float(d.max()), "mean_abs_diff": float(d.mean()),
+            "frac_indicator_active": float((out["indicator"] > 0).mean()),
+            "frac_network_active": float((out["network"] > 0).mean())}
+
+
 def fp32_variants(prob, u, ctx64, steps, warmup, stream, fp64_ms):
     """FP32 bulk with the indicator's alpha and with the learned alpha: device
     time per step on the same workload, and the normalised L1 difference per
@@ -315,8 +376,10 @@ def fp32_variants(prob, u, ctx64, steps, warmup, stream, fp64_ms):
         a = crkfr.cr_get_alpha(ctx, u.shape[1])
         out[name] = {"value": nodes / (ms * 1e-3), "unit": "DOF-updates/s", "ms_per_step": ms,
                      "speedup_vs_fp64": fp64_ms / ms, "l1_rel_vs_fp64": l1_rel(g, ref),
+                     "l1_flux_scaled_vs_fp64": l1_flux_scaled(prob, g, ref, steps, dt0),
                      "alpha_mean": float(a.mean()), "alpha_max": float(a.max())}
         crkfr.cr_destroy(ctx)
+    out["alpha_agreement_after_run"] = alpha_agreement(prob, ref, params, stream.cuda_stream)
     return out
 
 
@@ -361,22 +424,35 @@ def config_legs(steps, warmup):
         ref = crkfr.cr_get_state(c64, shape=u.shape)
         params, info = train_alpha_network(prob["degree"], sp, seeds=seeds, snaps=snaps, make=make,
                                            label=nin_label)
-        c32 = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, precision=crkfr.CR_FP32_BULK,
-                                                         alpha_mode=crkfr.CR_ALPHA_MLP, stream=sp))
-        crkfr.cr_mlp_load(c32, params)
-        crkfr.cr_set_state(c32, u)
-        ms32 = timed_steps(c32, steps, warmup, stream)
-        crkfr.cr_set_state(c32, u)
-        crkfr.cr_step(c32, steps, 1e300, dt0)
-        g = crkfr.cr_get_state(c32, shape=u.shape)
-        out[name] = {"dofs": nodes, "steps": steps,
+        out[name] = {"dofs": nodes, "steps": steps, "dt": dt0,
                      "fp64": {"value": nodes / (ms64 * 1e-3), "ms_per_step": ms64},
-                     "fp32_learned_alpha": {"value": nodes / (ms32 * 1e-3), "ms_per_step": ms32,
-                                            "speedup_vs_fp64": ms64 / ms32,
-                                            "l1_rel_vs_fp64": l1_rel(g, ref)},
-                     "alpha_network": info, "unit": "DOF-updates/s"}
-        for c in (c64, c32):
-            crkfr.cr_destroy(c)
+                     "alpha_network": info, "unit": "DOF-updates/s",
+                     "l1_reference": "FP64 path (indicator alpha) after the same steps at the same dt"}
+        for label, mode in (("fp32_indicator", crkfr.CR_ALPHA_INDICATOR),
+                            ("fp32_learned_alpha", crkfr.CR_ALPHA_MLP)):
+            c32 = crkfr.cr_init_mesh(crkfr.desc_from_problem(prob, precision=crkfr.CR_FP32_BULK,
+                                                             alpha_mode=mode, stream=sp))
+            if mode == crkfr.CR_ALPHA_MLP:
+                crkfr.cr_mlp_load(c32, params)
+            crkfr.cr_set_state(c32, u)
+            ms32 = timed_steps(c32, steps, warmup, stream)
+            crkfr.cr_set_state(c32, u)
+            crkfr.cr_step(c32, steps, 1e300, dt0)
+            g = crkfr.cr_get_state(c32, shape=u.shape)
+            a = crkfr.cr_get_alpha(c32, u.shape[1])
+            out[name][label] = {"value": nodes / (ms32 * 1e-3), "ms_per_step": ms32,
+                                "speedup_vs_fp64": ms64 / ms32, "l1_rel_vs_fp64": l1_rel(g, ref),
+                                "l1_flux_scaled_vs_fp64": l1_flux_scaled(prob, g, ref, steps, dt0),
+                                "alpha_mean": float(a.mean()), "alpha_frac_nonzero": float((a > 0).mean())}
+            crkfr.cr_destroy(c32)
+        li, ll = out[name]["fp32_indicator"], out[name]["fp32_learned_alpha"]
+        out[name]["learned_vs_indicator"] = {
+            "time_ratio": ll["ms_per_step"] / li["ms_per_step"],
+            "l1_flux_scaled_ratio_max_over_vars": max(
+                a / max(b, 1e-300) for a, b in zip(ll["l1_flux_scaled_vs_fp64"], li["l1_flux_scaled_vs_fp64"])),
+            "alpha_agreement_on_initial_state": alpha_agreement(prob, u, params, sp),
+            "alpha_agreement_after_run": alpha_agreement(prob, ref, params, sp)}
+        crkfr.cr_destroy(c64)
 
     prob, u = wl.euler1d_riemann(nx=4000, degree=4, seed=0)
     leg("euler1d_riemann_4000_N4", prob, u,
@@ -443,7 +519,8 @@ def widened_legs(steps, warmup, stream):
         out[name] = {"dofs": nodes, "steps": steps, "unit": "DOF-updates/s",
                      "fp64": {"ms_per_step": ms64, "value": nodes / (ms64 * 1e-3)},
                      "fp32_indicator": {"ms_per_step": ms32, "value": nodes / (ms32 * 1e-3),
-                                        "speedup_vs_fp64": ms64 / ms32, "l1_rel_vs_fp64": l1_rel(g, ref)}}
+                                        "speedup_vs_fp64": ms64 / ms32, "l1_rel_vs_fp64": l1_rel(g, ref),
+                                        "l1_flux_scaled_vs_fp64": l1_flux_scaled(prob, g, ref, steps, dt0)}}
     prob, u = wl.euler2d_vortex(nx=256, degree=4, seed=0, limiter=("scaling", "traces"))
     pts = {}
     for label in ("gl", "gll"):
