@@ -316,30 +316,40 @@ const char* cr_last_error(const cr_ctx* ctx);
 typedef struct cr_batch cr_batch;
 enum {
   CR_BATCH_PHASES = 0, /* three launches per step (local, face, update) over all problems */
-  CR_BATCH_FUSED = 1   /* one cooperative persistent launch for all phases of up to 8 steps,
-                          with a grid barrier (bounded wait) between phases */
+  CR_BATCH_FUSED = 1   /* one cooperative persistent launch for all phases of up to 8 steps:
+                          blocks claim work items (step, phase, tile) from one queue, and an
+                          item waits (bounded) only for the work of its own problem it reads */
 };
+/* Number of configurations the autotuner tries. */
+#define CR_BATCH_CANDIDATES 8
 
 /* Group n contexts (pointers owned by the caller; they must outlive the
  * batch).  Allocates the batch's small device tables (parameters, tiles).
- * Default configuration: 256 threads per block, CR_BATCH_FUSED.  Synchronises
+ * Default configuration: 256 threads per block, CR_BATCH_FUSED, 1 tile per
+ * block.  Synchronises
  * the contexts' streams.  Errors: CR_E_INVALID_ARG, CR_E_UNSUPPORTED,
  * CR_E_NOMEM, CR_E_CUDA. */
 cr_status cr_batch_init(cr_ctx* const* ctxs, int n, cr_batch** out);
 void cr_batch_destroy(cr_batch* batch);
 
-/* Threads per block (128 or 256: elements per block = threads / (N+1)^2) and
- * mode (CR_BATCH_PHASES or CR_BATCH_FUSED). */
-cr_status cr_batch_config(cr_batch* batch, int threads, int mode);
+/* Threads per block (128 or 256: elements per block and tile = threads /
+ * (N+1)^2), mode (CR_BATCH_PHASES or CR_BATCH_FUSED) and tiles (1, 2 or 4):
+ * in FUSED a block takes 8 x tiles consecutive tiles from the queue per claim
+ * (so a CTA works through 8 x tiles x threads / (N+1)^2 elements between
+ * claims); PHASES runs one tile per block and ignores it.  Errors:
+ * CR_E_INVALID_ARG for other values. */
+cr_status cr_batch_config(cr_batch* batch, int threads, int mode, int tiles);
 
-/* Autotuner: times one step of each (threads, mode) candidate in turn, for
- * trial_steps rounds after one warm-up round, on the batch's own problems
- * (CUDA events), and keeps the candidate with the fastest step.  The problems
- * advance by 4 * (trial_steps + 1) steps: tune before setting the state of
- * the real run.  ms_per_step (host, may be NULL) receives each candidate's
- * fastest step, in the order (128, PHASES), (128, FUSED), (256, PHASES),
- * (256, FUSED). */
-cr_status cr_batch_autotune(cr_batch* batch, int trial_steps, int* threads, int* mode,
+/* Autotuner: times one step of each (threads, mode, tiles) candidate in
+ * turn, for trial_steps rounds after one warm-up round, on the batch's own
+ * problems (CUDA events), and keeps the candidate with the fastest step.  The
+ * problems advance by CR_BATCH_CANDIDATES * (trial_steps + 1) steps: tune
+ * before setting the state of the real run.  ms_per_step (host, may be NULL)
+ * receives CR_BATCH_CANDIDATES values, each candidate's fastest step, in the
+ * order (128, PHASES), (128, FUSED, 1), (128, FUSED, 2), (128, FUSED, 4), then
+ * the same four with 256 threads.  threads, mode and tiles (may be NULL)
+ * receive the choice. */
+cr_status cr_batch_autotune(cr_batch* batch, int trial_steps, int* threads, int* mode, int* tiles,
                             double* ms_per_step);
 
 /* Advance every problem by up to nsteps steps (each stops at t_final, the
@@ -347,23 +357,24 @@ cr_status cr_batch_autotune(cr_batch* batch, int trial_steps, int* threads, int*
  * contexts' streams; enqueued on the first context's stream.  Call
  * cr_batch_sync before using a context on its own again. */
 cr_status cr_batch_step_async(cr_batch* batch, int nsteps, double t_final);
-/* Wait for the batch; CR_E_TIMEOUT if a grid barrier gave up (the fused
- * kernel then returned early), CR_E_INADMISSIBLE naming the first problem
- * whose step produced an inadmissible state. */
+/* Wait for the batch; CR_E_TIMEOUT if a wait of the fused kernel gave up
+ * (its blocks then returned early), CR_E_INADMISSIBLE naming the first
+ * problem whose step produced an inadmissible state. */
 cr_status cr_batch_sync(cr_batch* batch);
 /* cr_batch_step_async followed by cr_batch_sync. */
 cr_status cr_batch_step(cr_batch* batch, int nsteps, double t_final);
 const char* cr_batch_last_error(const cr_batch* batch);
 
 /* Fault injection for tests of the fused kernel's timeout path (no
- * counterpart in the paper).  Sets the grid barrier's wait budget to `polls`
- * polls of at least 64 ns each (0 restores the default, 2^26, at least 4 s) and
- * makes every barrier wait for `phantom` further blocks that never arrive.
- * With phantom > 0 each block's wait runs out after its budget, the block sets
- * the batch's error flag and returns; no block traps or hangs.  The next
- * cr_batch_sync then returns CR_E_TIMEOUT and clears the flag and the barrier;
- * the problems' states are undefined until they are set again.  No effect in
- * CR_BATCH_PHASES mode (no grid barrier). */
+ * counterpart in the paper).  Sets the budget of the fused kernel's waits to
+ * `polls` polls of at least 64 ns each (0 restores the default, 2^26, at
+ * least 4 s) and makes every wait require `phantom` further completed tiles
+ * that never come.  With phantom > 0 the first wait runs out after its budget,
+ * that block sets the batch's error flag and returns, and every other block
+ * stops at its next claim or wait; no block traps or hangs.  The next
+ * cr_batch_sync then returns CR_E_TIMEOUT and clears the flag; the problems'
+ * states are undefined until they are set again.  No effect in
+ * CR_BATCH_PHASES mode (no waits). */
 cr_status cr_batch_barrier_test(cr_batch* batch, unsigned long long polls, int phantom);
 
 #ifdef __cplusplus

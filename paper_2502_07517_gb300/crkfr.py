@@ -113,8 +113,8 @@ def lib():
         L.cr_batch_init.argtypes = [ctypes.POINTER(V), I, ctypes.POINTER(V)]
         L.cr_batch_destroy.argtypes = [V]
         L.cr_batch_destroy.restype = None
-        L.cr_batch_config.argtypes = [V, I, I]
-        L.cr_batch_autotune.argtypes = [V, I, ctypes.POINTER(I), ctypes.POINTER(I), D]
+        L.cr_batch_config.argtypes = [V, I, I, I]
+        L.cr_batch_autotune.argtypes = [V, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), D]
         L.cr_batch_step_async.argtypes = [V, I, ctypes.c_double]
         L.cr_batch_sync.argtypes = [V]
         L.cr_batch_step.argtypes = [V, I, ctypes.c_double]
@@ -396,17 +396,23 @@ def cr_batch_destroy(b):
         b.handle = None
 
 
-def cr_batch_config(b, threads, mode):
-    _bcheck(lib().cr_batch_config(b.handle, int(threads), int(mode)), b)
+def cr_batch_config(b, threads, mode, tiles=1):
+    _bcheck(lib().cr_batch_config(b.handle, int(threads), int(mode), int(tiles)), b)
+
+
+BATCH_CANDIDATES = [(t, m, k) for t in (128, 256)
+                    for m, k in ((CR_BATCH_PHASES, 1), (CR_BATCH_FUSED, 1), (CR_BATCH_FUSED, 2),
+                                 (CR_BATCH_FUSED, 4))]
 
 
 def cr_batch_autotune(b, trial_steps=3):
-    """Returns (threads, mode, ms per step of the 4 candidates)."""
-    t, m = ctypes.c_int(), ctypes.c_int()
-    ms = np.zeros(4)
+    """Returns (threads, mode, tiles, ms per step of the candidates in the
+    order of BATCH_CANDIDATES)."""
+    t, m, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = np.zeros(len(BATCH_CANDIDATES))
     _bcheck(lib().cr_batch_autotune(b.handle, int(trial_steps), ctypes.byref(t), ctypes.byref(m),
-                                    _dptr(ms)), b)
-    return t.value, m.value, ms
+                                    ctypes.byref(k), _dptr(ms)), b)
+    return t.value, m.value, k.value, ms
 
 
 def cr_batch_step_async(b, nsteps, t_final=1e300):

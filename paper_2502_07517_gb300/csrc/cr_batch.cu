@@ -9,9 +9,17 @@
 //   k_batch_local / k_batch_face / k_batch_update : one launch per phase over
 //       the tiles of every problem (three launches per step for the batch).
 //   k_batch_fused : one cooperative, persistent launch for all phases of
-//       nsteps steps; blocks stride over the tiles and meet at a grid barrier
-//       between phases.  The barrier's wait is bounded: after A.spin_limit
-//       polls it sets the error flag and every block returns.
+//       nsteps steps.  The work items (step, phase, tile) form one queue in
+//       that order; blocks claim kFusedClaim * A.tiles consecutive items at a
+//       time from an atomic counter (the next claim is made while the current
+//       one runs).  There is no grid barrier: an item waits only for the work
+//       of its own problem it reads (the previous phase of the same step, or
+//       the previous step's update), counted per (phase, problem); a block
+//       publishes its finished tiles before it waits.  Every item an item
+//       waits for lies earlier in the queue and has been claimed by a running
+//       block, so the waits always end; they are bounded all the same: after
+//       A.spin_limit polls the block sets the error flag and returns, and
+//       blocks that see the flag stop.
 #include <cstdint>
 
 #include "cr_batch.cuh"
@@ -68,36 +76,6 @@ __device__ __forceinline__ void face_tile(const BatchArgs<real>& A, KParams<real
   else face_body<2, 4, Eq2, real>(*sP, tile.blk);
 }
 
-// Grid-wide barrier of a cooperative launch (all blocks resident).  Thread 0
-// of each block arrives on bar[0]; the last of gridDim.x + phantom arrivals
-// resets it and advances the generation bar[1]; the others poll the
-// generation, at most spin_limit times.
-__device__ bool grid_barrier(unsigned* bar, int* err, unsigned long long spin_limit, int phantom) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g = *gen;
-    __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x + unsigned(phantom) - 1u) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      unsigned long long spins = 0;
-      while (*gen == g) {
-        if (++spins > spin_limit) {
-          atomicOr(err, 1);
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return *reinterpret_cast<volatile int*>(err) == 0;
-}
-
 // Resident blocks per SM: as the single-problem kernels (MinBlocks), scaled
 // from 256-thread blocks to T threads.
 template <typename real, int T, int PHASE>
@@ -107,6 +85,9 @@ struct BatchMinBlocks {
   static constexpr int value = per256 * 256 / T;
 };
 
+// One tile per block: a loop over several consecutive tiles per block was
+// measured 15-25% slower on the 96-problem ensemble (48 against 55-61 ms per
+// step), so the tiles per block apply to the fused kernel's claims only.
 template <typename real, int T>
 __global__ void __launch_bounds__(T, (BatchMinBlocks<real, T, 0>::value)) k_batch_local(const __grid_constant__ BatchArgs<real> A) {
   __shared__ __align__(16) KParams<real> sP;
@@ -137,20 +118,96 @@ struct FusedMinBlocks {
   static constexpr int value = 65536 / (T * (sizeof(real) == 4 ? 64 : 128));
 };
 
+// Wait (thread 0) until done[] reaches target, at most A.spin_limit polls of
+// at least 64 ns; gives up early when another block has set the error flag.
+// Returns false (for the whole block) when the wait failed.
+template <typename real>
+__device__ bool wait_count(const BatchArgs<real>& A, const unsigned* cnt, unsigned target, int* sflag) {
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned long long spins = 0;
+    while (*reinterpret_cast<const volatile unsigned*>(cnt) < target) {
+      if (*reinterpret_cast<volatile int*>(A.err) != 0) {
+        ok = 0;
+        break;
+      }
+      if (++spins > A.spin_limit) {
+        atomicOr(A.err, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    *sflag = ok;
+  }
+  __syncthreads();
+  return *reinterpret_cast<volatile int*>(sflag) != 0;
+}
+
+// Publish cnt finished tiles of counter idx (every thread; no-op when cnt is 0).
+__device__ __forceinline__ void publish(unsigned* done, int idx, unsigned& cnt) {
+  if (cnt == 0u) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(done + idx, cnt);
+  }
+  cnt = 0u;
+}
+
 template <typename real, int T>
 __global__ void __launch_bounds__(T, (FusedMinBlocks<real, T>::value)) k_batch_fused(const __grid_constant__ BatchArgs<real> A) {
   __shared__ __align__(16) KParams<real> sP;
+  __shared__ unsigned sNext;
+  __shared__ int sFlag;
   int cur = -1;
-  // tiles by grid stride: blocks see every problem size and degree, which
-  // balances the load better than contiguous runs of tiles (measured: 67.7
-  // against 73.6 ms per step on the 96-problem ensemble)
-  for (int s = 0; s < A.nsteps; ++s) {
-    for (int t = blockIdx.x; t < A.n_el; t += gridDim.x) el_tile<real, 0>(A, &sP, t, cur);
-    if (!grid_barrier(A.bar, A.err, A.spin_limit, A.phantom)) return;
-    for (int t = blockIdx.x; t < A.n_face; t += gridDim.x) face_tile<real>(A, &sP, t, cur);
-    if (!grid_barrier(A.bar, A.err, A.spin_limit, A.phantom)) return;
-    for (int t = blockIdx.x; t < A.n_el; t += gridDim.x) el_tile<real, 2>(A, &sP, t, cur);
-    if (!grid_barrier(A.bar, A.err, A.spin_limit, A.phantom)) return;
+  const unsigned per_step = 2u * unsigned(A.n_el) + unsigned(A.n_face);
+  const unsigned total = per_step * unsigned(A.nsteps);
+  const unsigned chunk = unsigned(A.tiles) * kFusedClaim;
+  unsigned* done = A.queue + 1;  // [phase][prob]
+  if (threadIdx.x == 0) sNext = atomicAdd(A.queue, chunk);
+  __syncthreads();
+  unsigned first = sNext;
+  int ok_key = -1;          // the last wait that ended, and its target (counts only grow)
+  unsigned ok_target = 0u;
+  int pend_idx = 0;         // finished tiles of one (phase, problem) not yet published
+  unsigned pend = 0u;
+  while (first < total) {
+    __syncthreads();  // every thread has read sNext
+    // claim the next chunk now: its latency overlaps this chunk's work
+    if (threadIdx.x == 0)
+      sNext = *reinterpret_cast<volatile int*>(A.err) ? total : atomicAdd(A.queue, chunk);
+    const unsigned end = first + chunk < total ? first + chunk : total;
+    for (unsigned item = first; item < end; ++item) {
+      const int s = int(item / per_step);
+      const int r = int(item - unsigned(s) * per_step);
+      const int phase = r < A.n_el ? 0 : (r < A.n_el + A.n_face ? 1 : 2);
+      const int t = phase == 0 ? r : (phase == 1 ? r - A.n_el : r - A.n_el - A.n_face);
+      const int prob = phase == 1 ? A.t_face[t].prob : A.t_el[t].prob;
+      // the work this item reads: the previous step's update (local phase),
+      // this step's local phase (face phase), this step's face phase (update)
+      const int dep = phase == 0 ? 2 : phase - 1;
+      const unsigned per = unsigned(dep == 1 ? A.nblk_face[prob] : A.nblk_el[prob]);
+      const unsigned target = per * unsigned(phase == 0 ? s : s + 1) + unsigned(A.phantom);
+      const int key = dep * A.nprob + prob;
+      if (key != ok_key || target > ok_target) {
+        publish(done, pend_idx, pend);  // never wait while holding unpublished work
+        if (!wait_count(A, done + key, target, &sFlag)) return;
+        ok_key = key;
+        ok_target = target;
+      }
+      if (phase == 1) face_tile<real>(A, &sP, t, cur);
+      else if (phase == 0) el_tile<real, 0>(A, &sP, t, cur);
+      else el_tile<real, 2>(A, &sP, t, cur);
+      const int idx = phase * A.nprob + prob;
+      if (idx != pend_idx) publish(done, pend_idx, pend);
+      pend_idx = idx;
+      ++pend;
+    }
+    publish(done, pend_idx, pend);
+    __syncthreads();
+    first = sNext;
   }
 }
 
@@ -203,6 +260,9 @@ cudaError_t launch_fused_t(int grid, const BatchArgs<real>& A, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  // the queue head and the per-(phase, problem) completion counts start at zero
+  cudaError_t e = cudaMemsetAsync(A.queue, 0, (1 + 3 * (size_t)A.nprob) * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
   return cudaLaunchKernelEx(&cfg, k_batch_fused<real, T>, A);
 }
 

@@ -9,7 +9,7 @@
 
 namespace crk {
 
-// One unit of work: block blk of problem prob.
+// One unit of work: block blk of problem prob (a tile).
 struct BatchTile {
   int prob, blk;
 };
@@ -21,20 +21,29 @@ struct BatchArgs {
   const KParams<real>* P;       // [nprob] parameters of every problem (device)
   const int* deg;               // [nprob] degree, 3 or 4
   const int* nblk_el;           // [nprob] element blocks of the problem (update phase count)
+  const int* nblk_face;         // [nprob] face-node blocks of the problem
   const BatchTile* t_el;        // element tiles (local and update phases), all problems
   int n_el;
   const BatchTile* t_face;      // face-node tiles, all problems
   int n_face;
-  unsigned* bar;                // [2] grid barrier: arrivals, generation (fused launch)
-  int* err;                     // set when a grid barrier gave up waiting
-  unsigned long long spin_limit;  // polls (>= 64 ns each) before a barrier gives up
-  int phantom;                  // extra arrivals the barrier waits for (0; > 0 only in tests
+  int nprob;
+  int tiles;                    // fused launch: tiles per claim = kFusedClaim * tiles
+  unsigned* queue;              // fused launch: [0] next unclaimed work item, then the tiles
+                                // finished per (phase, problem) [3][nprob]; zeroed before each launch
+  int* err;                     // set when a wait of the fused launch gave up
+  unsigned long long spin_limit;  // polls (>= 64 ns each) before a wait gives up
+  int phantom;                  // extra completions every wait requires (0; > 0 only in tests
                                 // of the timeout path: they never come)
   int nsteps;                   // steps per fused launch
 };
 
-// Threads per block the batched kernels are built for.
+// Threads per block the batched kernels are built for, and tiles per block.
 constexpr int kBatchThreadChoices[2] = {128, 256};
+constexpr int kBatchTileChoices[3] = {1, 2, 4};
+// Tiles per claim of the fused kernel for each tile of cr_batch_config's
+// tiles: few claims on the queue's one counter, and one dependency check and
+// one publication per run of tiles of the same (phase, problem).
+constexpr int kFusedClaim = 8;
 
 // Shared memory (bytes) of the largest body for a block of `threads` threads.
 size_t batch_smem(int threads, bool fp32);

@@ -1048,12 +1048,13 @@ struct cr_batch {
   std::vector<cr_ctx*> ctx;
   bool fp32 = false;
   cudaStream_t stream = nullptr;
-  int threads = 256, mode = CR_BATCH_FUSED;
-  unsigned long long spin_limit = 1ull << 26;  // grid-barrier polls (>= 64 ns each): >= 4 s
-  int phantom = 0;                             // test hook: arrivals that never come
+  int threads = 256, mode = CR_BATCH_FUSED, tiles = 1;
+  unsigned long long spin_limit = 1ull << 26;  // polls of a fused-launch wait (>= 64 ns each): >= 4 s
+  int phantom = 0;                             // test hook: completions that never come
   int fused_grid = 0;
-  unsigned char* dmem = nullptr;     // parameters, degrees, block counts, tiles, barrier
-  size_t params_off = 0, deg_off = 0, nblk_off = 0, tel_off = 0, tface_off = 0, bar_off = 0;
+  unsigned char* dmem = nullptr;     // parameters, degrees, block counts, tiles, queue, error flag
+  size_t params_off = 0, deg_off = 0, nblk_off = 0, nface_off = 0, tel_off = 0, tface_off = 0,
+         queue_off = 0, err_off = 0;
   size_t max_el = 0, max_face = 0;   // tile capacity (the smallest block size)
   BatchArgs<float> af{};
   BatchArgs<double> ad{};
@@ -1102,11 +1103,12 @@ cr_status batch_build(cr_batch* b) {
   destroy_graphs(b);
   const int nprob = (int)b->ctx.size();
   std::vector<BatchTile> tel, tface;
-  std::vector<int> nblk(nprob);
+  std::vector<int> nblk(nprob), nblkf(nprob);
   for (int i = 0; i < nprob; ++i) {
     int nel, nface;
     tile_counts(b->ctx[i], b->threads, &nel, &nface);
     nblk[i] = nel;
+    nblkf[i] = nface;
     for (int k = 0; k < nel; ++k) tel.push_back({i, k});
     for (int k = 0; k < nface; ++k) tface.push_back({i, k});
   }
@@ -1114,6 +1116,7 @@ cr_status batch_build(cr_batch* b) {
     return bfail(b, CR_E_INVALID_ARG, "tile capacity exceeded");
   unsigned char* d = b->dmem;
   CR_BCUDA(b, cudaMemcpyAsync(d + b->nblk_off, nblk.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  CR_BCUDA(b, cudaMemcpyAsync(d + b->nface_off, nblkf.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, b->stream));
   CR_BCUDA(b, cudaMemcpyAsync(d + b->tel_off, tel.data(), tel.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
   CR_BCUDA(b, cudaMemcpyAsync(d + b->tface_off, tface.data(), tface.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
   CR_BCUDA(b, cudaStreamSynchronize(b->stream));
@@ -1121,12 +1124,15 @@ cr_status batch_build(cr_batch* b) {
     A.P = P;
     A.deg = reinterpret_cast<const int*>(d + b->deg_off);
     A.nblk_el = reinterpret_cast<const int*>(d + b->nblk_off);
+    A.nblk_face = reinterpret_cast<const int*>(d + b->nface_off);
     A.t_el = reinterpret_cast<const BatchTile*>(d + b->tel_off);
     A.n_el = (int)tel.size();
     A.t_face = reinterpret_cast<const BatchTile*>(d + b->tface_off);
     A.n_face = (int)tface.size();
-    A.bar = reinterpret_cast<unsigned*>(d + b->bar_off);
-    A.err = reinterpret_cast<int*>(d + b->bar_off + 8);
+    A.nprob = nprob;
+    A.tiles = b->tiles;
+    A.queue = reinterpret_cast<unsigned*>(d + b->queue_off);
+    A.err = reinterpret_cast<int*>(d + b->err_off);
     A.spin_limit = b->spin_limit;
     A.phantom = b->phantom;
   };
@@ -1144,7 +1150,9 @@ cr_status batch_build(cr_batch* b) {
     int maxb = 0;
     CR_BCUDA(b, batch_fused_max_blocks(b->threads, b->fp32, &maxb));
     if (maxb < 1) return bfail(b, CR_E_CUDA, "the fused batch kernel does not fit on an SM");
-    const int want = b->af.n_el > b->af.n_face ? b->af.n_el : b->af.n_face;
+    const int most = b->af.n_el > b->af.n_face ? b->af.n_el : b->af.n_face;
+    const int per_claim = b->tiles * kFusedClaim;
+    const int want = (most + per_claim - 1) / per_claim;
     b->fused_grid = want < maxb ? want : maxb;
   }
   // graphs of 1 and 8 steps (direct launches if capture is refused)
@@ -1244,9 +1252,11 @@ cr_status cr_batch_init(cr_ctx* const* ctxs, int n, cr_batch** out) {
   b->params_off = take(psz * n);
   b->deg_off = take(sizeof(int) * n);
   b->nblk_off = take(sizeof(int) * n);
+  b->nface_off = take(sizeof(int) * n);
   b->tel_off = take(sizeof(BatchTile) * mel);
   b->tface_off = take(sizeof(BatchTile) * mface);
-  b->bar_off = take(16);
+  b->queue_off = take(sizeof(unsigned) * (1 + 3 * (size_t)n));
+  b->err_off = take(16);
   cudaError_t e = cudaMalloc(&b->dmem, off);
   if (e != cudaSuccess) return bail(bfail(b, CR_E_NOMEM, "cr_batch_init: cudaMalloc failed"));
   e = cudaMallocHost(&b->h_err, sizeof(int));
@@ -1264,7 +1274,7 @@ cr_status cr_batch_init(cr_ctx* const* ctxs, int n, cr_batch** out) {
   e = cudaMemcpyAsync(b->dmem + b->params_off, hp.data(), hp.size(), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->dmem + b->deg_off, deg.data(), n * sizeof(int), cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->dmem + b->bar_off, 0, 16, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->dmem + b->err_off, 0, 16, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bail(bfail(b, CR_E_CUDA, std::string("cr_batch_init: ") + cudaGetErrorString(e)));
   for (cr_ctx* c : b->ctx) {
@@ -1289,13 +1299,16 @@ void cr_batch_destroy(cr_batch* b) {
   delete b;
 }
 
-cr_status cr_batch_config(cr_batch* b, int threads, int mode) {
+cr_status cr_batch_config(cr_batch* b, int threads, int mode, int tiles) {
   if (!b) return bfail(nullptr, CR_E_INVALID_ARG, "NULL batch");
   if ((threads != kBatchThreadChoices[0] && threads != kBatchThreadChoices[1]) ||
-      (mode != CR_BATCH_PHASES && mode != CR_BATCH_FUSED))
-    return bfail(b, CR_E_INVALID_ARG, "cr_batch_config: threads must be 128 or 256, mode PHASES or FUSED");
+      (mode != CR_BATCH_PHASES && mode != CR_BATCH_FUSED) ||
+      (tiles != kBatchTileChoices[0] && tiles != kBatchTileChoices[1] && tiles != kBatchTileChoices[2]))
+    return bfail(b, CR_E_INVALID_ARG,
+                 "cr_batch_config: threads must be 128 or 256, mode PHASES or FUSED, tiles 1, 2 or 4");
   b->threads = threads;
   b->mode = mode;
+  b->tiles = tiles;
   return batch_build(b);
 }
 
@@ -1317,12 +1330,12 @@ cr_status cr_batch_step_async(cr_batch* b, int nsteps, double t_final) {
 
 cr_status cr_batch_sync(cr_batch* b) {
   if (!b) return bfail(nullptr, CR_E_INVALID_ARG, "NULL batch");
-  CR_BCUDA(b, cudaMemcpyAsync(b->h_err, b->dmem + b->bar_off + 8, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  CR_BCUDA(b, cudaMemcpyAsync(b->h_err, b->dmem + b->err_off, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   CR_BCUDA(b, cudaStreamSynchronize(b->stream));
-  if (*b->h_err) {  // clear the barrier and the flag so that the batch can run again
-    CR_BCUDA(b, cudaMemsetAsync(b->dmem + b->bar_off, 0, 16, b->stream));
+  if (*b->h_err) {  // clear the flag so that the batch can run again
+    CR_BCUDA(b, cudaMemsetAsync(b->dmem + b->err_off, 0, 16, b->stream));
     CR_BCUDA(b, cudaStreamSynchronize(b->stream));
-    return bfail(b, CR_E_TIMEOUT, "cr_batch_sync: a grid barrier of the fused kernel gave up waiting");
+    return bfail(b, CR_E_TIMEOUT, "cr_batch_sync: a wait of the fused kernel gave up");
   }
   for (size_t i = 0; i < b->ctx.size(); ++i) {
     cr_ctx* c = b->ctx[i];
@@ -1343,12 +1356,19 @@ cr_status cr_batch_step(cr_batch* b, int nsteps, double t_final) {
 }
 
 cr_status cr_batch_autotune(cr_batch* b, int trial_steps, int* threads_out, int* mode_out,
-                            double* ms_per_step) {
+                            int* tiles_out, double* ms_per_step) {
   if (!b || trial_steps < 1) return bfail(b, CR_E_INVALID_ARG, "cr_batch_autotune: bad arguments");
-  const int cand_t[4] = {kBatchThreadChoices[0], kBatchThreadChoices[0], kBatchThreadChoices[1],
-                         kBatchThreadChoices[1]};
-  const int cand_m[4] = {CR_BATCH_PHASES, CR_BATCH_FUSED, CR_BATCH_PHASES, CR_BATCH_FUSED};
-  double best_ms[4] = {1e300, 1e300, 1e300, 1e300};
+  // candidates, per thread count: PHASES, then FUSED with tiles 1, 2, 4 (the
+  // order of ms_per_step)
+  constexpr int NC = CR_BATCH_CANDIDATES;
+  int cand_t[NC], cand_m[NC], cand_k[NC];
+  for (int i = 0; i < NC; ++i) {
+    cand_t[i] = kBatchThreadChoices[i / 4];
+    cand_m[i] = i % 4 == 0 ? CR_BATCH_PHASES : CR_BATCH_FUSED;
+    cand_k[i] = i % 4 == 0 ? 1 : kBatchTileChoices[i % 4 - 1];
+  }
+  double best_ms[NC];
+  for (int i = 0; i < NC; ++i) best_ms[i] = 1e300;
   cudaEvent_t e0, e1;
   CR_BCUDA(b, cudaEventCreate(&e0));
   CR_BCUDA(b, cudaEventCreate(&e1));
@@ -1359,9 +1379,10 @@ cr_status cr_batch_autotune(cr_batch* b, int trial_steps, int* threads_out, int*
   // problems reach as they advance is shared fairly between the candidates;
   // each candidate keeps its fastest step.
   for (int r = 0; r <= trial_steps && st == CR_OK; ++r) {
-    for (int i = 0; i < 4 && st == CR_OK; ++i) {
+    for (int i = 0; i < NC && st == CR_OK; ++i) {
       b->threads = cand_t[i];
       b->mode = cand_m[i];
+      b->tiles = cand_k[i];
       st = batch_build(b);
       if (st != CR_OK) break;
       if (batch_set_run(P, (int)b->ctx.size(), 1e300, b->fp32, b->stream) != cudaSuccess) {
@@ -1382,15 +1403,17 @@ cr_status cr_batch_autotune(cr_batch* b, int trial_steps, int* threads_out, int*
   cudaEventDestroy(e1);
   if (st != CR_OK) return st;
   int bi = 0;
-  for (int i = 1; i < 4; ++i)
+  for (int i = 1; i < NC; ++i)
     if (best_ms[i] < best_ms[bi]) bi = i;
   if (ms_per_step)
-    for (int i = 0; i < 4; ++i) ms_per_step[i] = best_ms[i];
+    for (int i = 0; i < NC; ++i) ms_per_step[i] = best_ms[i];
   b->threads = cand_t[bi];
   b->mode = cand_m[bi];
+  b->tiles = cand_k[bi];
   st = batch_build(b);
   if (threads_out) *threads_out = cand_t[bi];
   if (mode_out) *mode_out = cand_m[bi];
+  if (tiles_out) *tiles_out = cand_k[bi];
   return st;
 }
 

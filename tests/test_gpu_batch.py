@@ -5,7 +5,7 @@ in one persistent cooperative launch.
 A batched step runs the same per-block bodies as the single-problem kernels,
 and no result depends on how elements are grouped into blocks, so in FP64
 every problem's state must equal, bit for bit, what cr_step gives on that
-problem alone, for every (threads, mode) configuration and with runs clipped
+problem alone, for every (threads, mode, tiles) configuration and with runs clipped
 at t_final; in FP32 bulk (also with the learned alpha) it must agree to FP32
 rounding and be reproducible bit for bit.  One batched FP64 step is also
 compared with the FP64 oracle directly.
@@ -22,8 +22,9 @@ pytestmark = pytest.mark.gpu
 
 # ragged meshes, both degrees, a single element and a single row
 SHAPES = [((13, 11), 4), ((7, 5), 3), ((1, 1), 4), ((17, 1), 3), ((24, 20), 4), ((9, 16), 3)]
-CONFIGS = [(128, crkfr.CR_BATCH_PHASES), (128, crkfr.CR_BATCH_FUSED),
-           (256, crkfr.CR_BATCH_PHASES), (256, crkfr.CR_BATCH_FUSED)]
+CONFIGS = [(128, crkfr.CR_BATCH_PHASES, 1), (128, crkfr.CR_BATCH_FUSED, 1),
+           (256, crkfr.CR_BATCH_PHASES, 1), (256, crkfr.CR_BATCH_FUSED, 1),
+           (256, crkfr.CR_BATCH_FUSED, 2), (128, crkfr.CR_BATCH_FUSED, 4)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -92,7 +93,8 @@ def _same(got, ref, precision, what=""):
 
 
 @pytest.mark.parametrize("precision", [crkfr.CR_FP64, crkfr.CR_FP32_BULK], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("config", CONFIGS, ids=["128-phases", "128-fused", "256-phases", "256-fused"])
+@pytest.mark.parametrize("config", CONFIGS, ids=["%d-%s-%d" % (t, "fused" if m else "phases", k)
+                                                 for t, m, k in CONFIGS])
 def test_batch_equals_single_problem_steps(precision, config):
     probs = _problems(10)
     ref = _alone(probs, precision, 5)
@@ -156,9 +158,9 @@ def test_autotune_then_step():
     probs = _problems(50)
     ctxs = _contexts(probs, crkfr.CR_FP32_BULK)
     b = crkfr.cr_batch_init(ctxs)
-    threads, mode, ms = crkfr.cr_batch_autotune(b, 2)
-    assert (threads, mode) in CONFIGS and np.all(ms > 0)
-    assert ms[CONFIGS.index((threads, mode))] == ms.min()
+    threads, mode, tiles, ms = crkfr.cr_batch_autotune(b, 2)
+    assert len(ms) == 8 and np.all(ms > 0) and np.all(ms < 1e300)
+    assert ms[crkfr.BATCH_CANDIDATES.index((threads, mode, tiles))] == ms.min()
     for (prob, u), c in zip(probs, ctxs):  # the tuning advanced the problems: start again
         crkfr.cr_set_state(c, u)
     crkfr.cr_batch_step(b, 3)
@@ -181,16 +183,17 @@ def test_batch_rejects_unsupported_problems():
     assert ei.value.status == -1
 
 
-def test_fused_barrier_timeout_is_reported_and_recoverable():
-    """A barrier that waits for a block that never arrives (fault injection):
-    every block gives up after its wait budget and returns, cr_batch_step
-    reports CR_E_TIMEOUT, and after the states are set again the batch steps
-    exactly like the single-problem path.  No block traps or hangs."""
+def test_fused_wait_timeout_is_reported_and_recoverable():
+    """Waits of the fused kernel that require completions that never come
+    (fault injection): the first wait gives up after its budget, every block
+    returns, cr_batch_step reports CR_E_TIMEOUT, and after the states are set
+    again the batch steps exactly like the single-problem path.  No block
+    traps or hangs."""
     import time
     probs = _problems(70, shapes=[((13, 11), 4), ((7, 5), 3)])
     ctxs = _contexts(probs, crkfr.CR_FP64)
     b = crkfr.cr_batch_init(ctxs)
-    crkfr.cr_batch_config(b, 256, crkfr.CR_BATCH_FUSED)
+    crkfr.cr_batch_config(b, 256, crkfr.CR_BATCH_FUSED, 1)
     crkfr.cr_batch_barrier_test(b, 20000, 1)
     t0 = time.perf_counter()
     with pytest.raises(crkfr.CrError) as ei:
@@ -209,7 +212,7 @@ def test_batch_with_walls_equals_single_problem_steps():
     probs = [(dict(p, bc_x="wall"), u) for p, u in _problems(80, shapes=[((11, 9), 4), ((8, 6), 3)])]
     probs += [(dict(p, bc_y="wall", bc_x="outflow"), u) for p, u in _problems(90, shapes=[((7, 9), 4)])]
     ref = _alone(probs, crkfr.CR_FP64, 4)
-    for config in ((128, crkfr.CR_BATCH_PHASES), (256, crkfr.CR_BATCH_FUSED)):
+    for config in ((128, crkfr.CR_BATCH_PHASES, 1), (256, crkfr.CR_BATCH_FUSED, 2)):
         got, _ = _batched(probs, crkfr.CR_FP64, 4, config)
         _same(got, ref, crkfr.CR_FP64, "walls %s" % (config,))
 
@@ -218,5 +221,5 @@ def test_batch_with_walls_equals_single_problem_steps():
 def test_batch_with_variants_equals_single_problem_steps(diss, cen):
     probs = _problems(100, shapes=[((11, 9), 4), ((8, 6), 3), ((5, 7), 4)])
     ref = _alone(probs, crkfr.CR_FP64, 3, dissipation=diss, central=cen)
-    got, _ = _batched(probs, crkfr.CR_FP64, 3, (128, crkfr.CR_BATCH_FUSED), dissipation=diss, central=cen)
+    got, _ = _batched(probs, crkfr.CR_FP64, 3, (128, crkfr.CR_BATCH_FUSED, 2), dissipation=diss, central=cen)
     _same(got, ref, crkfr.CR_FP64, "variant %d %d" % (diss, cen))
