@@ -37,9 +37,11 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # lanes per SM per clock (1.25 TFLOP/s nominal), FP32 128 FMA lanes per SM.
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 # DRAM bytes (read + write) per element of the dominant kernel, from one ncu
-# capture of the current kernel (profiles/k_local_euler2d_384x384_N4_fp64.md:
-# 593.3 MB at 147,456 elements; the traffic scales with the element count).
-NCU_TRAFFIC_PER_ELEMENT = {("fp64", "k_local"): 593.33e6 / 147456}
+# capture of the current kernel at 384x384 (147,456 elements; the traffic
+# scales with the element count): FP64 k_local 587.2 MB
+# (profiles/k_local_euler2d_384x384_N4_fp64.md), FP32 bulk k_local 280.1 MB
+# (profiles/k_local_k_update_euler2d_384x384_N4_fp32.md).
+NCU_TRAFFIC_PER_ELEMENT = {("fp64", "k_local"): 587.24e6 / 147456, ("fp32", "k_local"): 280.13e6 / 147456}
 PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -267,6 +269,28 @@ def train_alpha_network(degree, stream, seeds=range(1000, 1008), nx=96, snaps=(0
     return params, info
 
 
+def alu_roofline(prob, nodes, kms, mixed, ms_per_step):
+    """ALU roofline of the dominant kernel of a 2D Euler step: algorithmic
+    flops (flop_model) per launch over the kernel's CUDA-event time, against
+    the FP64 or FP32 peak; kms = per-kernel ms (k_local, k_face, k_update)."""
+    names = ["k_local", "k_face", "k_update"]
+    dom = int(np.argmax(kms))
+    flops = flop_model(2, prob["degree"], "euler2d")
+    achieved = flops[dom] * nodes / (kms[dom] * 1e-3) / 1e12
+    peak = PEAK_FP32_TFLOPS if mixed else PEAK_FP64_TFLOPS
+    mode = "fp32" if mixed else "fp64"
+    ne = nodes // (prob["degree"] + 1) ** 2
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "kernel": names[dom],
+            "traffic": (NCU_TRAFFIC_PER_ELEMENT[(mode, names[dom])] * ne
+                        if (mode, names[dom]) in NCU_TRAFFIC_PER_ELEMENT else None),
+            "peak_source": "derived: 152 SMs x %s FMA lanes x 2 x 2070 MHz"
+                           % ("128 FP32" if mixed else "2 FP64"),
+            "algorithmic_flops_per_point": flops[dom],
+            "kernel_ms": {nm: float(x) for nm, x in zip(names, kms)},
+            "step_tflops": sum(flops) * nodes / (ms_per_step * 1e-3) / 1e12}
+
+
 def timed_steps(ctx, steps, warmup, stream):
     import torch
     from paper_2502_07517_gb300 import crkfr
@@ -374,10 +398,13 @@ def fp32_variants(prob, u, ctx64, steps, warmup, stream, fp64_ms):
         crkfr.cr_step(ctx, steps, 1e300, dt0)
         g = crkfr.cr_get_state(ctx, shape=u.shape)
         a = crkfr.cr_get_alpha(ctx, u.shape[1])
+        crkfr.cr_set_state(ctx, u)
+        kms = crkfr.cr_profile_steps(ctx, steps, 1e300) / steps
         out[name] = {"value": nodes / (ms * 1e-3), "unit": "DOF-updates/s", "ms_per_step": ms,
                      "speedup_vs_fp64": fp64_ms / ms, "l1_rel_vs_fp64": l1_rel(g, ref),
                      "l1_flux_scaled_vs_fp64": l1_flux_scaled(prob, g, ref, steps, dt0),
-                     "alpha_mean": float(a.mean()), "alpha_max": float(a.max())}
+                     "alpha_mean": float(a.mean()), "alpha_max": float(a.max()),
+                     "roofline": alu_roofline(prob, nodes, kms, True, ms)}
         crkfr.cr_destroy(ctx)
     out["alpha_agreement_after_run"] = alpha_agreement(prob, ref, params, stream.cuda_stream)
     return out
@@ -575,6 +602,12 @@ def widened_legs(steps, warmup, stream):
     return out
 
 
+def _finite_min(xs):
+    """Smallest finite value, or None (JSON has no NaN)."""
+    xs = [float(x) for x in xs if np.isfinite(x)]
+    return min(xs) if xs else None
+
+
 def ensemble_leg(steps, warmup, nprob=96, seed=0, config=None, learned=True, nmin=32, nmax=512):
     """Batched ensemble: nprob independent 2D Euler problems (sides uniform in
     32..512, N in {3, 4}, vortex plus planar Riemann jump), FP32 bulk with the
@@ -599,12 +632,14 @@ def ensemble_leg(steps, warmup, nprob=96, seed=0, config=None, learned=True, nmi
         ctxs.append(c)
     nodes = sum(u.shape[1] * u.shape[2] for _, u in probs)
     b = crkfr.cr_batch_init(ctxs)
-    if config:  # "threads/mode", e.g. "256/fused": fixed instead of tuned
-        threads, mode = int(config.split("/")[0]), int(config.split("/")[1] == "fused")
-        crkfr.cr_batch_config(b, threads, mode)
-        cand = np.full(4, np.nan)
+    if config:  # "threads/mode[/tiles]", e.g. "256/fused/2": fixed instead of tuned
+        parts = config.split("/")
+        threads, mode = int(parts[0]), int(parts[1] == "fused")
+        tiles = int(parts[2]) if len(parts) > 2 else 1
+        crkfr.cr_batch_config(b, threads, mode, tiles)
+        cand = np.full(len(crkfr.BATCH_CANDIDATES), np.nan)
     else:
-        threads, mode, cand = crkfr.cr_batch_autotune(b, 2)
+        threads, mode, tiles, cand = crkfr.cr_batch_autotune(b, 2)
 
     def reset():
         for (prob, u), c in zip(probs, ctxs):
@@ -631,7 +666,7 @@ def ensemble_leg(steps, warmup, nprob=96, seed=0, config=None, learned=True, nmi
         crkfr.cr_step(c, steps, 1e300)
     seq_s = time.perf_counter() - t0
     a = np.concatenate([crkfr.cr_get_alpha(c, u.shape[1]) for (prob, u), c in zip(probs, ctxs)])
-    names = ["128/phases", "128/fused", "256/phases", "256/fused"]
+    names = ["%d/%s/%d" % (t, "fused" if m else "phases", k) for t, m, k in crkfr.BATCH_CANDIDATES]
     return {"problems": nprob, "sides": [nmin, nmax],
             "elements": int(sum(u.shape[1] for _, u in probs)), "dofs": int(nodes),
             "degrees": {"3": sum(p["degree"] == 3 for p, _ in probs), "4": sum(p["degree"] == 4 for p, _ in probs)},
@@ -639,8 +674,14 @@ def ensemble_leg(steps, warmup, nprob=96, seed=0, config=None, learned=True, nmi
             "ms_per_step": batch_ms / steps,
             "sequential_value": nodes * steps / seq_s, "sequential_ms_per_step": seq_s * 1e3 / steps,
             "speedup_vs_sequential": seq_s * 1e3 / batch_ms,
-            "autotune": {"chosen": "%d/%s" % (threads, "fused" if mode else "phases"),
-                         "ms_per_step": {nm: float(x) for nm, x in zip(names, cand)}},
+            "autotune": {"chosen": "%d/%s/%d" % (threads, "fused" if mode else "phases", tiles),
+                         "candidates": "threads/mode/tiles: threads per block (elements per tile = threads / "
+                                       "(N+1)^2); fused: 8 x tiles tiles per queue claim",
+                         "best_phases_ms": _finite_min(x for (t, m, k), x in zip(crkfr.BATCH_CANDIDATES, cand)
+                                                       if m == crkfr.CR_BATCH_PHASES),
+                         "best_fused_ms": _finite_min(x for (t, m, k), x in zip(crkfr.BATCH_CANDIDATES, cand)
+                                                      if m == crkfr.CR_BATCH_FUSED),
+                         "ms_per_step": {nm: (float(x) if np.isfinite(x) else None) for nm, x in zip(names, cand)}},
             "alpha_networks": {str(N): nets[N][1] for N in (3, 4)} if learned else None,
             "alpha_mean": float(a.mean()), "generate_s": gen_s,
             "precision": "FP32 bulk + FP64 means/limiter theta, " +
@@ -727,20 +768,7 @@ def run_ours(args):
 
     # ---- per-kernel device times (same workload, every kernel between events) ----
     kms = crkfr.cr_profile_steps(ctx, args.steps, 1e300) / args.steps
-    names = ["k_local", "k_face", "k_update"]
-    dom = int(np.argmax(kms))
-    flops = flop_model(2, prob["degree"], "euler2d")
-    achieved = flops[dom] * nodes / (kms[dom] * 1e-3) / 1e12
-    peak = PEAK_FP32_TFLOPS if mixed else PEAK_FP64_TFLOPS
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "kernel": names[dom],
-                "traffic": (NCU_TRAFFIC_PER_ELEMENT[(args.mode, names[dom])] * ne
-                            if (args.mode, names[dom]) in NCU_TRAFFIC_PER_ELEMENT else None),
-                "peak_source": "derived: 152 SMs x %s FMA lanes x 2 x 2070 MHz"
-                               % ("128 FP32" if mixed else "2 FP64"),
-                "algorithmic_flops_per_point": flops[dom],
-                "kernel_ms": {nm: float(x) for nm, x in zip(names, kms)},
-                "step_tflops": sum(flops) * nodes / (ms_per_step * 1e-3) / 1e12}
+    roofline = alu_roofline(prob, nodes, kms, mixed, ms_per_step)
 
     # ---- HBM view: the method's own bytes (read u^n, write u^{n+1}) per step ----
     state_bytes = u.size * (4 if mixed else 8) + (2 * M * ne * 8 if mixed else 0)
@@ -830,7 +858,8 @@ def main():
                     help="run only the legs of the further rows (boundaries, sources, points, Burgers)")
     ap.add_argument("--ens-problems", type=int, default=96, help="problems in the ensemble leg")
     ap.add_argument("--ens-config", default=None,
-                    help="fixed batch configuration threads/mode (128|256 / phases|fused) instead of autotuning")
+                    help="fixed batch configuration threads/mode[/tiles] (128|256 / phases|fused / 1|2|4) "
+                         "instead of autotuning")
     ap.add_argument("--ens-indicator", action="store_true",
                     help="ensemble leg with the indicator's alpha (no network training)")
     ap.add_argument("--no-variants", action="store_true",

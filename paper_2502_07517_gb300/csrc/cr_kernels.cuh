@@ -673,9 +673,11 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
 // 2D Euler N = 4, 512x512): FP32_BULK blocks are latency bound and gain from
 // four 256-thread blocks per SM (64 registers; k_local 1.39 -> 1.05 ms,
 // k_update 0.91 -> 0.60 ms); the FP64 k_local is bound by the FP64 pipe and
-// gains 3% from two blocks (128 registers instead of 130).
+// gains 3% from two blocks (128 registers instead of 130); the FP64 k_update
+// is bound by its barriers and gains 11% from three blocks (85 registers
+// instead of 106: 2.15 -> 1.91 ms).
 template <bool MIXED> struct MinBlocks {
-  static constexpr int local = MIXED ? 4 : 2, update = MIXED ? 4 : 1;
+  static constexpr int local = MIXED ? 4 : 2, update = MIXED ? 4 : 3;
 };
 
 template <int DIM, int N, class EQ, typename real, bool MIXED>

@@ -2,9 +2,10 @@
 memory (their device memory belongs to another allocator, or allocation's
 implicit synchronisation or any allocation after start-up is not allowed):
 two calls in a row must give what the context-based entry point gives, while
-the fixed scratch array carries the previous call's contents into the next.
-Collected last on purpose, so that a run stopping at the first failure has
-already run everything else."""
+the fixed scratch array carries the previous call's contents into the next,
+and one call must match the FP64 oracle directly.  Collected last on
+purpose, so that a run stopping at the first failure has already run
+everything else."""
 import numpy as np
 import pytest
 
@@ -102,3 +103,29 @@ def test_static_scratch_other_equations(name):
     torch.cuda.synchronize()
     _close(b.cpu().numpy(), refs[0])
     _close(a.cpu().numpy(), refs[1])
+
+
+@pytest.mark.parametrize("name", ["euler1d_outflow_N4", "tenmoment2d_source_N3"])
+def test_static_scratch_step_matches_oracle(name):
+    """One static-scratch step against the FP64 oracle directly, at the parity
+    tests' tolerance (1e-12 of the larger of the variable's size and its flux
+    increment)."""
+    import torch
+    import oracle
+    from tests._oracle_util import oracle_desc
+    prob, u0 = CASES[name]()
+    d = oracle_desc(prob)
+    dt = oracle.dt(d, u0)
+    ref, st, dg = oracle.step(d, u0, dt, want_diag=True)
+    assert st == 0
+    a = torch.from_numpy(u0).cuda()
+    b = torch.empty_like(a)
+    crkfr.cr_step_static(crkfr.desc_from_problem(prob), a, b, dt)
+    g = b.cpu().numpy()
+    dx = (prob["x1"] - prob["x0"]) / prob["nx"]
+    inc = dt / dx * np.abs(dg["fnum_x"]).max(axis=(1, 2))
+    if prob["dim"] == 2:
+        inc = inc + dt / ((prob["y1"] - prob["y0"]) / prob["ny"]) * np.abs(dg["fnum_y"]).max(axis=(1, 2))
+    for v in range(ref.shape[0]):
+        scale = max(np.abs(ref[v]).max(), inc[v])
+        assert np.abs(g[v] - ref[v]).max() <= 1e-12 * scale, v
