@@ -226,8 +226,17 @@ template <> struct Tableau<4> {
 //   constraint(u, k)           admissibility constraint P_k (Sec. 2 eq. (uad.form))
 //   admissible_fast(u)         all P_k > 0, tested without division (multiplied by rho > 0)
 //   indicator_var(u)           variable the smoothness indicator looks at
+// x > 0, with the FP64 test on the integer pipe (the FP64 pipe is the scarce
+// unit): as a signed 64-bit integer a double is positive exactly when its sign
+// bit is clear and it is not +0; NaN patterns (above +inf) are excluded, as the
+// floating-point comparison excludes them.
+__device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
+__device__ __forceinline__ bool gt0(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0ll && b <= 0x7ff0000000000000ll;
+}
 template <typename real>
-__device__ __forceinline__ real sqrt_pos(real x) { return sqrt(x > real(0) ? x : real(0)); }
+__device__ __forceinline__ real sqrt_pos(real x) { return sqrt(gt0(x) ? x : real(0)); }
 
 struct EqLinAdv {  // u_t + a . grad u = 0, Sec. 5.1.1
   static constexpr int M = 1, K = 0;
@@ -444,7 +453,7 @@ struct EqEuler {
   }
   template <typename real>
   __device__ static bool admissible_fast(const real* u, const Phys<real>&) {
-    return u[0] > real(0) && u[E] * u[0] - kinetic_rho(u) > real(0);
+    return gt0(u[0]) && gt0(u[E] * u[0] - kinetic_rho(u));
   }
   template <typename real>
   __device__ static real indicator_var(const real* u, const Phys<real>& ph) {
@@ -521,7 +530,7 @@ struct EqTenMoment {
     const real a11 = real(2) * u[0] * u[3] - u[1] * u[1];
     const real a22 = real(2) * u[0] * u[5] - u[2] * u[2];
     const real a12 = real(2) * u[0] * u[4] - u[1] * u[2];
-    return u[0] > real(0) && a11 > real(0) && a11 * a22 - a12 * a12 > real(0);
+    return gt0(u[0]) && gt0(a11) && gt0(a11 * a22 - a12 * a12);
   }
   template <typename real>
   __device__ static real indicator_var(const real* u, const Phys<real>&) {

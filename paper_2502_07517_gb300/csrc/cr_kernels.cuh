@@ -674,10 +674,10 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
 // four 256-thread blocks per SM (64 registers; k_local 1.39 -> 1.05 ms,
 // k_update 0.91 -> 0.60 ms); the FP64 k_local is bound by the FP64 pipe and
 // gains 3% from two blocks (128 registers instead of 130); the FP64 k_update
-// is bound by its barriers and gains 11% from three blocks (85 registers
-// instead of 106: 2.15 -> 1.91 ms).
+// is bound by its barriers and gains from more resident blocks: 2.15 ms at
+// one (106 registers), 1.91 at three (85), 1.75 at four (64).
 template <bool MIXED> struct MinBlocks {
-  static constexpr int local = MIXED ? 4 : 2, update = MIXED ? 4 : 3;
+  static constexpr int local = MIXED ? 4 : 2, update = 4;
 };
 
 template <int DIM, int N, class EQ, typename real, bool MIXED>
@@ -1368,6 +1368,27 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
     for (int v = 0; v < M; ++v) ubar[v] = RED0(v);
     for (int v = k; v < M; v += NP) sEl[el * 16 + 4 + v] = RED0(v);  // for the CFL rate
   }
+  // node value in the kernel's type (FP64 mode the update itself; FP32_BULK the
+  // FP64 mean plus the re-centred FP32 fluctuation), stored for the face traces of
+  // the scaling limiter; the barrier after the limiter scalars covers it (sU is
+  // free here: the face-flux integrals it held are consumed)
+  real fl[M];
+  real ur[M];
+  real ubr[M];  // mean in the kernel's type
+#pragma unroll
+  for (int v = 0; v < M; ++v) {
+    if constexpr (MIXED) ubr[v] = sElr[el * ES + ER + 1 + v];
+    else ubr[v] = real(ubar[v]);
+    if constexpr (MIXED) {
+      fl[v] = val[v] - m32[v];
+      ur[v] = ubr[v] + fl[v];
+    } else {
+      ur[v] = val[v];
+    }
+  }
+  real* sUr = reinterpret_cast<real*>(sU);
+#pragma unroll
+  for (int v = 0; v < M; ++v) sUr[v * stride + el * NP + k] = ur[v];
   // per-element limiter scalars: sEl[el*16 + 0..3] = mean_ok, eps1, eps2, P2(u_bar),
   // for the block's elements side by side in its first epb threads (one warp)
   // from the means in shared memory.  FP32_BULK: when the FP32 copy of the mean
@@ -1410,31 +1431,11 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
   __syncthreads();
 
   // ---- positivity scaling limiter (FP64 theta) ----------------------------
-  // node value in the kernel's type: FP64 mode the update itself; FP32_BULK the
-  // FP64 mean plus the re-centred FP32 fluctuation
-  real fl[M];
-  real ur[M];
-  real ubr[M];  // mean in the kernel's type
-#pragma unroll
-  for (int v = 0; v < M; ++v) {
-    if constexpr (MIXED) ubr[v] = sElr[el * ES + ER + 1 + v];
-    else ubr[v] = real(ubar[v]);
-    if constexpr (MIXED) {
-      fl[v] = val[v] - m32[v];
-      ur[v] = ubr[v] + fl[v];
-    } else {
-      ur[v] = val[v];
-    }
-  }
   int bad = 0;
   const bool mean_ok = MIXED ? sElr[el * ES + ER + 8] != real(0) : sEl[el * 16 + 0] != 0.0;
   if (EQ::K > 0 && !mean_ok) bad |= kStInadmissible;
   const bool do_scale = (m.limiter & kLimScaling) && EQ::K > 0;
   const bool traces = (m.limiter & kLimTraces) != 0;
-  real* sUr = reinterpret_cast<real*>(sU);  // node values in the kernel's type
-#pragma unroll
-  for (int v = 0; v < M; ++v) sUr[v * stride + el * NP + k] = ur[v];
-  __syncthreads();
   if (do_scale) {
     const double eps1 = sEl[el * 16 + 1], eps2 = sEl[el * 16 + 2];
     const real P2r = MIXED ? sElr[el * ES + ER + 7] : real(sEl[el * 16 + 3]);
