@@ -31,7 +31,7 @@ struct Impl {
 
   static size_t smem_local(int epb) {
     return (((size_t)5 * M * epb * NP * sizeof(real) + 15) & ~(size_t)15) + (size_t)epb * sizeof(double) +
-           (size_t)4 * n * n * sizeof(real);
+           (size_t)4 * n * n * sizeof(real) + (size_t)epb * 4 * sizeof(int);
   }
   static constexpr int RW = 2 * M > 4 ? 2 * M : 4;
   static constexpr int MU = M > 2 ? M : 2;
