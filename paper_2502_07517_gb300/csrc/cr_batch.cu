@@ -47,7 +47,7 @@ __device__ __forceinline__ void load_params(KParams<real>* sP, const KParams<rea
   __syncthreads();
 }
 
-template <typename real, int PHASE>
+template <typename real, int PHASE, int T>
 __device__ __forceinline__ void el_tile(const BatchArgs<real>& A, KParams<real>* sP, int t, int& cur) {
   constexpr bool MIXED = sizeof(real) == 4;
   const BatchTile tile = A.t_el[t];
@@ -56,11 +56,11 @@ __device__ __forceinline__ void el_tile(const BatchArgs<real>& A, KParams<real>*
     cur = tile.prob;
   }
   if (A.deg[tile.prob] == 3) {
-    if (PHASE == 0) local_body<2, 3, Eq2, real, MIXED>(*sP, A.tb[0], tile.blk);
-    else update_body<2, 3, Eq2, real, MIXED>(*sP, A.tb[0], A.td[0], tile.blk, A.nblk_el[tile.prob]);
+    if (PHASE == 0) local_body<2, 3, Eq2, real, MIXED, T>(*sP, A.tb[0], tile.blk);
+    else update_body<2, 3, Eq2, real, MIXED, T>(*sP, A.tb[0], A.td[0], tile.blk, A.nblk_el[tile.prob]);
   } else {
-    if (PHASE == 0) local_body<2, 4, Eq2, real, MIXED>(*sP, A.tb[1], tile.blk);
-    else update_body<2, 4, Eq2, real, MIXED>(*sP, A.tb[1], A.td[1], tile.blk, A.nblk_el[tile.prob]);
+    if (PHASE == 0) local_body<2, 4, Eq2, real, MIXED, T>(*sP, A.tb[1], tile.blk);
+    else update_body<2, 4, Eq2, real, MIXED, T>(*sP, A.tb[1], A.td[1], tile.blk, A.nblk_el[tile.prob]);
   }
   __syncthreads();  // the next tile reuses the dynamic shared memory
 }
@@ -92,14 +92,14 @@ template <typename real, int T>
 __global__ void __launch_bounds__(T, (BatchMinBlocks<real, T, 0>::value)) k_batch_local(const __grid_constant__ BatchArgs<real> A) {
   __shared__ __align__(16) KParams<real> sP;
   int cur = -1;
-  el_tile<real, 0>(A, &sP, blockIdx.x, cur);
+  el_tile<real, 0, T>(A, &sP, blockIdx.x, cur);
 }
 
 template <typename real, int T>
 __global__ void __launch_bounds__(T, (BatchMinBlocks<real, T, 2>::value)) k_batch_update(const __grid_constant__ BatchArgs<real> A) {
   __shared__ __align__(16) KParams<real> sP;
   int cur = -1;
-  el_tile<real, 2>(A, &sP, blockIdx.x, cur);
+  el_tile<real, 2, T>(A, &sP, blockIdx.x, cur);
 }
 
 template <typename real, int T>
@@ -198,8 +198,8 @@ __global__ void __launch_bounds__(T, (FusedMinBlocks<real, T>::value)) k_batch_f
         ok_target = target;
       }
       if (phase == 1) face_tile<real>(A, &sP, t, cur);
-      else if (phase == 0) el_tile<real, 0>(A, &sP, t, cur);
-      else el_tile<real, 2>(A, &sP, t, cur);
+      else if (phase == 0) el_tile<real, 0, T>(A, &sP, t, cur);
+      else el_tile<real, 2, T>(A, &sP, t, cur);
       const int idx = phase * A.nprob + prob;
       if (idx != pend_idx) publish(done, pend_idx, pend);
       pend_idx = idx;

@@ -179,7 +179,7 @@ __device__ __forceinline__ FaceSlot face_slot(int gs) {
 // Body of k_local for block blk of a problem (the standalone kernel and the
 // batched kernels of cr_batch.cu call it).  Threads past the block's last whole
 // element form an invalid "ghost" slot, so any block size works.
-template <int DIM, int N, class EQ, typename real, bool MIXED>
+template <int DIM, int N, class EQ, typename real, bool MIXED, int T>
 __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<real>& tb,
                                            const int blk) {
   constexpr int n = N + 1;
@@ -193,8 +193,8 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   using TB = Tableau<N>;
   const Mesh& m = P.m;
   const Phys<real>& ph = P.ph;
-  const int epb = (blockDim.x + NP - 1) / NP;  // element slots in shared memory
-  const int epr = blockDim.x / NP;             // whole elements of the block
+  constexpr int epb = (T + NP - 1) / NP;  // element slots in shared memory
+  constexpr int epr = T / NP;             // whole elements of the block
   const int tid = threadIdx.x;
   const int el = tid / NP, k = tid - el * NP;
   const int p = DIM == 2 ? k % n : k, q = DIM == 2 ? k / n : 0;
@@ -212,8 +212,8 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sh = reinterpret_cast<real*>(smem_raw);
-  const int stride = epb * NP;
-  const int arr = M * stride;
+  constexpr int stride = epb * NP;
+  constexpr int arr = M * stride;
   real* s0 = sh;
   real* sA = sh + arr;
   real* sB = sA + arr;
@@ -261,7 +261,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   if constexpr (MIXED) {
     if (k == 0) smooth_alpha(el, ee, valid);
   } else {
-    for (int e2 = tid; e2 < epb; e2 += blockDim.x) {
+    for (int e2 = tid; e2 < epb; e2 += T) {
       const int eg0 = blk * epr + e2;
       const bool v2 = e2 < epr && eg0 < m.ne;
       smooth_alpha(e2, v2 ? eg0 : m.ne - 1, v2);
@@ -274,7 +274,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   real* sDy = sDx + n * n;
   real* sDtx = sDy + n * n;
   real* sDty = sDtx + n * n;
-  for (int t = tid; t < n * n; t += blockDim.x) {
+  for (int t = tid; t < n * n; t += T) {
     sDx[t] = P.ds.Dx[t];
     sDy[t] = P.ds.Dy[t];
     sDtx[t] = P.ds.Dtx[t];
@@ -365,7 +365,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
       const real bi = real(TB::b(i));
 #pragma unroll
       for (int mm = 0; mm < SPT; ++mm) {
-        const FaceSlot fs = face_slot<NSLOT, NFN>(tid + mm * blockDim.x);
+        const FaceSlot fs = face_slot<NSLOT, NFN>(tid + mm * T);
         if (fs.el < epr) {
           const int side = fs.side, j = fs.j;
           real ut[M], fn[M];
@@ -438,7 +438,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   }
 #pragma unroll
   for (int mm = 0; mm < SPT; ++mm) {
-    const FaceSlot fs = face_slot<NSLOT, NFN>(tid + mm * blockDim.x);
+    const FaceSlot fs = face_slot<NSLOT, NFN>(tid + mm * T);
     const int eg = blk * epr + fs.el;
     if (fs.el < epr && eg < m.ne) {
       const int side = fs.side, j = fs.j;
@@ -601,7 +601,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     // subface right of (above) node (p2, q2) reads that node's x+ (y+) state,
     // which no other flux reads, and overwrites it in place.
     constexpr int NSX = N * NFN, NSF = DIM == 2 ? 2 * N * n : N;
-    for (int gs = tid; gs < epr * NSF; gs += blockDim.x) {
+    for (int gs = tid; gs < epr * NSF; gs += T) {
       const int el2 = gs / NSF, r = gs - el2 * NSF;
       const bool isx = r < NSX;
       const int rr = isx ? r : r - NSX;
@@ -641,7 +641,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
     // candidate base of the flux limiter, u_b -+ c f_adj
 #pragma unroll
     for (int mm = 0; mm < SPT; ++mm) {
-      const FaceSlot fs = face_slot<NSLOT, NFN>(tid + mm * blockDim.x);
+      const FaceSlot fs = face_slot<NSLOT, NFN>(tid + mm * T);
       const int eg = blk * epr + fs.el;
       if (fs.el < epr && eg < m.ne) {
         const int side = fs.side, j = fs.j;
@@ -688,9 +688,19 @@ template <bool MIXED> struct MinBlocks {
   static constexpr int local = MIXED ? 4 : 2, update = 4;
 };
 
+// Threads per block of the single-problem step kernels: the whole elements
+// that fit in 256 threads (at least one); the FP32-bulk update kernel in 128
+// (barrier bound: smaller blocks wait less at each barrier, 0.482 -> 0.411 ms
+// at 512x512 N = 4; the FP64 update was slower so, 1.75 -> 1.88 ms).
+template <int NP, int THREADS = 256> struct BlockShape {
+  static constexpr int EPB = (THREADS / NP) > 0 ? (THREADS / NP) : 1;
+  static constexpr int T = EPB * NP;
+};
+template <int NP, bool MIXED> using UpdateShape = BlockShape<NP, MIXED ? 128 : 256>;
+
 template <int DIM, int N, class EQ, typename real, bool MIXED>
 __global__ void __launch_bounds__(256, MinBlocks<MIXED>::local) k_local(const __grid_constant__ KParams<real> P) {
-  local_body<DIM, N, EQ, real, MIXED>(P, P.tb, blockIdx.x);
+  local_body<DIM, N, EQ, real, MIXED, BlockShape<DIM == 2 ? (N + 1) * (N + 1) : N + 1>::T>(P, P.tb, blockIdx.x);
 }
 
 // ===========================================================================
@@ -1243,7 +1253,7 @@ __device__ __forceinline__ void rate_and_finish(const Mesh& m, const Phys<T>& ph
 // ===========================================================================
 // k_update.  Shared memory (doubles): sU [MU][epb][NP] node values, sRed
 // [RW][epb][NP] reduction buffer, sEl [epb][16] per-element values.
-template <int DIM, int N, class EQ, typename real, bool MIXED>
+template <int DIM, int N, class EQ, typename real, bool MIXED, int T>
 __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<real>& tb,
                                             const Tab<double>& td, const int blk, const int nblk) {
   constexpr int n = N + 1;
@@ -1259,8 +1269,8 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
   const double dtd = P.b.ctl->dt_step;
   const int last_step = P.b.ctl->last_step;
   if (!(dtd > 0.0)) return;
-  const int epb = (blockDim.x + NP - 1) / NP;  // element slots in shared memory
-  const int epr = blockDim.x / NP;             // whole elements of the block
+  constexpr int epb = (T + NP - 1) / NP;  // element slots in shared memory
+  constexpr int epr = T / NP;             // whole elements of the block
   const int tid = threadIdx.x;
   const int el = tid / NP, k = tid - el * NP;
   const int p = DIM == 2 ? k % n : k, q = DIM == 2 ? k / n : 0;
@@ -1268,7 +1278,7 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
   const bool valid = el < epr && e < m.ne;
   const int ee = valid ? e : m.ne - 1;
   const int ix = ee % m.nx, iy = ee / m.nx;
-  const int stride = epb * NP;
+  constexpr int stride = epb * NP;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sU = reinterpret_cast<double*>(smem_raw);  // [MU][epb][NP]
@@ -1287,7 +1297,7 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
 
   // ---- node update: partial update + element-face flux terms ------------
   const bool blend = (m.limiter & kLimBlend) || m.alpha_mode == 1;
-  for (int e2 = tid; e2 < epb; e2 += blockDim.x) {  // the block's elements side by side
+  for (int e2 = tid; e2 < epb; e2 += T) {  // the block's elements side by side
     const int eg0 = blk * epr + e2;
     sElr[e2 * ES + ER] = real(P.b.alpha[(e2 < epr && eg0 < m.ne) ? eg0 : m.ne - 1]);
   }
@@ -1352,7 +1362,7 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
     elem_reduce<NP, M>(fRed, epb, el, k, OpSum());
     // conservative FP64 mean update of eq. (upmean): one thread per (element,
     // variable), the block's elements side by side in its first threads
-    for (int t = tid; t < epb * M; t += blockDim.x) {
+    for (int t = tid; t < epb * M; t += T) {
       const int e2 = t / M, v = t - e2 * M;
       const int eg0 = blk * epr + e2;
       const int eg = (e2 < epr && eg0 < m.ne) ? eg0 : m.ne - 1;
@@ -1630,7 +1640,8 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
 
 template <int DIM, int N, class EQ, typename real, bool MIXED>
 __global__ void __launch_bounds__(256, MinBlocks<MIXED>::update) k_update(const __grid_constant__ KParams<real> P) {
-  update_body<DIM, N, EQ, real, MIXED>(P, P.tb, P.td, blockIdx.x, gridDim.x);
+  update_body<DIM, N, EQ, real, MIXED, UpdateShape<DIM == 2 ? (N + 1) * (N + 1) : N + 1, MIXED>::T>(
+      P, P.tb, P.td, blockIdx.x, gridDim.x);
 }
 
 // ===========================================================================

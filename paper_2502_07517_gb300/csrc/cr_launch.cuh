@@ -26,8 +26,9 @@ struct Impl {
   static constexpr int M = EQ::M;
   static constexpr int NFN = DIM == 2 ? n : 1;
 
-  // elements per block: about 256 threads per block (at least one element)
-  static constexpr int EPB = (256 / NP) > 0 ? (256 / NP) : 1;
+  // elements per block: about 256 threads per block (at least one element);
+  // the FP32-bulk update kernel takes UpdateShape's (128 threads)
+  static constexpr int EPB = BlockShape<NP>::EPB;
 
   static size_t smem_local(int epb) {
     return (((size_t)5 * M * epb * NP * sizeof(real) + 15) & ~(size_t)15) + (size_t)epb * sizeof(double) +
@@ -66,8 +67,9 @@ struct Impl {
   }
   static cudaError_t launch_update(const void* pv, cudaStream_t s) {
     const KParams<real>& P = *static_cast<const KParams<real>*>(pv);
-    const int grid = (P.m.ne + EPB - 1) / EPB;
-    k_update<DIM, N, EQ, real, MIXED><<<grid, EPB * NP, smem_update(EPB), s>>>(P);
+    constexpr int EU = UpdateShape<NP, MIXED>::EPB;
+    const int grid = (P.m.ne + EU - 1) / EU;
+    k_update<DIM, N, EQ, real, MIXED><<<grid, EU * NP, smem_update(EU), s>>>(P);
     return cudaGetLastError();
   }
   static cudaError_t step(const void* pv, cudaStream_t s) {
