@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(T, (BatchMinBlocks<real, T, 2>::value)) k_batc
 }
 
 template <typename real, int T>
-__global__ void __launch_bounds__(T) k_batch_face(const __grid_constant__ BatchArgs<real> A) {
+__global__ void __launch_bounds__(T, (sizeof(real) == 4 ? 4 : 3) * 256 / T) k_batch_face(const __grid_constant__ BatchArgs<real> A) {
   __shared__ __align__(16) KParams<real> sP;
   int cur = -1;
   face_tile<real>(A, &sP, blockIdx.x, cur);
