@@ -50,17 +50,17 @@ __device__ __forceinline__ void load_params(KParams<real>* sP, const KParams<rea
 template <typename real, int PHASE, int T>
 __device__ __forceinline__ void el_tile(const BatchArgs<real>& A, KParams<real>* sP, int t, int& cur) {
   constexpr bool MIXED = sizeof(real) == 4;
-  const BatchTile tile = A.t_el[t];
+  const BatchTile tile = PHASE == 2 ? A.t_upd[t] : A.t_el[t];
   if (tile.prob != cur) {
     load_params(sP, A.P + tile.prob);
     cur = tile.prob;
   }
   if (A.deg[tile.prob] == 3) {
     if (PHASE == 0) local_body<2, 3, Eq2, real, MIXED, T>(*sP, A.tb[0], tile.blk);
-    else update_body<2, 3, Eq2, real, MIXED, T>(*sP, A.tb[0], A.td[0], tile.blk, A.nblk_el[tile.prob]);
+    else update_body<2, 3, Eq2, real, MIXED, T>(*sP, A.tb[0], A.td[0], tile.blk, A.nblk_upd[tile.prob]);
   } else {
     if (PHASE == 0) local_body<2, 4, Eq2, real, MIXED, T>(*sP, A.tb[1], tile.blk);
-    else update_body<2, 4, Eq2, real, MIXED, T>(*sP, A.tb[1], A.td[1], tile.blk, A.nblk_el[tile.prob]);
+    else update_body<2, 4, Eq2, real, MIXED, T>(*sP, A.tb[1], A.td[1], tile.blk, A.nblk_upd[tile.prob]);
   }
   __syncthreads();  // the next tile reuses the dynamic shared memory
 }
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(T, (FusedMinBlocks<real, T>::value)) k_batch_f
   __shared__ unsigned sNext;
   __shared__ int sFlag;
   int cur = -1;
-  const unsigned per_step = 2u * unsigned(A.n_el) + unsigned(A.n_face);
+  const unsigned per_step = unsigned(A.n_el) + unsigned(A.n_face) + unsigned(A.n_upd);
   const unsigned total = per_step * unsigned(A.nsteps);
   const unsigned chunk = unsigned(A.tiles) * kFusedClaim;
   unsigned* done = A.queue + 1;  // [phase][prob]
@@ -184,11 +184,11 @@ __global__ void __launch_bounds__(T, (FusedMinBlocks<real, T>::value)) k_batch_f
       const int r = int(item - unsigned(s) * per_step);
       const int phase = r < A.n_el ? 0 : (r < A.n_el + A.n_face ? 1 : 2);
       const int t = phase == 0 ? r : (phase == 1 ? r - A.n_el : r - A.n_el - A.n_face);
-      const int prob = phase == 1 ? A.t_face[t].prob : A.t_el[t].prob;
+      const int prob = phase == 1 ? A.t_face[t].prob : (phase == 0 ? A.t_el[t].prob : A.t_upd[t].prob);
       // the work this item reads: the previous step's update (local phase),
       // this step's local phase (face phase), this step's face phase (update)
       const int dep = phase == 0 ? 2 : phase - 1;
-      const unsigned per = unsigned(dep == 1 ? A.nblk_face[prob] : A.nblk_el[prob]);
+      const unsigned per = unsigned(dep == 0 ? A.nblk_el[prob] : (dep == 1 ? A.nblk_face[prob] : A.nblk_upd[prob]));
       const unsigned target = per * unsigned(phase == 0 ? s : s + 1) + unsigned(A.phantom);
       const int key = dep * A.nprob + prob;
       if (key != ok_key || target > ok_target) {
@@ -243,7 +243,7 @@ cudaError_t launch_phase_t(int phase, const BatchArgs<real>& A, cudaStream_t s) 
   } else if (phase == 1) {
     if (A.n_face > 0) k_batch_face<real, T><<<A.n_face, T, 0, s>>>(A);
   } else {
-    if (A.n_el > 0) k_batch_update<real, T><<<A.n_el, T, sm, s>>>(A);
+    if (A.n_upd > 0) k_batch_update<real, T><<<A.n_upd, T, sm, s>>>(A);
   }
   return cudaGetLastError();
 }
@@ -303,9 +303,11 @@ size_t batch_smem(int threads, bool fp32) {
 }
 
 cudaError_t batch_configure(int threads, bool fp32) {
-  if (threads == 128) return fp32 ? configure_t<float, 128>() : configure_t<double, 128>();
-  if (threads == 256) return fp32 ? configure_t<float, 256>() : configure_t<double, 256>();
-  return cudaErrorInvalidValue;
+  if (threads != 128 && threads != 256) return cudaErrorInvalidValue;
+  // both sizes: the update phase may run in blocks of its own size
+  cudaError_t e = fp32 ? configure_t<float, 128>() : configure_t<double, 128>();
+  if (e == cudaSuccess) e = fp32 ? configure_t<float, 256>() : configure_t<double, 256>();
+  return e;
 }
 
 cudaError_t batch_fused_max_blocks(int threads, bool fp32, int* blocks) {
@@ -317,12 +319,14 @@ cudaError_t batch_fused_max_blocks(int threads, bool fp32, int* blocks) {
 cudaError_t batch_launch_phase(int threads, int phase, const void* args, bool fp32, cudaStream_t s) {
   if (fp32) {
     const BatchArgs<float>& A = *static_cast<const BatchArgs<float>*>(args);
-    if (threads == 128) return launch_phase_t<float, 128>(phase, A, s);
-    if (threads == 256) return launch_phase_t<float, 256>(phase, A, s);
+    const int t = phase == 2 ? A.upd_threads : threads;
+    if (t == 128) return launch_phase_t<float, 128>(phase, A, s);
+    if (t == 256) return launch_phase_t<float, 256>(phase, A, s);
   } else {
     const BatchArgs<double>& A = *static_cast<const BatchArgs<double>*>(args);
-    if (threads == 128) return launch_phase_t<double, 128>(phase, A, s);
-    if (threads == 256) return launch_phase_t<double, 256>(phase, A, s);
+    const int t = phase == 2 ? A.upd_threads : threads;
+    if (t == 128) return launch_phase_t<double, 128>(phase, A, s);
+    if (t == 256) return launch_phase_t<double, 256>(phase, A, s);
   }
   return cudaErrorInvalidValue;
 }

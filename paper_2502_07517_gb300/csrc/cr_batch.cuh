@@ -26,6 +26,10 @@ struct BatchArgs {
   int n_el;
   const BatchTile* t_face;      // face-node tiles, all problems
   int n_face;
+  const BatchTile* t_upd;       // element tiles of the update phase (blocks of upd_threads)
+  int n_upd;
+  const int* nblk_upd;          // [nprob] update blocks of the problem
+  int upd_threads;              // threads per block of the update phase
   int nprob;
   int tiles;                    // fused launch: tiles per claim = kFusedClaim * tiles
   unsigned* queue;              // fused launch: [0] next unclaimed work item, then the tiles

@@ -1053,8 +1053,8 @@ struct cr_batch {
   int phantom = 0;                             // test hook: completions that never come
   int fused_grid = 0;
   unsigned char* dmem = nullptr;     // parameters, degrees, block counts, tiles, queue, error flag
-  size_t params_off = 0, deg_off = 0, nblk_off = 0, nface_off = 0, tel_off = 0, tface_off = 0,
-         queue_off = 0, err_off = 0;
+  size_t params_off = 0, deg_off = 0, nblk_off = 0, nface_off = 0, nupd_off = 0, tel_off = 0,
+         tface_off = 0, tupd_off = 0, queue_off = 0, err_off = 0;
   size_t max_el = 0, max_face = 0;   // tile capacity (the smallest block size)
   BatchArgs<float> af{};
   BatchArgs<double> ad{};
@@ -1102,21 +1102,30 @@ void destroy_graphs(cr_batch* b) {
 cr_status batch_build(cr_batch* b) {
   destroy_graphs(b);
   const int nprob = (int)b->ctx.size();
-  std::vector<BatchTile> tel, tface;
-  std::vector<int> nblk(nprob), nblkf(nprob);
+  // the update phase of FP32-bulk batches launched per phase runs in 128-thread
+  // blocks, as the single-problem FP32-bulk update (barrier bound: smaller
+  // blocks wait less); every other phase in blocks of b->threads
+  const int upd_threads = (b->fp32 && b->mode == CR_BATCH_PHASES) ? kBatchThreadChoices[0] : b->threads;
+  std::vector<BatchTile> tel, tface, tupd;
+  std::vector<int> nblk(nprob), nblkf(nprob), nblku(nprob);
   for (int i = 0; i < nprob; ++i) {
-    int nel, nface;
+    int nel, nface, nupd, unused;
     tile_counts(b->ctx[i], b->threads, &nel, &nface);
+    tile_counts(b->ctx[i], upd_threads, &nupd, &unused);
     nblk[i] = nel;
     nblkf[i] = nface;
+    nblku[i] = nupd;
+    for (int k = 0; k < nupd; ++k) tupd.push_back({i, k});
     for (int k = 0; k < nel; ++k) tel.push_back({i, k});
     for (int k = 0; k < nface; ++k) tface.push_back({i, k});
   }
-  if (tel.size() > b->max_el || tface.size() > b->max_face)
+  if (tel.size() > b->max_el || tface.size() > b->max_face || tupd.size() > b->max_el)
     return bfail(b, CR_E_INVALID_ARG, "tile capacity exceeded");
   unsigned char* d = b->dmem;
   CR_BCUDA(b, cudaMemcpyAsync(d + b->nblk_off, nblk.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, b->stream));
   CR_BCUDA(b, cudaMemcpyAsync(d + b->nface_off, nblkf.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  CR_BCUDA(b, cudaMemcpyAsync(d + b->nupd_off, nblku.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  CR_BCUDA(b, cudaMemcpyAsync(d + b->tupd_off, tupd.data(), tupd.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
   CR_BCUDA(b, cudaMemcpyAsync(d + b->tel_off, tel.data(), tel.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
   CR_BCUDA(b, cudaMemcpyAsync(d + b->tface_off, tface.data(), tface.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
   CR_BCUDA(b, cudaStreamSynchronize(b->stream));
@@ -1129,6 +1138,10 @@ cr_status batch_build(cr_batch* b) {
     A.n_el = (int)tel.size();
     A.t_face = reinterpret_cast<const BatchTile*>(d + b->tface_off);
     A.n_face = (int)tface.size();
+    A.t_upd = reinterpret_cast<const BatchTile*>(d + b->tupd_off);
+    A.n_upd = (int)tupd.size();
+    A.nblk_upd = reinterpret_cast<const int*>(d + b->nupd_off);
+    A.upd_threads = upd_threads;
     A.nprob = nprob;
     A.tiles = b->tiles;
     A.queue = reinterpret_cast<unsigned*>(d + b->queue_off);
@@ -1253,8 +1266,10 @@ cr_status cr_batch_init(cr_ctx* const* ctxs, int n, cr_batch** out) {
   b->deg_off = take(sizeof(int) * n);
   b->nblk_off = take(sizeof(int) * n);
   b->nface_off = take(sizeof(int) * n);
+  b->nupd_off = take(sizeof(int) * n);
   b->tel_off = take(sizeof(BatchTile) * mel);
   b->tface_off = take(sizeof(BatchTile) * mface);
+  b->tupd_off = take(sizeof(BatchTile) * mel);
   b->queue_off = take(sizeof(unsigned) * (1 + 3 * (size_t)n));
   b->err_off = take(16);
   cudaError_t e = cudaMalloc(&b->dmem, off);
