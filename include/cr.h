@@ -157,9 +157,10 @@ void cr_destroy(cr_ctx* ctx);
 
 /* Copy the state u[M][Ne][Np] (FP64) in, reset time to 0, and compute the
  * first time step (eq. (time.step.2d)) and the indicator.  Synchronises.
- * on_device == 0: u is host memory that the GPU reads directly (pinned memory,
- * or any host memory on a system where the GPU shares the CPU's address
- * translation, as on GB300); on_device == 1: a device pointer.  The input is
+ * on_device == 0: u is host memory (pageable or pinned); on_device == 1: a
+ * device pointer.  In FP64, pinned host input is read by the kernel that
+ * checks it (over the host link, the transfer overlapping the check, the
+ * indicator and the CFL rate); other input is copied first.  The input is
  * checked on the device.  Errors: CR_E_INVALID_STATE when a solution point is
  * not finite or (for equations with an admissible set, Sec. 2 eq. (uad.form))
  * not admissible. */

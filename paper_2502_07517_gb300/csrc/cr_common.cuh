@@ -113,6 +113,8 @@ struct Bufs {
   const int* mlp_flag;              // != 0 once network weights are loaded
   const unsigned short* mlp_w;      // BF16 network weights (learned alpha)
   float* feat;                      // when not null, the prologue writes network inputs [Ne][Np]
+  const double* u_src;              // when not null (FP64), the prologue reads the state from
+                                    // here (pinned host memory) and stores it into u
 };
 
 // Physical constants in the arithmetic type of the kernel (no FP64 work leaks

@@ -624,6 +624,7 @@ void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
   b.mlp_flag = reinterpret_cast<const int*>(w + c->L.mlp);
   b.mlp_w = reinterpret_cast<const unsigned short*>(w + c->L.mlp + 16);
   b.feat = nullptr;
+  b.u_src = nullptr;
 }
 
 cr_status read_ctl(cr_ctx* c) {
@@ -837,13 +838,30 @@ cr_status cr_set_state(cr_ctx* c, const double* u, int on_device) {
   k_reset_ctl<<<1, 1, 0, c->stream>>>(c->d_ctl, c->d.cfl_safety * c->cfl);
   CR_CUDA(c, cudaGetLastError());
   const double* src = u;
-  if (c->ks->mixed) {
-    double* staging = reinterpret_cast<double*>(c->ws + c->L.staging);
-    CR_CUDA(c, cudaMemcpyAsync(staging, u, nvals * sizeof(double), cudaMemcpyDefault, c->stream));
-    src = staging;
+  // FP64 input in pinned host memory: the prologue kernel reads it over the
+  // host link itself and keeps the copy, so the transfer and the input check,
+  // indicator and CFL rate overlap instead of running one after the other
+  const double* pinned = nullptr;
+  if (!on_device && !c->ks->mixed) {
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, u) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer)
+      pinned = static_cast<const double*>(pa.devicePointer);
+    cudaGetLastError();
   }
-  CR_CUDA(c, c->ks->split(c->params, src, c->stream));
-  CR_CUDA(c, c->ks->prologue(c->params, c->stream));
+  if (pinned) {
+    KParams<double> P = c->pd;
+    P.b.u_src = pinned;
+    CR_CUDA(c, c->ks->prologue(&P, c->stream));
+  } else {
+    if (c->ks->mixed) {
+      double* staging = reinterpret_cast<double*>(c->ws + c->L.staging);
+      CR_CUDA(c, cudaMemcpyAsync(staging, u, nvals * sizeof(double), cudaMemcpyDefault, c->stream));
+      src = staging;
+    }
+    CR_CUDA(c, c->ks->split(c->params, src, c->stream));
+    CR_CUDA(c, c->ks->prologue(c->params, c->stream));
+  }
   cr_status st = read_ctl(c);
   if (st != CR_OK) return st;
   if (c->h_ctl->status & kStInvalidInput)

@@ -1677,8 +1677,17 @@ __global__ void k_prologue(const __grid_constant__ KParams<real> P) {
   int bad = 0;
 #pragma unroll
   for (int v = 0; v < M; ++v) {
-    u[v] = double(P.b.u[((size_t)v * m.ne + ee) * NP + k]);
-    if constexpr (MIXED) u[v] += P.b.umean[(size_t)v * m.ne + ee];
+    const size_t gi = ((size_t)v * m.ne + ee) * NP + k;
+    if constexpr (!MIXED) {
+      if (P.b.u_src) {  // the state straight from pinned host memory: load once, keep a copy
+        u[v] = P.b.u_src[gi];
+        if (valid) P.b.u[gi] = real(u[v]);
+      } else {
+        u[v] = double(P.b.u[gi]);
+      }
+    } else {
+      u[v] = double(P.b.u[gi]) + P.b.umean[(size_t)v * m.ne + ee];
+    }
     if (!isfinite(u[v])) bad = kStInvalidInput;
     sRed[(v * epb + el) * NP + k] = W * u[v];
   }
