@@ -1096,20 +1096,40 @@ __device__ float mlp_alpha(const unsigned short* __restrict__ w, float x, float*
   const unsigned short* W3 = B2 + kMlpH;
   const unsigned short* B3 = W3 + kMlpH;
   if (warp < nw) {  // full warps only (blockDim need not be a multiple of 32)
-    for (int e2 = warp; e2 < epb; e2 += nw) {
-      const float* xe = X + e2 * NP;
-      float h = bf16_to_float(B1[lane]);
+    // two elements per warp at a time: their dependent FMA chains interleave
+    // (each element's arithmetic in the same order as alone)
+    for (int e2 = warp; e2 < epb; e2 += 2 * nw) {
+      const int e3 = e2 + nw < epb ? e2 + nw : e2;  // a second element, or e2 again
+      const float* xa = X + e2 * NP;
+      const float* xb = X + e3 * NP;
+      float ha = bf16_to_float(B1[lane]), hb = ha;
 #pragma unroll
-      for (int i = 0; i < NP; ++i) h = fmaf(bf16_to_float(W1[i * kMlpH + lane]), xe[i], h);
-      h = fmaxf(h, 0.0f);
-      float a = bf16_to_float(B2[lane]);
+      for (int i = 0; i < NP; ++i) {
+        const float wv = bf16_to_float(W1[i * kMlpH + lane]);
+        ha = fmaf(wv, xa[i], ha);
+        hb = fmaf(wv, xb[i], hb);
+      }
+      ha = fmaxf(ha, 0.0f);
+      hb = fmaxf(hb, 0.0f);
+      float aa = bf16_to_float(B2[lane]), ab = aa;
 #pragma unroll
-      for (int i = 0; i < kMlpH; ++i)
-        a = fmaf(bf16_to_float(W2[i * kMlpH + lane]), __shfl_sync(0xffffffffu, h, i), a);
-      float z = bf16_to_float(W3[lane]) * fmaxf(a, 0.0f);
+      for (int i = 0; i < kMlpH; ++i) {
+        const float wv = bf16_to_float(W2[i * kMlpH + lane]);
+        aa = fmaf(wv, __shfl_sync(0xffffffffu, ha, i), aa);
+        ab = fmaf(wv, __shfl_sync(0xffffffffu, hb, i), ab);
+      }
+      const float w3 = bf16_to_float(W3[lane]);
+      float za = w3 * fmaxf(aa, 0.0f), zb = w3 * fmaxf(ab, 0.0f);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-      if (lane == 0) Y[e2] = 1.0f / (1.0f + expf(-(z + bf16_to_float(B3[0]))));
+      for (int o = 16; o > 0; o >>= 1) {
+        za += __shfl_xor_sync(0xffffffffu, za, o);
+        zb += __shfl_xor_sync(0xffffffffu, zb, o);
+      }
+      if (lane == 0) {
+        const float b3 = bf16_to_float(B3[0]);
+        Y[e2] = 1.0f / (1.0f + expf(-(za + b3)));
+        Y[e3] = 1.0f / (1.0f + expf(-(zb + b3)));
+      }
     }
   }
   __syncthreads();
