@@ -6,8 +6,9 @@
 // block body as the single-problem kernels; the reference tables, which depend
 // only on the degree, stay kernel parameters as in the single-problem kernels.
 //
-//   k_batch_local / k_batch_face / k_batch_update : one launch per phase over
-//       the tiles of every problem (three launches per step for the batch).
+//   k_batch_local_n / k_batch_face / k_batch_update_n : one launch per phase
+//       over the tiles of every problem (per degree for the element phases:
+//       up to five launches per step for the batch).
 //   k_batch_fused : one cooperative, persistent launch for all phases of
 //       nsteps steps.  The work items (step, phase, tile) form one queue in
 //       that order; blocks claim kFusedClaim * A.tiles consecutive items at a
@@ -85,21 +86,35 @@ struct BatchMinBlocks {
   static constexpr int value = per256 * 256 / T;
 };
 
-// One tile per block: a loop over several consecutive tiles per block was
-// measured 15-25% slower on the 96-problem ensemble (48 against 55-61 ms per
-// step), so the tiles per block apply to the fused kernel's claims only.
-template <typename real, int T>
-__global__ void __launch_bounds__(T, (BatchMinBlocks<real, T, 0>::value)) k_batch_local(const __grid_constant__ BatchArgs<real> A) {
+// Phase kernels for the tiles of one degree N: blocks of exactly the whole
+// elements that fit in T threads (TB threads, as the single-problem kernels),
+// the body of that degree only.  One tile per block: a loop over several
+// consecutive tiles per block was measured 15-25% slower on the 96-problem
+// ensemble (48 against 55-61 ms per step), so the tiles per block apply to the
+// fused kernel's claims only.
+template <int N, int T> struct DegShape {
+  static constexpr int NP = (N + 1) * (N + 1);
+  static constexpr int EPB = T / NP;
+  static constexpr int TB = EPB * NP;
+};
+
+template <typename real, int N, int T>
+__global__ void __launch_bounds__(DegShape<N, T>::TB, (BatchMinBlocks<real, T, 0>::value)) k_batch_local_n(const __grid_constant__ BatchArgs<real> A) {
   __shared__ __align__(16) KParams<real> sP;
-  int cur = -1;
-  el_tile<real, 0, T>(A, &sP, blockIdx.x, cur);
+  constexpr bool MIXED = sizeof(real) == 4;
+  const BatchTile tile = A.t_el[A.el_first[N - 3] + blockIdx.x];
+  load_params(&sP, A.P + tile.prob);
+  local_body<2, N, Eq2, real, MIXED, DegShape<N, T>::TB>(sP, A.tb[N - 3], tile.blk);
 }
 
-template <typename real, int T>
-__global__ void __launch_bounds__(T, (BatchMinBlocks<real, T, 2>::value)) k_batch_update(const __grid_constant__ BatchArgs<real> A) {
+template <typename real, int N, int T>
+__global__ void __launch_bounds__(DegShape<N, T>::TB, (BatchMinBlocks<real, T, 2>::value)) k_batch_update_n(const __grid_constant__ BatchArgs<real> A) {
   __shared__ __align__(16) KParams<real> sP;
-  int cur = -1;
-  el_tile<real, 2, T>(A, &sP, blockIdx.x, cur);
+  constexpr bool MIXED = sizeof(real) == 4;
+  const BatchTile tile = A.t_upd[A.upd_first[N - 3] + blockIdx.x];
+  load_params(&sP, A.P + tile.prob);
+  update_body<2, N, Eq2, real, MIXED, DegShape<N, T>::TB>(sP, A.tb[N - 3], A.td[N - 3], tile.blk,
+                                                           A.nblk_upd[tile.prob]);
 }
 
 template <typename real, int T>
@@ -224,26 +239,49 @@ size_t smem_for(int threads) {
   return m;
 }
 
+// Dynamic shared memory of the one-degree phase kernels (whole elements only).
+template <typename real, int N, int T>
+size_t smem_local_n() {
+  return Impl<2, N, Eq2, real, sizeof(real) == 4>::smem_local(DegShape<N, T>::EPB);
+}
+template <typename real, int N, int T>
+size_t smem_update_n() {
+  return Impl<2, N, Eq2, real, sizeof(real) == 4>::smem_update(DegShape<N, T>::EPB);
+}
+
 template <typename real, int T>
 cudaError_t configure_t() {
   const int sm = (int)smem_for<real>(T);
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_batch_local<real, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+  if ((e = cudaFuncSetAttribute(k_batch_local_n<real, 3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_local_n<real, 3, T>())))
     return e;
-  if ((e = cudaFuncSetAttribute(k_batch_update<real, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+  if ((e = cudaFuncSetAttribute(k_batch_local_n<real, 4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_local_n<real, 4, T>())))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_batch_update_n<real, 3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_update_n<real, 3, T>())))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_batch_update_n<real, 4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_update_n<real, 4, T>())))
     return e;
   return cudaFuncSetAttribute(k_batch_fused<real, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 template <typename real, int T>
 cudaError_t launch_phase_t(int phase, const BatchArgs<real>& A, cudaStream_t s) {
-  const size_t sm = smem_for<real>(T);
-  if (phase == 0) {
-    if (A.n_el > 0) k_batch_local<real, T><<<A.n_el, T, sm, s>>>(A);
+  if (phase == 0) {  // one launch per degree present
+    if (A.el_count[0] > 0)
+      k_batch_local_n<real, 3, T><<<A.el_count[0], DegShape<3, T>::TB, smem_local_n<real, 3, T>(), s>>>(A);
+    if (A.el_count[1] > 0)
+      k_batch_local_n<real, 4, T><<<A.el_count[1], DegShape<4, T>::TB, smem_local_n<real, 4, T>(), s>>>(A);
   } else if (phase == 1) {
     if (A.n_face > 0) k_batch_face<real, T><<<A.n_face, T, 0, s>>>(A);
   } else {
-    if (A.n_upd > 0) k_batch_update<real, T><<<A.n_upd, T, sm, s>>>(A);
+    if (A.upd_count[0] > 0)
+      k_batch_update_n<real, 3, T><<<A.upd_count[0], DegShape<3, T>::TB, smem_update_n<real, 3, T>(), s>>>(A);
+    if (A.upd_count[1] > 0)
+      k_batch_update_n<real, 4, T><<<A.upd_count[1], DegShape<4, T>::TB, smem_update_n<real, 4, T>(), s>>>(A);
   }
   return cudaGetLastError();
 }

@@ -30,6 +30,8 @@ struct BatchArgs {
   int n_upd;
   const int* nblk_upd;          // [nprob] update blocks of the problem
   int upd_threads;              // threads per block of the update phase
+  int el_first[2], el_count[2];   // element tiles of degree 3 and 4 (t_el holds them in that order)
+  int upd_first[2], upd_count[2]; // likewise for t_upd
   int nprob;
   int tiles;                    // fused launch: tiles per claim = kFusedClaim * tiles
   unsigned* queue;              // fused launch: [0] next unclaimed work item, then the tiles

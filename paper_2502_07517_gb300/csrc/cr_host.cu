@@ -1124,18 +1124,28 @@ cr_status batch_build(cr_batch* b) {
   // blocks, as the single-problem FP32-bulk update (barrier bound: smaller
   // blocks wait less); every other phase in blocks of b->threads
   const int upd_threads = (b->fp32 && b->mode == CR_BATCH_PHASES) ? kBatchThreadChoices[0] : b->threads;
+  // element tiles grouped by degree (3, then 4): the element phases launch one
+  // kernel per degree over its contiguous range
   std::vector<BatchTile> tel, tface, tupd;
   std::vector<int> nblk(nprob), nblkf(nprob), nblku(nprob);
-  for (int i = 0; i < nprob; ++i) {
-    int nel, nface, nupd, unused;
-    tile_counts(b->ctx[i], b->threads, &nel, &nface);
-    tile_counts(b->ctx[i], upd_threads, &nupd, &unused);
-    nblk[i] = nel;
-    nblkf[i] = nface;
-    nblku[i] = nupd;
-    for (int k = 0; k < nupd; ++k) tupd.push_back({i, k});
-    for (int k = 0; k < nel; ++k) tel.push_back({i, k});
-    for (int k = 0; k < nface; ++k) tface.push_back({i, k});
+  int el_first[2] = {0, 0}, el_count[2] = {0, 0}, upd_first[2] = {0, 0}, upd_count[2] = {0, 0};
+  for (int g = 0; g < 2; ++g) {
+    el_first[g] = (int)tel.size();
+    upd_first[g] = (int)tupd.size();
+    for (int i = 0; i < nprob; ++i) {
+      if (b->ctx[i]->d.degree != 3 + g) continue;
+      int nel, nface, nupd, unused;
+      tile_counts(b->ctx[i], b->threads, &nel, &nface);
+      tile_counts(b->ctx[i], upd_threads, &nupd, &unused);
+      nblk[i] = nel;
+      nblkf[i] = nface;
+      nblku[i] = nupd;
+      for (int k = 0; k < nupd; ++k) tupd.push_back({i, k});
+      for (int k = 0; k < nel; ++k) tel.push_back({i, k});
+      for (int k = 0; k < nface; ++k) tface.push_back({i, k});
+    }
+    el_count[g] = (int)tel.size() - el_first[g];
+    upd_count[g] = (int)tupd.size() - upd_first[g];
   }
   if (tel.size() > b->max_el || tface.size() > b->max_face || tupd.size() > b->max_el)
     return bfail(b, CR_E_INVALID_ARG, "tile capacity exceeded");
@@ -1160,6 +1170,12 @@ cr_status batch_build(cr_batch* b) {
     A.n_upd = (int)tupd.size();
     A.nblk_upd = reinterpret_cast<const int*>(d + b->nupd_off);
     A.upd_threads = upd_threads;
+    for (int g = 0; g < 2; ++g) {
+      A.el_first[g] = el_first[g];
+      A.el_count[g] = el_count[g];
+      A.upd_first[g] = upd_first[g];
+      A.upd_count[g] = upd_count[g];
+    }
     A.nprob = nprob;
     A.tiles = b->tiles;
     A.queue = reinterpret_cast<unsigned*>(d + b->queue_off);
