@@ -1423,7 +1423,7 @@ cr_status cr_batch_autotune(cr_batch* b, int trial_steps, int* threads_out, int*
   CR_BCUDA(b, cudaEventCreate(&e1));
   const void* P = b->dmem + b->params_off;
   cr_status st = CR_OK;
-  // Round 0 warms every candidate up (graph upload, first launch); rounds
+  // Pass 0 warms every candidate up (graph upload, first launch); passes
   // 1..trial_steps time one step of each candidate in turn, so the state the
   // problems reach as they advance is shared fairly between the candidates;
   // each candidate keeps its fastest step.
