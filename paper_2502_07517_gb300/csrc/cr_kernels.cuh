@@ -158,6 +158,119 @@ struct OpMin {
   __device__ T operator()(T a, T b) const { return fmin(a, b); }
 };
 
+// ---------------------------------------------------------------------------
+// Arithmetic over the M variables of a point.  In FP32 the variables go two at
+// a time through Blackwell's packed FP32 instructions (FFMA2, FADD2, FMUL2: one
+// instruction for two lanes, each lane rounded exactly like the scalar
+// instruction), so the results equal those of the scalar loop bit for bit with
+// half the issue slots; FP64 stays scalar.  The element kernel's shared-memory
+// node arrays keep the two variables of a pair side by side in FP32
+// (VarPack<float>::VL = 2, one 64-bit access per pair): variable v of node
+// slot i sits at base[((v / VL) * stride + i) * VL + v % VL], so the groups of
+// a node lie GS = VL * stride apart.
+template <typename real> struct VarPack { static constexpr int VL = 1; };
+template <> struct VarPack<float> { static constexpr int VL = 2; };
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// y = fma(a, x, z) per variable (y may alias x or z)
+template <int M>
+__device__ __forceinline__ void vfma(float (&y)[M], float a, const float (&x)[M], const float (&z)[M]) {
+#pragma unroll
+  for (int v = 0; v + 1 < M; v += 2) {
+    const float2 r = __ffma2_rn(f2(a, a), f2(x[v], x[v + 1]), f2(z[v], z[v + 1]));
+    y[v] = r.x;
+    y[v + 1] = r.y;
+  }
+  if (M & 1) y[M - 1] = fmaf(a, x[M - 1], z[M - 1]);
+}
+template <int M>
+__device__ __forceinline__ void vfma(double (&y)[M], double a, const double (&x)[M], const double (&z)[M]) {
+#pragma unroll
+  for (int v = 0; v < M; ++v) y[v] = fma(a, x[v], z[v]);
+}
+// y = fma(a, x, y) per variable
+template <int M, typename real>
+__device__ __forceinline__ void vfma(real (&y)[M], real a, const real (&x)[M]) {
+  vfma(y, a, x, y);
+}
+// y = x - z per variable (as fma(z, -1, x): the same rounding as the subtraction)
+template <int M>
+__device__ __forceinline__ void vsub(float (&y)[M], const float (&x)[M], const float (&z)[M]) {
+#pragma unroll
+  for (int v = 0; v + 1 < M; v += 2) {
+    const float2 r = __ffma2_rn(f2(z[v], z[v + 1]), f2(-1.0f, -1.0f), f2(x[v], x[v + 1]));
+    y[v] = r.x;
+    y[v + 1] = r.y;
+  }
+  if (M & 1) y[M - 1] = x[M - 1] - z[M - 1];
+}
+template <int M>
+__device__ __forceinline__ void vsub(double (&y)[M], const double (&x)[M], const double (&z)[M]) {
+#pragma unroll
+  for (int v = 0; v < M; ++v) y[v] = x[v] - z[v];
+}
+// y = x * a per variable
+template <int M>
+__device__ __forceinline__ void vmul(float (&y)[M], const float (&x)[M], float a) {
+#pragma unroll
+  for (int v = 0; v + 1 < M; v += 2) {
+    const float2 r = __fmul2_rn(f2(x[v], x[v + 1]), f2(a, a));
+    y[v] = r.x;
+    y[v + 1] = r.y;
+  }
+  if (M & 1) y[M - 1] = x[M - 1] * a;
+}
+template <int M>
+__device__ __forceinline__ void vmul(double (&y)[M], const double (&x)[M], double a) {
+#pragma unroll
+  for (int v = 0; v < M; ++v) y[v] = x[v] * a;
+}
+// y = fma(a, (node values at p), y): p points at the node's first variable
+template <int M, int GS>
+__device__ __forceinline__ void vfma_sh(float (&y)[M], float a, const float* p) {
+#pragma unroll
+  for (int v = 0; v + 1 < M; v += 2) {
+    const float2 x = *reinterpret_cast<const float2*>(p + (v / 2) * GS);
+    const float2 r = __ffma2_rn(f2(a, a), x, f2(y[v], y[v + 1]));
+    y[v] = r.x;
+    y[v + 1] = r.y;
+  }
+  if (M & 1) y[M - 1] = fmaf(a, p[(M / 2) * GS], y[M - 1]);
+}
+template <int M, int GS>
+__device__ __forceinline__ void vfma_sh(double (&y)[M], double a, const double* p) {
+#pragma unroll
+  for (int v = 0; v < M; ++v) y[v] = fma(a, p[v * GS], y[v]);
+}
+// node values at p -> x, and x -> node values at p
+template <int M, int GS>
+__device__ __forceinline__ void vld_sh(float (&x)[M], const float* p) {
+#pragma unroll
+  for (int v = 0; v + 1 < M; v += 2) {
+    const float2 w = *reinterpret_cast<const float2*>(p + (v / 2) * GS);
+    x[v] = w.x;
+    x[v + 1] = w.y;
+  }
+  if (M & 1) x[M - 1] = p[(M / 2) * GS];
+}
+template <int M, int GS>
+__device__ __forceinline__ void vld_sh(double (&x)[M], const double* p) {
+#pragma unroll
+  for (int v = 0; v < M; ++v) x[v] = p[v * GS];
+}
+template <int M, int GS>
+__device__ __forceinline__ void vst_sh(float* p, const float (&x)[M]) {
+#pragma unroll
+  for (int v = 0; v + 1 < M; v += 2) *reinterpret_cast<float2*>(p + (v / 2) * GS) = f2(x[v], x[v + 1]);
+  if (M & 1) p[(M / 2) * GS] = x[M - 1];
+}
+template <int M, int GS>
+__device__ __forceinline__ void vst_sh(double* p, const double (&x)[M]) {
+#pragma unroll
+  for (int v = 0; v < M; ++v) p[v * GS] = x[v];
+}
+
 // Face-node slot gs of a block, the slots numbered across the block so that
 // the threads left without one form whole idle warps (FP64 pipe time and
 // issue slots are charged per warp instruction): element el of the block
@@ -212,29 +325,33 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* sh = reinterpret_cast<real*>(smem_raw);
+  // node arrays [M / VL][epb][NP][VL] (VarPack: FP32 variable pairs side by side)
+  constexpr int VL = VarPack<real>::VL;
+  constexpr int MV = (M + VL - 1) / VL * VL;
   constexpr int stride = epb * NP;
-  constexpr int arr = M * stride;
+  constexpr int GS = VL * stride;
+  constexpr int arr = MV * stride;
   real* s0 = sh;
   real* sA = sh + arr;
   real* sB = sA + arr;
   real* sC = sB + arr;
   real* sD = sC + arr;
-#define AT(base, v, node) base[(v) * stride + el * NP + (node)]
-#define ATE(base, v, elx, node) base[(v) * stride + (elx) * NP + (node)]
+#define AT(base, v, node) base[(((v) / VL) * stride + el * NP + (node)) * VL + (v) % VL]
+#define ATE(base, v, elx, node) base[(((v) / VL) * stride + (elx) * NP + (node)) * VL + (v) % VL]
+#define ATP(base, node) (&AT(base, 0, node))
+#define ATPE(base, elx, node) (&ATE(base, 0, elx, node))
 
   real un[M];
 #pragma unroll
-  for (int v = 0; v < M; ++v) {
-    un[v] = load_state<real, MIXED>(P.b, m.ne, NP, v, ee, k);
-    AT(s0, v, k) = un[v];
-  }
+  for (int v = 0; v < M; ++v) un[v] = load_state<real, MIXED>(P.b, m.ne, NP, v, ee, k);
+  vst_sh<M, GS>(ATP(s0, k), un);
 
   // blending coefficient alpha_e, smoothed with the face neighbours, broadcast
   // through shared memory.  FP64: the block's elements side by side in its
   // first threads (one FP64-pipe warp instruction per operation for the whole
   // block); FP32 bulk: thread 0 of each element (measured 2.5% faster there).
   double* sAlpha = reinterpret_cast<double*>(
-      smem_raw + (((size_t)5 * M * epb * NP * sizeof(real) + 15) & ~(size_t)15));
+      smem_raw + (((size_t)5 * MV * epb * NP * sizeof(real) + 15) & ~(size_t)15));
   // the element's face neighbours (-1: a boundary side) are kept in shared
   // memory for the MUSCL-Hancock halo as well (measured 2.3% faster FP32 bulk
   // k_local than every boundary node recomputing them)
@@ -312,50 +429,42 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
 
 #pragma unroll
   for (int i = 0; i < S; ++i) {
+    // u^(i) = u^n - dt sum_j a_ij L_j; the arithmetic over the variables goes
+    // through the v* helpers (FP32: two variables per instruction)
     real ui[M];
 #pragma unroll
-    for (int v = 0; v < M; ++v) {
-      real acc = un[v];
+    for (int v = 0; v < M; ++v) ui[v] = un[v];
 #pragma unroll
-      for (int j = 0; j < i; ++j)
-        if (TB::a(i, j) != 0.0) acc -= (dt * real(TB::a(i, j))) * Lst[j][v];
-      ui[v] = acc;
-    }
+    for (int j = 0; j < i; ++j)
+      if (TB::a(i, j) != 0.0) vfma(ui, -(dt * real(TB::a(i, j))), Lst[j]);
     real f[M], g[M];
     if (DIM == 2) EQ::flux_xy(ui, f, g, ph);
     else flux_at<EQ>(ui, 0, f, ph, xnode);
     if (TB::b(i) != 0.0) {
       const real bi = real(TB::b(i));
-#pragma unroll
-      for (int v = 0; v < M; ++v) {
-        Fa[v] += bi * f[v];
-        if (DIM == 2) Ga[v] += bi * g[v];
-        Ua[v] += bi * ui[v];
-      }
+      vfma(Fa, bi, f);
+      if (DIM == 2) vfma(Ga, bi, g);
+      vfma(Ua, bi, ui);
     }
-#pragma unroll
-    for (int v = 0; v < M; ++v) {
-      AT(sA, v, k) = ui[v];
-      AT(sB, v, k) = f[v];
-      if (DIM == 2) AT(sC, v, k) = g[v];
-    }
+    vst_sh<M, GS>(ATP(sA, k), ui);
+    vst_sh<M, GS>(ATP(sB, k), f);
+    if (DIM == 2) vst_sh<M, GS>(ATP(sC, k), g);
     __syncthreads();
     if (i < S - 1) {
+      real h[M];  // (D f)/dx + (D g)/dy as one chain per variable
 #pragma unroll
-      for (int v = 0; v < M; ++v) {
-        real h = real(0);  // (D f)/dx + (D g)/dy as one chain
+      for (int v = 0; v < M; ++v) h[v] = real(0);
 #pragma unroll
-        for (int r = 0; r < n; ++r) h += sDx[p * n + r] * AT(sB, v, r + n * q);
-        if (DIM == 2) {
+      for (int r = 0; r < n; ++r) vfma_sh<M, GS>(h, sDx[p * n + r], ATP(sB, r + n * q));
+      if (DIM == 2) {
 #pragma unroll
-          for (int r = 0; r < n; ++r) h += sDy[q * n + r] * AT(sC, v, p + n * r);
-        }
-        Lst[i < S - 1 ? i : 0][v] = h;
+        for (int r = 0; r < n; ++r) vfma_sh<M, GS>(h, sDy[q * n + r], ATP(sC, p + n * r));
       }
+#pragma unroll
+      for (int v = 0; v < M; ++v) Lst[i < S - 1 ? i : 0][v] = h[v];
       if (has_src) {  // the stage's source, from its node value still in shared memory
         real us[M], s[M];
-#pragma unroll
-        for (int v = 0; v < M; ++v) us[v] = AT(sA, v, k);
+        vld_sh<M, GS>(us, ATP(sA, k));
         source_eval<EQ>(us, dWx, dWy, s);
 #pragma unroll
         for (int v = 0; v < M; ++v) Lst[i < S - 1 ? i : 0][v] -= s[v];
@@ -370,14 +479,11 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
           const int side = fs.side, j = fs.j;
           real ut[M], fn[M];
 #pragma unroll
-          for (int v = 0; v < M; ++v) {
-            real acc = real(0);
+          for (int v = 0; v < M; ++v) ut[v] = real(0);
 #pragma unroll
-            for (int r = 0; r < n; ++r) {
-              const real l = (side & 1) ? tb.l1[r] : tb.l0[r];
-              acc += l * ATE(sA, v, fs.el, side < 2 ? r + n * j : j + n * r);
-            }
-            ut[v] = acc;
+          for (int r = 0; r < n; ++r) {
+            const real l = (side & 1) ? tb.l1[r] : tb.l0[r];
+            vfma_sh<M, GS>(ut, l, ATPE(sA, fs.el, side < 2 ? r + n * j : j + n * r));
           }
           const int eg = blk * epr + fs.el;
           if (m.dissipation == 2 && eg < m.ne) {  // D-CSX: the stage trace, for the face kernel
@@ -388,8 +494,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
           if (m.central == 0) {  // EA, eq. (evaluate)
             flux_at<EQ>(ut, side >> 1, fn, ph,
                         XDEP ? real(m.x0 + (min(eg, m.ne - 1) % m.nx + side) * m.dx) : real(0));
-#pragma unroll
-            for (int v = 0; v < M; ++v) ea[mm][v] += bi * fn[v];
+            vfma(ea[mm], bi, fn);
           }
         }
       }
@@ -398,24 +503,18 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   }
 
   // ---------------- time averages: high-order volume part, face data ----
-#pragma unroll
-  for (int v = 0; v < M; ++v) {
-    AT(sA, v, k) = Ua[v];
-    AT(sB, v, k) = Fa[v];
-    if (DIM == 2) AT(sC, v, k) = Ga[v];
-  }
+  vst_sh<M, GS>(ATP(sA, k), Ua);
+  vst_sh<M, GS>(ATP(sB, k), Fa);
+  if (DIM == 2) vst_sh<M, GS>(ATP(sC, k), Ga);
   __syncthreads();
   real HO[M];
 #pragma unroll
-  for (int v = 0; v < M; ++v) {
-    real h = real(0);
+  for (int v = 0; v < M; ++v) HO[v] = real(0);
 #pragma unroll
-    for (int r = 0; r < n; ++r) h += sDtx[p * n + r] * AT(sB, v, r + n * q);
-    if (DIM == 2) {
+  for (int r = 0; r < n; ++r) vfma_sh<M, GS>(HO, sDtx[p * n + r], ATP(sB, r + n * q));
+  if (DIM == 2) {
 #pragma unroll
-      for (int r = 0; r < n; ++r) h += sDty[q * n + r] * AT(sC, v, p + n * r);
-    }
-    HO[v] = h;
+    for (int r = 0; r < n; ++r) vfma_sh<M, GS>(HO, sDty[q * n + r], ATP(sC, p + n * r));
   }
   // time-averaged source S = sum_i b_i s(u^(i)) (App. B eq. (crkfr.source)):
   // both sources are linear in u (the ten-moment one for fixed grad W), so it
@@ -426,16 +525,12 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   for (int v = 0; v < M; ++v) Sa[v] = real(0);
   if (has_src) {
     real us[M];
-#pragma unroll
-    for (int v = 0; v < M; ++v) us[v] = AT(sA, v, k);
+    vld_sh<M, GS>(us, ATP(sA, k));
     source_eval<EQ>(us, dWx, dWy, Sa);
   }
   const real dho = dt * (real(1) - a);  // per-thread constants, one rounding each
-#pragma unroll
-  for (int v = 0; v < M; ++v) {
-    HO[v] = un[v] - dho * HO[v];
-    if (has_src) HO[v] += dt * Sa[v];
-  }
+  vfma(HO, -dho, HO, un);
+  if (has_src) vfma(HO, dt, Sa);
 #pragma unroll
   for (int mm = 0; mm < SPT; ++mm) {
     const FaceSlot fs = face_slot<NSLOT, NFN>(tid + mm * T);
@@ -447,19 +542,14 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
       // time-averaged flux F (x faces) or G (y faces), eq. (extrapolate))
       real Ut[M], ut[M], Ft[M];
 #pragma unroll
-      for (int v = 0; v < M; ++v) {
-        real a1 = real(0), a2 = real(0), a3 = real(0);
+      for (int v = 0; v < M; ++v) Ut[v] = ut[v] = Ft[v] = real(0);
 #pragma unroll
-        for (int r = 0; r < n; ++r) {
-          const real l = (side & 1) ? tb.l1[r] : tb.l0[r];
-          const int node = side < 2 ? r + n * j : j + n * r;
-          a1 += l * ATE(sA, v, fs.el, node);
-          a2 += l * ATE(s0, v, fs.el, node);
-          if (m.central == 1) a3 += l * (side < 2 ? ATE(sB, v, fs.el, node) : ATE(sC, v, fs.el, node));
-        }
-        Ut[v] = a1;
-        ut[v] = a2;
-        Ft[v] = a3;
+      for (int r = 0; r < n; ++r) {
+        const real l = (side & 1) ? tb.l1[r] : tb.l0[r];
+        const int node = side < 2 ? r + n * j : j + n * r;
+        vfma_sh<M, GS>(Ut, l, ATPE(sA, fs.el, node));
+        vfma_sh<M, GS>(ut, l, ATPE(s0, fs.el, node));
+        if (m.central == 1) vfma_sh<M, GS>(Ft, l, side < 2 ? ATPE(sB, fs.el, node) : ATPE(sC, fs.el, node));
       }
       real* sl_out = P.b.slot;
       sl_out[slot_index(0, side, eg, j, NSIDE, m.ne, NFN)] =
@@ -479,7 +569,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
       __syncthreads();
       const real W = DIM == 2 ? tb.w[p] * tb.w[q] : tb.w[p];
 #pragma unroll
-      for (int v = 0; v < M; ++v) AT(sA, v, k) = W * Sa[v];
+      for (int v = 0; v < M; ++v) sA[v * stride + el * NP + k] = W * Sa[v];  // elem_reduce's layout
       elem_reduce<NP, M>(sA, epb, el, k, OpSum());
       for (int v = k; valid && v < M; v += NP)
         P.b.smean[(size_t)v * m.ne + e] = double(sA[v * stride + el * NP]);
@@ -522,9 +612,22 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
                       : (nbL >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbL, N + n * q) : gx);
         up[v] = p < N ? AT(s0, v, k + 1)
                       : (nbR >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbR, n * q) : gx);
-        sx[v] = minmod3((un[v] - um[v]) * bmx, (up[v] - um[v]) * tb.ihc[p], (up[v] - un[v]) * bpx);
-        sy[v] = real(0);
       }
+      // minmod of the scaled one-sided and central differences
+      auto slopes = [&](real (&sl)[M], real b_m, real b_c, real b_p) {
+        real d1[M], d2[M], d3[M];
+        vsub(d1, un, um);
+        vsub(d2, up, um);
+        vsub(d3, up, un);
+        vmul(d1, d1, b_m);
+        vmul(d2, d2, b_c);
+        vmul(d3, d3, b_p);
+#pragma unroll
+        for (int v = 0; v < M; ++v) sl[v] = minmod3(d1[v], d2[v], d3[v]);
+      };
+      slopes(sx, bmx, tb.ihc[p], bpx);
+#pragma unroll
+      for (int v = 0; v < M; ++v) sy[v] = real(0);
       if (DIM == 2) {
         const int nbB = q == 0 ? sNbr[el * 4 + 2] : -1;
         const int nbT = q == N ? sNbr[el * 4 + 3] : -1;
@@ -541,17 +644,14 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
                         : (nbB >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbB, p + n * N) : gy);
           up[v] = q < N ? AT(s0, v, k + n)
                         : (nbT >= 0 ? load_state<real, MIXED>(P.b, m.ne, NP, v, nbT, p) : gy);
-          sy[v] = minmod3((un[v] - um[v]) * bmy, (up[v] - um[v]) * tb.ihc[q], (up[v] - un[v]) * bpy);
         }
+        slopes(sy, bmy, tb.ihc[q], bpy);
       }
       real fxm[M], fxp[M], fym[M], fyp[M], Fm[M], Fp[M], Gm[M], Gp[M];
-#pragma unroll
-      for (int v = 0; v < M; ++v) {
-        fxm[v] = un[v] + sx[v] * tb.dm[p];
-        fxp[v] = un[v] + sx[v] * tb.dp[p];
-        fym[v] = un[v] + sy[v] * tb.dm[q];
-        fyp[v] = un[v] + sy[v] * tb.dp[q];
-      }
+      vfma(fxm, tb.dm[p], sx, un);
+      vfma(fxp, tb.dp[p], sx, un);
+      vfma(fym, tb.dm[q], sy, un);
+      vfma(fyp, tb.dp[q], sy, un);
       flux_at<EQ>(fxm, 0, Fm, ph, XDEP ? real(m.x0 + (ix + double(tb.xs[p])) * m.dx) : real(0));
       flux_at<EQ>(fxp, 0, Fp, ph, XDEP ? real(m.x0 + (ix + double(tb.xs[p + 1])) * m.dx) : real(0));
       if (DIM == 2) {
@@ -561,15 +661,17 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
       real ex[M], exm[M], exp_[M], eym[M], eyp[M];
       const real hx = real(0.5) * dt * (tb.invw[p] * invdx);
       const real hy = DIM == 2 ? real(0.5) * dt * (tb.invw[q] * invdy) : real(0);
-#pragma unroll
-      for (int v = 0; v < M; ++v) {
-        ex[v] = (Fp[v] - Fm[v]) * hx;
-        if (DIM == 2) ex[v] += (Gp[v] - Gm[v]) * hy;
-        exm[v] = fxm[v] - ex[v];
-        exp_[v] = fxp[v] - ex[v];
-        eym[v] = fym[v] - ex[v];
-        eyp[v] = fyp[v] - ex[v];
+      vsub(ex, Fp, Fm);
+      vmul(ex, ex, hx);
+      if (DIM == 2) {
+        real dg[M];
+        vsub(dg, Gp, Gm);
+        vfma(ex, hy, dg);
       }
+      vsub(exm, fxm, ex);
+      vsub(exp_, fxp, ex);
+      vsub(eym, fym, ex);
+      vsub(eyp, fyp, ex);
       bool ok = EQ::admissible_fast(fxm, ph) && EQ::admissible_fast(fxp, ph) &&
                 EQ::admissible_fast(exm, ph) && EQ::admissible_fast(exp_, ph);
       if (DIM == 2)
@@ -585,14 +687,11 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
         }
       }
     }
-#pragma unroll
-    for (int v = 0; v < M; ++v) {
-      AT(sA, v, k) = xm[v];
-      AT(sB, v, k) = xp[v];
-      if (DIM == 2) {
-        AT(sC, v, k) = ym[v];
-        AT(sD, v, k) = yp[v];
-      }
+    vst_sh<M, GS>(ATP(sA, k), xm);
+    vst_sh<M, GS>(ATP(sB, k), xp);
+    if (DIM == 2) {
+      vst_sh<M, GS>(ATP(sC, k), ym);
+      vst_sh<M, GS>(ATP(sD, k), yp);
     }
     __syncthreads();
     // subcell fluxes, numbered across the block (element r / NSF of the block:
@@ -611,30 +710,34 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
       const real* sR = isx ? sA : sC;
       const int nodeR = node + (isx ? 1 : n);
       real uL[M], uR[M], fr[M];
-#pragma unroll
-      for (int v = 0; v < M; ++v) {
-        uL[v] = ATE(sL, v, el2, node);
-        uR[v] = ATE(sR, v, el2, nodeR);
-      }
+      vld_sh<M, GS>(uL, ATPE(sL, el2, node));
+      vld_sh<M, GS>(uR, ATPE(sR, el2, nodeR));
       real xf = real(0);
       if constexpr (XDEP) {
         const int e2 = min(blk * epr + el2, m.ne - 1);
         xf = real(m.x0 + (e2 % m.nx + double(tb.xs[p2 + 1])) * m.dx);
       }
       rusanov<EQ>(uL, uR, isx ? 0 : 1, fr, ph, xf);
-#pragma unroll
-      for (int v = 0; v < M; ++v) ATE(sL, v, el2, node) = fr[v];
+      vst_sh<M, GS>(ATPE(sL, el2, node), fr);
     }
     __syncthreads();
     // low-order residual of the interior subfaces (eq. (low.order.update))
     const real wx = tb.invw[p] * invdx, wy = DIM == 2 ? tb.invw[q] * invdy : real(0);
+    {
+      real fr[M], fl[M];  // subcell fluxes right of and left of the node (0 at the element faces)
 #pragma unroll
-    for (int v = 0; v < M; ++v) {
-      real rx = (p < N ? AT(sB, v, k) : real(0)) - (p > 0 ? AT(sB, v, k - 1) : real(0));
-      LO[v] = rx * wx;
+      for (int v = 0; v < M; ++v) fr[v] = fl[v] = real(0);
+      if (p < N) vld_sh<M, GS>(fr, ATP(sB, k));
+      if (p > 0) vld_sh<M, GS>(fl, ATP(sB, k - 1));
+      vsub(fr, fr, fl);
+      vmul(LO, fr, wx);
       if (DIM == 2) {
-        real ry = (q < N ? AT(sD, v, k) : real(0)) - (q > 0 ? AT(sD, v, k - n) : real(0));
-        LO[v] += ry * wy;
+#pragma unroll
+        for (int v = 0; v < M; ++v) fr[v] = fl[v] = real(0);
+        if (q < N) vld_sh<M, GS>(fr, ATP(sD, k));
+        if (q > 0) vld_sh<M, GS>(fl, ATP(sD, k - n));
+        vsub(fr, fr, fl);
+        vfma(LO, wy, fr);
       }
     }
     // face-node data for the face kernel: evolved boundary state u* and the
@@ -653,12 +756,15 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
         else if (side == 2) { nb_node = j; adj_node = j; ust = sC; adj = sD; }
         else { nb_node = j + n * N; adj_node = j + n * (N - 1); ust = sD; adj = sD; }
         const real c = dt * real(m.cflim[side]) * ((side & 1) ? real(1) : real(-1));
+        real us[M], ub[M], fa[M];
+        vld_sh<M, GS>(us, ATPE(ust, fs.el, nb_node));
+        vld_sh<M, GS>(ub, ATPE(s0, fs.el, nb_node));
+        vld_sh<M, GS>(fa, ATPE(adj, fs.el, adj_node));
+        vfma(ub, c, fa);
 #pragma unroll
         for (int v = 0; v < M; ++v) {
-          P.b.slot[slot_index(1 + 2 * M + v, side, eg, j, NSIDE, m.ne, NFN)] =
-              ATE(ust, v, fs.el, nb_node);
-          P.b.slot[slot_index(1 + 3 * M + v, side, eg, j, NSIDE, m.ne, NFN)] =
-              ATE(s0, v, fs.el, nb_node) + c * ATE(adj, v, fs.el, adj_node);
+          P.b.slot[slot_index(1 + 2 * M + v, side, eg, j, NSIDE, m.ne, NFN)] = us[v];
+          P.b.slot[slot_index(1 + 3 * M + v, side, eg, j, NSIDE, m.ne, NFN)] = ub[v];
         }
       }
     }
@@ -667,14 +773,15 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   // ---------------- partial update --------------------------------------
   if (valid) {
     const real dlo = dt * a;
+    real val[M];
+    vfma(val, -dlo, LO, HO);
 #pragma unroll
-    for (int v = 0; v < M; ++v) {
-      const real val = HO[v] - dlo * LO[v];
-      P.b.P[((size_t)v * m.ne + e) * NP + k] = val;
-    }
+    for (int v = 0; v < M; ++v) P.b.P[((size_t)v * m.ne + e) * NP + k] = val[v];
   }
 #undef AT
 #undef ATE
+#undef ATP
+#undef ATPE
 }
 
 // Resident blocks per SM the step kernels ask for (measured on GB300,

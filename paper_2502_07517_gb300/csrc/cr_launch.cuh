@@ -25,13 +25,15 @@ struct Impl {
   static constexpr int NP = DIM == 2 ? n * n : n;
   static constexpr int M = EQ::M;
   static constexpr int NFN = DIM == 2 ? n : 1;
+  // variables per node in the element kernel's shared arrays (VarPack pads FP32 to pairs)
+  static constexpr int MV = (M + VarPack<real>::VL - 1) / VarPack<real>::VL * VarPack<real>::VL;
 
   // elements per block: about 256 threads per block (at least one element);
   // the FP32-bulk update kernel takes UpdateShape's (128 threads)
   static constexpr int EPB = BlockShape<NP>::EPB;
 
   static size_t smem_local(int epb) {
-    return (((size_t)5 * M * epb * NP * sizeof(real) + 15) & ~(size_t)15) + (size_t)epb * sizeof(double) +
+    return (((size_t)5 * MV * epb * NP * sizeof(real) + 15) & ~(size_t)15) + (size_t)epb * sizeof(double) +
            (size_t)4 * n * n * sizeof(real) + (size_t)epb * 4 * sizeof(int);
   }
   static constexpr int RW = 2 * M > 4 ? 2 * M : 4;
