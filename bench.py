@@ -272,9 +272,10 @@ def train_alpha_network(degree, stream, seeds=range(1000, 1008), nx=96, snaps=(0
 def alu_roofline(prob, nodes, kms, mixed, ms_per_step):
     """ALU roofline of the dominant kernel of a 2D Euler step: algorithmic
     flops (flop_model) per launch over the kernel's CUDA-event time, against
-    the FP64 or FP32 peak; kms = per-kernel ms (k_local, k_face, k_update)."""
-    names = ["k_local", "k_face", "k_update"]
-    dom = int(np.argmax(kms))
+    the FP64 or FP32 peak; kms = per-kernel ms (k_local, k_face, k_update,
+    k_finish_step)."""
+    names = ["k_local", "k_face", "k_update", "k_finish_step"]
+    dom = int(np.argmax(kms[:3]))
     flops = flop_model(2, prob["degree"], "euler2d")
     achieved = flops[dom] * nodes / (kms[dom] * 1e-3) / 1e12
     peak = PEAK_FP32_TFLOPS if mixed else PEAK_FP64_TFLOPS

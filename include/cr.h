@@ -248,7 +248,8 @@ cr_status cr_launches_per_step(cr_ctx* ctx, int* launches);
 /* As cr_step_async, but launches every kernel of every step directly (no CUDA
  * graph) between CUDA events on the context's stream and adds each kernel's
  * device time in milliseconds to kernel_ms[i], i < cr_launches_per_step()
- * (in launch order: element-local kernel, face kernel, update kernel).
+ * (in launch order: element-local kernel, face kernel, update kernel, and the
+ * one-thread kernel that ends the step: time, rate, next step size).
  * Synchronises.  For measurement; the state advances exactly as in cr_step. */
 cr_status cr_profile_steps(cr_ctx* ctx, int max_steps, double t_final, double dt_fixed,
                            double* kernel_ms);

@@ -35,6 +35,20 @@ struct TimeCtl {
   int last_step;            // 1 when that step lands on t_final
 };
 
+// The running maximum of the CFL rate in a single-problem step is spread over
+// kRateParts counters, one per 256-byte line after the TimeCtl block of a
+// context (its device allocation is kCtlBytes): the update blocks fold their
+// rate into counter (block % kRateParts) without waiting, and k_finish_step
+// takes the maximum of the counters.  One counter for all blocks serialised
+// their reductions at one L2 slice.
+constexpr int kRateParts = 32;
+constexpr size_t kRateLine = 256;
+constexpr size_t kCtlBytes = kRateLine * (1 + kRateParts);
+static_assert(sizeof(TimeCtl) <= kRateLine, "TimeCtl fits its line");
+__host__ __device__ inline unsigned long long* rate_part(TimeCtl* c, int i) {
+  return reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(c) + kRateLine * (1 + i));
+}
+
 // Plan the next step from the current time, rate and run limits (one thread).
 __device__ __forceinline__ void plan_step(TimeCtl* c) {
   double dt = 0.0;

@@ -306,6 +306,7 @@ __global__ void k_reset_ctl(TimeCtl* c, double cfl_factor) {
   c->dt_step = 0.0;
   c->dt_step_f = 0.0f;
   c->last_step = 0;
+  for (int i = 0; i < kRateParts; ++i) *rate_part(c, i) = 0ull;
 }
 
 __global__ void k_set_run(TimeCtl* c, double t_final, double dt_fixed) {
@@ -342,7 +343,7 @@ Layout layout_of(const cr_mesh_desc* d) {
     off += align256(bytes);
     return o;
   };
-  L.ctl = take(sizeof(TimeCtl));
+  L.ctl = take(kCtlBytes);
   L.u = take(M * ne * np * rs);
   L.umean = take(mixed ? M * ne * sizeof(double) : 0);
   L.umean_f = take(mixed ? M * ne * sizeof(float) : 0);
@@ -902,7 +903,7 @@ cr_status cr_profile_steps(cr_ctx* c, int max_steps, double t_final, double dt_f
                            double* kernel_ms) {
   if (!c || !kernel_ms || max_steps < 0) return fail(c, CR_E_INVALID_ARG, "bad argument");
   const int nk = c->ks->launches_per_step;
-  cudaEvent_t ev[4];
+  cudaEvent_t ev[5];
   for (int i = 0; i <= nk; ++i) CR_CUDA(c, cudaEventCreate(&ev[i]));
   k_set_run<<<1, 1, 0, c->stream>>>(c->d_ctl, t_final, dt_fixed);
   CR_CUDA(c, cudaGetLastError());

@@ -1339,8 +1339,36 @@ __device__ __forceinline__ void finish_block(TimeCtl* ctl, double block_rate, in
   }
 }
 
+// End of a step of the single-problem path (one warp, launched after the
+// update kernel): the maximum of the rate counters (rate_part) becomes the
+// state's rate, the counters are cleared, time advances and the next step is
+// planned.  The update blocks then only fold their rate into a counter (a
+// reduction nobody waits for), where finish_block has every block wait for two
+// round trips to one counter before it can retire (measured 11% of the
+// FP32-bulk update kernel at 512x512 N = 4).
+static __global__ void k_finish_step(TimeCtl* ctl) {
+  const double dtd = ctl->dt_step;
+  if (!(dtd > 0.0)) return;  // no step was taken
+  unsigned long long bits = 0ull;
+  if (threadIdx.x < kRateParts) {
+    unsigned long long* part = rate_part(ctl, threadIdx.x);
+    bits = *part;
+    *part = 0ull;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {  // bit patterns of non-negative doubles order as the values
+    const unsigned long long other = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = other > bits ? other : bits;
+  }
+  if (threadIdx.x != 0) return;
+  ctl->rate_last = __longlong_as_double((long long)bits);
+  ctl->t = ctl->last_step ? ctl->t_final : ctl->t + dtd;
+  ctl->steps += 1;
+  plan_step(ctl);
+}
+
 // CFL rate sigma_x(u_bar)/dx + sigma_y(u_bar)/dy of each element, block max,
-// then finish_block.  The block's elements are evaluated side by side by its
+// then finish_block (deferred: only the running maximum, k_finish_step does the rest).  The block's elements are evaluated side by side by its
 // first DIM * epb threads (one per element and direction) from the means in
 // shared memory (means[e * mstride + v]; the elements of the block start at
 // e_first, epr of them are whole).  A flux that depends on the position
@@ -1350,7 +1378,7 @@ template <int DIM, int NP, class EQ, typename T>
 __device__ __forceinline__ void rate_and_finish(const Mesh& m, const Phys<T>& ph, const T* means,
                                                 int mstride, T* rbuf, int epb, int epr, int e_first,
                                                 TimeCtl* ctl, int advance, double dtd, int last,
-                                                int nblk, const T* xi) {
+                                                int nblk, const T* xi, bool deferred = false) {
   if (threadIdx.x < DIM * epb) {
     const int e2 = threadIdx.x / DIM, kk = threadIdx.x - e2 * DIM;
     const int eg = e_first + e2;
@@ -1377,6 +1405,11 @@ __device__ __forceinline__ void rate_and_finish(const Mesh& m, const Phys<T>& ph
       if (DIM == 2) r += double(rbuf[j * 2 + 1]);
       brate = fmax(brate, r);
     }
+  if (deferred) {
+    if (threadIdx.x == 0)
+      atomicMax(rate_part(ctl, blockIdx.x % kRateParts), (unsigned long long)__double_as_longlong(brate));
+    return;
+  }
   finish_block(ctl, brate, advance, dtd, last, nblk);
 }
 
@@ -1385,7 +1418,8 @@ __device__ __forceinline__ void rate_and_finish(const Mesh& m, const Phys<T>& ph
 // [RW][epb][NP] reduction buffer, sEl [epb][16] per-element values.
 template <int DIM, int N, class EQ, typename real, bool MIXED, int T>
 __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<real>& tb,
-                                            const Tab<double>& td, const int blk, const int nblk) {
+                                            const Tab<double>& td, const int blk, const int nblk,
+                                            const bool deferred = false) {
   constexpr int n = N + 1;
   constexpr int NP = DIM == 2 ? n * n : n;
   constexpr int M = EQ::M;
@@ -1758,10 +1792,11 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
   __syncthreads();
   if constexpr (MIXED) {
     rate_and_finish<DIM, NP, EQ, float>(m, P.ph, sElr + ER + 1, ES, reinterpret_cast<float*>(sRed),
-                                        epb, epr, blk * epr, P.b.ctl, 1, dtd, last_step, nblk, tb.xi);
+                                        epb, epr, blk * epr, P.b.ctl, 1, dtd, last_step, nblk, tb.xi,
+                                        deferred);
   } else {
     rate_and_finish<DIM, NP, EQ, double>(m, P.phd, sEl + 4, 16, sRed, epb, epr, blk * epr, P.b.ctl, 1,
-                                         dtd, last_step, nblk, td.xi);
+                                         dtd, last_step, nblk, td.xi, deferred);
   }
 #undef ATU
 #undef RED
@@ -1771,7 +1806,7 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
 template <int DIM, int N, class EQ, typename real, bool MIXED>
 __global__ void __launch_bounds__(256, MinBlocks<MIXED>::update) k_update(const __grid_constant__ KParams<real> P) {
   update_body<DIM, N, EQ, real, MIXED, UpdateShape<DIM == 2 ? (N + 1) * (N + 1) : N + 1, MIXED>::T>(
-      P, P.tb, P.td, blockIdx.x, gridDim.x);
+      P, P.tb, P.td, blockIdx.x, gridDim.x, true);  // k_finish_step ends the step
 }
 
 // ===========================================================================

@@ -10,8 +10,8 @@ struct KernelSet {
   int launches_per_step;
   // params points at a KParams<double> (FP64) or KParams<float> (FP32_BULK)
   cudaError_t (*step)(const void* params, cudaStream_t s);
-  cudaError_t (*launch[3])(const void* params, cudaStream_t s);  // local, face, update
-  const char* names[3];
+  cudaError_t (*launch[4])(const void* params, cudaStream_t s);  // local, face, update, finish
+  const char* names[4];
   cudaError_t (*prologue)(const void* params, cudaStream_t s);
   cudaError_t (*split)(const void* params, const double* in, cudaStream_t s);  // FP64 -> state
   cudaError_t (*join)(const void* params, double* out, cudaStream_t s);        // state -> FP64
@@ -74,10 +74,16 @@ struct Impl {
     k_update<DIM, N, EQ, real, MIXED><<<grid, EU * NP, smem_update(EU), s>>>(P);
     return cudaGetLastError();
   }
+  static cudaError_t launch_finish(const void* pv, cudaStream_t s) {
+    const KParams<real>& P = *static_cast<const KParams<real>*>(pv);
+    k_finish_step<<<1, 32, 0, s>>>(P.b.ctl);
+    return cudaGetLastError();
+  }
   static cudaError_t step(const void* pv, cudaStream_t s) {
     cudaError_t e = launch_local(pv, s);
     if (e == cudaSuccess) e = launch_face(pv, s);
     if (e == cudaSuccess) e = launch_update(pv, s);
+    if (e == cudaSuccess) e = launch_finish(pv, s);
     return e;
   }
 
@@ -124,9 +130,9 @@ struct Impl {
   }
 
   static const KernelSet* set() {
-    static const KernelSet ks = {DIM, N, M, NP, MIXED ? 1 : 0, 3, &step,
-                                 {&launch_local, &launch_face, &launch_update},
-                                 {"k_local", "k_face", "k_update"},
+    static const KernelSet ks = {DIM, N, M, NP, MIXED ? 1 : 0, 4, &step,
+                                 {&launch_local, &launch_face, &launch_update, &launch_finish},
+                                 {"k_local", "k_face", "k_update", "k_finish_step"},
                                  &prologue, &split, &join, &means, &configure};
     return &ks;
   }

@@ -64,6 +64,7 @@ __global__ void k_static_reset(TimeCtl* c, double dt) {
   c->dt_step = 0.0;
   c->dt_step_f = 0.0f;
   c->last_step = 0;
+  for (int i = 0; i < kRateParts; ++i) *rate_part(c, i) = 0ull;
 }
 
 }  // namespace
@@ -107,7 +108,7 @@ extern "C" cr_status cr_step_static(const cr_mesh_desc* d, const double* u_in, d
     off += round256(bytes);
     return o;
   };
-  const size_t o_ctl = take(sizeof(TimeCtl));
+  const size_t o_ctl = take(kCtlBytes);
   const size_t o_P = take((size_t)M * ne * np * sizeof(double));
   const size_t o_slot = take((size_t)(4 * M + 1) * nside * ne * nfn * sizeof(double));
   const size_t o_fx = take((size_t)M * ny * nfx * nfn * sizeof(double));
