@@ -6,9 +6,10 @@
 // block body as the single-problem kernels; the reference tables, which depend
 // only on the degree, stay kernel parameters as in the single-problem kernels.
 //
-//   k_batch_local_n / k_batch_face / k_batch_update_n : one launch per phase
+//   k_batch_local_n / k_batch_face / k_batch_update_n (+ k_batch_finish, one warp
+//       per problem ending its step) : one launch per phase
 //       over the tiles of every problem (per degree for the element phases:
-//       up to five launches per step for the batch).
+//       up to six launches per step for the batch).
 //   k_batch_fused : one cooperative, persistent launch for all phases of
 //       nsteps steps.  The work items (step, phase, tile) form one queue in
 //       that order; blocks claim kFusedClaim * A.tiles consecutive items at a
@@ -114,7 +115,15 @@ __global__ void __launch_bounds__(DegShape<N, T>::TB, (BatchMinBlocks<real, T, 2
   const BatchTile tile = A.t_upd[A.upd_first[N - 3] + blockIdx.x];
   load_params(&sP, A.P + tile.prob);
   update_body<2, N, Eq2, real, MIXED, DegShape<N, T>::TB>(sP, A.tb[N - 3], A.td[N - 3], tile.blk,
-                                                           A.nblk_upd[tile.prob]);
+                                                           A.nblk_upd[tile.prob], true);
+}
+
+// End of the step of every problem after the update phase: one warp per
+// problem (finish_step_warp; the update blocks only folded their rates into
+// the problem's rate counters).
+template <typename real>
+__global__ void k_batch_finish(const __grid_constant__ BatchArgs<real> A) {
+  finish_step_warp(A.P[blockIdx.x].b.ctl);
 }
 
 template <typename real, int T>
@@ -282,6 +291,7 @@ cudaError_t launch_phase_t(int phase, const BatchArgs<real>& A, cudaStream_t s) 
       k_batch_update_n<real, 3, T><<<A.upd_count[0], DegShape<3, T>::TB, smem_update_n<real, 3, T>(), s>>>(A);
     if (A.upd_count[1] > 0)
       k_batch_update_n<real, 4, T><<<A.upd_count[1], DegShape<4, T>::TB, smem_update_n<real, 4, T>(), s>>>(A);
+    k_batch_finish<real><<<A.nprob, 32, 0, s>>>(A);
   }
   return cudaGetLastError();
 }

@@ -1346,7 +1346,7 @@ __device__ __forceinline__ void finish_block(TimeCtl* ctl, double block_rate, in
 // reduction nobody waits for), where finish_block has every block wait for two
 // round trips to one counter before it can retire (measured 11% of the
 // FP32-bulk update kernel at 512x512 N = 4).
-static __global__ void k_finish_step(TimeCtl* ctl) {
+__device__ __forceinline__ void finish_step_warp(TimeCtl* ctl) {
   const double dtd = ctl->dt_step;
   if (!(dtd > 0.0)) return;  // no step was taken
   unsigned long long bits = 0ull;
@@ -1366,6 +1366,7 @@ static __global__ void k_finish_step(TimeCtl* ctl) {
   ctl->steps += 1;
   plan_step(ctl);
 }
+static __global__ void k_finish_step(TimeCtl* ctl) { finish_step_warp(ctl); }
 
 // CFL rate sigma_x(u_bar)/dx + sigma_y(u_bar)/dy of each element, block max,
 // then finish_block (deferred: only the running maximum, k_finish_step does the rest).  The block's elements are evaluated side by side by its
