@@ -798,16 +798,16 @@ def run_ours(args):
     host_in = torch.from_numpy(u).pin_memory()
     host_out = torch.empty(u.shape, dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 5))
-    parts = np.zeros(3)
+    parts = np.zeros(2)
 
     def e2e_step():
+        # cr_set_state reads the pinned input in its checking kernel; cr_step_get's
+        # update kernel writes the new state into the pinned output while it runs
         ta = time.perf_counter()
         crkfr.lib().cr_set_state(ctx.handle, host_in.data_ptr(), 0)
         tb = time.perf_counter()
-        crkfr.cr_step(ctx, 1, 1e300)
-        tc = time.perf_counter()
-        crkfr.lib().cr_get_state(ctx.handle, host_out.data_ptr(), 0)
-        return np.array([tb - ta, tc - tb, time.perf_counter() - tc])
+        crkfr.cr_step_get(ctx, 1, 1e300, host_out)
+        return np.array([tb - ta, time.perf_counter() - tb])
 
     e2e_step()  # untimed: first use of the pinned buffers
     torch.cuda.synchronize()
@@ -818,7 +818,7 @@ def run_ours(args):
     nbytes = u.size * 8
     e2e = {"value": world * nodes / e2e_s, "unit": "DOF-updates/s", "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes, "ms_per_step": e2e_s * 1e3,
-           "ms_set_step_get": [float(x) for x in parts / e2e_steps * 1e3]}
+           "ms_set_and_step_get": [float(x) for x in parts / e2e_steps * 1e3]}
 
     if rank != 0:
         if world > 1:

@@ -183,6 +183,16 @@ cr_status cr_get_state(cr_ctx* ctx, double* u, int on_device);
 cr_status cr_step(cr_ctx* ctx, int max_steps, double t_final, double dt_fixed, double* t_out,
                   int* steps_out);
 
+/* cr_step followed by cr_get_state(ctx, u, 0), for host memory u.  When u is
+ * page-locked (pinned) host memory the update kernel of the last step writes
+ * the new FP64 state into it while it runs, so the device->host transfer
+ * overlaps that kernel instead of following the steps; otherwise, and when the
+ * run reaches t_final before its last step, the state is copied after the
+ * steps.  Synchronises.  Arguments and errors as cr_step; on an error the
+ * contents of u are unspecified. */
+cr_status cr_step_get(cr_ctx* ctx, int max_steps, double t_final, double dt_fixed, double* u,
+                      double* t_out, int* steps_out);
+
 /* As cr_step but only enqueues the work on the stream; cr_sync reports. */
 cr_status cr_step_async(cr_ctx* ctx, int max_steps, double t_final, double dt_fixed);
 

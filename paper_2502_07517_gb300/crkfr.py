@@ -30,7 +30,7 @@ CR_CENTRAL_EA, CR_CENTRAL_AE = 0, 1
 
 # C symbols declared in include/cr.h
 SYMBOLS = ("cr_workspace_bytes", "cr_init_mesh", "cr_destroy", "cr_set_state", "cr_get_state",
-           "cr_step", "cr_step_async", "cr_sync", "cr_get_alpha", "cr_get_means", "cr_next_dt",
+           "cr_step", "cr_step_get", "cr_step_async", "cr_sync", "cr_get_alpha", "cr_get_means", "cr_next_dt",
            "cr_cfl_number_for", "cr_cfl_number_points", "cr_reference_tables_points",
            "cr_launches_per_step", "cr_profile_steps", "cr_cfl_number", "cr_reference_tables",
            "cr_step_static", "cr_last_error", "cr_mlp_param_count", "cr_mlp_load",
@@ -89,6 +89,7 @@ def lib():
         L.cr_set_state.argtypes = [V, V, I]
         L.cr_get_state.argtypes = [V, V, I]
         L.cr_step.argtypes = [V, I, ctypes.c_double, ctypes.c_double, D, ctypes.POINTER(I)]
+        L.cr_step_get.argtypes = [V, I, ctypes.c_double, ctypes.c_double, V, D, ctypes.POINTER(I)]
         L.cr_step_async.argtypes = [V, I, ctypes.c_double, ctypes.c_double]
         L.cr_sync.argtypes = [V, D, ctypes.POINTER(I)]
         L.cr_get_alpha.argtypes = [V, V, I]
@@ -239,6 +240,28 @@ def cr_step(ctx, max_steps, t_final, dt_fixed=0.0):
     n = ctypes.c_int()
     _check(lib().cr_step(ctx.handle, int(max_steps), float(t_final), float(dt_fixed),
                          ctypes.byref(t), ctypes.byref(n)), ctx.handle)
+    return t.value, n.value
+
+
+def cr_step_get(ctx, max_steps, t_final, out, dt_fixed=0.0):
+    """cr_step, then the state into out: host memory, a C-contiguous float64
+    numpy array or CPU torch tensor of M * Ne * Np values (pinned: written by
+    the last step's update kernel).  Returns (t, steps)."""
+    want = _state_numel(ctx.desc)
+    if isinstance(out, np.ndarray):
+        ok = out.dtype == np.float64 and out.flags.c_contiguous and out.size == want
+        ptr = out.ctypes.data
+    else:
+        import torch
+        ok = (isinstance(out, torch.Tensor) and not out.is_cuda and out.dtype == torch.float64
+              and out.is_contiguous() and out.numel() == want)
+        ptr = out.data_ptr() if ok else 0
+    if not ok:
+        raise CrError(-1, "cr_step_get: out must be contiguous float64 host memory of %d values" % want)
+    t = ctypes.c_double()
+    n = ctypes.c_int()
+    _check(lib().cr_step_get(ctx.handle, int(max_steps), float(t_final), float(dt_fixed), ptr,
+                             ctypes.byref(t), ctypes.byref(n)), ctx.handle)
     return t.value, n.value
 
 

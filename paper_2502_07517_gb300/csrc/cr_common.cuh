@@ -33,6 +33,9 @@ struct TimeCtl {
   double dt_step;           // dt of the next step (0: nothing to do)
   float dt_step_f;          // the same in FP32
   int last_step;            // 1 when that step lands on t_final
+  double* out;              // when set (cr_step_get), the single-problem update kernel also
+                            // writes the new FP64 state here (page-locked host memory)
+  int out_done;             // set by the step that wrote out
 };
 
 // The running maximum of the CFL rate in a single-problem step is spread over

@@ -306,7 +306,14 @@ __global__ void k_reset_ctl(TimeCtl* c, double cfl_factor) {
   c->dt_step = 0.0;
   c->dt_step_f = 0.0f;
   c->last_step = 0;
+  c->out = nullptr;
+  c->out_done = 0;
   for (int i = 0; i < kRateParts; ++i) *rate_part(c, i) = 0ull;
+}
+
+__global__ void k_set_out(TimeCtl* c, double* out) {
+  c->out = out;
+  if (out) c->out_done = 0;
 }
 
 __global__ void k_set_run(TimeCtl* c, double t_final, double dt_fixed) {
@@ -959,6 +966,34 @@ cr_status cr_step(cr_ctx* c, int max_steps, double t_final, double dt_fixed, dou
     left -= n;
   }
   return cr_sync(c, t_out, steps_out);
+}
+
+cr_status cr_step_get(cr_ctx* c, int max_steps, double t_final, double dt_fixed, double* u,
+                      double* t_out, int* steps_out) {
+  Range range("cr_step_get");
+  if (!c || !u) return fail(c, CR_E_INVALID_ARG, "NULL argument");
+  cudaPointerAttributes attr;
+  const bool pinned = cudaPointerGetAttributes(&attr, u) == cudaSuccess && attr.type == cudaMemoryTypeHost;
+  cudaGetLastError();  // a pageable pointer may leave an error behind
+  if (!pinned || max_steps <= 0) {
+    cr_status st = cr_step(c, max_steps, t_final, dt_fixed, t_out, steps_out);
+    return st != CR_OK ? st : cr_get_state(c, u, 0);
+  }
+  if (max_steps > 1) {
+    cr_status st = cr_step(c, max_steps - 1, t_final, dt_fixed, nullptr, nullptr);
+    if (st != CR_OK) return st;
+  }
+  // the last step writes the state into u while its update kernel runs
+  k_set_out<<<1, 1, 0, c->stream>>>(c->d_ctl, u);
+  CR_CUDA(c, cudaGetLastError());
+  cr_status st = cr_step_async(c, 1, t_final, dt_fixed);
+  k_set_out<<<1, 1, 0, c->stream>>>(c->d_ctl, nullptr);
+  CR_CUDA(c, cudaGetLastError());
+  if (st != CR_OK) return st;
+  st = cr_sync(c, t_out, steps_out);
+  if (st != CR_OK) return st;
+  // the run ended before that step (t_final reached): copy the state
+  return c->h_ctl->out_done ? CR_OK : cr_get_state(c, u, 0);
 }
 
 cr_status cr_get_alpha(cr_ctx* c, double* alpha, int on_device) {

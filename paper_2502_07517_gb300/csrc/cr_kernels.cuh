@@ -1364,13 +1364,15 @@ __device__ __forceinline__ void finish_step_warp(TimeCtl* ctl) {
   ctl->rate_last = __longlong_as_double((long long)bits);
   ctl->t = ctl->last_step ? ctl->t_final : ctl->t + dtd;
   ctl->steps += 1;
+  if (ctl->out) ctl->out_done = 1;
   plan_step(ctl);
 }
 static __global__ void k_finish_step(TimeCtl* ctl) { finish_step_warp(ctl); }
 
 // CFL rate sigma_x(u_bar)/dx + sigma_y(u_bar)/dy of each element, block max,
-// then finish_block (deferred: only the running maximum, k_finish_step does the rest).  The block's elements are evaluated side by side by its
-// first DIM * epb threads (one per element and direction) from the means in
+// then finish_block (deferred: the block max goes into a rate counter, and
+// finish_step_warp ends the step).  The block's elements are evaluated side
+// by side by its first DIM * epb threads (one per element and direction) from the means in
 // shared memory (means[e * mstride + v]; the elements of the block start at
 // e_first, epr of them are whole).  A flux that depends on the position
 // (variable advection, 1D) takes the largest sigma over the element's faces
@@ -1763,6 +1765,18 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
       for (int v = k; v < M; v += NP) {
         P.b.umean[(size_t)v * m.ne + e] = ubar[v];
         P.b.umean_f[(size_t)v * m.ne + e] = float(ubar[v]);
+      }
+    }
+    // cr_step_get: the new state in FP64 straight into the caller's host
+    // memory (the transfer overlaps the rest of the kernel); FP32 bulk as
+    // mean + fluctuation, the sum the state read-back forms
+    double* const out = deferred ? P.b.ctl->out : nullptr;
+    if (out) {
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        const size_t gi = ((size_t)v * m.ne + e) * NP + k;
+        if constexpr (MIXED) out[gi] = ubar[v] + double(fl[v]);
+        else out[gi] = double(ur[v]);
       }
     }
   }

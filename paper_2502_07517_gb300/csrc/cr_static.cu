@@ -64,6 +64,8 @@ __global__ void k_static_reset(TimeCtl* c, double dt) {
   c->dt_step = 0.0;
   c->dt_step_f = 0.0f;
   c->last_step = 0;
+  c->out = nullptr;
+  c->out_done = 0;
   for (int i = 0; i < kRateParts; ++i) *rate_part(c, i) = 0ull;
 }
 
