@@ -317,7 +317,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
   const int ix = ee % m.nx, iy = ee / m.nx;
 
   const double dtd = P.b.ctl->dt_step;
-  if (!(dtd > 0.0)) return;
+  if (!gt0(dtd)) return;  // (integer test: the FP64 pipe is the scarce unit)
   const real dt = sizeof(real) == 4 ? real(P.b.ctl->dt_step_f) : real(dtd);
   // position of the node along x, for a flux that depends on it (variable advection)
   constexpr bool XDEP = IsVarAdv<EQ>::value;
@@ -819,7 +819,7 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
   constexpr int NFN = DIM == 2 ? n : 1;
   const Mesh& m = P.m;
   const double dtd = P.b.ctl->dt_step;
-  if (!(dtd > 0.0)) return;
+  if (!gt0(dtd)) return;  // (integer test: the FP64 pipe is the scarce unit)
   const int nX = m.ny * m.nfx * NFN;
   const int nY = DIM == 2 ? m.nfy * m.nx * n : 0;
   const int idx = blk * blockDim.x + threadIdx.x;
@@ -1401,13 +1401,19 @@ __device__ __forceinline__ void rate_and_finish(const Mesh& m, const Phys<T>& ph
     rbuf[e2 * 2 + kk] = ok ? r : T(0);
   }
   __syncthreads();
+  // block max over the elements by the first warp (lane j: elements j, j + 32, ...),
+  // then a shuffle tree: the maximum is the serial loop's, bit for bit, with one
+  // dependent FP64 step per 32 elements instead of one per element
   double brate = 0.0;
-  if (threadIdx.x == 0)
-    for (int j = 0; j < epb; ++j) {
+  if (threadIdx.x < 32) {
+    for (int j = threadIdx.x; j < epb; j += 32) {
       double r = double(rbuf[j * 2]);
       if (DIM == 2) r += double(rbuf[j * 2 + 1]);
       brate = fmax(brate, r);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) brate = fmax(brate, __shfl_xor_sync(0xffffffffu, brate, o));
+  }
   if (deferred) {
     if (threadIdx.x == 0)
       atomicMax(rate_part(ctl, blockIdx.x % kRateParts), (unsigned long long)__double_as_longlong(brate));
@@ -1435,7 +1441,7 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
   const Mesh& m = P.m;
   const double dtd = P.b.ctl->dt_step;
   const int last_step = P.b.ctl->last_step;
-  if (!(dtd > 0.0)) return;
+  if (!gt0(dtd)) return;  // (integer test: the FP64 pipe is the scarce unit)
   constexpr int epb = (T + NP - 1) / NP;  // element slots in shared memory
   constexpr int epr = T / NP;             // whole elements of the block
   const int tid = threadIdx.x;
