@@ -82,6 +82,28 @@ def test_static_step_wrapper_refuses_bad_tensors(built):
     assert crkfr._state_numel(crkfr.desc_from_problem(prob2)) == u2.size
 
 
+def test_step_get_wrapper_refuses_bad_output(built):
+    """The cr_step_get binding writes only into contiguous float64 host memory of
+    the state's size: a wrong dtype or size, a non-contiguous array or tensor are
+    refused with CR_E_INVALID_ARG before the library is called (the context is
+    never touched, so a stand-in with the description serves)."""
+    import torch
+
+    class _Ctx:
+        handle = None
+
+    prob, u = wl.euler2d_vortex(nx=4, ny=3, degree=3, seed=0)
+    ctx = _Ctx()
+    ctx.desc = crkfr.desc_from_problem(prob)
+    t = torch.from_numpy(u.copy())
+    bad = [u.astype(np.float32), u[:, :, :-1].copy(), np.asfortranarray(u), u.reshape(-1)[::2],
+           t.float(), t.transpose(1, 2), t[:, :, :-1]]
+    for out in bad:
+        with pytest.raises(crkfr.CrError) as ei:
+            crkfr.cr_step_get(ctx, 1, 1.0, out)
+        assert ei.value.status == -1
+
+
 @pytest.mark.parametrize("N", [1, 2, 3, 4])
 def test_library_cfl_for_dissipation_models_matches_oracle(N):
     from oracle.cfl import cfl_number
