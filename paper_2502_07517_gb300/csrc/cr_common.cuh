@@ -125,6 +125,7 @@ struct Bufs {
   real* fx;          // x-face numerical flux [M][ny][nfx][nq]
   real* fy;          // y-face numerical flux [M][nfy][nx][n]
   double* alpha_raw; // indicator alpha of the current state [Ne]
+  float* alpha_raw_f; // FP32_BULK: the same in FP32, what the FP32 element kernel reads [Ne]
   double* alpha;     // smoothed alpha used by the last step [Ne]
   TimeCtl* ctl;
   const int* mlp_flag;              // != 0 once network weights are loaded
@@ -141,6 +142,7 @@ struct Phys {
   real gamma, gm1, ax, ay;
   real invdx, invdy;  // 1/dx, 1/dy of the mesh
   real a0, a1, a2, a3;  // a(x) = a0 + a1 x + a2 x^2 + a3 x^3 of variable advection
+  real cflim[4];        // Mesh::cflim in the kernel's type (no FP64 conversion in the kernels)
 };
 
 // Differentiation matrix D[i*n+j] = l_j'(xi_i) (Sec. 2 eq. (diff.matrix)) and

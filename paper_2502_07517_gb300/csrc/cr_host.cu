@@ -325,7 +325,8 @@ __global__ void k_set_run(TimeCtl* c, double t_final, double dt_fixed) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t ctl, u, umean, umean_f, P, smean, slot, fx, fy, alpha_raw, alpha, mlp, staging, total;
+  size_t ctl, u, umean, umean_f, P, smean, slot, fx, fy, alpha_raw, alpha_raw_f, alpha, mlp, staging,
+      total;
 };
 
 int nvars_of(const cr_mesh_desc* d) {
@@ -363,6 +364,7 @@ Layout layout_of(const cr_mesh_desc* d) {
   L.fx = take(M * ny * nfx * nfn * rs);
   L.fy = take(dim == 2 ? M * nfy * nx * n * rs : 0);
   L.alpha_raw = take(ne * sizeof(double));
+  L.alpha_raw_f = take(mixed ? ne * sizeof(float) : 0);
   L.alpha = take(ne * sizeof(double));
   L.mlp = take(16 + 2 * (size_t)(32 * np + 32 + 32 * 32 + 32 + 32 + 1));  // flag + BF16 weights
   L.staging = take(mixed ? M * ne * np * sizeof(double) : 0);
@@ -598,6 +600,10 @@ void fill_desc_params(const cr_mesh_desc& d, KParams<real>* P, const HostTables&
   P->ph.a3 = real(d.adv_poly[3]);
   P->ph.invdx = real(m.invdx);
   P->ph.invdy = real(m.invdy);
+  for (int i = 0; i < 4; ++i) {
+    P->ph.cflim[i] = real(m.cflim[i]);
+    P->phd.cflim[i] = m.cflim[i];
+  }
   P->phd.invdx = m.invdx;
   P->phd.invdy = m.invdy;
   P->phd.gamma = d.gamma;
@@ -628,6 +634,7 @@ void fill_params(cr_ctx* c, KParams<real>* P, const HostTables& h) {
   b.fx = reinterpret_cast<real*>(w + c->L.fx);
   b.fy = reinterpret_cast<real*>(w + c->L.fy);
   b.alpha_raw = reinterpret_cast<double*>(w + c->L.alpha_raw);
+  b.alpha_raw_f = sizeof(real) == 4 ? reinterpret_cast<float*>(w + c->L.alpha_raw_f) : nullptr;
   b.alpha = reinterpret_cast<double*>(w + c->L.alpha);
   b.mlp_flag = reinterpret_cast<const int*>(w + c->L.mlp);
   b.mlp_w = reinterpret_cast<const unsigned short*>(w + c->L.mlp + 16);

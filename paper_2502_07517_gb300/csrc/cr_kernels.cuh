@@ -363,17 +363,36 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
       nbs[f] = neighbour(m, eg, f);
       sNbr[e2 * 4 + f] = nbs[f];
     }
-    double al = 0.0;
-    if (m.alpha_mode == 1) {
-      al = m.alpha_fixed;
-    } else if (m.limiter & kLimBlend) {
-      al = P.b.alpha_raw[eg];
+    if constexpr (MIXED) {
+      // from the FP32 copies: max and halving commute with the rounding to FP32,
+      // so this is the FP32 value of the FP64 smoothing, without FP64 work
+      float al = 0.0f;
+      double ald = 0.0;
+      if (m.alpha_mode == 1) {
+        ald = m.alpha_fixed;
+        al = float(ald);
+      } else if (m.limiter & kLimBlend) {
+        al = P.b.alpha_raw_f[eg];
 #pragma unroll
-      for (int f = 0; f < NSIDE; ++f)
-        if (nbs[f] >= 0) al = fmax(al, 0.5 * P.b.alpha_raw[nbs[f]]);
+        for (int f = 0; f < NSIDE; ++f)
+          if (nbs[f] >= 0) al = fmaxf(al, 0.5f * P.b.alpha_raw_f[nbs[f]]);
+        ald = double(al);
+      }
+      reinterpret_cast<real*>(sAlpha)[e2] = al;
+      if (v2) P.b.alpha[eg] = ald;
+    } else {
+      double al = 0.0;
+      if (m.alpha_mode == 1) {
+        al = m.alpha_fixed;
+      } else if (m.limiter & kLimBlend) {
+        al = P.b.alpha_raw[eg];
+#pragma unroll
+        for (int f = 0; f < NSIDE; ++f)
+          if (nbs[f] >= 0) al = fmax(al, 0.5 * P.b.alpha_raw[nbs[f]]);
+      }
+      reinterpret_cast<real*>(sAlpha)[e2] = real(al);
+      if (v2) P.b.alpha[eg] = al;
     }
-    reinterpret_cast<real*>(sAlpha)[e2] = real(al);
-    if (v2) P.b.alpha[eg] = al;
   };
   if constexpr (MIXED) {
     if (k == 0) smooth_alpha(el, ee, valid);
@@ -755,7 +774,7 @@ __device__ __forceinline__ void local_body(const KParams<real>& P, const Tab<rea
         else if (side == 1) { nb_node = N + n * j; adj_node = N - 1 + n * j; ust = sB; adj = sB; }
         else if (side == 2) { nb_node = j; adj_node = j; ust = sC; adj = sD; }
         else { nb_node = j + n * N; adj_node = j + n * (N - 1); ust = sD; adj = sD; }
-        const real c = dt * real(m.cflim[side]) * ((side & 1) ? real(1) : real(-1));
+        const real c = dt * ph.cflim[side] * ((side & 1) ? real(1) : real(-1));
         real us[M], ub[M], fa[M];
         vld_sh<M, GS>(us, ATPE(ust, fs.el, nb_node));
         vld_sh<M, GS>(ub, ATPE(s0, fs.el, nb_node));
@@ -1057,7 +1076,7 @@ __device__ __forceinline__ void face_body(const KParams<real>& P, const int blk)
     // threshold 0.1 min P_k(candidate with f_LO) by a margin above FP32
     // rounding, the FP64 solve below would return theta = 1; skip it.
     const real dtf = real(P.b.ctl->dt_step_f);
-    const real cLf = dtf * real(m.cflim[dir == 0 ? 1 : 3]), cRf = dtf * real(m.cflim[dir == 0 ? 0 : 2]);
+    const real cLf = dtf * P.ph.cflim[dir == 0 ? 1 : 3], cRf = dtf * P.ph.cflim[dir == 0 ? 0 : 2];
     const real* Ff = Fr;
     bool safe = true;
 #pragma unroll
@@ -1798,7 +1817,10 @@ __device__ __forceinline__ void update_body(const KParams<real>& P, const Tab<re
       __syncthreads();
       const real al = indicator_alpha<DIM, N, real>(m, tb, rE, rT, rR, epb, el, k, P.b.mlp_flag,
                                                     P.b.mlp_w, sMlp, nullptr, -1);
-      if (valid && k == 0) P.b.alpha_raw[e] = double(al);
+      if (valid && k == 0) {
+        P.b.alpha_raw[e] = double(al);
+        P.b.alpha_raw_f[e] = al;
+      }
     } else {
       double* dE = sU;
       double* dT = sU + stride;
@@ -1891,7 +1913,10 @@ __global__ void k_prologue(const __grid_constant__ KParams<real> P) {
     const double al = indicator_alpha<DIM, N, double>(m, P.td, sU, sU + stride, sRed, epb, el, k,
                                                       P.b.mlp_flag, P.b.mlp_w, sMlp, P.b.feat,
                                                       valid ? e : -1);
-    if (valid && k == 0) P.b.alpha_raw[e] = al;
+    if (valid && k == 0) {
+      P.b.alpha_raw[e] = al;
+      if constexpr (MIXED) P.b.alpha_raw_f[e] = float(al);
+    }
   }
   __syncthreads();
   rate_and_finish<DIM, NP, EQ, double>(m, P.phd, sEl + 4, 16, sRed, epb, epr, blockIdx.x * epr, P.b.ctl,
