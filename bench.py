@@ -38,9 +38,9 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 # DRAM bytes (read + write) per element of the dominant kernel, from one ncu
 # capture of the current kernel at 384x384 (147,456 elements; the traffic
-# scales with the element count): FP64 k_local 587.1 MB, FP32 bulk k_local
-# 284.0 MB (the k_local summaries under profiles/).
-NCU_TRAFFIC_PER_ELEMENT = {("fp64", "k_local"): 587.07e6 / 147456, ("fp32", "k_local"): 284.03e6 / 147456}
+# scales with the element count): FP64 k_local 589.5 MB, FP32 bulk k_local
+# 283.4 MB (the k_local summaries under profiles/).
+NCU_TRAFFIC_PER_ELEMENT = {("fp64", "k_local"): 589.46e6 / 147456, ("fp32", "k_local"): 283.41e6 / 147456}
 PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
