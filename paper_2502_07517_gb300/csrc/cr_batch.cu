@@ -22,6 +22,7 @@
 //       block, so the waits always end; they are bounded all the same: after
 //       A.spin_limit polls the block sets the error flag and returns, and
 //       blocks that see the flag stop.
+#include <cstddef>
 #include <cstdint>
 
 #include "cr_batch.cuh"
@@ -32,14 +33,18 @@ namespace {
 
 using Eq2 = EqEuler<2>;
 
+// The part of a problem's parameter block the bodies read from shared memory:
+// everything before the reference tables (the kernels take those per degree).
 template <typename real>
 struct SharedParams {
-  static_assert(sizeof(KParams<real>) % 8 == 0, "parameter block copied as 8-byte words");
-  static constexpr int kWords = int(sizeof(KParams<real>) / 8);
+  static constexpr size_t kBytes = offsetof(KParams<real>, tb);
+  static_assert(kBytes % 8 == 0, "parameter block copied as 8-byte words");
+  static constexpr int kWords = int(kBytes / 8);
 };
 
-// Copy problem prob's parameters into shared memory (all threads; barriers
-// around the copy because the previous tile's body may still read it).
+// Copy problem prob's parameters (all but the tables) into shared memory (all
+// threads; barriers around the copy because the previous tile's body may still
+// read it).
 template <typename real>
 __device__ __forceinline__ void load_params(KParams<real>* sP, const KParams<real>* src) {
   __syncthreads();

@@ -162,10 +162,12 @@ struct KParams {
   Mesh m;
   Phys<real> ph;        // constants in the bulk type
   Phys<double> phd;     // FP64 constants (limiters, means)
-  Tab<real> tb;         // tables in the bulk type
-  Tab<double> td;       // FP64 tables (limiters, means)
   DiffScaled<real> ds;  // scaled differentiation matrices in the bulk type
   Bufs<real> b;
+  // The tables last: they depend only on the degree, so the batched kernels take
+  // them as kernel parameters and copy only the part before tb per problem.
+  Tab<real> tb;         // tables in the bulk type
+  Tab<double> td;       // FP64 tables (limiters, means)
 };
 
 // Host: fill ds from D and Dt of degree N (FP64, row-major n x n; each
