@@ -16,9 +16,10 @@ enum : int { kStInadmissible = 1, kStNonFinite = 2, kStInvalidInput = 4 };
 
 // Time control of one context, resident in device memory.  The step size of
 // the next step is planned once (plan_step) by whoever changed its inputs: the
-// last block of the update/prologue kernel, or the run-setup kernel; the step
-// kernels only read dt_step, so a whole run can be enqueued without host
-// round trips.
+// one-warp kernel that ends a step (k_finish_step, k_batch_finish), the last
+// block of the prologue or of the persistent batched kernel's update phase, or
+// the run-setup kernel; the step kernels only read dt_step, so a whole run can
+// be enqueued without host round trips.
 struct TimeCtl {
   double t;                 // current time
   double t_final;           // the run stops here; the last step is clipped to it
@@ -26,7 +27,7 @@ struct TimeCtl {
   double cfl_factor;        // C_s * CFL(N), eq. (time.step.2d)
   double rate_last;         // max_e sigma_x(mean)/dx + sigma_y(mean)/dy of the current state
   unsigned long long rate_acc;  // running max (bit pattern of a non-negative double)
-  unsigned int blocks_done; // last-block counter of the update kernel
+  unsigned int blocks_done; // last-block counter (prologue, persistent batched update phase)
   int status;               // kSt* bits, sticky until cr_set_state
   int bad_elem;             // smallest element index that set a status bit
   int steps;                // steps taken since cr_set_state
